@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""QMC-CPW Greeks throughput on GB300.
+
+One step = one pass of the whole hot path (Sobol' + scramble, inverse normal,
+path construction, conditional pathwise Greeks, per-replicate reduction and
+statistics) over one batch: the d = 64 grid of 36 contracts
+({arith, binary, lookback} x {bridge, PCA} x K in {90,100,110} x sigma in
+{0.1, 0.3}, N = 2^20 points, R = 32 replicates), in MIXED precision.  The
+FP64 form of the same batch is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the full batch on its own GPU (independent
+contracts, no data-path collective: weak scaling); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle (the test oracle, on the host cores)
+on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "QMC-CPW Greeks throughput (N·d points/s) mixed vs FP64; serving p50/p99 latency"
+UNIT = "point-dates/s"
+WORKLOAD = ("d=64 grid: {arith,binary,lookback} x {bridge,pca} x K{90,100,110} x sigma{0.1,0.3}, "
+            "S0=100 r=0.05 T=1, N=2^20 points x R=32 replicates per contract (36 contracts)")
+# algorithmic FP32 flops per point-date of the mixed fused kernel (FMA = 2): uniform 2,
+# inverse normal 15, bridge 5 (PCA: 2(d-1)), exponent argument 3, exp 2, path sums 5
+FLOPS_BRIDGE = 32
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def elements(contracts) -> int:
+    return sum(c.N * c.R * c.d for c in contracts)
+
+
+def algorithmic_flops(contracts) -> float:
+    total = 0.0
+    for c in contracts:
+        per_elem = FLOPS_BRIDGE if c.construction == W.BB else FLOPS_BRIDGE - 5 + 2 * (c.d - 1)
+        total += float(c.N) * c.R * c.d * per_elem
+    return total
+
+
+def fp32_peak_tflops() -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(contracts, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands, on every host core, over a bounded sample of the workload:
+    each contract with N = 2^11 points (all 32 replicates), contracts in order until the
+    time budget is spent."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.build()
+    done, elems, t0 = 0, 0, time.perf_counter()
+    for c in contracts:
+        n = 2 ** 11
+        oracle.greeks(W.SCRAMBLE_SEED, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.construction, n, c.R,
+                      threads=cores)
+        done += 1
+        elems += n * c.R * c.d
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": elems / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {len(contracts)} contracts at N=2^11, R=32, d=64 ({elems} point-dates, "
+                      f"{dt:.1f} s wall)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    contracts = W.grid_d64()
+    n = 2 ** 10
+
+    def step():
+        for c in contracts:
+            oracle.greeks(W.SCRAMBLE_SEED, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.construction, n, c.R,
+                          threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    elems = sum(n * c.R * c.d for c in contracts)
+    value = elems / dt
+    sample = f"each step: the 36 contracts at N=2^10 (R=32, d=64), {elems} point-dates"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2209_11337_gb300 import build as lib_build
+    from paper_2209_11337_gb300 import qmccpw as q
+    lib_build.build()
+
+    stream = torch.cuda.Stream()  # one non-default stream for the library, the events and the L2 flush
+    torch.cuda.set_stream(stream)
+    plan = q.qmccpw_plan(device=local, d_max=65, r_max=32, seed=W.SCRAMBLE_SEED + rank,
+                         stream=stream.cuda_stream)
+    contracts = W.grid_d64()
+    elems = elements(contracts)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def timed(precision, steps, warmup, with_clocks=False):
+        batch = q.Batch(plan, contracts, precision)
+        for _ in range(warmup):
+            flush.zero_()
+            batch.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        batch.set_timing(max(1, steps))
+        sampler = ClockSampler(local) if with_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        events = []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.launch(stream.cuda_stream)
+            e1.record(stream)
+            events.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
+        step_ms = [a.elapsed_time(b) for a, b in events]
+        fused_ms, nl = batch.timing()
+        launches = batch.launch_count() * steps
+        res = batch.results()
+        batch.free()
+        return {"ms_per_step": sum(step_ms) / steps, "wall_s": wall, "fused_ms": fused_ms / max(1, nl),
+                "clocks": clocks, "launches": launches, "results": res}
+
+    mixed = timed(q.QMCCPW_MIXED, args.steps, args.warmup, with_clocks=True)
+    fp64 = timed(q.QMCCPW_FP64, args.fp64_steps, 1) if args.fp64_steps > 0 else None
+
+    # end to end through the public API with host buffers: contracts in, results out
+    def e2e_once():
+        return q.qmccpw_greeks_batch(plan, contracts, q.QMCCPW_MIXED)
+
+    e2e_once()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_once()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+
+    ms = max_over_ranks(mixed["ms_per_step"])
+    fused_ms = max_over_ranks(mixed["fused_ms"])
+    value = world * elems / (ms / 1e3)
+    flops = algorithmic_flops(contracts)
+    achieved = flops / (fused_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+
+    # MIXED against FP64 on the same points, in units of the FP64 standard error
+    err_se = None
+    if fp64 is not None:
+        worst = 0.0
+        for (m32, _, _), (m64, se64, _) in zip(mixed["results"], fp64["results"]):
+            for g in range(4):
+                if se64[g] > 0:
+                    worst = max(worst, abs(m32[g] - m64[g]) / se64[g])
+        err_se = worst
+
+    sizeof_contract = 200  # bytes per qmccpw_contract descriptor uploaded, rounded up
+    h2d = len(contracts) * (sizeof_contract + 8) + sum(c.R for c in contracts) * 8
+    d2h = len(contracts) * 8 * 8 + sum(c.R for c in contracts) * 4 * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "contracts": len(contracts), "d": 64, "N": 2 ** 20, "R": 32,
+                   "precision": "MIXED: inverse normal, path and payoff in f32; switch point and reductions in f64",
+                   "point_dates_per_step": elems, "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"dp{world} (independent contracts per GPU)"},
+        "fp64": None if fp64 is None else {
+            "value": world * elems / (max_over_ranks(fp64["ms_per_step"]) / 1e3), "unit": UNIT,
+            "ms_per_step": max_over_ranks(fp64["ms_per_step"]), "steps": args.fp64_steps},
+        "mixed_vs_fp64_max_err_in_se": err_se,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "fused_kernel<float>", "fused_ms_per_launch": fused_ms,
+                     "note": "FP32 pipe peak from 152 SMs x 128 lanes x 2 flops x 2070 MHz (unit counts and "
+                             "max clock); algorithmic flops: 32 per point-date (bridge), 27+2(d-1) (PCA)"},
+        "e2e": {"value": world * elems / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": mixed["launches"],
+        "clocks": mixed["clocks"],
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(contracts)
+    elif rank == 0 and world == 1:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line))
+    q.qmccpw_free(plan)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * qmccpw — QMC conditional-pathwise (QMC-CPW) Greeks on NVIDIA GB300 (sm_103a).
+ *
+ * C-ABI of the hot path of Bilokon, Kucherenko & Williams, "Quasi-Monte Carlo
+ * methods for calculating derivatives sensitivities on the GPU" (arXiv
+ * 2209.11337).  Per point of a randomised Sobol' set the library builds the
+ * separated GBM path S~(t_1..t_d) (Sec. 3.3.1), integrates the first Gaussian
+ * out in closed form (Sec. 3.3, eq. QmcCpwNewTargetDefinition), evaluates the
+ * conditional price and its pathwise delta, vega and gamma (Sec. 3.3.2,
+ * Sec. 4.5) and reduces them to one estimate per randomised replicate; the
+ * reported estimate is the mean over replicates and its standard error
+ * (Sec. 5).  Everything runs in CUDA kernels; no path leaves the GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Dates are equally spaced: t_j = j*T/d, j = 1..d.  n = d-1 Gaussians are
+ *     sampled per point; the first Gaussian x_1 is integrated out.
+ *   - Value order of every 4-vector: price, delta (d/dS0), vega (d/dsigma,
+ *     per unit of sigma, not per 1%), gamma (d^2/dS0^2).
+ *   - Point k (0-based) of replicate r uses Sobol' index g(k) = k ^ (k >> 1)
+ *     (Gray-code order), so for N = 2^m the point set is the first 2^m points.
+ *   - All host pointers are caller-owned and only read/written during the
+ *     call.  Device pointers are CUDA global-memory addresses of the plan's
+ *     device.
+ *   - Every function returns a qmccpw_status; QMCCPW_OK is 0.  On failure no
+ *     output is written unless stated, and qmccpw_last_error() describes it.
+ *   - One plan may be used by one host thread at a time.
+ */
+#ifndef QMCCPW_H
+#define QMCCPW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef enum {
+    QMCCPW_OK = 0,
+    QMCCPW_ERR_INVALID_ARG = 1, /* an argument is out of range or NULL */
+    QMCCPW_ERR_OOM = 2,         /* device or host memory (or the plan's workspace budget) exhausted */
+    QMCCPW_ERR_CUDA = 3,        /* a CUDA runtime call failed; last_error names it */
+    QMCCPW_ERR_TIMEOUT = 4,     /* a bounded wait expired */
+    QMCCPW_NOT_READY = 5,       /* asynchronous result not yet available (not an error) */
+    QMCCPW_ERR_UNSUPPORTED = 6  /* combination not provided (e.g. tensor-core precision with the bridge) */
+} qmccpw_status;
+
+/* ---- limits -------------------------------------------------------------- */
+#define QMCCPW_D_LIMIT 1024          /* largest number of monitoring dates d of any plan */
+#define QMCCPW_R_LIMIT 4096          /* largest number of replicates R of any plan */
+
+/* ---- products (Sec. 4.2, 4.5) -------------------------------------------- */
+typedef enum {
+    QMCCPW_ARITH_ASIAN_CALL = 0,     /* (mean_j S(t_j) - K)^+                          (Sec. 4.5.2) */
+    QMCCPW_BINARY_ASIAN = 1,         /* 1{mean_j S(t_j) > K}                            (Sec. 3.3.2, 4.5.1) */
+    QMCCPW_LOOKBACK_FIXED_CALL = 2,  /* (max_j S(t_j) - K)^+                           (Sec. 4.5.3) */
+    QMCCPW_GEOMETRIC_ASIAN_CALL = 3  /* (geomean_j S(t_j) - K)^+: same separated form, closed-form price */
+} qmccpw_option_type;
+
+/* ---- path construction of W~ = A z with A A^T = Sigma (eq. WboldTilde) -- */
+typedef enum {
+    QMCCPW_BB = 0,                   /* Brownian bridge, Sec. 4.4: terminal value, then midpoints breadth first */
+    QMCCPW_PCA = 1                   /* principal components of Sigma (named in Sec. 6 as the next reduction) */
+} qmccpw_construction;
+
+/* ---- arithmetic precision ----------------------------------------------- */
+typedef enum {
+    QMCCPW_FP64 = 0,                 /* every step in double precision */
+    QMCCPW_MIXED = 1,                /* inverse normal, path and payoff in float; switch point psi in
+                                        double; per-point values summed in double */
+    QMCCPW_MIXED_TC_BF16X3 = 2,      /* MIXED with the PCA product on tensor cores, 3-term bf16 split */
+    QMCCPW_MIXED_TC_TF32X3 = 3       /* MIXED with the PCA product on tensor cores, 3-term tf32 split */
+} qmccpw_precision;
+
+typedef struct qmccpw_plan_s *qmccpw_plan_t;
+typedef struct qmccpw_batch_s *qmccpw_batch_t;
+
+/* Plan descriptor (read once by qmccpw_plan). */
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    int32_t d_max;             /* largest d this plan accepts, 1..QMCCPW_D_LIMIT */
+    int32_t r_max;             /* largest R this plan accepts, 2..QMCCPW_R_LIMIT */
+    int32_t reserved;          /* must be 0 */
+    uint64_t seed;             /* key of the random linear scrambles and digital shifts */
+    void *stream;              /* cudaStream_t to run on; NULL: the plan creates and owns one */
+    uint64_t workspace_bytes;  /* device scratch budget in bytes; 0: 1 GiB */
+} qmccpw_plan_desc;
+
+typedef struct {
+    int32_t type;              /* qmccpw_option_type */
+    int32_t d;                 /* monitoring dates, 1..plan d_max */
+    double K;                  /* strike, > 0 */
+    double T;                  /* maturity in years, > 0 */
+} qmccpw_option;
+
+typedef struct {
+    double S0;                 /* spot, > 0 */
+    double r;                  /* risk-free rate (continuous), finite */
+    double sigma;              /* volatility, > 0 */
+} qmccpw_market;
+
+typedef struct {
+    double mean[4];            /* estimate: mean over replicates of (price, delta, vega, gamma) */
+    double se[4];              /* standard error of that mean: sd of replicate estimates / sqrt(R) */
+    double *per_replicate;     /* optional caller-owned host array of R*4 doubles (replicate-major);
+                                  NULL to skip */
+} qmccpw_result;
+
+typedef struct {
+    qmccpw_option option;
+    qmccpw_market market;
+    uint64_t N;                /* points per replicate, 1..2^32 (powers of two recommended) */
+    int32_t R;                 /* replicates, 2..plan r_max */
+    int32_t construction;      /* qmccpw_construction */
+} qmccpw_contract;
+
+/*
+ * Create a plan: selects the device, builds the Sobol' direction numbers
+ * (Sec. 2.2.2: primitive polynomials in increasing degree and value, initial
+ * odd m_i < 2^i drawn by SplitMix64 under a fixed key) and the scrambled
+ * tables of replicates 0..r_max-1 for d_max-1 dimensions (Sec. 2.2.3: unit
+ * lower-triangular GF(2) matrix and digital shift, bits drawn by SplitMix64
+ * under `seed`), and reserves the scratch workspace.
+ * *out receives an opaque handle owned by the caller until qmccpw_free.
+ * Errors: INVALID_ARG (NULL, d_max or r_max out of range, reserved != 0),
+ * CUDA (device selection or allocation), OOM.
+ */
+int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc);
+
+/*
+ * Estimate price, delta, vega and gamma of one contract with N points per
+ * replicate and R replicates.  Synchronous: the result is in *out when the
+ * call returns.  Path construction per `construction`, arithmetic per
+ * `precision` (tensor-core precisions require QMCCPW_PCA).
+ * Errors: INVALID_ARG (d, R outside the plan; N = 0 or > 2^32; S0, K, T,
+ * sigma not positive and finite; r not finite), UNSUPPORTED, OOM (workspace
+ * budget), CUDA.
+ */
+int qmccpw_greeks(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
+                  uint64_t N, int32_t R, int32_t construction, int32_t precision, qmccpw_result *out);
+
+/*
+ * Batched form: `count` contracts of any mix of products, d, N and R, run in
+ * one persistent launch sequence (one grid over every (contract, replicate,
+ * tile) work item).  out[i] receives contract i's result; each out[i]
+ * .per_replicate may be NULL.  Results equal those of qmccpw_greeks for the
+ * same contract (same points, same per-tile order).
+ */
+int qmccpw_greeks_batch(qmccpw_plan_t plan, const qmccpw_contract *contracts, int32_t count,
+                        int32_t precision, qmccpw_result *out);
+
+/*
+ * Prepared batch for device-resident repetition: qmccpw_batch_create uploads
+ * the contract descriptors and the work list once; qmccpw_batch_launch
+ * enqueues the kernels on `stream` (NULL: the plan's stream) and returns
+ * without waiting; results stay on the device until qmccpw_batch_results
+ * (synchronises, copies, fills out[0..count-1]).  qmccpw_batch_device_results
+ * exposes the device arrays: per_replicate (sum over contracts of R*4
+ * doubles, contract-major) and stats (count*8 doubles: mean[4], se[4]).
+ */
+int qmccpw_batch_create(qmccpw_plan_t plan, const qmccpw_contract *contracts, int32_t count,
+                        int32_t precision, qmccpw_batch_t *out);
+int qmccpw_batch_launch(qmccpw_batch_t batch, void *stream);
+int qmccpw_batch_results(qmccpw_batch_t batch, qmccpw_result *out);
+int qmccpw_batch_device_results(qmccpw_batch_t batch, const double **per_replicate,
+                                const double **stats);
+/* number of CUDA kernel launches one qmccpw_batch_launch enqueues */
+int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches);
+/*
+ * Kernel timing (measurement aid, no counterpart in the paper): with
+ * capacity > 0, every following qmccpw_batch_launch records a CUDA event
+ * pair on its stream around the fused kernel (up to `capacity` launches are
+ * kept).  qmccpw_batch_timing waits for those events, returns the summed
+ * fused-kernel time in milliseconds and the number of launches it covers,
+ * and clears the record.  capacity = 0 turns timing off.
+ */
+int qmccpw_batch_set_timing(qmccpw_batch_t batch, int32_t capacity);
+int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches);
+int qmccpw_batch_free(qmccpw_batch_t batch);
+
+/*
+ * Diagnostics for bit-exact checks.  qmccpw_sobol_points writes the 32-bit
+ * scrambled Sobol' integers of points k0..k0+count-1 (Gray index g(k)) of
+ * replicate `replicate`, dimensions 0..ndims-1, row-major into the host
+ * array out[count*ndims], produced by the same device code as the fused
+ * kernel.  qmccpw_point_values writes the per-point values (price, delta,
+ * vega, gamma) of those points into out[count*4] (host), also from the fused
+ * kernel's device code.  count <= 2^20 per call.
+ */
+int qmccpw_sobol_points(qmccpw_plan_t plan, uint32_t replicate, int32_t ndims, uint64_t k0,
+                        uint64_t count, uint32_t *out);
+int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
+                        int32_t construction, int32_t precision, uint32_t replicate, uint64_t k0,
+                        uint64_t count, double *out);
+
+/* Release a plan after waiting for its work; NULL is accepted (no-op). */
+int qmccpw_free(qmccpw_plan_t plan);
+
+/* Thread-local description of the last failure of this thread ("" if none).
+ * The string stays valid until the thread's next qmccpw call. */
+const char *qmccpw_last_error(void);
+
+/* Library version string, e.g. "qmccpw 0.1 sm_103a". */
+const char *qmccpw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCCPW_H */

@@ -1,0 +1,586 @@
+// C-ABI of libqmccpw (declared in include/qmccpw.h): plans, batches and
+// diagnostics.  Host code only validates, builds per-d tables, lays out the
+// work list and enqueues kernels; every step of the estimator runs on the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qmccpw_internal.h"
+
+using namespace qmccpw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define QMC_CUDA(call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? QMCCPW_ERR_OOM : QMCCPW_ERR_CUDA,       \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+#define QMC_TRY(expr)                     \
+    do {                                  \
+        int rc_ = (expr);                 \
+        if (rc_ != QMCCPW_OK) return rc_; \
+    } while (0)
+
+// device buffer with RAII release
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&ptr, b);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            return fail(QMCCPW_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        bytes = b;
+        return QMCCPW_OK;
+    }
+    // grow-only: keep the allocation when it is already large enough
+    int ensure(size_t b) { return (ptr && bytes >= b) ? QMCCPW_OK : alloc(b); }
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Device arrays of one batch: contract descriptors, work list and results.
+struct BatchBuffers {
+    DevBuf contracts, item_base, rep_owner, tile_sums, per_rep, stats;
+    void release() {
+        for (DevBuf *d : {&contracts, &item_base, &rep_owner, &tile_sums, &per_rep, &stats}) d->release();
+    }
+};
+
+// Tables that depend only on d (and T through dt): bridge schedule and PCA factor.
+struct DTables {
+    int n = 0;
+    int n_levels = 0;
+    DevBuf steps, w64, w32, level_start, pca64, pca32;
+};
+
+}  // namespace
+
+struct qmccpw_plan_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t seed = 0;
+    int d_max = 0, r_max = 0, ndims = 0, jstride = 0;
+    size_t workspace_bytes = 0;
+    int sm_count = 0;
+    DevBuf dir;          // unscrambled direction integers, ndims x 32
+    DevBuf table;        // [r][b][j]
+    DevBuf shift;        // [r][j]
+    // per (d, T) tables, keyed by d and the bit pattern of T
+    std::map<std::pair<int, uint64_t>, std::unique_ptr<DTables>> dtables;
+    // grow-only buffers reused by the one-shot entry points
+    BatchBuffers ws;
+    std::mutex mu;
+};
+
+struct qmccpw_batch_s {
+    qmccpw_plan_t plan = nullptr;
+    int count = 0;
+    int precision = 0;
+    std::vector<ContractDev> host;
+    std::vector<int32_t> R;
+    uint64_t items = 0, total_reps = 0;
+    size_t smem = 0;
+    int grid = 0;
+    BatchBuffers own;          // used by prepared batches
+    BatchBuffers *buf = &own;  // one-shot calls point this at the plan's workspace
+    // diagnostics
+    double *point_out = nullptr;
+    uint64_t point_k0 = 0;
+    uint32_t rep_offset = 0;
+    // fused-kernel timing: event pairs of the most recent launches
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    int32_t timed = 0;  // launches recorded since the last read
+    ~qmccpw_batch_s() {
+        for (auto e : ev_start) cudaEventDestroy(e);
+        for (auto e : ev_stop) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmccpw_market &m, uint64_t N,
+                      int32_t R, int32_t construction, int32_t precision, bool diagnostic) {
+    if (o.type < 0 || o.type > 3) return fail(QMCCPW_ERR_INVALID_ARG, "option.type out of range");
+    if (o.d < 1 || o.d > p->d_max)
+        return fail(QMCCPW_ERR_INVALID_ARG, "option.d " + std::to_string(o.d) + " outside 1..d_max=" +
+                                                std::to_string(p->d_max));
+    if (!finite_pos(o.K) || !finite_pos(o.T)) return fail(QMCCPW_ERR_INVALID_ARG, "K and T must be positive and finite");
+    if (!finite_pos(m.S0) || !finite_pos(m.sigma) || !std::isfinite(m.r))
+        return fail(QMCCPW_ERR_INVALID_ARG, "S0, sigma must be positive and finite, r finite");
+    if (N < 1 || N > (1ull << 32)) return fail(QMCCPW_ERR_INVALID_ARG, "N must be in 1..2^32");
+    if (!diagnostic && (R < 2 || R > p->r_max))
+        return fail(QMCCPW_ERR_INVALID_ARG, "R " + std::to_string(R) + " outside 2..r_max=" + std::to_string(p->r_max));
+    if (construction != QMCCPW_BB && construction != QMCCPW_PCA)
+        return fail(QMCCPW_ERR_INVALID_ARG, "construction out of range");
+    if (precision < QMCCPW_FP64 || precision > QMCCPW_MIXED_TC_TF32X3)
+        return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
+    if (precision >= QMCCPW_MIXED_TC_BF16X3 && construction != QMCCPW_PCA)
+        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core precisions apply to the PCA construction only");
+    return QMCCPW_OK;
+}
+
+// Bridge / PCA tables for (d, T), built on first use and cached by the plan.
+int get_dtables(qmccpw_plan_s *p, int d, double T, const DTables **out) {
+    uint64_t tbits;
+    std::memcpy(&tbits, &T, sizeof(tbits));
+    auto key = std::make_pair(d, tbits);
+    auto it = p->dtables.find(key);
+    if (it != p->dtables.end()) {
+        *out = it->second.get();
+        return QMCCPW_OK;
+    }
+    auto t = std::make_unique<DTables>();
+    const int n = d - 1;
+    const double dt = T / d;
+    t->n = n;
+    BridgePlan bp = bridge_plan(n, dt);
+    t->n_levels = static_cast<int>(bp.level_start.size()) - 1;
+    std::vector<float> w32(bp.w.begin(), bp.w.end());
+    std::vector<double> A = n > 0 ? pca_factor(n, dt) : std::vector<double>();
+    std::vector<float> A32(A.begin(), A.end());
+    QMC_TRY(t->steps.alloc(sizeof(BridgeStep) * std::max<size_t>(1, bp.steps.size())));
+    QMC_TRY(t->w64.alloc(sizeof(double) * std::max<size_t>(1, bp.w.size())));
+    QMC_TRY(t->w32.alloc(sizeof(float) * std::max<size_t>(1, w32.size())));
+    QMC_TRY(t->level_start.alloc(sizeof(int32_t) * bp.level_start.size()));
+    QMC_TRY(t->pca64.alloc(sizeof(double) * std::max<size_t>(1, A.size())));
+    QMC_TRY(t->pca32.alloc(sizeof(float) * std::max<size_t>(1, A32.size())));
+    if (n > 0) {
+        QMC_CUDA(cudaMemcpy(t->steps.ptr, bp.steps.data(), sizeof(BridgeStep) * bp.steps.size(), cudaMemcpyHostToDevice));
+        QMC_CUDA(cudaMemcpy(t->w64.ptr, bp.w.data(), sizeof(double) * bp.w.size(), cudaMemcpyHostToDevice));
+        QMC_CUDA(cudaMemcpy(t->w32.ptr, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+        QMC_CUDA(cudaMemcpy(t->pca64.ptr, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice));
+        QMC_CUDA(cudaMemcpy(t->pca32.ptr, A32.data(), sizeof(float) * A32.size(), cudaMemcpyHostToDevice));
+    }
+    QMC_CUDA(cudaMemcpy(t->level_start.ptr, bp.level_start.data(), sizeof(int32_t) * bp.level_start.size(),
+                        cudaMemcpyHostToDevice));
+    *out = t.get();
+    p->dtables.emplace(key, std::move(t));
+    return QMCCPW_OK;
+}
+
+// Shared-memory budget of the z/W tile of one CTA: 65 KiB lets three CTAs
+// share an SM (228 KiB) with room for the static reduction scratch.
+constexpr size_t kTileBudget = 66560;
+
+int choose_tile_log2(int precision, int n) {
+    const size_t elem = precision == QMCCPW_FP64 ? 8 : 4;
+    const int stride = (n + 1) | 1;
+    int lg = kMaxTileLog2;
+    while (lg > 0 && (static_cast<size_t>(1u << lg) * stride * elem) > kTileBudget) --lg;
+    return lg;
+}
+
+int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, uint64_t item_base,
+                   uint64_t rep_base, ContractDev *out) {
+    const DTables *t = nullptr;
+    QMC_TRY(get_dtables(p, in.option.d, in.option.T, &t));
+    ContractDev c{};
+    c.type = in.option.type;
+    c.d = in.option.d;
+    c.n = in.option.d - 1;
+    c.construction = in.construction;
+    c.tile_log2 = choose_tile_log2(precision, c.n);
+    const int P = 1 << c.tile_log2;
+    int chunk_log2 = c.tile_log2;
+    while (chunk_log2 > 0 && static_cast<long>(c.n) * (P >> chunk_log2) < 2L * kThreads) --chunk_log2;
+    c.chunk_log2 = chunk_log2;
+    c.R = in.R;
+    c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
+    c.groups = kThreads / P;
+    c.n_levels = t->n_levels;
+    c.row_stride = (c.n + 1) | 1;
+    c.N = in.N;
+    c.item_base = item_base;
+    c.rep_base = rep_base;
+    c.steps = t->steps.as<BridgeStep>();
+    c.w64 = t->w64.as<double>();
+    c.w32 = t->w32.as<float>();
+    c.level_start = t->level_start.as<int32_t>();
+    c.pca64 = t->pca64.as<double>();
+    c.pca32 = t->pca32.as<float>();
+    c.S0 = in.market.S0;
+    c.K = in.option.K;
+    c.T = in.option.T;
+    c.r = in.market.r;
+    c.sigma = in.market.sigma;
+    c.dt = in.option.T / in.option.d;
+    c.a = c.sigma * std::sqrt(c.dt);
+    c.omega = c.r - 0.5 * c.sigma * c.sigma;
+    c.psi0 = std::log(c.K / c.S0) - c.omega * c.dt;
+    c.disc = std::exp(-c.r * c.T);
+    c.disc1 = std::exp(c.r * (c.dt - c.T));
+    c.sqrt_t1 = std::sqrt(c.dt);
+    *out = c;
+    return QMCCPW_OK;
+}
+
+int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int32_t precision, bool diagnostic,
+                qmccpw_batch_s *b) {
+    if (count < 1) return fail(QMCCPW_ERR_INVALID_ARG, "count must be >= 1");
+    for (int i = 0; i < count; ++i)
+        QMC_TRY(validate_contract(p, cs[i].option, cs[i].market, cs[i].N, cs[i].R, cs[i].construction, precision,
+                                  diagnostic));
+    if (precision >= QMCCPW_MIXED_TC_BF16X3)
+        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA precisions are not built in this library version");
+    QMC_CUDA(cudaSetDevice(p->device));
+    b->plan = p;
+    b->count = count;
+    b->precision = precision;
+    b->host.resize(count);
+    b->R.resize(count);
+    uint64_t items = 0, reps = 0;
+    size_t smem = 0;
+    std::vector<uint64_t> item_base(count), rep_owner;
+    for (int i = 0; i < count; ++i) {
+        QMC_TRY(build_contract(p, cs[i], precision, items, reps, &b->host[i]));
+        const ContractDev &c = b->host[i];
+        item_base[i] = items;
+        items += static_cast<uint64_t>(c.R) * c.tiles;
+        for (int r = 0; r < c.R; ++r) rep_owner.push_back(static_cast<uint64_t>(i));
+        reps += c.R;
+        b->R[i] = c.R;
+        smem = std::max(smem, fused_smem_bytes(precision, c.n, c.tile_log2));
+    }
+    b->items = items;
+    b->total_reps = reps;
+    b->smem = smem;
+    const size_t scratch = items * 4 * sizeof(double);
+    if (scratch > p->workspace_bytes)
+        return fail(QMCCPW_ERR_OOM, "tile partial sums need " + std::to_string(scratch) +
+                                        " bytes, more than the plan's workspace budget");
+    BatchBuffers &B = *b->buf;
+    QMC_TRY(B.contracts.ensure(sizeof(ContractDev) * count));
+    QMC_TRY(B.item_base.ensure(sizeof(uint64_t) * count));
+    QMC_TRY(B.rep_owner.ensure(sizeof(uint64_t) * reps));
+    QMC_TRY(B.tile_sums.ensure(scratch));
+    QMC_TRY(B.per_rep.ensure(sizeof(double) * 4 * reps));
+    QMC_TRY(B.stats.ensure(sizeof(double) * 8 * count));
+    QMC_CUDA(cudaMemcpyAsync(B.contracts.ptr, b->host.data(), sizeof(ContractDev) * count, cudaMemcpyHostToDevice,
+                             p->stream));
+    QMC_CUDA(cudaMemcpyAsync(B.item_base.ptr, item_base.data(), sizeof(uint64_t) * count, cudaMemcpyHostToDevice,
+                             p->stream));
+    QMC_CUDA(cudaMemcpyAsync(B.rep_owner.ptr, rep_owner.data(), sizeof(uint64_t) * reps, cudaMemcpyHostToDevice,
+                             p->stream));
+    QMC_CUDA(cudaStreamSynchronize(p->stream));  // the host vectors go out of scope
+    int per_sm = 0;
+    QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, smem, &per_sm)));
+    if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
+    const uint64_t slots = static_cast<uint64_t>(per_sm) * p->sm_count;
+    b->grid = static_cast<int>(std::min<uint64_t>(items, slots));
+    return QMCCPW_OK;
+}
+
+int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
+    qmccpw_plan_s *p = b->plan;
+    const BatchBuffers &B = *b->buf;
+    LaunchParams lp{};
+    lp.contracts = B.contracts.as<ContractDev>();
+    lp.count = b->count;
+    lp.items = b->items;
+    lp.item_base = B.item_base.as<uint64_t>();
+    lp.sobol_table = p->table.as<uint32_t>();
+    lp.sobol_shift = p->shift.as<uint32_t>();
+    lp.jstride = p->jstride;
+    lp.rep_offset = b->rep_offset;
+    lp.tile_sums = B.tile_sums.as<double>();
+    lp.point_out = b->point_out;
+    lp.point_k0 = b->point_k0;
+    const size_t cap = b->ev_start.size();
+    const size_t slot = cap ? static_cast<size_t>(b->timed) % cap : 0;
+    if (cap) QMC_CUDA(cudaEventRecord(b->ev_start[slot], s));
+    QMC_CUDA(static_cast<cudaError_t>(launch_fused(lp, b->precision, b->smem, b->grid, s)));
+    if (cap) {
+        QMC_CUDA(cudaEventRecord(b->ev_stop[slot], s));
+        ++b->timed;
+    }
+    if (!b->point_out)
+        QMC_CUDA(static_cast<cudaError_t>(launch_reduce(B.contracts.as<ContractDev>(), b->count,
+                                                        B.tile_sums.as<double>(), B.per_rep.as<double>(),
+                                                        B.stats.as<double>(), b->total_reps,
+                                                        B.rep_owner.as<uint64_t>(), s)));
+    return QMCCPW_OK;
+}
+
+int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
+    const BatchBuffers &B = *b->buf;
+    std::vector<double> stats(8 * static_cast<size_t>(b->count));
+    std::vector<double> per(4 * b->total_reps);
+    QMC_CUDA(cudaMemcpyAsync(stats.data(), B.stats.ptr, sizeof(double) * stats.size(), cudaMemcpyDeviceToHost, s));
+    QMC_CUDA(cudaMemcpyAsync(per.data(), B.per_rep.ptr, sizeof(double) * per.size(), cudaMemcpyDeviceToHost, s));
+    QMC_CUDA(cudaStreamSynchronize(s));
+    uint64_t rep = 0;
+    for (int i = 0; i < b->count; ++i) {
+        std::memcpy(out[i].mean, &stats[8 * i], 4 * sizeof(double));
+        std::memcpy(out[i].se, &stats[8 * i + 4], 4 * sizeof(double));
+        if (out[i].per_replicate)
+            std::memcpy(out[i].per_replicate, per.data() + 4 * rep, sizeof(double) * 4 * b->R[i]);
+        rep += b->R[i];
+    }
+    return QMCCPW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qmccpw_last_error(void) { return g_last_error.c_str(); }
+
+const char *qmccpw_version(void) { return "qmccpw 0.1 sm_103a"; }
+
+int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
+    g_last_error.clear();
+    if (!out || !desc) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (desc->d_max < 1 || desc->d_max > QMCCPW_D_LIMIT) return fail(QMCCPW_ERR_INVALID_ARG, "d_max out of range");
+    if (desc->r_max < 2 || desc->r_max > QMCCPW_R_LIMIT) return fail(QMCCPW_ERR_INVALID_ARG, "r_max out of range");
+    if (desc->reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "reserved must be 0");
+    auto p = std::make_unique<qmccpw_plan_s>();
+    p->device = desc->device;
+    QMC_CUDA(cudaSetDevice(p->device));
+    QMC_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
+    int smem_optin = 0;
+    QMC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    // allow every tile size up front (occupancy follows the bytes each launch asks for)
+    for (int prec : {QMCCPW_FP64, QMCCPW_MIXED})
+        QMC_CUDA(static_cast<cudaError_t>(fused_set_smem_limit(prec, static_cast<size_t>(smem_optin) - 1024)));
+    p->seed = desc->seed;
+    p->d_max = desc->d_max;
+    p->r_max = desc->r_max;
+    p->ndims = std::max(1, desc->d_max - 1);
+    p->jstride = (p->ndims + 31) & ~31;
+    p->workspace_bytes = desc->workspace_bytes ? desc->workspace_bytes : (1ull << 30);
+    if (desc->stream) {
+        p->stream = static_cast<cudaStream_t>(desc->stream);
+    } else {
+        QMC_CUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    std::vector<uint32_t> v = direction_integers(p->ndims);
+    QMC_TRY(p->dir.alloc(sizeof(uint32_t) * v.size()));
+    QMC_TRY(p->table.alloc(sizeof(uint32_t) * 32u * p->jstride * static_cast<size_t>(p->r_max)));
+    QMC_TRY(p->shift.alloc(sizeof(uint32_t) * p->jstride * static_cast<size_t>(p->r_max)));
+    QMC_CUDA(cudaMemcpy(p->dir.ptr, v.data(), sizeof(uint32_t) * v.size(), cudaMemcpyHostToDevice));
+    QMC_CUDA(cudaMemsetAsync(p->table.ptr, 0, p->table.bytes, p->stream));
+    QMC_CUDA(cudaMemsetAsync(p->shift.ptr, 0, p->shift.bytes, p->stream));
+    QMC_CUDA(static_cast<cudaError_t>(launch_scramble(p->seed, p->dir.as<uint32_t>(), p->ndims, p->jstride,
+                                                      p->r_max, p->table.as<uint32_t>(), p->shift.as<uint32_t>(),
+                                                      p->stream)));
+    QMC_CUDA(cudaStreamSynchronize(p->stream));
+    *out = p.release();
+    return QMCCPW_OK;
+}
+
+int qmccpw_free(qmccpw_plan_t plan) {
+    g_last_error.clear();
+    if (!plan) return QMCCPW_OK;
+    cudaSetDevice(plan->device);
+    cudaStreamSynchronize(plan->stream);
+    plan->dtables.clear();
+    plan->ws.release();
+    plan->dir.release();
+    plan->table.release();
+    plan->shift.release();
+    if (plan->own_stream) cudaStreamDestroy(plan->stream);
+    delete plan;
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_create(qmccpw_plan_t plan, const qmccpw_contract *contracts, int32_t count, int32_t precision,
+                        qmccpw_batch_t *out) {
+    g_last_error.clear();
+    if (!plan || !contracts || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lock(plan->mu);
+    auto b = std::make_unique<qmccpw_batch_s>();
+    QMC_TRY(batch_build(plan, contracts, count, precision, false, b.get()));
+    *out = b.release();
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_launch(qmccpw_batch_t batch, void *stream) {
+    g_last_error.clear();
+    if (!batch) return fail(QMCCPW_ERR_INVALID_ARG, "NULL batch");
+    QMC_CUDA(cudaSetDevice(batch->plan->device));
+    return batch_enqueue(batch, stream ? static_cast<cudaStream_t>(stream) : batch->plan->stream);
+}
+
+int qmccpw_batch_results(qmccpw_batch_t batch, qmccpw_result *out) {
+    g_last_error.clear();
+    if (!batch || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    QMC_CUDA(cudaSetDevice(batch->plan->device));
+    QMC_CUDA(cudaDeviceSynchronize());
+    return batch_collect(batch, out, batch->plan->stream);
+}
+
+int qmccpw_batch_device_results(qmccpw_batch_t batch, const double **per_replicate, const double **stats) {
+    g_last_error.clear();
+    if (!batch) return fail(QMCCPW_ERR_INVALID_ARG, "NULL batch");
+    if (per_replicate) *per_replicate = batch->buf->per_rep.as<double>();
+    if (stats) *stats = batch->buf->stats.as<double>();
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches) {
+    g_last_error.clear();
+    if (!batch || !launches) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    *launches = 3;  // fused, per-replicate reduction, statistics
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_set_timing(qmccpw_batch_t batch, int32_t capacity) {
+    g_last_error.clear();
+    if (!batch || capacity < 0 || capacity > 4096) return fail(QMCCPW_ERR_INVALID_ARG, "bad batch or capacity");
+    QMC_CUDA(cudaSetDevice(batch->plan->device));
+    QMC_CUDA(cudaStreamSynchronize(batch->plan->stream));
+    for (auto e : batch->ev_start) cudaEventDestroy(e);
+    for (auto e : batch->ev_stop) cudaEventDestroy(e);
+    batch->ev_start.clear();
+    batch->ev_stop.clear();
+    batch->timed = 0;
+    for (int i = 0; i < capacity; ++i) {
+        cudaEvent_t a, b;
+        QMC_CUDA(cudaEventCreate(&a));
+        QMC_CUDA(cudaEventCreate(&b));
+        batch->ev_start.push_back(a);
+        batch->ev_stop.push_back(b);
+    }
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches) {
+    g_last_error.clear();
+    if (!batch || !fused_ms || !launches) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    const int cap = static_cast<int>(batch->ev_start.size());
+    const int n = std::min(batch->timed, cap);
+    float total = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        QMC_CUDA(cudaEventSynchronize(batch->ev_stop[i]));
+        float ms = 0.0f;
+        QMC_CUDA(cudaEventElapsedTime(&ms, batch->ev_start[i], batch->ev_stop[i]));
+        total += ms;
+    }
+    *fused_ms = total;
+    *launches = n;
+    batch->timed = 0;
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_free(qmccpw_batch_t batch) {
+    g_last_error.clear();
+    if (!batch) return QMCCPW_OK;
+    cudaSetDevice(batch->plan->device);
+    cudaStreamSynchronize(batch->plan->stream);
+    delete batch;
+    return QMCCPW_OK;
+}
+
+int qmccpw_greeks_batch(qmccpw_plan_t plan, const qmccpw_contract *contracts, int32_t count, int32_t precision,
+                        qmccpw_result *out) {
+    g_last_error.clear();
+    if (!plan || !contracts || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    qmccpw_batch_s b;
+    b.buf = &plan->ws;
+    QMC_TRY(batch_build(plan, contracts, count, precision, false, &b));
+    QMC_TRY(batch_enqueue(&b, plan->stream));
+    return batch_collect(&b, out, plan->stream);
+}
+
+int qmccpw_greeks(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market, uint64_t N,
+                  int32_t R, int32_t construction, int32_t precision, qmccpw_result *out) {
+    g_last_error.clear();
+    if (!plan || !option || !market || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    qmccpw_contract c{};
+    c.option = *option;
+    c.market = *market;
+    c.N = N;
+    c.R = R;
+    c.construction = construction;
+    return qmccpw_greeks_batch(plan, &c, 1, precision, out);
+}
+
+int qmccpw_sobol_points(qmccpw_plan_t plan, uint32_t replicate, int32_t ndims, uint64_t k0, uint64_t count,
+                        uint32_t *out) {
+    g_last_error.clear();
+    if (!plan || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    if (ndims < 1 || ndims > plan->ndims) return fail(QMCCPW_ERR_INVALID_ARG, "ndims outside 1..d_max-1");
+    if (replicate >= static_cast<uint32_t>(plan->r_max)) return fail(QMCCPW_ERR_INVALID_ARG, "replicate >= r_max");
+    if (count < 1 || count > (1ull << 20) || k0 + count > (1ull << 32))
+        return fail(QMCCPW_ERR_INVALID_ARG, "count must be 1..2^20 and k0+count <= 2^32");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    QMC_CUDA(cudaSetDevice(plan->device));
+    DevBuf dout;
+    QMC_TRY(dout.alloc(sizeof(uint32_t) * count * ndims));
+    QMC_CUDA(static_cast<cudaError_t>(launch_sobol_dump(
+        plan->table.as<uint32_t>() + static_cast<size_t>(replicate) * 32u * plan->jstride,
+        plan->shift.as<uint32_t>() + static_cast<size_t>(replicate) * plan->jstride, plan->jstride, ndims, k0, count,
+        dout.as<uint32_t>(), plan->stream)));
+    QMC_CUDA(cudaStreamSynchronize(plan->stream));
+    QMC_CUDA(cudaMemcpy(out, dout.ptr, sizeof(uint32_t) * count * ndims, cudaMemcpyDeviceToHost));
+    return QMCCPW_OK;
+}
+
+int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
+                        int32_t construction, int32_t precision, uint32_t replicate, uint64_t k0, uint64_t count,
+                        double *out) {
+    g_last_error.clear();
+    if (!plan || !option || !market || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    if (replicate >= static_cast<uint32_t>(plan->r_max)) return fail(QMCCPW_ERR_INVALID_ARG, "replicate >= r_max");
+    if (count < 1 || count > (1ull << 20) || k0 + count > (1ull << 32))
+        return fail(QMCCPW_ERR_INVALID_ARG, "count must be 1..2^20 and k0+count <= 2^32");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    qmccpw_contract c{};
+    c.option = *option;
+    c.market = *market;
+    c.N = count;
+    c.R = 1;
+    c.construction = construction;
+    qmccpw_batch_s b;
+    b.buf = &plan->ws;
+    QMC_TRY(batch_build(plan, &c, 1, precision, true, &b));
+    DevBuf dout;
+    QMC_TRY(dout.alloc(sizeof(double) * 4 * count));
+    b.point_out = dout.as<double>();
+    b.point_k0 = k0;
+    b.rep_offset = replicate;
+    QMC_TRY(batch_enqueue(&b, plan->stream));
+    QMC_CUDA(cudaStreamSynchronize(plan->stream));
+    QMC_CUDA(cudaMemcpy(out, dout.ptr, sizeof(double) * 4 * count, cudaMemcpyDeviceToHost));
+    return QMCCPW_OK;
+}
+
+}  // extern "C"

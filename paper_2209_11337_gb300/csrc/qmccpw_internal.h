@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of libqmccpw.
+// Not part of the C-ABI (include/qmccpw.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qmccpw.h"
+
+namespace qmccpw {
+
+// ----------------------------------------------------------------------------
+// Host tables (tables.cpp)
+// ----------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea & Flood 2014), evaluated counter-style: the value
+// for `counter` under `key` is output number counter+1 of the generator whose
+// state starts at `key`.
+uint64_t splitmix64_at(uint64_t key, uint64_t counter);
+
+// Key of the stream that draws the initial direction integers.
+constexpr uint64_t kDirectionKey = 0x2209113370D1CE5Dull;
+
+// Direction integers v[j*32 + b] (b = 0..31 is the index bit) of Sobol'
+// dimensions j = 0..ndims-1 (Sec. 2.2.2).
+std::vector<uint32_t> direction_integers(int ndims);
+
+// One step of the breadth-first Brownian bridge (Sec. 4.4) on s_i = i*dt:
+// W[m] = wl*W[l] + wr*W[r] + sd*z, z being Sobol' dimension `step`.
+struct BridgeStep {
+    int32_t m, l, r, pad;
+};
+struct BridgePlan {
+    int n = 0;
+    std::vector<BridgeStep> steps;       // n steps in consumption order
+    std::vector<double> w;               // 3 per step: wl, wr, sd
+    std::vector<int32_t> level_start;    // steps of level L are [level_start[L], level_start[L+1])
+};
+BridgePlan bridge_plan(int n, double dt);
+
+// PCA factor A (n x n, row-major, A[i-1][k-1]) of Sigma_ik = dt*min(i,k).
+std::vector<double> pca_factor(int n, double dt);
+
+// ----------------------------------------------------------------------------
+// Device-side descriptors (shared by api.cu and kernels.cu)
+// ----------------------------------------------------------------------------
+
+constexpr int kThreads = 256;            // threads per CTA of the fused kernel
+constexpr int kMaxTileLog2 = 8;          // at most 256 points per tile
+
+// Everything a CTA needs about its contract.  Built on the host, uploaded
+// once per batch, read through the constant/L1 path.
+struct ContractDev {
+    int32_t type, d, n, construction;
+    int32_t tile_log2;                   // P = 1 << tile_log2 points per tile
+    int32_t chunk_log2;                  // Gray-code chunk length in the Sobol' phase
+    int32_t R, tiles;                    // replicates, tiles per replicate
+    int32_t groups;                      // kThreads / P threads per point in the path phase
+    int32_t n_levels;                    // bridge levels
+    int32_t row_stride;                  // shared-memory row (point) stride in elements, odd
+    int32_t pad0;
+    uint64_t N;
+    uint64_t item_base;                  // first work item of this contract
+    uint64_t rep_base;                   // first replicate slot of this contract (in per-replicate arrays)
+    // per-d tables (device pointers)
+    const BridgeStep *steps;
+    const double *w64;                   // 3 per step
+    const float *w32;
+    const int32_t *level_start;
+    const double *pca64;                 // n x n row-major
+    const float *pca32;
+    // market-derived constants
+    double S0, K, T, r, sigma;
+    double dt;                           // t_1 = T/d: spacing of the separated dates
+    double a;                            // sigma*sqrt(t_1)
+    double omega;                        // r - sigma^2/2
+    double psi0;                         // ln(K/S0) - omega*t_1 (switch point numerator before ln X^)
+    double disc;                         // exp(-r T)
+    double disc1;                        // exp(r (t_1 - T))
+    double sqrt_t1;
+};
+
+// Per-launch parameters of the fused kernel.
+struct LaunchParams {
+    const ContractDev *contracts;
+    int32_t count;
+    int32_t pad;
+    uint64_t items;                      // total work items (CTAs)
+    const uint64_t *item_base;           // contract item bases, for the binary search
+    const uint32_t *sobol_table;         // [rep][b][j] scrambled direction integers
+    const uint32_t *sobol_shift;         // [rep][j]
+    int32_t jstride;                     // j stride of the table rows
+    uint32_t rep_offset;                 // added to every replicate index (diagnostics; 0 otherwise)
+    double *tile_sums;                   // items x 4 partial sums (scratch)
+    double *point_out;                   // optional per-point values, point x 4 (diagnostics)
+    uint64_t point_k0;                   // index of the contract's point 0 (diagnostics; 0 otherwise)
+};
+
+// Launchers (kernels.cu).  Return the cudaError_t as int.
+int launch_fused(const LaunchParams &p, int precision, size_t smem_bytes, int grid, void *stream);
+int launch_reduce(const ContractDev *contracts, int32_t count, const double *tile_sums,
+                  double *per_rep, double *stats, uint64_t total_reps, const uint64_t *rep_owner,
+                  void *stream);
+int launch_scramble(uint64_t seed, const uint32_t *v, int ndims, int jstride, int reps,
+                    uint32_t *table, uint32_t *shift, void *stream);
+int launch_sobol_dump(const uint32_t *table, const uint32_t *shift, int jstride, int ndims,
+                      uint64_t k0, uint64_t count, uint32_t *out, void *stream);
+// dynamic shared memory of one CTA for a contract with n dims and 2^tile_log2 points
+size_t fused_smem_bytes(int precision, int n, int tile_log2);
+int fused_set_smem_limit(int precision, size_t bytes);
+int fused_occupancy(int precision, size_t smem_bytes, int *blocks_per_sm);
+
+}  // namespace qmccpw

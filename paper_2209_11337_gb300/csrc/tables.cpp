@@ -1,0 +1,170 @@
+// Host-side tables of the QMC-CPW path: Sobol' direction integers (Sec. 2.2.2),
+// random linear scrambles with digital shifts (Sec. 2.2.3), the breadth-first
+// Brownian bridge schedule (Sec. 4.4) and the PCA factor of the Brownian
+// covariance (eq. WboldTilde).  All are built once per plan / per d and
+// uploaded; none is touched on the hot path.
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "qmccpw_internal.h"
+
+namespace qmccpw {
+
+uint64_t splitmix64_at(uint64_t key, uint64_t counter) {
+    uint64_t z = key + (counter + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+namespace {
+
+int degree_of(uint32_t p) { return 31 - __builtin_clz(p); }
+
+// a*b mod P over GF(2), P of degree q.
+uint32_t gf2_mulmod(uint32_t a, uint32_t b, uint32_t P, int q) {
+    uint32_t acc = 0;
+    const uint32_t top = 1u << q;
+    while (b) {
+        if (b & 1u) acc ^= a;
+        b >>= 1;
+        a <<= 1;
+        if (a & top) a ^= P;
+    }
+    return acc;
+}
+
+// x^e mod P by square-and-multiply.
+uint32_t gf2_pow_x(uint64_t e, uint32_t P, int q) {
+    uint32_t base = 2u;
+    if (base & (1u << q)) base ^= P;  // q == 1: x == 1 mod (x+1)
+    uint32_t acc = 1u;
+    while (e) {
+        if (e & 1u) acc = gf2_mulmod(acc, base, P, q);
+        base = gf2_mulmod(base, base, P, q);
+        e >>= 1;
+    }
+    return acc;
+}
+
+// Primitive iff the multiplicative order of x modulo P is exactly 2^q - 1:
+// x^(2^q-1) = 1 and x^((2^q-1)/p) != 1 for each prime p dividing 2^q - 1.
+bool primitive(uint32_t P) {
+    if (!(P & 1u)) return false;
+    const int q = degree_of(P);
+    if (q < 1) return false;
+    const uint64_t order = (1ull << q) - 1u;
+    if (gf2_pow_x(order, P, q) != 1u) return false;
+    uint64_t rest = order;
+    for (uint64_t f = 2; f * f <= rest; ++f) {
+        if (rest % f) continue;
+        while (rest % f == 0) rest /= f;
+        if (gf2_pow_x(order / f, P, q) == 1u) return false;
+    }
+    if (rest > 1 && gf2_pow_x(order / rest, P, q) == 1u) return false;
+    return true;
+}
+
+}  // namespace
+
+std::vector<uint32_t> direction_integers(int ndims) {
+    std::vector<uint32_t> v(static_cast<size_t>(ndims) * 32u, 0u);
+    uint32_t P = 2;  // candidate polynomial, enumerated upward
+    for (int j = 0; j < ndims; ++j) {
+        uint32_t *vj = v.data() + 32 * j;
+        if (j == 0) {  // generator matrix I: van der Corput
+            for (int b = 0; b < 32; ++b) vj[b] = 1u << (31 - b);
+            continue;
+        }
+        do { ++P; } while (!primitive(P));
+        const int q = degree_of(P);
+        // initial direction integers from odd m_i < 2^i
+        for (int i = 1; i <= q && i <= 32; ++i) {
+            const uint64_t draw = splitmix64_at(kDirectionKey, (static_cast<uint64_t>(j) << 8) | i) >> 32;
+            const uint32_t m = static_cast<uint32_t>((draw & ((1ull << i) - 1u)) | 1u);
+            vj[i - 1] = m << (32 - i);
+        }
+        // recurrence on direction integers: v_i = v_{i-q} ^ (v_{i-q} >> q) ^ sum_k c_k v_{i-k}
+        for (int i = q + 1; i <= 32; ++i) {
+            uint32_t x = vj[i - q - 1] ^ (vj[i - q - 1] >> q);
+            for (int k = 1; k < q; ++k)
+                if ((P >> (q - k)) & 1u) x ^= vj[i - k - 1];
+            vj[i - 1] = x;
+        }
+    }
+    return v;
+}
+
+void scrambled_table(uint64_t seed, uint32_t rep, const std::vector<uint32_t> &v, int ndims,
+                     int jstride, uint32_t *table_bj, uint32_t *shift) {
+    for (int j = 0; j < ndims; ++j) {
+        const uint64_t base = (static_cast<uint64_t>(rep) << 32) | (static_cast<uint64_t>(j) << 8);
+        // columns of L: column of digit c (bit 32-c) holds the digits i >= c whose row has digit c
+        uint32_t col[33];
+        for (int c = 1; c <= 32; ++c) col[c] = 1u << (32 - c);  // unit diagonal
+        for (int i = 2; i <= 32; ++i) {
+            const uint32_t row = static_cast<uint32_t>(splitmix64_at(seed, base | static_cast<uint64_t>(i - 1)) >> 32)
+                                 & (0xFFFFFFFFu << (33 - i));  // digits 1..i-1
+            for (int c = 1; c < i; ++c)
+                if (row & (1u << (32 - c))) col[c] |= 1u << (32 - i);
+        }
+        for (int b = 0; b < 32; ++b) {
+            const uint32_t x = v[32 * j + b];
+            uint32_t y = 0;
+            for (int c = 1; c <= 32; ++c)
+                if (x & (1u << (32 - c))) y ^= col[c];
+            table_bj[static_cast<size_t>(b) * jstride + j] = y;
+        }
+        shift[j] = static_cast<uint32_t>(splitmix64_at(seed, base | 32u) >> 32);
+    }
+}
+
+BridgePlan bridge_plan(int n, double dt) {
+    BridgePlan bp;
+    bp.n = n;
+    if (n <= 0) {
+        bp.level_start = {0};
+        return bp;
+    }
+    // level 0: the terminal value from W(0) = 0
+    bp.steps.push_back({n, 0, 0, 0});
+    bp.w.insert(bp.w.end(), {0.0, 0.0, std::sqrt(n * dt)});
+    bp.level_start = {0, 1};
+    std::vector<std::pair<int, int>> level = {{0, n}};
+    while (true) {
+        std::vector<std::pair<int, int>> next;
+        for (auto [l, r] : level) {
+            if (r - l < 2) continue;
+            const int m = (l + r) / 2;
+            const double den = static_cast<double>(r - l);
+            bp.steps.push_back({m, l, r, 0});
+            bp.w.insert(bp.w.end(), {(r - m) / den, (m - l) / den, std::sqrt(dt * (m - l) * (r - m) / den)});
+            next.push_back({l, m});
+            next.push_back({m, r});
+        }
+        if (static_cast<int>(bp.steps.size()) == bp.level_start.back()) break;
+        bp.level_start.push_back(static_cast<int32_t>(bp.steps.size()));
+        level.swap(next);
+    }
+    if (static_cast<int>(bp.steps.size()) != n) throw std::logic_error("bridge schedule size");
+    return bp;
+}
+
+std::vector<double> pca_factor(int n, double dt) {
+    // Sigma = dt*min(i,k): eigenvalues dt/(4 sin^2(theta_k/2)), eigenvectors
+    // sin(i theta_k) with theta_k = (2k-1) pi/(2n+1), normalised by 2/sqrt(2n+1).
+    std::vector<double> A(static_cast<size_t>(n) * n);
+    const double pi = 3.14159265358979323846;
+    const double norm = 2.0 / std::sqrt(2.0 * n + 1.0);
+    for (int k = 1; k <= n; ++k) {
+        const double theta = (2.0 * k - 1.0) * pi / (2.0 * n + 1.0);
+        const double s = std::sin(0.5 * theta);
+        const double root_lambda = std::sqrt(dt) / (2.0 * s);
+        for (int i = 1; i <= n; ++i)
+            A[static_cast<size_t>(i - 1) * n + (k - 1)] = norm * std::sin(i * theta) * root_lambda;
+    }
+    return A;
+}
+
+}  // namespace qmccpw

@@ -1,0 +1,265 @@
+"""Python binding of libqmccpw (C-ABI in include/qmccpw.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name; all computation runs in the library's CUDA kernels.  PyTorch is
+used, where a caller wants it, for device memory and streams (pass
+``torch.cuda.Stream.cuda_stream`` as a stream handle).
+
+The library is loaded from ``paper_2209_11337_gb300/_lib/libqmccpw.so``
+(built by ``paper_2209_11337_gb300.build``); importing this module does not
+build it, and every call raises ``QmcCpwError`` if it is missing.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libqmccpw.so")
+
+# ---- constants mirrored from include/qmccpw.h --------------------------------
+QMCCPW_OK = 0
+QMCCPW_ERR_INVALID_ARG = 1
+QMCCPW_ERR_OOM = 2
+QMCCPW_ERR_CUDA = 3
+QMCCPW_ERR_TIMEOUT = 4
+QMCCPW_NOT_READY = 5
+QMCCPW_ERR_UNSUPPORTED = 6
+
+QMCCPW_D_LIMIT = 1024
+QMCCPW_R_LIMIT = 4096
+
+QMCCPW_ARITH_ASIAN_CALL = 0
+QMCCPW_BINARY_ASIAN = 1
+QMCCPW_LOOKBACK_FIXED_CALL = 2
+QMCCPW_GEOMETRIC_ASIAN_CALL = 3
+
+QMCCPW_BB = 0
+QMCCPW_PCA = 1
+
+QMCCPW_FP64 = 0
+QMCCPW_MIXED = 1
+QMCCPW_MIXED_TC_BF16X3 = 2
+QMCCPW_MIXED_TC_TF32X3 = 3
+
+#: the symbols include/qmccpw.h declares
+EXPORTS = (
+    "qmccpw_plan", "qmccpw_greeks", "qmccpw_greeks_batch", "qmccpw_batch_create",
+    "qmccpw_batch_launch", "qmccpw_batch_results", "qmccpw_batch_device_results",
+    "qmccpw_batch_launch_count", "qmccpw_batch_set_timing", "qmccpw_batch_timing",
+    "qmccpw_batch_free", "qmccpw_sobol_points",
+    "qmccpw_point_values", "qmccpw_free", "qmccpw_last_error", "qmccpw_version",
+)
+
+
+class QmcCpwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qmccpw error {code}: {msg}")
+        self.code = code
+
+
+# ---- structures ---------------------------------------------------------------
+class qmccpw_plan_desc(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("d_max", ctypes.c_int32), ("r_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
+class qmccpw_option(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("d", ctypes.c_int32), ("K", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+class qmccpw_market(ctypes.Structure):
+    _fields_ = [("S0", ctypes.c_double), ("r", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class qmccpw_result(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double * 4), ("se", ctypes.c_double * 4),
+                ("per_replicate", ctypes.POINTER(ctypes.c_double))]
+
+
+class qmccpw_contract(ctypes.Structure):
+    _fields_ = [("option", qmccpw_option), ("market", qmccpw_market), ("N", ctypes.c_uint64),
+                ("R", ctypes.c_int32), ("construction", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library() -> ctypes.CDLL:
+    """The loaded libqmccpw (raises QmcCpwError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise QmcCpwError(QMCCPW_ERR_CUDA, f"{LIB_PATH} is missing: build it with "
+                                                   "python -m paper_2209_11337_gb300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            vp, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+            L.qmccpw_plan.argtypes = [P(vp), P(qmccpw_plan_desc)]
+            L.qmccpw_greeks.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), u64, i32, i32, i32, P(qmccpw_result)]
+            L.qmccpw_greeks_batch.argtypes = [vp, P(qmccpw_contract), i32, i32, P(qmccpw_result)]
+            L.qmccpw_batch_create.argtypes = [vp, P(qmccpw_contract), i32, i32, P(vp)]
+            L.qmccpw_batch_launch.argtypes = [vp, vp]
+            L.qmccpw_batch_results.argtypes = [vp, P(qmccpw_result)]
+            L.qmccpw_batch_device_results.argtypes = [vp, P(vp), P(vp)]
+            L.qmccpw_batch_launch_count.argtypes = [vp, P(i32)]
+            L.qmccpw_batch_set_timing.argtypes = [vp, i32]
+            L.qmccpw_batch_timing.argtypes = [vp, P(ctypes.c_float), P(i32)]
+            L.qmccpw_batch_free.argtypes = [vp]
+            L.qmccpw_sobol_points.argtypes = [vp, u32, i32, u64, u64, P(u32)]
+            L.qmccpw_point_values.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), i32, i32, u32, u64, u64,
+                                              P(ctypes.c_double)]
+            L.qmccpw_free.argtypes = [vp]
+            L.qmccpw_last_error.restype = ctypes.c_char_p
+            L.qmccpw_version.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name not in ("qmccpw_last_error", "qmccpw_version"):
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+        return _lib
+
+
+def _check(rc: int) -> int:
+    if rc not in (QMCCPW_OK, QMCCPW_NOT_READY):
+        msg = library().qmccpw_last_error().decode(errors="replace")
+        raise QmcCpwError(rc, msg)
+    return rc
+
+
+# ---- thin functions with the C names ---------------------------------------------
+def qmccpw_plan(device: int = 0, d_max: int = 366, r_max: int = 64, seed: int = 0x220911337,
+                stream: Optional[int] = None, workspace_bytes: int = 0) -> ctypes.c_void_p:
+    desc = qmccpw_plan_desc(device, d_max, r_max, 0, seed, stream, workspace_bytes)
+    h = ctypes.c_void_p()
+    _check(library().qmccpw_plan(ctypes.byref(h), ctypes.byref(desc)))
+    return h
+
+
+def qmccpw_free(plan) -> None:
+    _check(library().qmccpw_free(plan))
+
+
+def _result(R: int):
+    per = np.zeros((R, 4))
+    res = qmccpw_result()
+    res.per_replicate = per.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return res, per
+
+
+def qmccpw_greeks(plan, type: int, d: int, K: float, T: float, S0: float, r: float, sigma: float,
+                  N: int, R: int, construction: int = QMCCPW_BB, precision: int = QMCCPW_FP64):
+    """One contract; returns (mean[4], se[4], per_replicate[R,4]) as numpy arrays."""
+    res, per = _result(R)
+    _check(library().qmccpw_greeks(plan, ctypes.byref(qmccpw_option(type, d, K, T)),
+                                   ctypes.byref(qmccpw_market(S0, r, sigma)), N, R, construction, precision,
+                                   ctypes.byref(res)))
+    return np.array(res.mean[:]), np.array(res.se[:]), per
+
+
+def contract_array(contracts: Sequence) -> ctypes.Array:
+    """ctypes array of qmccpw_contract from objects with type, d, K, T, S0, r, sigma, N, R, construction."""
+    arr = (qmccpw_contract * len(contracts))()
+    for i, c in enumerate(contracts):
+        arr[i] = qmccpw_contract(qmccpw_option(c.type, c.d, c.K, c.T), qmccpw_market(c.S0, c.r, c.sigma),
+                                 c.N, c.R, c.construction)
+    return arr
+
+
+def qmccpw_greeks_batch(plan, contracts: Sequence, precision: int = QMCCPW_FP64):
+    """Returns a list of (mean[4], se[4], per_replicate[R,4])."""
+    arr = contract_array(contracts)
+    results = (qmccpw_result * len(contracts))()
+    pers = []
+    for i, c in enumerate(contracts):
+        per = np.zeros((c.R, 4))
+        pers.append(per)
+        results[i].per_replicate = per.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(library().qmccpw_greeks_batch(plan, arr, len(contracts), precision, results))
+    return [(np.array(results[i].mean[:]), np.array(results[i].se[:]), pers[i]) for i in range(len(contracts))]
+
+
+class Batch:
+    """Prepared batch (qmccpw_batch_create / _launch / _results / _free)."""
+
+    def __init__(self, plan, contracts: Sequence, precision: int):
+        self.contracts = list(contracts)
+        self._arr = contract_array(self.contracts)
+        self.handle = ctypes.c_void_p()
+        _check(library().qmccpw_batch_create(plan, self._arr, len(self.contracts), precision,
+                                             ctypes.byref(self.handle)))
+
+    def launch(self, stream: Optional[int] = None) -> None:
+        _check(library().qmccpw_batch_launch(self.handle, stream))
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int32()
+        _check(library().qmccpw_batch_launch_count(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def set_timing(self, capacity: int) -> None:
+        _check(library().qmccpw_batch_set_timing(self.handle, capacity))
+
+    def timing(self):
+        """(summed fused-kernel milliseconds, launches covered) since the last call."""
+        ms, n = ctypes.c_float(), ctypes.c_int32()
+        _check(library().qmccpw_batch_timing(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def device_results(self):
+        per, st = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(library().qmccpw_batch_device_results(self.handle, ctypes.byref(per), ctypes.byref(st)))
+        return per.value, st.value
+
+    def results(self):
+        results = (qmccpw_result * len(self.contracts))()
+        pers = []
+        for i, c in enumerate(self.contracts):
+            per = np.zeros((c.R, 4))
+            pers.append(per)
+            results[i].per_replicate = per.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(library().qmccpw_batch_results(self.handle, results))
+        return [(np.array(results[i].mean[:]), np.array(results[i].se[:]), pers[i])
+                for i in range(len(self.contracts))]
+
+    def free(self) -> None:
+        if self.handle:
+            _check(library().qmccpw_batch_free(self.handle))
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def qmccpw_sobol_points(plan, replicate: int, ndims: int, k0: int, count: int) -> np.ndarray:
+    out = np.zeros((count, ndims), dtype=np.uint32)
+    _check(library().qmccpw_sobol_points(plan, replicate, ndims, k0, count,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return out
+
+
+def qmccpw_point_values(plan, type: int, d: int, K: float, T: float, S0: float, r: float, sigma: float,
+                        construction: int, precision: int, replicate: int, k0: int, count: int) -> np.ndarray:
+    out = np.zeros((count, 4))
+    _check(library().qmccpw_point_values(plan, ctypes.byref(qmccpw_option(type, d, K, T)),
+                                         ctypes.byref(qmccpw_market(S0, r, sigma)), construction, precision,
+                                         replicate, k0, count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def qmccpw_last_error() -> str:
+    return library().qmccpw_last_error().decode(errors="replace")
+
+
+def qmccpw_version() -> str:
+    return library().qmccpw_version().decode()
