@@ -207,7 +207,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()  # one non-default stream for the library, the events and the L2 flush
     torch.cuda.set_stream(stream)
-    plan = q.qmccpw_plan(device=local, d_max=65, r_max=32, seed=W.SCRAMBLE_SEED + rank,
+    plan = q.qmccpw_plan(device=local, d_max=max(65, args.case_d + 1), r_max=32, seed=W.SCRAMBLE_SEED + rank,
                          stream=stream.cuda_stream)
     contracts = W.grid_d64()
     elems = elements(contracts)
@@ -248,6 +248,29 @@ def run_ours(args):
         return {"ms_per_step": sum(step_ms) / steps, "wall_s": wall, "fused_ms": fused_ms / max(1, nl),
                 "clocks": clocks, "launches": launches, "results": res}
 
+    if args.case:
+        # single-contract run for profiling: no JSON line
+        typ, cons = args.case.split("-")
+        tmap = {"arith": W.ARITH, "binary": W.BINARY, "lookback": W.LOOKBACK, "geometric": W.GEOMETRIC}
+        one = [W.Contract(tmap[typ], args.case_d, 100.0, 1.0, 100.0, 0.05, 0.2, args.case_N, args.case_R,
+                          W.BB if cons == "bb" else W.PCA)]
+        prec = q.QMCCPW_FP64 if args.case_precision == "fp64" else q.QMCCPW_MIXED
+        batch = q.Batch(plan, one, prec)
+        batch.set_timing(args.steps)
+        for _ in range(args.warmup):
+            batch.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        batch.timing()
+        for _ in range(args.steps):
+            batch.launch(stream.cuda_stream)
+        ms, n = batch.timing()
+        el = elements(one)
+        print(f"case {args.case} d={args.case_d} N={args.case_N} R={args.case_R} {args.case_precision}: "
+              f"fused {ms / n:.3f} ms/launch, {el / (ms / n / 1e3):.4g} point-dates/s")
+        batch.free()
+        q.qmccpw_free(plan)
+        return
+
     mixed = timed(q.QMCCPW_MIXED, args.steps, args.warmup, with_clocks=True)
     fp64 = timed(q.QMCCPW_FP64, args.fp64_steps, 1) if args.fp64_steps > 0 else None
 
@@ -274,13 +297,24 @@ def run_ours(args):
 
     # MIXED against FP64 on the same points, in units of the FP64 standard error
     err_se = None
+    err_frac = None
     if fp64 is not None:
         worst = 0.0
-        for (m32, _, _), (m64, se64, _) in zip(mixed["results"], fp64["results"]):
+        table = []
+        met = 0
+        for c, (m32, _, _), (m64, se64, _) in zip(contracts, mixed["results"], fp64["results"]):
+            row = {"contract": c.label(), "fp64": list(m64), "se": list(se64), "mixed": list(m32),
+                   "err_in_se": [abs(m32[g] - m64[g]) / se64[g] if se64[g] > 0 else None for g in range(4)]}
+            table.append(row)
             for g in range(4):
                 if se64[g] > 0:
                     worst = max(worst, abs(m32[g] - m64[g]) / se64[g])
+                    met += int(abs(m32[g] - m64[g]) <= 0.1 * se64[g])
         err_se = worst
+        err_frac = met / (4.0 * len(contracts))
+        if args.errors_out and rank == 0:
+            with open(args.errors_out, "w") as f:
+                json.dump(table, f, indent=1)
 
     sizeof_contract = 200  # bytes per qmccpw_contract descriptor uploaded, rounded up
     h2d = len(contracts) * (sizeof_contract + 8) + sum(c.R for c in contracts) * 8
@@ -297,6 +331,7 @@ def run_ours(args):
             "value": world * elems / (max_over_ranks(fp64["ms_per_step"]) / 1e3), "unit": UNIT,
             "ms_per_step": max_over_ranks(fp64["ms_per_step"]), "steps": args.fp64_steps},
         "mixed_vs_fp64_max_err_in_se": err_se,
+        "mixed_vs_fp64_share_within_0p1_se": err_frac,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "fused_kernel<float>", "fused_ms_per_launch": fused_ms,
@@ -326,6 +361,12 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--errors-out", default=None, help="write the per-contract MIXED vs FP64 table (JSON)")
+    ap.add_argument("--case", default=None, help="time one contract only, e.g. arith-bb or lookback-pca")
+    ap.add_argument("--case-d", type=int, default=64)
+    ap.add_argument("--case-N", type=int, default=2 ** 16)
+    ap.add_argument("--case-R", type=int, default=4)
+    ap.add_argument("--case-precision", choices=["mixed", "fp64"], default="mixed")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -108,11 +108,13 @@ struct qmccpw_batch_s {
     qmccpw_plan_t plan = nullptr;
     int count = 0;
     int precision = 0;
-    std::vector<ContractDev> host;
+    std::vector<ContractDev> host;   // contracts in launch order: bridge first, then PCA
+    std::vector<int32_t> order;      // order[i] = caller's index of host[i]
     std::vector<int32_t> R;
     uint64_t items = 0, total_reps = 0;
-    size_t smem = 0;
-    int grid = 0;
+    uint64_t items_bb = 0;           // items [0, items_bb) use the bridge, the rest PCA
+    size_t smem[2] = {0, 0};         // per construction
+    int grid[2] = {0, 0};
     BatchBuffers own;          // used by prepared batches
     BatchBuffers *buf = &own;  // one-shot calls point this at the plan's workspace
     // diagnostics
@@ -169,9 +171,22 @@ int get_dtables(qmccpw_plan_s *p, int d, double T, const DTables **out) {
     t->n = n;
     BridgePlan bp = bridge_plan(n, dt);
     t->n_levels = static_cast<int>(bp.level_start.size()) - 1;
-    std::vector<float> w32(bp.w.begin(), bp.w.end());
+    // float bridge coefficients are carried as hi + lo (hi = float(x), lo = float(x - hi)),
+    // which keeps the path covariance exact to ~2^-48 at three extra FMAs per node
+    // bridge: 8 floats per step (wl hi/lo, wr hi/lo, sd hi/lo, 2 pad) so a step is two aligned float4
+    std::vector<float> w32(8 * bp.steps.size(), 0.0f);
+    for (size_t b = 0; b < bp.steps.size(); ++b)
+        for (int k = 0; k < 3; ++k) {
+            const double x = bp.w[3 * b + k];
+            w32[8 * b + 2 * k] = static_cast<float>(x);
+            w32[8 * b + 2 * k + 1] = static_cast<float>(x - static_cast<double>(w32[8 * b + 2 * k]));
+        }
     std::vector<double> A = n > 0 ? pca_factor(n, dt) : std::vector<double>();
-    std::vector<float> A32(A.begin(), A.end());
+    // float A^T, rows k, columns i padded to a multiple of 16 (the register block of the product)
+    const int n_pad = (n + 15) & ~15;
+    std::vector<float> A32(static_cast<size_t>(n) * n_pad, 0.0f);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) A32[static_cast<size_t>(k) * n_pad + i] = static_cast<float>(A[static_cast<size_t>(i) * n + k]);
     QMC_TRY(t->steps.alloc(sizeof(BridgeStep) * std::max<size_t>(1, bp.steps.size())));
     QMC_TRY(t->w64.alloc(sizeof(double) * std::max<size_t>(1, bp.w.size())));
     QMC_TRY(t->w32.alloc(sizeof(float) * std::max<size_t>(1, w32.size())));
@@ -231,7 +246,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
     c.w32 = t->w32.as<float>();
     c.level_start = t->level_start.as<int32_t>();
     c.pca64 = t->pca64.as<double>();
-    c.pca32 = t->pca32.as<float>();
+    c.pcaT32 = t->pca32.as<float>();
     c.S0 = in.market.S0;
     c.K = in.option.K;
     c.T = in.option.T;
@@ -244,6 +259,13 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
     c.disc = std::exp(-c.r * c.T);
     c.disc1 = std::exp(c.r * (c.dt - c.T));
     c.sqrt_t1 = std::sqrt(c.dt);
+    c.inv_a = 1.0 / c.a;
+    c.disc1_S0 = c.disc1 * c.S0;
+    c.disc_K = c.disc * c.K;
+    c.k_bin_delta = c.disc / (c.S0 * c.a);
+    c.k_bin_gamma = c.disc / (c.S0 * c.S0 * c.a);
+    c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
+    c.inv_sigma = 1.0 / c.sigma;
     *out = c;
     return QMCCPW_OK;
 }
@@ -262,22 +284,27 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     b->precision = precision;
     b->host.resize(count);
     b->R.resize(count);
+    b->order.clear();
+    for (int cons : {QMCCPW_BB, QMCCPW_PCA})
+        for (int i = 0; i < count; ++i)
+            if (cs[i].construction == cons) b->order.push_back(i);
     uint64_t items = 0, reps = 0;
-    size_t smem = 0;
     std::vector<uint64_t> item_base(count), rep_owner;
-    for (int i = 0; i < count; ++i) {
-        QMC_TRY(build_contract(p, cs[i], precision, items, reps, &b->host[i]));
-        const ContractDev &c = b->host[i];
-        item_base[i] = items;
+    for (int k = 0; k < count; ++k) {
+        const qmccpw_contract &in = cs[b->order[k]];
+        QMC_TRY(build_contract(p, in, precision, items, reps, &b->host[k]));
+        const ContractDev &c = b->host[k];
+        item_base[k] = items;
         items += static_cast<uint64_t>(c.R) * c.tiles;
-        for (int r = 0; r < c.R; ++r) rep_owner.push_back(static_cast<uint64_t>(i));
+        if (in.construction == QMCCPW_BB) b->items_bb = items;
+        for (int r = 0; r < c.R; ++r) rep_owner.push_back(static_cast<uint64_t>(k));
         reps += c.R;
-        b->R[i] = c.R;
-        smem = std::max(smem, fused_smem_bytes(precision, c.n, c.tile_log2));
+        b->R[k] = c.R;
+        size_t &sm = b->smem[in.construction == QMCCPW_BB ? 0 : 1];
+        sm = std::max(sm, fused_smem_bytes(precision, c.n, c.tile_log2));
     }
     b->items = items;
     b->total_reps = reps;
-    b->smem = smem;
     const size_t scratch = items * 4 * sizeof(double);
     if (scratch > p->workspace_bytes)
         return fail(QMCCPW_ERR_OOM, "tile partial sums need " + std::to_string(scratch) +
@@ -296,11 +323,15 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     QMC_CUDA(cudaMemcpyAsync(B.rep_owner.ptr, rep_owner.data(), sizeof(uint64_t) * reps, cudaMemcpyHostToDevice,
                              p->stream));
     QMC_CUDA(cudaStreamSynchronize(p->stream));  // the host vectors go out of scope
-    int per_sm = 0;
-    QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, smem, &per_sm)));
-    if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
-    const uint64_t slots = static_cast<uint64_t>(per_sm) * p->sm_count;
-    b->grid = static_cast<int>(std::min<uint64_t>(items, slots));
+    const uint64_t range[2] = {b->items_bb, items - b->items_bb};
+    for (int k = 0; k < 2; ++k) {
+        if (range[k] == 0) continue;
+        int per_sm = 0;
+        QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
+        if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
+        const uint64_t slots = static_cast<uint64_t>(per_sm) * p->sm_count;
+        b->grid[k] = static_cast<int>(std::min<uint64_t>(range[k], slots));
+    }
     return QMCCPW_OK;
 }
 
@@ -310,7 +341,6 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
     LaunchParams lp{};
     lp.contracts = B.contracts.as<ContractDev>();
     lp.count = b->count;
-    lp.items = b->items;
     lp.item_base = B.item_base.as<uint64_t>();
     lp.sobol_table = p->table.as<uint32_t>();
     lp.sobol_shift = p->shift.as<uint32_t>();
@@ -322,7 +352,14 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
     const size_t cap = b->ev_start.size();
     const size_t slot = cap ? static_cast<size_t>(b->timed) % cap : 0;
     if (cap) QMC_CUDA(cudaEventRecord(b->ev_start[slot], s));
-    QMC_CUDA(static_cast<cudaError_t>(launch_fused(lp, b->precision, b->smem, b->grid, s)));
+    const uint64_t bounds[3] = {0, b->items_bb, b->items};
+    for (int k = 0; k < 2; ++k) {
+        if (bounds[k + 1] == bounds[k]) continue;
+        lp.item_begin = bounds[k];
+        lp.item_end = bounds[k + 1];
+        QMC_CUDA(static_cast<cudaError_t>(
+            launch_fused(lp, b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
+    }
     if (cap) {
         QMC_CUDA(cudaEventRecord(b->ev_stop[slot], s));
         ++b->timed;
@@ -343,12 +380,12 @@ int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
     QMC_CUDA(cudaMemcpyAsync(per.data(), B.per_rep.ptr, sizeof(double) * per.size(), cudaMemcpyDeviceToHost, s));
     QMC_CUDA(cudaStreamSynchronize(s));
     uint64_t rep = 0;
-    for (int i = 0; i < b->count; ++i) {
-        std::memcpy(out[i].mean, &stats[8 * i], 4 * sizeof(double));
-        std::memcpy(out[i].se, &stats[8 * i + 4], 4 * sizeof(double));
-        if (out[i].per_replicate)
-            std::memcpy(out[i].per_replicate, per.data() + 4 * rep, sizeof(double) * 4 * b->R[i]);
-        rep += b->R[i];
+    for (int k = 0; k < b->count; ++k) {
+        qmccpw_result &o = out[b->order[k]];
+        std::memcpy(o.mean, &stats[8 * k], 4 * sizeof(double));
+        std::memcpy(o.se, &stats[8 * k + 4], 4 * sizeof(double));
+        if (o.per_replicate) std::memcpy(o.per_replicate, per.data() + 4 * rep, sizeof(double) * 4 * b->R[k]);
+        rep += b->R[k];
     }
     return QMCCPW_OK;
 }
@@ -457,7 +494,8 @@ int qmccpw_batch_device_results(qmccpw_batch_t batch, const double **per_replica
 int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches) {
     g_last_error.clear();
     if (!batch || !launches) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
-    *launches = 3;  // fused, per-replicate reduction, statistics
+    // one fused grid per construction present, the per-replicate reduction, the statistics
+    *launches = (batch->items_bb > 0 ? 1 : 0) + (batch->items > batch->items_bb ? 1 : 0) + 2;
     return QMCCPW_OK;
 }
 

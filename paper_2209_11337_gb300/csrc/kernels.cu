@@ -127,7 +127,7 @@ __device__ __forceinline__ double sf64(double x) { return 0.5 * erfc(x * 0.70710
 __device__ __forceinline__ double pdf64(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
 
 __device__ void values_fp64(const ContractDev &c, double xhat, double dhat, double v[4]) {
-    const double psi = (c.psi0 - log(xhat)) / c.a;
+    const double psi = (c.psi0 - log(xhat)) * c.inv_a;
     const double pdf = pdf64(psi);
     if (c.type == QMCCPW_BINARY_ASIAN) {
         v[0] = c.disc * sf64(psi);
@@ -143,34 +143,36 @@ __device__ void values_fp64(const ContractDev &c, double xhat, double dhat, doub
     }
 }
 
-// Mixed precision: psi in double (the switch point), the payoff terms in
-// float.  Beyond |psi| = 12 the float density and tail underflow, so those
-// (rare) points take the double formulas.
+// Mixed precision: the switch point psi in double; the normal tail and
+// density in float; the combination with the contract constants in double.
+// The price of a call is the difference of two terms of size ~K: float
+// constants there would bias every point by ~2^-24 K, which no averaging
+// removes.  Beyond |psi| = 12 the float density and tail underflow, so
+// those (rare) points take the double formulas.
 __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, double v[4]) {
-    const double psi = (c.psi0 - log(static_cast<double>(xhat))) / c.a;
+    const double psi = (c.psi0 - log(static_cast<double>(xhat))) * c.inv_a;
     if (fabs(psi) > 12.0) {
         values_fp64(c, static_cast<double>(xhat), static_cast<double>(dhat), v);
         return;
     }
     const float p = static_cast<float>(psi);
-    const float a = static_cast<float>(c.a);
     const float pdf = 0.398942280f * expf(-0.5f * p * p);
     if (c.type == QMCCPW_BINARY_ASIAN) {
-        const float disc = static_cast<float>(c.disc);
-        const float S0 = static_cast<float>(c.S0);
-        v[0] = disc * 0.5f * erfcf(p * 0.707106781f);
-        v[1] = disc * pdf / (S0 * a);
-        v[2] = disc * pdf * (dhat / (a * xhat) + p / static_cast<float>(c.sigma) - static_cast<float>(c.sqrt_t1));
-        v[3] = disc * pdf / (S0 * S0 * a) * (p / a - 1.0f);
+        const double sf = 0.5f * erfcf(p * 0.707106781f);
+        const double pd = pdf;
+        v[0] = c.disc * sf;
+        v[1] = c.k_bin_delta * pd;
+        v[2] = c.disc * pd * (static_cast<double>(dhat / xhat) * c.inv_a + psi * c.inv_sigma - c.sqrt_t1);
+        v[3] = c.k_bin_gamma * pd * (psi * c.inv_a - 1.0);
     } else {
-        const float disc = static_cast<float>(c.disc), disc1 = static_cast<float>(c.disc1);
-        const float S0 = static_cast<float>(c.S0), K = static_cast<float>(c.K);
-        const float sfs = 0.5f * erfcf((p - a) * 0.707106781f);
-        const float sf = 0.5f * erfcf(p * 0.707106781f);
-        v[0] = disc1 * S0 * xhat * sfs - disc * K * sf;
-        v[1] = disc1 * xhat * sfs;
-        v[2] = disc1 * sfs * S0 * dhat + disc * K * pdf * static_cast<float>(c.sqrt_t1);
-        v[3] = disc * K * pdf / (S0 * S0 * a);
+        const float a = static_cast<float>(c.a);
+        const double sfs = 0.5f * erfcf((p - a) * 0.707106781f);
+        const double sf = 0.5f * erfcf(p * 0.707106781f);
+        const double xh = xhat;
+        v[0] = c.disc1_S0 * xh * sfs - c.disc_K * sf;
+        v[1] = c.disc1 * xh * sfs;
+        v[2] = c.disc1_S0 * sfs * static_cast<double>(dhat) + c.disc_K * c.sqrt_t1 * static_cast<double>(pdf);
+        v[3] = c.k_call_gamma * static_cast<double>(pdf);
     }
 }
 
@@ -204,48 +206,208 @@ __device__ __forceinline__ int find_contract(const uint64_t *__restrict__ base, 
     return lo;
 }
 
+// Bridge (Sec. 4.4): levels breadth first; within a level the nodes of a
+// point are spread over its G threads; W~ overwrites z in the point's row.
 template <typename T, int TYPE>
-__device__ void path_phase(const ContractDev &c, T *zw, int P, int stride, PathAcc<T> &acc) {
+__device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &acc) {
+    const int P = 1 << c.tile_log2;
     const int pt = threadIdx.x & (P - 1);
     const int grp = threadIdx.x >> c.tile_log2;
     const int G = c.groups;
     T *row = zw + pt * stride;
     const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
-    if (c.construction == QMCCPW_BB) {
-        const T *w = nullptr;
-        if constexpr (sizeof(T) == 8) w = reinterpret_cast<const T *>(c.w64);
-        else w = reinterpret_cast<const T *>(c.w32);
-        for (int lvl = 0; lvl < c.n_levels; ++lvl) {
-            const int b_end = __ldg(c.level_start + lvl + 1);
-            for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += G) {
-                const int4 st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
-                const T wl = w[3 * b], wr = w[3 * b + 1], sd = w[3 * b + 2];
-                const T Wm = wl * row[st.y] + wr * row[st.z] + sd * row[st.x];
-                row[st.x] = Wm;
-                acc.template add<TYPE>(st.x, Wm, omega, sigma, dt);
+    for (int lvl = 0; lvl < c.n_levels; ++lvl) {
+        const int b_end = __ldg(c.level_start + lvl + 1);
+        for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += G) {
+            const int4 st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
+            const T Wl = row[st.y], Wr = row[st.z], z = row[st.x];
+            T Wm;
+            if constexpr (sizeof(T) == 8) {
+                const double *w = c.w64 + 3 * b;
+                Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * z;
+            } else {
+                // hi + lo coefficients: the low parts first, then the high parts
+                const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
+                const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
+                float lo = h.y * Wl;
+                lo = fmaf(h.w, Wr, lo);
+                lo = fmaf(g.y, z, lo);
+                Wm = fmaf(h.x, Wl, fmaf(h.z, Wr, fmaf(g.x, z, lo)));
             }
-            if (G > 1) __syncthreads();
+            row[st.x] = Wm;
+            acc.template add<TYPE>(st.x, Wm, omega, sigma, dt);
         }
-    } else {
-        const T *A = nullptr;
-        if constexpr (sizeof(T) == 8) A = reinterpret_cast<const T *>(c.pca64);
-        else A = reinterpret_cast<const T *>(c.pca32);
-        const int n = c.n;
-        for (int i = 1 + grp; i <= n; i += G) {
-            const T *Ai = A + static_cast<size_t>(i - 1) * n;
-            T Wi = T(0);
+        if (G > 1) __syncthreads();
+    }
+}
+
+// PCA, plain form (double precision, and tiles of fewer than 32 points): the
+// G threads of a point take every G-th row of A.
+template <typename T, int TYPE>
+__device__ void pca_rows_phase(const ContractDev &c, const T *zw, int stride, PathAcc<T> &acc) {
+    const int P = 1 << c.tile_log2;
+    const int pt = threadIdx.x & (P - 1);
+    const int grp = threadIdx.x >> c.tile_log2;
+    const T *row = zw + pt * stride;
+    const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
+    const int n = c.n;
+    for (int i = 1 + grp; i <= n; i += c.groups) {
+        T Wi = T(0);
+        if constexpr (sizeof(T) == 8) {
+            const double *Ai = c.pca64 + static_cast<size_t>(i - 1) * n;
             for (int k = 0; k < n; ++k) Wi += __ldg(Ai + k) * row[k + 1];
-            acc.template add<TYPE>(i, Wi, omega, sigma, dt);
+        } else {
+            const int n_pad = (n + 15) & ~15;
+            for (int k = 0; k < n; ++k) Wi = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k) * n_pad + (i - 1)), row[k + 1], Wi);
+        }
+        acc.template add<TYPE>(i, Wi, omega, sigma, dt);
+    }
+}
+
+// PCA as a register-blocked product W = Z A^T on the FP32 pipe: a thread owns
+// PB points (lanes are consecutive points, so the z loads are conflict free)
+// and 16 rows of A^T (the same for the whole warp, so each float4 of A^T is
+// one broadcast load).  Per k: PB shared loads, 4 uniform loads, 16 PB FMAs.
+template <int PB, int TYPE>
+__device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride, PathAcc<float> (&acc)[PB],
+                               int &slot, int &slots, int (&pts)[PB]) {
+    const int P = 1 << c.tile_log2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int groups = P / (32 * PB);
+    slots = (kThreads / 32) / groups;
+    const int g = warp % groups;
+    slot = warp / groups;
+    const int n = c.n, n4 = ((n + 15) & ~15) >> 2;
+    const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
+    const float *zr[PB];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+        pts[j] = g * 32 * PB + lane + 32 * j;
+        zr[j] = zw + pts[j] * stride + 1;
+        acc[j].init(TYPE, slot == 0);
+    }
+    const float4 *AT = reinterpret_cast<const float4 *>(c.pcaT32);
+    for (int rb = slot; rb * 16 < n; rb += slots) {
+        float w[PB][16];
+#pragma unroll
+        for (int j = 0; j < PB; ++j)
+#pragma unroll
+            for (int r = 0; r < 16; ++r) w[j][r] = 0.0f;
+        const float4 *a = AT + 4 * rb;
+        for (int k = 0; k < n; ++k, a += n4) {
+            const float4 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3);
+            const float av[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
+                                  a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
+#pragma unroll
+            for (int j = 0; j < PB; ++j) {
+                const float z = zr[j][k];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) w[j][r] = fmaf(av[r], z, w[j][r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int i = rb * 16 + r + 1;
+            if (i <= n) {
+#pragma unroll
+                for (int j = 0; j < PB; ++j) acc[j].template add<TYPE>(i, w[j][r], omega, sigma, dt);
+            }
         }
     }
 }
 
+// Partial accumulators of a point live in several threads; they are staged
+// in shared memory as slot-major arrays and merged by one thread per point in
+// slot order (a fixed order, so the result does not depend on scheduling).
 template <typename T>
+__device__ __forceinline__ void stage_partial(void *base, int P, int slot, int point, const PathAcc<T> &a) {
+    T *rx = reinterpret_cast<T *>(base);
+    T *rd = rx + kThreads * 4;
+    int32_t *rm = reinterpret_cast<int32_t *>(rd + kThreads * 4);
+    rx[slot * P + point] = a.x;
+    rd[slot * P + point] = a.dsum;
+    rm[slot * P + point] = a.m;
+}
+
+template <typename T>
+__device__ __forceinline__ void merge_partials(const void *base, int P, int slots, int point, int type, PathAcc<T> &a) {
+    const T *rx = reinterpret_cast<const T *>(base);
+    const T *rd = rx + kThreads * 4;
+    const int32_t *rm = reinterpret_cast<const int32_t *>(rd + kThreads * 4);
+    a.x = rx[point];
+    a.dsum = rd[point];
+    a.m = rm[point];
+    for (int s = 1; s < slots; ++s) {
+        PathAcc<T> o;
+        o.x = rx[s * P + point];
+        o.dsum = rd[s * P + point];
+        o.m = rm[s * P + point];
+        a.merge(type, o);
+    }
+}
+
+// Phase 2 for one product type: returns, for threads t < P, the merged
+// accumulator of point t in `acc` (other threads' acc is unspecified).
+template <typename T, int CONS, int TYPE>
+__device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &acc) {
+    const int P = 1 << c.tile_log2;
+    if constexpr (CONS == QMCCPW_BB) {
+        acc.init(TYPE, threadIdx.x < P);
+        bridge_phase<T, TYPE>(c, zw, stride, acc);
+        if (c.groups == 1) return;
+        __syncthreads();
+        stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
+        __syncthreads();
+        if (threadIdx.x < P) merge_partials<T>(zw, P, c.groups, threadIdx.x, TYPE, acc);
+        return;
+    } else {
+    if constexpr (sizeof(T) == 4) {
+        if (P >= 32) {
+            int slot = 0, slots = 1;
+            if (P >= 128) {
+                PathAcc<float> a4[4];
+                int pts[4];
+                pca_gemm_phase<4, TYPE>(c, zw, stride, a4, slot, slots, pts);
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) stage_partial<float>(zw, P, slot, pts[j], a4[j]);
+            } else if (P == 64) {
+                PathAcc<float> a2[2];
+                int pts[2];
+                pca_gemm_phase<2, TYPE>(c, zw, stride, a2, slot, slots, pts);
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < 2; ++j) stage_partial<float>(zw, P, slot, pts[j], a2[j]);
+            } else {
+                PathAcc<float> a1[1];
+                int pts[1];
+                pca_gemm_phase<1, TYPE>(c, zw, stride, a1, slot, slots, pts);
+                __syncthreads();
+                stage_partial<float>(zw, P, slot, pts[0], a1[0]);
+            }
+            __syncthreads();
+            if (threadIdx.x < P) merge_partials<float>(zw, P, slots, threadIdx.x, TYPE, acc);
+            return;
+        }
+    }
+    acc.init(TYPE, threadIdx.x < P);
+    pca_rows_phase<T, TYPE>(c, zw, stride, acc);
+    if (c.groups == 1) return;
+    __syncthreads();
+    stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
+    __syncthreads();
+    if (threadIdx.x < P) merge_partials<T>(zw, P, c.groups, threadIdx.x, TYPE, acc);
+    }
+}
+
+// CONS is the construction of every contract this launch covers (the host
+// launches one grid per construction over that construction's items).
+template <typename T, int CONS>
 __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ LaunchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double warp_part[kThreads / 32][4];
 
-    for (uint64_t item = blockIdx.x; item < p.items; item += gridDim.x) {
+    for (uint64_t item = p.item_begin + blockIdx.x; item < p.item_end; item += gridDim.x) {
         const int ci = find_contract(p.item_base, p.count, item);
         const ContractDev &c = p.contracts[ci];
         const int P = 1 << c.tile_log2;
@@ -265,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
             for (int it = threadIdx.x; it < work; it += kThreads) {
                 const int j = it % n;
                 const int ch = it / n;
-                const int slot = (c.construction == QMCCPW_BB) ? __ldg(&c.steps[j].m) : j + 1;
+                const int slot = (CONS == QMCCPW_BB) ? __ldg(&c.steps[j].m) : j + 1;
                 T *dst = zw + static_cast<size_t>(ch * chunk) * stride + slot;
                 // points at or past N (ragged last tile) are never generated: their
                 // index could pass 2^32; they are zero-filled and left out of the sums
@@ -286,43 +448,20 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
         for (int pt = threadIdx.x; pt < P; pt += kThreads) zw[pt * stride] = T(0);
         __syncthreads();
 
-        // ---- phase 2: path construction and running sums
-        const int pt = threadIdx.x & (P - 1);
-        const int grp = threadIdx.x >> c.tile_log2;
+        // ---- phase 2: path construction and running sums, merged per point
         PathAcc<T> acc;
-        acc.init(c.type, grp == 0);
         switch (c.type) {
-            case QMCCPW_ARITH_ASIAN_CALL: path_phase<T, QMCCPW_ARITH_ASIAN_CALL>(c, zw, P, stride, acc); break;
-            case QMCCPW_BINARY_ASIAN: path_phase<T, QMCCPW_BINARY_ASIAN>(c, zw, P, stride, acc); break;
-            case QMCCPW_LOOKBACK_FIXED_CALL: path_phase<T, QMCCPW_LOOKBACK_FIXED_CALL>(c, zw, P, stride, acc); break;
-            default: path_phase<T, QMCCPW_GEOMETRIC_ASIAN_CALL>(c, zw, P, stride, acc); break;
+            case QMCCPW_ARITH_ASIAN_CALL: path_phase<T, CONS, QMCCPW_ARITH_ASIAN_CALL>(c, zw, stride, acc); break;
+            case QMCCPW_BINARY_ASIAN: path_phase<T, CONS, QMCCPW_BINARY_ASIAN>(c, zw, stride, acc); break;
+            case QMCCPW_LOOKBACK_FIXED_CALL: path_phase<T, CONS, QMCCPW_LOOKBACK_FIXED_CALL>(c, zw, stride, acc); break;
+            default: path_phase<T, CONS, QMCCPW_GEOMETRIC_ASIAN_CALL>(c, zw, stride, acc); break;
         }
-
-        // combine the G partial accumulators of each point (fixed group order)
-        if (c.groups > 1) {
-            __syncthreads();  // zw is free now; reuse it for the partials
-            T *rx = zw;
-            T *rd = zw + kThreads;
-            int32_t *rm = reinterpret_cast<int32_t *>(zw + 2 * kThreads);
-            rx[threadIdx.x] = acc.x;
-            rd[threadIdx.x] = acc.dsum;
-            rm[threadIdx.x] = acc.m;
-            __syncthreads();
-            if (grp == 0) {
-                for (int g = 1; g < c.groups; ++g) {
-                    PathAcc<T> o;
-                    o.x = rx[g * P + pt];
-                    o.dsum = rd[g * P + pt];
-                    o.m = rm[g * P + pt];
-                    acc.merge(c.type, o);
-                }
-            }
-        }
+        const int pt = threadIdx.x;
 
         // ---- phase 3: conditional values of the point, tile sum
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         const uint64_t local_point = tile * P + pt;
-        if (grp == 0 && local_point < c.N) {
+        if (pt < P && local_point < c.N) {
             T xhat, dhat;
             if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
                 xhat = acc.x;
@@ -484,32 +623,45 @@ size_t fused_smem_bytes(int precision, int n, int tile_log2) {
     const size_t elem = (precision == QMCCPW_FP64) ? 8 : 4;
     const int stride = (n + 1) | 1;
     const size_t zw = static_cast<size_t>(1u << tile_log2) * stride * elem;
-    const size_t red = 2 * kThreads * elem + kThreads * sizeof(int32_t);
+    // staging of partial accumulators: up to 4 * kThreads (slot, point) entries of (x, dsum, m)
+    const size_t red = 4 * kThreads * (2 * elem + sizeof(int32_t));
     return ((zw > red ? zw : red) + 15) & ~size_t(15);
 }
 
+template <typename T>
+static cudaError_t set_limit_all(int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<T, QMCCPW_BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fused_kernel<T, QMCCPW_PCA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 int fused_set_smem_limit(int precision, size_t bytes) {
+    const int b = static_cast<int>(bytes);
+    return static_cast<int>(precision == QMCCPW_FP64 ? set_limit_all<double>(b) : set_limit_all<float>(b));
+}
+
+int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm) {
     cudaError_t e;
     if (precision == QMCCPW_FP64)
-        e = cudaFuncSetAttribute(fused_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+        e = construction == QMCCPW_BB
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<double, QMCCPW_BB>, kThreads, smem_bytes)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<double, QMCCPW_PCA>, kThreads, smem_bytes);
     else
-        e = cudaFuncSetAttribute(fused_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+        e = construction == QMCCPW_BB
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<float, QMCCPW_BB>, kThreads, smem_bytes)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<float, QMCCPW_PCA>, kThreads, smem_bytes);
     return static_cast<int>(e);
 }
 
-int fused_occupancy(int precision, size_t smem_bytes, int *blocks_per_sm) {
-    cudaError_t e;
-    if (precision == QMCCPW_FP64)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<double>, kThreads, smem_bytes);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<float>, kThreads, smem_bytes);
-    return static_cast<int>(e);
-}
-
-int launch_fused(const LaunchParams &p, int precision, size_t smem_bytes, int grid, void *stream) {
+int launch_fused(const LaunchParams &p, int precision, int construction, size_t smem_bytes, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (precision == QMCCPW_FP64) fused_kernel<double><<<grid, kThreads, smem_bytes, s>>>(p);
-    else fused_kernel<float><<<grid, kThreads, smem_bytes, s>>>(p);
+    if (precision == QMCCPW_FP64) {
+        if (construction == QMCCPW_BB) fused_kernel<double, QMCCPW_BB><<<grid, kThreads, smem_bytes, s>>>(p);
+        else fused_kernel<double, QMCCPW_PCA><<<grid, kThreads, smem_bytes, s>>>(p);
+    } else {
+        if (construction == QMCCPW_BB) fused_kernel<float, QMCCPW_BB><<<grid, kThreads, smem_bytes, s>>>(p);
+        else fused_kernel<float, QMCCPW_PCA><<<grid, kThreads, smem_bytes, s>>>(p);
+    }
     return static_cast<int>(cudaGetLastError());
 }
 

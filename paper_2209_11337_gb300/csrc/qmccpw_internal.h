@@ -66,11 +66,11 @@ struct ContractDev {
     uint64_t rep_base;                   // first replicate slot of this contract (in per-replicate arrays)
     // per-d tables (device pointers)
     const BridgeStep *steps;
-    const double *w64;                   // 3 per step
-    const float *w32;
+    const double *w64;                   // 3 per step: wl, wr, sd
+    const float *w32;                    // (hi, lo) float pairs of wl, wr, sd + 2 pad: 8 per step
     const int32_t *level_start;
     const double *pca64;                 // n x n row-major
-    const float *pca32;
+    const float *pcaT32;                 // A^T as float, [k][i], i padded to a multiple of 16 with zeros
     // market-derived constants
     double S0, K, T, r, sigma;
     double dt;                           // t_1 = T/d: spacing of the separated dates
@@ -80,6 +80,13 @@ struct ContractDev {
     double disc;                         // exp(-r T)
     double disc1;                        // exp(r (t_1 - T))
     double sqrt_t1;
+    double inv_a;                        // 1/a
+    double disc1_S0;                     // disc1 * S0
+    double disc_K;                       // disc * K
+    double k_bin_delta;                  // disc / (S0 a)
+    double k_bin_gamma;                  // disc / (S0^2 a)
+    double k_call_gamma;                 // disc K / (S0^2 a)
+    double inv_sigma;
 };
 
 // Per-launch parameters of the fused kernel.
@@ -87,7 +94,7 @@ struct LaunchParams {
     const ContractDev *contracts;
     int32_t count;
     int32_t pad;
-    uint64_t items;                      // total work items (CTAs)
+    uint64_t item_begin, item_end;       // work items [item_begin, item_end) of this launch
     const uint64_t *item_base;           // contract item bases, for the binary search
     const uint32_t *sobol_table;         // [rep][b][j] scrambled direction integers
     const uint32_t *sobol_shift;         // [rep][j]
@@ -99,7 +106,7 @@ struct LaunchParams {
 };
 
 // Launchers (kernels.cu).  Return the cudaError_t as int.
-int launch_fused(const LaunchParams &p, int precision, size_t smem_bytes, int grid, void *stream);
+int launch_fused(const LaunchParams &p, int precision, int construction, size_t smem_bytes, int grid, void *stream);
 int launch_reduce(const ContractDev *contracts, int32_t count, const double *tile_sums,
                   double *per_rep, double *stats, uint64_t total_reps, const uint64_t *rep_owner,
                   void *stream);
@@ -110,6 +117,6 @@ int launch_sobol_dump(const uint32_t *table, const uint32_t *shift, int jstride,
 // dynamic shared memory of one CTA for a contract with n dims and 2^tile_log2 points
 size_t fused_smem_bytes(int precision, int n, int tile_log2);
 int fused_set_smem_limit(int precision, size_t bytes);
-int fused_occupancy(int precision, size_t smem_bytes, int *blocks_per_sm);
+int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
 
 }  // namespace qmccpw
