@@ -194,6 +194,41 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
                         int32_t construction, int32_t precision, uint32_t replicate, uint64_t k0,
                         uint64_t count, double *out);
 
+/*
+ * Allocation-free form of qmccpw_greeks (the paper has no counterpart: this
+ * is a deployment aid).  Some callers must not allocate device memory per
+ * request: code that runs while a CUDA stream is being captured, latency-
+ * critical services (cudaMalloc can block and cudaFree synchronises the whole
+ * device), and hosts whose device memory is owned by another allocator such
+ * as a framework's caching pool.  This entry point performs no cudaMalloc,
+ * cudaFree or other device-memory allocation: every per-call device array
+ * (tile partial sums, the contract descriptor, the bridge or PCA tables) is
+ * placed in one fixed 16 MiB array compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  The plan (made
+ * beforehand with qmccpw_plan, which does allocate) supplies the Sobol'
+ * tables.
+ *   out: caller-owned device memory of (R + 2) * 4 doubles, written as the R
+ *        per-replicate estimates (replicate-major, 4 values each), then
+ *        mean[4], then se[4] (same meaning as qmccpw_result).
+ *   stream: cudaStream_t to enqueue on (NULL: the plan's stream).  The call
+ *        returns once the work is enqueued; read `out` after synchronising
+ *        that stream.
+ * All calls on a device share the one array and it keeps the previous
+ * call's contents (nothing in it needs to start at zero: every slot a call
+ * reads, the same call writes first).  Calls that can overlap on the GPU
+ * (issued on different streams without ordering between them) race on the
+ * array; serialise them on one stream.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) and caches it: make
+ * that first call before any stream capture begins.
+ * Errors: as qmccpw_greeks; OOM when the work of this call (about
+ * 32 * R * N / P bytes of tile sums, P = 256 for d <= 65 in MIXED, plus the
+ * d-dependent tables) exceeds the 16 MiB array; UNSUPPORTED for the
+ * tensor-core precisions.
+ */
+int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
+                          uint64_t N, int32_t R, int32_t construction, int32_t precision, double *out,
+                          void *stream);
+
 /* Release a plan after waiting for its work; NULL is accepted (no-op). */
 int qmccpw_free(qmccpw_plan_t plan);
 

@@ -390,6 +390,35 @@ int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
     return QMCCPW_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free form (qmccpw_greeks_noalloc): every per-call device array
+// lives in this file-scope array instead of cudaMalloc'd memory.  In host code
+// the symbol is only a host-side stand-in; its device address is looked up
+// once per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).
+int noalloc_scratch_address(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(QMCCPW_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *ptr = nullptr;
+        QMC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_addr[device] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_noalloc_addr[device];
+    return QMCCPW_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
 }  // namespace
 
 extern "C" {
@@ -618,6 +647,142 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
     QMC_TRY(batch_enqueue(&b, plan->stream));
     QMC_CUDA(cudaStreamSynchronize(plan->stream));
     QMC_CUDA(cudaMemcpy(out, dout.ptr, sizeof(double) * 4 * count, cudaMemcpyDeviceToHost));
+    return QMCCPW_OK;
+}
+
+
+int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market, uint64_t N,
+                          int32_t R, int32_t construction, int32_t precision, double *out, void *stream) {
+    g_last_error.clear();
+    if (!plan || !option || !market || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    QMC_TRY(validate_contract(plan, *option, *market, N, R, construction, precision, false));
+    if (precision >= QMCCPW_MIXED_TC_BF16X3)
+        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA precisions are not built in this library version");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    QMC_CUDA(cudaSetDevice(plan->device));
+    unsigned char *scratch = nullptr;
+    QMC_TRY(noalloc_scratch_address(plan->device, &scratch));
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : plan->stream;
+
+    // the contract and its bridge / PCA tables, built on the host
+    const int d = option->d, n = d - 1;
+    const double dt = option->T / d;
+    BridgePlan bp = bridge_plan(n, dt);
+    const int n_pad = (n + 15) & ~15;
+    const bool pca = construction == QMCCPW_PCA;
+    std::vector<double> A = (pca && n > 0) ? pca_factor(n, dt) : std::vector<double>();
+
+    ContractDev c{};
+    c.type = option->type;
+    c.d = d;
+    c.n = n;
+    c.construction = construction;
+    c.tile_log2 = choose_tile_log2(precision, n);
+    const int P = 1 << c.tile_log2;
+    int chunk_log2 = c.tile_log2;
+    while (chunk_log2 > 0 && static_cast<long>(n) * (P >> chunk_log2) < 2L * kThreads) --chunk_log2;
+    c.chunk_log2 = chunk_log2;
+    c.R = R;
+    c.tiles = static_cast<int32_t>((N + P - 1) / P);
+    c.groups = kThreads / P;
+    c.n_levels = static_cast<int>(bp.level_start.size()) - 1;
+    c.row_stride = (n + 1) | 1;
+    c.N = N;
+    c.item_base = 0;
+    c.rep_base = 0;
+    const uint64_t items = static_cast<uint64_t>(R) * c.tiles;
+
+    // layout of the scratch array (256-byte aligned pieces)
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
+    const size_t o_contract = take(sizeof(ContractDev));
+    const size_t o_item_base = take(sizeof(uint64_t));
+    const size_t o_rep_owner = take(sizeof(uint64_t) * R);
+    const size_t o_steps = take(sizeof(BridgeStep) * bp.steps.size());
+    const size_t o_w64 = take(sizeof(double) * bp.w.size());
+    const size_t o_w32 = take(sizeof(float) * 8 * bp.steps.size());
+    const size_t o_levels = take(sizeof(int32_t) * bp.level_start.size());
+    const size_t o_pca64 = take(pca && precision == QMCCPW_FP64 ? sizeof(double) * A.size() : 0);
+    const size_t o_pca32 = take(pca && precision != QMCCPW_FP64 ? sizeof(float) * n * n_pad : 0);
+    const size_t staged = off;
+    const size_t o_tiles = take(sizeof(double) * 4 * items);
+    if (off > kNoAllocScratchBytes)
+        return fail(QMCCPW_ERR_OOM, "qmccpw_greeks_noalloc needs " + std::to_string(off) +
+                                        " bytes of scratch; its fixed array holds " +
+                                        std::to_string(kNoAllocScratchBytes) + " bytes (reduce N or R)");
+
+    // stage the read-only part on the host, then one copy into the array
+    std::vector<unsigned char> host(staged, 0);
+    unsigned char *dev = scratch;
+    c.steps = reinterpret_cast<const BridgeStep *>(dev + o_steps);
+    c.w64 = reinterpret_cast<const double *>(dev + o_w64);
+    c.w32 = reinterpret_cast<const float *>(dev + o_w32);
+    c.level_start = reinterpret_cast<const int32_t *>(dev + o_levels);
+    c.pca64 = reinterpret_cast<const double *>(dev + o_pca64);
+    c.pcaT32 = reinterpret_cast<const float *>(dev + o_pca32);
+    c.S0 = market->S0;
+    c.K = option->K;
+    c.T = option->T;
+    c.r = market->r;
+    c.sigma = market->sigma;
+    c.dt = dt;
+    c.a = c.sigma * std::sqrt(dt);
+    c.omega = c.r - 0.5 * c.sigma * c.sigma;
+    c.psi0 = std::log(c.K / c.S0) - c.omega * dt;
+    c.disc = std::exp(-c.r * c.T);
+    c.disc1 = std::exp(c.r * (dt - c.T));
+    c.sqrt_t1 = std::sqrt(dt);
+    c.inv_a = 1.0 / c.a;
+    c.disc1_S0 = c.disc1 * c.S0;
+    c.disc_K = c.disc * c.K;
+    c.k_bin_delta = c.disc / (c.S0 * c.a);
+    c.k_bin_gamma = c.disc / (c.S0 * c.S0 * c.a);
+    c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
+    c.inv_sigma = 1.0 / c.sigma;
+    std::memcpy(host.data() + o_contract, &c, sizeof(c));
+    std::memset(host.data() + o_item_base, 0, sizeof(uint64_t));
+    std::memset(host.data() + o_rep_owner, 0, sizeof(uint64_t) * R);  // every replicate belongs to contract 0
+    if (!bp.steps.empty()) {
+        std::memcpy(host.data() + o_steps, bp.steps.data(), sizeof(BridgeStep) * bp.steps.size());
+        std::memcpy(host.data() + o_w64, bp.w.data(), sizeof(double) * bp.w.size());
+        float *w32 = reinterpret_cast<float *>(host.data() + o_w32);
+        for (size_t b = 0; b < bp.steps.size(); ++b)
+            for (int k = 0; k < 3; ++k) {
+                const double x = bp.w[3 * b + k];
+                w32[8 * b + 2 * k] = static_cast<float>(x);
+                w32[8 * b + 2 * k + 1] = static_cast<float>(x - static_cast<double>(w32[8 * b + 2 * k]));
+            }
+    }
+    std::memcpy(host.data() + o_levels, bp.level_start.data(), sizeof(int32_t) * bp.level_start.size());
+    if (pca && precision == QMCCPW_FP64 && !A.empty())
+        std::memcpy(host.data() + o_pca64, A.data(), sizeof(double) * A.size());
+    if (pca && precision != QMCCPW_FP64) {
+        float *at = reinterpret_cast<float *>(host.data() + o_pca32);
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) at[static_cast<size_t>(k) * n_pad + i] = static_cast<float>(A[static_cast<size_t>(i) * n + k]);
+    }
+    QMC_CUDA(cudaMemcpyAsync(dev, host.data(), staged, cudaMemcpyHostToDevice, s));
+
+    int per_sm = 0;
+    const size_t smem = fused_smem_bytes(precision, n, c.tile_log2);
+    QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, construction, smem, &per_sm)));
+    if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
+    const int grid = static_cast<int>(std::min<uint64_t>(items, static_cast<uint64_t>(per_sm) * plan->sm_count));
+
+    LaunchParams lp{};
+    lp.contracts = reinterpret_cast<const ContractDev *>(dev + o_contract);
+    lp.count = 1;
+    lp.item_begin = 0;
+    lp.item_end = items;
+    lp.item_base = reinterpret_cast<const uint64_t *>(dev + o_item_base);
+    lp.sobol_table = plan->table.as<uint32_t>();
+    lp.sobol_shift = plan->shift.as<uint32_t>();
+    lp.jstride = plan->jstride;
+    lp.tile_sums = reinterpret_cast<double *>(dev + o_tiles);
+    QMC_CUDA(static_cast<cudaError_t>(launch_fused(lp, precision, construction, smem, grid, s)));
+    QMC_CUDA(static_cast<cudaError_t>(launch_reduce(lp.contracts, 1, lp.tile_sums, out, out + 4 * static_cast<size_t>(R),
+                                                    static_cast<uint64_t>(R),
+                                                    reinterpret_cast<const uint64_t *>(dev + o_rep_owner), s)));
     return QMCCPW_OK;
 }
 

@@ -53,7 +53,7 @@ EXPORTS = (
     "qmccpw_batch_launch", "qmccpw_batch_results", "qmccpw_batch_device_results",
     "qmccpw_batch_launch_count", "qmccpw_batch_set_timing", "qmccpw_batch_timing",
     "qmccpw_batch_free", "qmccpw_sobol_points",
-    "qmccpw_point_values", "qmccpw_free", "qmccpw_last_error", "qmccpw_version",
+    "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_free", "qmccpw_last_error", "qmccpw_version",
 )
 
 
@@ -117,6 +117,8 @@ def library() -> ctypes.CDLL:
             L.qmccpw_sobol_points.argtypes = [vp, u32, i32, u64, u64, P(u32)]
             L.qmccpw_point_values.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), i32, i32, u32, u64, u64,
                                               P(ctypes.c_double)]
+            L.qmccpw_greeks_noalloc.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), u64, i32, i32, i32,
+                                                 ctypes.c_void_p, vp]
             L.qmccpw_free.argtypes = [vp]
             L.qmccpw_last_error.restype = ctypes.c_char_p
             L.qmccpw_version.restype = ctypes.c_char_p
@@ -255,6 +257,16 @@ def qmccpw_point_values(plan, type: int, d: int, K: float, T: float, S0: float, 
                                          ctypes.byref(qmccpw_market(S0, r, sigma)), construction, precision,
                                          replicate, k0, count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def qmccpw_greeks_noalloc(plan, type: int, d: int, K: float, T: float, S0: float, r: float, sigma: float,
+                          N: int, R: int, construction: int, precision: int, out_device_ptr: int,
+                          stream: Optional[int] = None) -> None:
+    """Allocation-free form: writes (R + 2) * 4 doubles to the caller's device buffer
+    at ``out_device_ptr`` (per-replicate estimates, mean, se) on ``stream``."""
+    _check(library().qmccpw_greeks_noalloc(plan, ctypes.byref(qmccpw_option(type, d, K, T)),
+                                           ctypes.byref(qmccpw_market(S0, r, sigma)), N, R, construction,
+                                           precision, ctypes.c_void_p(out_device_ptr), stream))
 
 
 def qmccpw_last_error() -> str:
