@@ -254,7 +254,8 @@ def run_ours(args):
         tmap = {"arith": W.ARITH, "binary": W.BINARY, "lookback": W.LOOKBACK, "geometric": W.GEOMETRIC}
         one = [W.Contract(tmap[typ], args.case_d, 100.0, 1.0, 100.0, 0.05, 0.2, args.case_N, args.case_R,
                           W.BB if cons == "bb" else W.PCA)]
-        prec = q.QMCCPW_FP64 if args.case_precision == "fp64" else q.QMCCPW_MIXED
+        prec = {"fp64": q.QMCCPW_FP64, "mixed": q.QMCCPW_MIXED, "tc-bf16": q.QMCCPW_MIXED_TC_BF16X3,
+                "tc-tf32": q.QMCCPW_MIXED_TC_TF32X3}[args.case_precision]
         batch = q.Batch(plan, one, prec)
         batch.set_timing(args.steps)
         for _ in range(args.warmup):
@@ -366,7 +367,7 @@ def main(argv=None):
     ap.add_argument("--case-d", type=int, default=64)
     ap.add_argument("--case-N", type=int, default=2 ** 16)
     ap.add_argument("--case-R", type=int, default=4)
-    ap.add_argument("--case-precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--case-precision", choices=["mixed", "fp64", "tc-bf16", "tc-tf32"], default="mixed")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":

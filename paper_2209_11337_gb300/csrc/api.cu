@@ -71,9 +71,9 @@ struct DevBuf {
 
 // Device arrays of one batch: contract descriptors, work list and results.
 struct BatchBuffers {
-    DevBuf contracts, item_base, rep_owner, tile_sums, per_rep, stats;
+    DevBuf contracts, item_base, rep_owner, tile_sums, per_rep, stats, counters;
     void release() {
-        for (DevBuf *d : {&contracts, &item_base, &rep_owner, &tile_sums, &per_rep, &stats}) d->release();
+        for (DevBuf *d : {&contracts, &item_base, &rep_owner, &tile_sums, &per_rep, &stats, &counters}) d->release();
     }
 };
 
@@ -82,7 +82,11 @@ struct DTables {
     int n = 0;
     int n_levels = 0;
     DevBuf steps, w64, w32, level_start, pca64, pca32;
+    DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32), built on first use
 };
+
+bool is_tc(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 || precision == QMCCPW_MIXED_TC_TF32X3; }
+int tc_kind(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1; }
 
 }  // namespace
 
@@ -94,6 +98,7 @@ struct qmccpw_plan_s {
     int d_max = 0, r_max = 0, ndims = 0, jstride = 0;
     size_t workspace_bytes = 0;
     int sm_count = 0;
+    DevBuf err;          // int: error status set by device code (bounded waits)
     DevBuf dir;          // unscrambled direction integers, ndims x 32
     DevBuf table;        // [r][b][j]
     DevBuf shift;        // [r][j]
@@ -152,6 +157,8 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
     if (precision >= QMCCPW_MIXED_TC_BF16X3 && construction != QMCCPW_PCA)
         return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core precisions apply to the PCA construction only");
+    if (precision >= QMCCPW_MIXED_TC_BF16X3 && o.d - 1 > pca_tc_npad())
+        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA supports d <= " + std::to_string(pca_tc_npad() + 1));
     return QMCCPW_OK;
 }
 
@@ -228,7 +235,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
     c.d = in.option.d;
     c.n = in.option.d - 1;
     c.construction = in.construction;
-    c.tile_log2 = choose_tile_log2(precision, c.n);
+    c.tile_log2 = is_tc(precision) ? 7 : choose_tile_log2(precision, c.n);
     const int P = 1 << c.tile_log2;
     int chunk_log2 = c.tile_log2;
     while (chunk_log2 > 0 && static_cast<long>(c.n) * (P >> chunk_log2) < 2L * kThreads) --chunk_log2;
@@ -247,25 +254,23 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
     c.level_start = t->level_start.as<int32_t>();
     c.pca64 = t->pca64.as<double>();
     c.pcaT32 = t->pca32.as<float>();
+    if (is_tc(precision)) {
+        DTables *mt = const_cast<DTables *>(t);
+        DevBuf &op = mt->tc[tc_kind(precision)];
+        if (!op.ptr) {
+            std::vector<unsigned char> bytes;
+            pca_tc_operand(tc_kind(precision), c.n, pca_factor(c.n, 1.0), bytes);
+            QMC_TRY(op.alloc(bytes.size()));
+            QMC_CUDA(cudaMemcpy(op.ptr, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
+        }
+        c.tc_operand = op.ptr;
+    }
     c.S0 = in.market.S0;
     c.K = in.option.K;
     c.T = in.option.T;
     c.r = in.market.r;
     c.sigma = in.market.sigma;
-    c.dt = in.option.T / in.option.d;
-    c.a = c.sigma * std::sqrt(c.dt);
-    c.omega = c.r - 0.5 * c.sigma * c.sigma;
-    c.psi0 = std::log(c.K / c.S0) - c.omega * c.dt;
-    c.disc = std::exp(-c.r * c.T);
-    c.disc1 = std::exp(c.r * (c.dt - c.T));
-    c.sqrt_t1 = std::sqrt(c.dt);
-    c.inv_a = 1.0 / c.a;
-    c.disc1_S0 = c.disc1 * c.S0;
-    c.disc_K = c.disc * c.K;
-    c.k_bin_delta = c.disc / (c.S0 * c.a);
-    c.k_bin_gamma = c.disc / (c.S0 * c.S0 * c.a);
-    c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
-    c.inv_sigma = 1.0 / c.sigma;
+    contract_constants(c);
     *out = c;
     return QMCCPW_OK;
 }
@@ -276,18 +281,23 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     for (int i = 0; i < count; ++i)
         QMC_TRY(validate_contract(p, cs[i].option, cs[i].market, cs[i].N, cs[i].R, cs[i].construction, precision,
                                   diagnostic));
-    if (precision >= QMCCPW_MIXED_TC_BF16X3)
-        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA precisions are not built in this library version");
     QMC_CUDA(cudaSetDevice(p->device));
     b->plan = p;
     b->count = count;
     b->precision = precision;
     b->host.resize(count);
     b->R.resize(count);
+    // launch order: bridge contracts, then PCA; within each, larger d first
+    // (their items are the costliest, and the dynamic schedule hands items
+    // out in order, so the tail of the launch holds the cheap ones)
     b->order.clear();
-    for (int cons : {QMCCPW_BB, QMCCPW_PCA})
+    for (int cons : {QMCCPW_BB, QMCCPW_PCA}) {
+        const size_t first = b->order.size();
         for (int i = 0; i < count; ++i)
             if (cs[i].construction == cons) b->order.push_back(i);
+        std::stable_sort(b->order.begin() + first, b->order.end(),
+                         [&](int x, int y) { return cs[x].option.d > cs[y].option.d; });
+    }
     uint64_t items = 0, reps = 0;
     std::vector<uint64_t> item_base(count), rep_owner;
     for (int k = 0; k < count; ++k) {
@@ -301,7 +311,8 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         reps += c.R;
         b->R[k] = c.R;
         size_t &sm = b->smem[in.construction == QMCCPW_BB ? 0 : 1];
-        sm = std::max(sm, fused_smem_bytes(precision, c.n, c.tile_log2));
+        sm = std::max(sm, is_tc(precision) ? pca_tc_smem_bytes(tc_kind(precision))
+                                           : fused_smem_bytes(precision, c.n, c.tile_log2));
     }
     b->items = items;
     b->total_reps = reps;
@@ -316,6 +327,7 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     QMC_TRY(B.tile_sums.ensure(scratch));
     QMC_TRY(B.per_rep.ensure(sizeof(double) * 4 * reps));
     QMC_TRY(B.stats.ensure(sizeof(double) * 8 * count));
+    QMC_TRY(B.counters.ensure(2 * sizeof(unsigned long long)));
     QMC_CUDA(cudaMemcpyAsync(B.contracts.ptr, b->host.data(), sizeof(ContractDev) * count, cudaMemcpyHostToDevice,
                              p->stream));
     QMC_CUDA(cudaMemcpyAsync(B.item_base.ptr, item_base.data(), sizeof(uint64_t) * count, cudaMemcpyHostToDevice,
@@ -327,7 +339,10 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     for (int k = 0; k < 2; ++k) {
         if (range[k] == 0) continue;
         int per_sm = 0;
-        QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
+        if (is_tc(precision))
+            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(precision), b->smem[k], &per_sm)));
+        else
+            QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
         if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
         const uint64_t slots = static_cast<uint64_t>(per_sm) * p->sm_count;
         b->grid[k] = static_cast<int>(std::min<uint64_t>(range[k], slots));
@@ -349,6 +364,7 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
     lp.tile_sums = B.tile_sums.as<double>();
     lp.point_out = b->point_out;
     lp.point_k0 = b->point_k0;
+    lp.error_flag = p->err.as<int>();
     const size_t cap = b->ev_start.size();
     const size_t slot = cap ? static_cast<size_t>(b->timed) % cap : 0;
     if (cap) QMC_CUDA(cudaEventRecord(b->ev_start[slot], s));
@@ -357,8 +373,13 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
         if (bounds[k + 1] == bounds[k]) continue;
         lp.item_begin = bounds[k];
         lp.item_end = bounds[k + 1];
-        QMC_CUDA(static_cast<cudaError_t>(
-            launch_fused(lp, b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
+        lp.work_counter = B.counters.as<unsigned long long>() + k;
+        QMC_CUDA(cudaMemsetAsync(lp.work_counter, 0, sizeof(unsigned long long), s));
+        if (is_tc(b->precision))
+            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(b->precision), b->smem[k], b->grid[k], s)));
+        else
+            QMC_CUDA(static_cast<cudaError_t>(
+                launch_fused(lp, b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
     }
     if (cap) {
         QMC_CUDA(cudaEventRecord(b->ev_stop[slot], s));
@@ -378,7 +399,14 @@ int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
     std::vector<double> per(4 * b->total_reps);
     QMC_CUDA(cudaMemcpyAsync(stats.data(), B.stats.ptr, sizeof(double) * stats.size(), cudaMemcpyDeviceToHost, s));
     QMC_CUDA(cudaMemcpyAsync(per.data(), B.per_rep.ptr, sizeof(double) * per.size(), cudaMemcpyDeviceToHost, s));
+    int flag = 0;
+    QMC_CUDA(cudaMemcpyAsync(&flag, b->plan->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     QMC_CUDA(cudaStreamSynchronize(s));
+    if (flag != 0) {
+        QMC_CUDA(cudaMemsetAsync(b->plan->err.ptr, 0, sizeof(int), s));
+        QMC_CUDA(cudaStreamSynchronize(s));
+        return fail(flag, "a kernel's bounded wait expired; results of this call are invalid");
+    }
     uint64_t rep = 0;
     for (int k = 0; k < b->count; ++k) {
         qmccpw_result &o = out[b->order[k]];
@@ -455,6 +483,10 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
         QMC_CUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
         p->own_stream = true;
     }
+    for (int kind : {0, 1})
+        QMC_CUDA(static_cast<cudaError_t>(pca_tc_prepare(kind, pca_tc_smem_bytes(kind))));
+    QMC_TRY(p->err.alloc(sizeof(int)));
+    QMC_CUDA(cudaMemset(p->err.ptr, 0, sizeof(int)));
     std::vector<uint32_t> v = direction_integers(p->ndims);
     QMC_TRY(p->dir.alloc(sizeof(uint32_t) * v.size()));
     QMC_TRY(p->table.alloc(sizeof(uint32_t) * 32u * p->jstride * static_cast<size_t>(p->r_max)));
@@ -705,6 +737,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     const size_t o_pca64 = take(pca && precision == QMCCPW_FP64 ? sizeof(double) * A.size() : 0);
     const size_t o_pca32 = take(pca && precision != QMCCPW_FP64 ? sizeof(float) * n * n_pad : 0);
     const size_t staged = off;
+    const size_t o_counter = take(sizeof(unsigned long long));
     const size_t o_tiles = take(sizeof(double) * 4 * items);
     if (off > kNoAllocScratchBytes)
         return fail(QMCCPW_ERR_OOM, "qmccpw_greeks_noalloc needs " + std::to_string(off) +
@@ -725,20 +758,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.T = option->T;
     c.r = market->r;
     c.sigma = market->sigma;
-    c.dt = dt;
-    c.a = c.sigma * std::sqrt(dt);
-    c.omega = c.r - 0.5 * c.sigma * c.sigma;
-    c.psi0 = std::log(c.K / c.S0) - c.omega * dt;
-    c.disc = std::exp(-c.r * c.T);
-    c.disc1 = std::exp(c.r * (dt - c.T));
-    c.sqrt_t1 = std::sqrt(dt);
-    c.inv_a = 1.0 / c.a;
-    c.disc1_S0 = c.disc1 * c.S0;
-    c.disc_K = c.disc * c.K;
-    c.k_bin_delta = c.disc / (c.S0 * c.a);
-    c.k_bin_gamma = c.disc / (c.S0 * c.S0 * c.a);
-    c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
-    c.inv_sigma = 1.0 / c.sigma;
+    contract_constants(c);
     std::memcpy(host.data() + o_contract, &c, sizeof(c));
     std::memset(host.data() + o_item_base, 0, sizeof(uint64_t));
     std::memset(host.data() + o_rep_owner, 0, sizeof(uint64_t) * R);  // every replicate belongs to contract 0
@@ -779,6 +799,8 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     lp.sobol_shift = plan->shift.as<uint32_t>();
     lp.jstride = plan->jstride;
     lp.tile_sums = reinterpret_cast<double *>(dev + o_tiles);
+    lp.work_counter = reinterpret_cast<unsigned long long *>(dev + o_counter);
+    QMC_CUDA(cudaMemsetAsync(lp.work_counter, 0, sizeof(unsigned long long), s));
     QMC_CUDA(static_cast<cudaError_t>(launch_fused(lp, precision, construction, smem, grid, s)));
     QMC_CUDA(static_cast<cudaError_t>(launch_reduce(lp.contracts, 1, lp.tile_sums, out, out + 4 * static_cast<size_t>(R),
                                                     static_cast<uint64_t>(R),

@@ -25,7 +25,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
+#include "qmccpw_device.cuh"
 #include "qmccpw_internal.h"
 
 namespace qmccpw {
@@ -33,179 +35,8 @@ namespace qmccpw {
 namespace {
 
 // ---------------------------------------------------------------------------
-// precision traits
-// ---------------------------------------------------------------------------
-template <typename T> struct Arith;
-
-template <> struct Arith<double> {
-    // z = Phi^{-1}(u), u = (y + 1/2) 2^-32, evaluated on the lower half
-    // q = min(u, 1-u) (exact in double) and reflected.
-    __device__ static double inv_normal(uint32_t y) {
-        const bool upper = y >= 0x80000000u;
-        const uint32_t lo = upper ? ~y : y;
-        const double q = fma(static_cast<double>(lo), 0x1p-32, 0x1p-33);
-        const double z = normcdfinv(q);
-        return upper ? -z : z;
-    }
-    __device__ static double ex(double x) { return exp(x); }
-};
-
-template <> struct Arith<float> {
-    __device__ static float inv_normal(uint32_t y) {
-        const bool upper = y >= 0x80000000u;
-        const uint32_t lo = upper ? ~y : y;
-        const float q = fmaf(__uint2float_rn(lo), 0x1p-32f, 0x1p-33f);
-        const float z = normcdfinvf(q);
-        return upper ? -z : z;
-    }
-    __device__ static float ex(float x) { return expf(x); }
-};
-
-// ---------------------------------------------------------------------------
-// per-thread path accumulator (Sec. 4.5: S~_A or S~_max and the vega sum,
-// formed on the fly)
-// ---------------------------------------------------------------------------
-template <typename T> struct PathAcc {
-    T x;       // sum of S~/S0 (arith, binary), max S~/S0 (lookback), sum of log(S~/S0) (geometric)
-    T dsum;    // sum of S~/S0 (W - sigma s) (arith, binary), at the max (lookback), sum of (W - sigma s) (geometric)
-    int32_t m; // lookback: date index of the max (lowest on ties)
-
-    __device__ void init(int type, bool has_first_date) {
-        // date t_1 (s = 0, W~ = 0): S~/S0 = 1, log = 0, no vega term
-        if (type == QMCCPW_LOOKBACK_FIXED_CALL) {
-            x = has_first_date ? T(1) : T(-1);
-            dsum = T(0);
-            m = has_first_date ? 0 : 0x7fffffff;
-        } else {
-            x = (type == QMCCPW_GEOMETRIC_ASIAN_CALL || !has_first_date) ? T(0) : T(1);
-            dsum = T(0);
-            m = 0;
-        }
-    }
-
-    template <int TYPE>
-    __device__ __forceinline__ void add(int32_t node, T W, T omega, T sigma, T dt) {
-        const T s = static_cast<T>(node) * dt;
-        const T lx = omega * s + sigma * W;
-        const T wv = W - sigma * s;
-        if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-            x += lx;
-            dsum += wv;
-        } else {
-            const T e = Arith<T>::ex(lx);
-            if constexpr (TYPE == QMCCPW_LOOKBACK_FIXED_CALL) {
-                if (e > x || (e == x && node < m)) {
-                    x = e;
-                    dsum = e * wv;
-                    m = node;
-                }
-            } else {
-                x += e;
-                dsum += e * wv;
-            }
-        }
-    }
-
-    __device__ void merge(int type, const PathAcc &o) {
-        if (type == QMCCPW_LOOKBACK_FIXED_CALL) {
-            if (o.x > x || (o.x == x && o.m < m)) {
-                x = o.x;
-                dsum = o.dsum;
-                m = o.m;
-            }
-        } else {
-            x += o.x;
-            dsum += o.dsum;
-        }
-    }
-};
-
-// ---------------------------------------------------------------------------
-// conditional step: values of one point from X^ = X/S0 and D^ = D/S0
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double sf64(double x) { return 0.5 * erfc(x * 0.70710678118654752440); }
-__device__ __forceinline__ double pdf64(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
-
-__device__ void values_fp64(const ContractDev &c, double xhat, double dhat, double v[4]) {
-    const double psi = (c.psi0 - log(xhat)) * c.inv_a;
-    const double pdf = pdf64(psi);
-    if (c.type == QMCCPW_BINARY_ASIAN) {
-        v[0] = c.disc * sf64(psi);
-        v[1] = c.disc * pdf / (c.S0 * c.a);
-        v[2] = c.disc * pdf * (dhat / (c.a * xhat) + psi / c.sigma - c.sqrt_t1);
-        v[3] = c.disc * pdf / (c.S0 * c.S0 * c.a) * (psi / c.a - 1.0);
-    } else {
-        const double sfs = sf64(psi - c.a);
-        v[0] = c.disc1 * c.S0 * xhat * sfs - c.disc * c.K * sf64(psi);
-        v[1] = c.disc1 * xhat * sfs;
-        v[2] = c.disc1 * sfs * c.S0 * dhat + c.disc * c.K * pdf * c.sqrt_t1;
-        v[3] = c.disc * c.K * pdf / (c.S0 * c.S0 * c.a);
-    }
-}
-
-// Mixed precision: the switch point psi in double; the normal tail and
-// density in float; the combination with the contract constants in double.
-// The price of a call is the difference of two terms of size ~K: float
-// constants there would bias every point by ~2^-24 K, which no averaging
-// removes.  Beyond |psi| = 12 the float density and tail underflow, so
-// those (rare) points take the double formulas.
-__device__ void values_mixed(const ContractDev &c, float xhat, float dhat, double v[4]) {
-    const double psi = (c.psi0 - log(static_cast<double>(xhat))) * c.inv_a;
-    if (fabs(psi) > 12.0) {
-        values_fp64(c, static_cast<double>(xhat), static_cast<double>(dhat), v);
-        return;
-    }
-    const float p = static_cast<float>(psi);
-    const float pdf = 0.398942280f * expf(-0.5f * p * p);
-    if (c.type == QMCCPW_BINARY_ASIAN) {
-        const double sf = 0.5f * erfcf(p * 0.707106781f);
-        const double pd = pdf;
-        v[0] = c.disc * sf;
-        v[1] = c.k_bin_delta * pd;
-        v[2] = c.disc * pd * (static_cast<double>(dhat / xhat) * c.inv_a + psi * c.inv_sigma - c.sqrt_t1);
-        v[3] = c.k_bin_gamma * pd * (psi * c.inv_a - 1.0);
-    } else {
-        const float a = static_cast<float>(c.a);
-        const double sfs = 0.5f * erfcf((p - a) * 0.707106781f);
-        const double sf = 0.5f * erfcf(p * 0.707106781f);
-        const double xh = xhat;
-        v[0] = c.disc1_S0 * xh * sfs - c.disc_K * sf;
-        v[1] = c.disc1 * xh * sfs;
-        v[2] = c.disc1_S0 * sfs * static_cast<double>(dhat) + c.disc_K * c.sqrt_t1 * static_cast<double>(pdf);
-        v[3] = c.k_call_gamma * static_cast<double>(pdf);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Sobol' integers of one dimension over a run of consecutive points
-// ---------------------------------------------------------------------------
-// First point k0: XOR of the direction integers of the set bits of g(k0),
-// starting from the digital shift.
-__device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab, int jstride, int j,
-                                                uint32_t shift, uint32_t k0) {
-    uint32_t g = k0 ^ (k0 >> 1);
-    uint32_t y = shift;
-    while (g) {
-        const int b = __ffs(g) - 1;
-        y ^= __ldg(tab + b * jstride + j);
-        g &= g - 1u;
-    }
-    return y;
-}
-
-// ---------------------------------------------------------------------------
 // the fused kernel
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_contract(const uint64_t *__restrict__ base, int count, uint64_t item) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(base + mid) <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Bridge (Sec. 4.4): levels breadth first; within a level the nodes of a
 // point are spread over its G threads; W~ overwrites z in the point's row.
 template <typename T, int TYPE>
@@ -235,9 +66,67 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
                 Wm = fmaf(h.x, Wl, fmaf(h.z, Wr, fmaf(g.x, z, lo)));
             }
             row[st.x] = Wm;
-            acc.template add<TYPE>(st.x, Wm, omega, sigma, dt);
+            acc.template add<TYPE>(st.x, Wm, omega, sigma, static_cast<T>(__int_as_float(st.w)) * dt);
         }
         if (G > 1) __syncthreads();
+    }
+}
+
+// Bridge with a compile-time schedule (n = N dates after t_1) and W~ in
+// registers: the breadth-first order, the endpoints and the weights are
+// constants, so each node is one shared-memory load of z and four flops.
+// Used by the float path when one thread owns one point (P = 256).
+struct BridgeSchedule {
+    static constexpr int kMax = 128;
+    int m[kMax], l[kMax], r[kMax];
+    double wr[kMax], c[kMax];  // W_m = W_l + wr (W_r - W_l) + c sqrt(dt) z
+    int count;
+};
+
+__host__ __device__ constexpr double cx_sqrt(double v) {  // Newton's method, for compile-time constants only
+    if (v <= 0.0) return 0.0;
+    double x = v > 1.0 ? v : 1.0;
+    for (int i = 0; i < 64; ++i) x = 0.5 * (x + v / x);
+    return x;
+}
+
+__host__ __device__ constexpr BridgeSchedule make_schedule(int n) {
+    BridgeSchedule s{};
+    int ql[2 * BridgeSchedule::kMax + 2] = {}, qr[2 * BridgeSchedule::kMax + 2] = {};
+    int head = 0, tail = 0, k = 0;
+    s.m[k] = n; s.l[k] = 0; s.r[k] = 0; s.wr[k] = 0.0; s.c[k] = cx_sqrt(static_cast<double>(n)); ++k;
+    ql[tail] = 0; qr[tail] = n; ++tail;
+    while (head < tail) {
+        const int a = ql[head], b = qr[head];
+        ++head;
+        if (b - a < 2) continue;
+        const int mm = (a + b) / 2;
+        s.m[k] = mm; s.l[k] = a; s.r[k] = b;
+        s.wr[k] = static_cast<double>(mm - a) / (b - a);
+        s.c[k] = cx_sqrt(static_cast<double>(mm - a) * (b - mm) / (b - a));
+        ++k;
+        ql[tail] = a; qr[tail] = mm; ++tail;
+        ql[tail] = mm; qr[tail] = b; ++tail;
+    }
+    s.count = k;
+    return s;
+}
+
+template <int N, int TYPE>
+__device__ __forceinline__ void bridge_registers(const ContractDev &c, const float *row, PathAcc<float> &acc) {
+    constexpr BridgeSchedule S = make_schedule(N);
+    static_assert(S.count == N, "bridge schedule size");
+    const float sdt = static_cast<float>(c.sqrt_t1);
+    const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
+    float W[N + 1];
+    W[0] = 0.0f;
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+        const float z = row[S.m[b]] * sdt;
+        const float Wl = W[S.l[b]], Wr = W[S.r[b]];
+        const float Wm = fmaf(static_cast<float>(S.c[b]), z, fmaf(static_cast<float>(S.wr[b]), Wr - Wl, Wl));
+        W[S.m[b]] = Wm;
+        acc.template add<TYPE>(S.m[b], Wm, omega, sigma, static_cast<float>(S.m[b]) * dt);
     }
 }
 
@@ -251,7 +140,9 @@ __device__ void pca_rows_phase(const ContractDev &c, const T *zw, int stride, Pa
     const T *row = zw + pt * stride;
     const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
     const int n = c.n;
-    for (int i = 1 + grp; i <= n; i += c.groups) {
+    T s_i = static_cast<T>(1 + grp) * dt;
+    const T ds = static_cast<T>(c.groups) * dt;
+    for (int i = 1 + grp; i <= n; i += c.groups, s_i += ds) {
         T Wi = T(0);
         if constexpr (sizeof(T) == 8) {
             const double *Ai = c.pca64 + static_cast<size_t>(i - 1) * n;
@@ -260,7 +151,7 @@ __device__ void pca_rows_phase(const ContractDev &c, const T *zw, int stride, Pa
             const int n_pad = (n + 15) & ~15;
             for (int k = 0; k < n; ++k) Wi = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k) * n_pad + (i - 1)), row[k + 1], Wi);
         }
-        acc.template add<TYPE>(i, Wi, omega, sigma, dt);
+        acc.template add<TYPE>(i, Wi, omega, sigma, s_i);
     }
 }
 
@@ -305,44 +196,16 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
                 for (int r = 0; r < 16; ++r) w[j][r] = fmaf(av[r], z, w[j][r]);
             }
         }
+        const float s0 = static_cast<float>(rb * 16 + 1) * dt;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int i = rb * 16 + r + 1;
             if (i <= n) {
+                const float s_i = fmaf(static_cast<float>(r), dt, s0);
 #pragma unroll
-                for (int j = 0; j < PB; ++j) acc[j].template add<TYPE>(i, w[j][r], omega, sigma, dt);
+                for (int j = 0; j < PB; ++j) acc[j].template add<TYPE>(i, w[j][r], omega, sigma, s_i);
             }
         }
-    }
-}
-
-// Partial accumulators of a point live in several threads; they are staged
-// in shared memory as slot-major arrays and merged by one thread per point in
-// slot order (a fixed order, so the result does not depend on scheduling).
-template <typename T>
-__device__ __forceinline__ void stage_partial(void *base, int P, int slot, int point, const PathAcc<T> &a) {
-    T *rx = reinterpret_cast<T *>(base);
-    T *rd = rx + kThreads * 4;
-    int32_t *rm = reinterpret_cast<int32_t *>(rd + kThreads * 4);
-    rx[slot * P + point] = a.x;
-    rd[slot * P + point] = a.dsum;
-    rm[slot * P + point] = a.m;
-}
-
-template <typename T>
-__device__ __forceinline__ void merge_partials(const void *base, int P, int slots, int point, int type, PathAcc<T> &a) {
-    const T *rx = reinterpret_cast<const T *>(base);
-    const T *rd = rx + kThreads * 4;
-    const int32_t *rm = reinterpret_cast<const int32_t *>(rd + kThreads * 4);
-    a.x = rx[point];
-    a.dsum = rd[point];
-    a.m = rm[point];
-    for (int s = 1; s < slots; ++s) {
-        PathAcc<T> o;
-        o.x = rx[s * P + point];
-        o.dsum = rd[s * P + point];
-        o.m = rm[s * P + point];
-        a.merge(type, o);
     }
 }
 
@@ -353,6 +216,14 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
     const int P = 1 << c.tile_log2;
     if constexpr (CONS == QMCCPW_BB) {
         acc.init(TYPE, threadIdx.x < P);
+        if constexpr (sizeof(T) == 4) {
+            if (c.groups == 1 && (c.n == 63 || c.n == 15)) {
+                const float *row = zw + threadIdx.x * stride;
+                if (c.n == 63) bridge_registers<63, TYPE>(c, row, acc);
+                else bridge_registers<15, TYPE>(c, row, acc);
+                return;
+            }
+        }
         bridge_phase<T, TYPE>(c, zw, stride, acc);
         if (c.groups == 1) return;
         __syncthreads();
@@ -405,9 +276,15 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
 template <typename T, int CONS>
 __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ LaunchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double warp_part[kThreads / 32][4];
 
-    for (uint64_t item = p.item_begin + blockIdx.x; item < p.item_end; item += gridDim.x) {
+    __shared__ uint64_t next_item;
+    while (true) {
+        // dynamic schedule: CTAs take the next item as they finish one (the
+        // result of an item never depends on which CTA ran it)
+        if (threadIdx.x == 0) next_item = p.item_begin + atomicAdd(p.work_counter, 1ull);
+        __syncthreads();
+        const uint64_t item = next_item;
+        if (item >= p.item_end) break;
         const int ci = find_contract(p.item_base, p.count, item);
         const ContractDev &c = p.contracts[ci];
         const int P = 1 << c.tile_log2;
@@ -459,44 +336,24 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
         const int pt = threadIdx.x;
 
         // ---- phase 3: conditional values of the point, tile sum
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        using V = typename std::conditional<sizeof(T) == 8, double, ff>::type;
+        V v[4];
+        for (int g = 0; g < 4; ++g) v[g] = V{};
         const uint64_t local_point = tile * P + pt;
         if (pt < P && local_point < c.N) {
             T xhat, dhat;
-            if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
-                xhat = acc.x;
-                dhat = acc.dsum;
-            } else if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-                const T inv_d = T(1) / static_cast<T>(c.d);
-                xhat = Arith<T>::ex(acc.x * inv_d);
-                dhat = xhat * acc.dsum * inv_d;
-            } else {
-                const T inv_d = T(1) / static_cast<T>(c.d);
-                xhat = acc.x * inv_d;
-                dhat = acc.dsum * inv_d;
-            }
+            finish_functional(c, acc, xhat, dhat);
             if constexpr (sizeof(T) == 8) values_fp64(c, xhat, dhat, v);
             else values_mixed(c, xhat, dhat, v);
             if (p.point_out) {
                 double *o = p.point_out + local_point * 4;
-                o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
+                for (int g = 0; g < 4; ++g) {
+                    if constexpr (sizeof(T) == 8) o[g] = v[g];
+                    else o[g] = ff_to_double(v[g]);
+                }
             }
         }
-        // block sum: warp shuffle tree, then the 8 warp partials in order
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            double s = v[g];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5][g] = s;
-        }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double s = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) s += warp_part[w][threadIdx.x];
-            p.tile_sums[item * 4 + threadIdx.x] = s;
-        }
-        __syncthreads();  // smem and warp_part are reused by the next item
+        tile_sum(p, item, v, smem);
     }
 }
 
@@ -624,7 +481,7 @@ size_t fused_smem_bytes(int precision, int n, int tile_log2) {
     const int stride = (n + 1) | 1;
     const size_t zw = static_cast<size_t>(1u << tile_log2) * stride * elem;
     // staging of partial accumulators: up to 4 * kThreads (slot, point) entries of (x, dsum, m)
-    const size_t red = 4 * kThreads * (2 * elem + sizeof(int32_t));
+    const size_t red = 4 * kThreads * (2 * elem + sizeof(int32_t));  // >= 4 * kThreads doubles for the tile sum
     return ((zw > red ? zw : red) + 15) & ~size_t(15);
 }
 

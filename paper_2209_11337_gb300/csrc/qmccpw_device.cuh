@@ -1,0 +1,395 @@
+// Device code shared by the CUDA-core kernel (kernels.cu) and the
+// tensor-core PCA kernel (pca_tc.cu): precision traits, the inverse normal,
+// the path accumulator, the conditional step and the tile reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "invnorm_coeffs.h"
+#include "qmccpw_internal.h"
+
+namespace qmccpw {
+namespace {
+
+// ---------------------------------------------------------------------------
+// precision traits
+// ---------------------------------------------------------------------------
+template <typename T> struct Arith;
+
+template <> struct Arith<double> {
+    // z = Phi^{-1}(u), u = (y + 1/2) 2^-32, evaluated on the lower half
+    // q = min(u, 1-u) (exact in double) and reflected.
+    __device__ static double inv_normal(uint32_t y) {
+        const bool upper = y >= 0x80000000u;
+        const uint32_t lo = upper ? ~y : y;
+        const double q = fma(static_cast<double>(lo), 0x1p-32, 0x1p-33);
+        const double z = normcdfinv(q);
+        return upper ? -z : z;
+    }
+    __device__ static double ex(double x) { return exp(x); }
+};
+
+// Float inverse normal in the two-branch form of Giles ("Approximating the
+// erfinv function", GPU Computing Gems Jade, 2011): with x = 1 - 2q and
+// w = -ln(4q(1-q)), Phi^{-1}(q) = -x p(w) for w < W0 and -x p_t(sqrt w)
+// beyond.  The polynomials are this project's own fits (gen_invnorm.py);
+// max relative error 1.8e-7 in float.  The central branch serves 99.9% of
+// draws, so a warp rarely takes the tail.
+__device__ __forceinline__ float horner_c(float t) {
+    constexpr float c[] = QMC_INVN_CENTRAL;
+    float acc = c[9];
+#pragma unroll
+    for (int i = 8; i >= 0; --i) acc = fmaf(acc, t, c[i]);
+    return acc;
+}
+
+__device__ __forceinline__ float horner_t(float t) {
+    constexpr float c[] = QMC_INVN_TAIL;
+    float acc = c[9];
+#pragma unroll
+    for (int i = 8; i >= 0; --i) acc = fmaf(acc, t, c[i]);
+    return acc;
+}
+
+// Exact float of an integer below 2^23 without a conversion instruction
+// (conversions share the slow FP64 pipe on this GPU): place it in the
+// mantissa of 2^23 and subtract 2^23.
+__device__ __forceinline__ float small_uint_to_float(uint32_t x) {
+    return __uint_as_float(0x4B000000u | x) - 8388608.0f;
+}
+
+template <> struct Arith<float> {
+    __device__ static float inv_normal(uint32_t y) {
+        const bool upper = y >= 0x80000000u;
+        const uint32_t lo = upper ? ~y : y;
+        // q = (lo + 1/2) 2^-32 <= 1/2 from lo = a 2^23 + b: one rounding
+        const float fa = small_uint_to_float(lo >> 23);
+        const float fb = small_uint_to_float(lo & 0x007FFFFFu);
+        const float q = fmaf(fa, 0x1p-9f, fmaf(fb, 0x1p-32f, 0x1p-33f));
+        const float x = fmaf(-2.0f, q, 1.0f);
+        const float q4 = 4.0f * q;
+        const float w = -0.693147181f * __log2f(fmaf(-q4, q, q4));       // -ln(4q(1-q))
+        float p;
+        if (w < QMC_INVN_W0) p = horner_c(w - QMC_INVN_SHIFT_C);
+        else p = horner_t(sqrtf(w) - QMC_INVN_SHIFT_T);
+        const float z = -x * p;  // <= 0 on the lower half
+        return upper ? -z : z;
+    }
+    __device__ static float ex(float x) { return expf(x); }
+};
+
+// ---------------------------------------------------------------------------
+// per-thread path accumulator (Sec. 4.5: S~_A or S~_max and the vega sum,
+// formed on the fly)
+// ---------------------------------------------------------------------------
+template <typename T> struct PathAcc {
+    T x;       // sum of S~/S0 (arith, binary), max S~/S0 (lookback), sum of log(S~/S0) (geometric)
+    T dsum;    // sum of S~/S0 (W - sigma s) (arith, binary), at the max (lookback), sum of (W - sigma s) (geometric)
+    int32_t m; // lookback: date index of the max (lowest on ties)
+
+    __device__ void init(int type, bool has_first_date) {
+        // date t_1 (s = 0, W~ = 0): S~/S0 = 1, log = 0, no vega term
+        if (type == QMCCPW_LOOKBACK_FIXED_CALL) {
+            x = has_first_date ? T(1) : T(-1);
+            dsum = T(0);
+            m = has_first_date ? 0 : 0x7fffffff;
+        } else {
+            x = (type == QMCCPW_GEOMETRIC_ASIAN_CALL || !has_first_date) ? T(0) : T(1);
+            dsum = T(0);
+            m = 0;
+        }
+    }
+
+    // node: date index after t_1 (ties of the lookback maximum); s = node * dt
+    template <int TYPE>
+    __device__ __forceinline__ void add(int32_t node, T W, T omega, T sigma, T s) {
+        const T lx = omega * s + sigma * W;
+        const T wv = W - sigma * s;
+        if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+            x += lx;
+            dsum += wv;
+        } else {
+            const T e = Arith<T>::ex(lx);
+            if constexpr (TYPE == QMCCPW_LOOKBACK_FIXED_CALL) {
+                if (e > x || (e == x && node < m)) {
+                    x = e;
+                    dsum = e * wv;
+                    m = node;
+                }
+            } else {
+                x += e;
+                dsum += e * wv;
+            }
+        }
+    }
+
+    __device__ void merge(int type, const PathAcc &o) {
+        if (type == QMCCPW_LOOKBACK_FIXED_CALL) {
+            if (o.x > x || (o.x == x && o.m < m)) {
+                x = o.x;
+                dsum = o.dsum;
+                m = o.m;
+            }
+        } else {
+            x += o.x;
+            dsum += o.dsum;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// conditional step: values of one point from X^ = X/S0 and D^ = D/S0
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sf64(double x) { return 0.5 * erfc(x * 0.70710678118654752440); }
+__device__ __forceinline__ double pdf64(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
+
+__device__ void values_fp64(const ContractDev &c, double xhat, double dhat, double v[4]) {
+    const double psi = (c.psi0 - log(xhat)) * c.inv_a;
+    const double pdf = pdf64(psi);
+    if (c.type == QMCCPW_BINARY_ASIAN) {
+        v[0] = c.disc * sf64(psi);
+        v[1] = c.disc * pdf / (c.S0 * c.a);
+        v[2] = c.disc * pdf * (dhat / (c.a * xhat) + psi / c.sigma - c.sqrt_t1);
+        v[3] = c.disc * pdf / (c.S0 * c.S0 * c.a) * (psi / c.a - 1.0);
+    } else {
+        const double sfs = sf64(psi - c.a);
+        v[0] = c.disc1 * c.S0 * xhat * sfs - c.disc * c.K * sf64(psi);
+        v[1] = c.disc1 * xhat * sfs;
+        v[2] = c.disc1 * sfs * c.S0 * dhat + c.disc * c.K * pdf * c.sqrt_t1;
+        v[3] = c.disc * c.K * pdf / (c.S0 * c.S0 * c.a);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi)/2): Dekker
+// products through FMA and Knuth's TwoSum, on the FP32 pipe, which on GB300
+// runs 64x the FP64 rate
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, float b) {
+    const float p = a.hi * b;
+    const float e = fmaf(a.hi, b, -p);
+    return ff_fast_two_sum(p, fmaf(a.lo, b, e));
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_of(const float (&c)[2]) { return {c[0], c[1]}; }
+__device__ __forceinline__ ff ff_of_double(double x) {
+    const float h = static_cast<float>(x);
+    return {h, static_cast<float>(x - static_cast<double>(h))};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+
+// ln x in double for a positive normal float x: x = 2^e m, m in [1/sqrt2,
+// sqrt2), ln m = 2 atanh(f), f = (m-1)/(m+1), |f| <= 0.172, series to f^15
+// (truncation < 2e-14); f from a float reciprocal and one Newton step.
+__device__ __forceinline__ double ln_of_float(float x) {
+    const uint32_t b = __float_as_uint(x);
+    int e = static_cast<int>((b >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421356f) {
+        m *= 0.5f;
+        e += 1;
+    }
+    const double md = m;
+    const double num = md - 1.0, den = md + 1.0;
+    double r = static_cast<double>(__frcp_rn(static_cast<float>(den)));
+    r = r * fma(-den, r, 2.0);
+    const double f = num * r;
+    const double f2 = f * f;
+    double s = 1.0 / 15.0;
+    s = fma(s, f2, 1.0 / 13.0);
+    s = fma(s, f2, 1.0 / 11.0);
+    s = fma(s, f2, 1.0 / 9.0);
+    s = fma(s, f2, 1.0 / 7.0);
+    s = fma(s, f2, 1.0 / 5.0);
+    s = fma(s, f2, 1.0 / 3.0);
+    s = fma(s, f2, 1.0);
+    const double lnm = 2.0 * f * s;
+    return fma(static_cast<double>(e), 0.69314718055994530942, lnm);
+}
+
+// Mixed precision: the switch point psi in double; the normal tail and
+// density in float; their combination with the contract constants in
+// float-float.  The price of a call is the difference of two terms of size
+// ~K: a float product there would bias every point by ~2^-24 K, which no
+// averaging removes.  Beyond |psi| = 12 the float density and tail
+// underflow, so those (rare) points take the double formulas.
+__device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[4]) {
+    const double psi = (c.psi0 - ln_of_float(xhat)) * c.inv_a;
+    if (fabs(psi) > 12.0) {
+        double d[4];
+        values_fp64(c, static_cast<double>(xhat), static_cast<double>(dhat), d);
+        for (int g = 0; g < 4; ++g) v[g] = ff_of_double(d[g]);
+        return;
+    }
+    const float p = static_cast<float>(psi);
+    const float pdf = 0.398942280f * expf(-0.5f * p * p);
+    if (c.type == QMCCPW_BINARY_ASIAN) {
+        const float sf = 0.5f * erfcf(p * 0.707106781f);
+        v[0] = ff_mul(ff_of(c.ff_disc), sf);
+        v[1] = ff_mul(ff_of(c.ff_k_bin_delta), pdf);
+        const double bracket = static_cast<double>(dhat / xhat) * c.inv_a + psi * c.inv_sigma - c.sqrt_t1;
+        v[2] = ff_mul(ff_of_double(c.disc * bracket), pdf);
+        v[3] = ff_mul(ff_of_double(c.k_bin_gamma * (psi * c.inv_a - 1.0)), pdf);
+    } else {
+        const float a = static_cast<float>(c.a);
+        const float sfs = 0.5f * erfcf((p - a) * 0.707106781f);
+        const float sf = 0.5f * erfcf(p * 0.707106781f);
+        const ff cx = ff_mul(ff_of(c.ff_disc1_S0), xhat);
+        v[0] = ff_add(ff_mul(cx, sfs), ff_neg(ff_mul(ff_of(c.ff_disc_K), sf)));
+        v[1] = ff_mul(ff_mul(ff_of(c.ff_disc1), xhat), sfs);
+        v[2] = ff_add(ff_mul(ff_mul(ff_of(c.ff_disc1_S0), sfs), dhat), ff_mul(ff_of(c.ff_disc_K_sqrt_t1), pdf));
+        v[3] = ff_mul(ff_of(c.ff_k_call_gamma), pdf);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sobol' integers of one dimension over a run of consecutive points
+// ---------------------------------------------------------------------------
+// First point k0: XOR of the direction integers of the set bits of g(k0),
+// starting from the digital shift.
+__device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab, int jstride, int j,
+                                                uint32_t shift, uint32_t k0) {
+    uint32_t g = k0 ^ (k0 >> 1);
+    uint32_t y = shift;
+    while (g) {
+        const int b = __ffs(g) - 1;
+        y ^= __ldg(tab + b * jstride + j);
+        g &= g - 1u;
+    }
+    return y;
+}
+
+__device__ __forceinline__ int find_contract(const uint64_t *__restrict__ base, int count, uint64_t item) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Partial accumulators of a point live in several threads; they are staged
+// in shared memory as slot-major arrays and merged by one thread per point in
+// slot order (a fixed order, so the result does not depend on scheduling).
+template <typename T>
+__device__ __forceinline__ void stage_partial(void *base, int P, int slot, int point, const PathAcc<T> &a) {
+    T *rx = reinterpret_cast<T *>(base);
+    T *rd = rx + kThreads * 4;
+    int32_t *rm = reinterpret_cast<int32_t *>(rd + kThreads * 4);
+    rx[slot * P + point] = a.x;
+    rd[slot * P + point] = a.dsum;
+    rm[slot * P + point] = a.m;
+}
+
+template <typename T>
+__device__ __forceinline__ void merge_partials(const void *base, int P, int slots, int point, int type, PathAcc<T> &a) {
+    const T *rx = reinterpret_cast<const T *>(base);
+    const T *rd = rx + kThreads * 4;
+    const int32_t *rm = reinterpret_cast<const int32_t *>(rd + kThreads * 4);
+    a.x = rx[point];
+    a.dsum = rd[point];
+    a.m = rm[point];
+    for (int s = 1; s < slots; ++s) {
+        PathAcc<T> o;
+        o.x = rx[s * P + point];
+        o.dsum = rd[s * P + point];
+        o.m = rm[s * P + point];
+        a.merge(type, o);
+    }
+}
+
+// X^ = X/S0 and D^ = D/S0 of a point from its merged accumulator.
+template <typename T>
+__device__ __forceinline__ void finish_functional(const ContractDev &c, const PathAcc<T> &acc, T &xhat, T &dhat) {
+    if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
+        xhat = acc.x;
+        dhat = acc.dsum;
+    } else if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+        const T inv_d = T(1) / static_cast<T>(c.d);
+        xhat = Arith<T>::ex(acc.x * inv_d);
+        dhat = xhat * acc.dsum * inv_d;
+    } else {
+        const T inv_d = T(1) / static_cast<T>(c.d);
+        xhat = acc.x * inv_d;
+        dhat = acc.dsum * inv_d;
+    }
+}
+
+// Tile sum of the 4 values of every thread (zero for threads without a
+// point): the kThreads x 4 values go through shared memory; warp g < 4 sums
+// Greek g (each lane kThreads/32 consecutive threads, then a shuffle tree),
+// a fixed order.  `smem` needs 4 * kThreads doubles; the caller's shared
+// memory must be free on entry.  Ends with a barrier.
+__device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, const double (&v)[4], unsigned char *smem) {
+    __syncthreads();
+    double *vals = reinterpret_cast<double *>(smem);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) vals[g * kThreads + threadIdx.x] = v[g];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        const double *col = vals + warp * kThreads + lane * (kThreads / 32);
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < kThreads / 32; ++i) s += col[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) p.tile_sums[item * 4 + warp] = s;
+    }
+    __syncthreads();
+}
+
+// The same tile sum for float-float values: TwoSum-based adds on the FP32
+// pipe, one conversion to double per Greek.  `smem` needs 8 * kThreads floats.
+__device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, const ff (&v)[4], unsigned char *smem) {
+    __syncthreads();
+    float *vals = reinterpret_cast<float *>(smem);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        vals[(2 * g) * kThreads + threadIdx.x] = v[g].hi;
+        vals[(2 * g + 1) * kThreads + threadIdx.x] = v[g].lo;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        const float *hi = vals + (2 * warp) * kThreads + lane * (kThreads / 32);
+        const float *lo = vals + (2 * warp + 1) * kThreads + lane * (kThreads / 32);
+        ff s = {0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < kThreads / 32; ++i) s = ff_add(s, ff{hi[i], lo[i]});
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const ff o = {__shfl_down_sync(0xffffffffu, s.hi, off), __shfl_down_sync(0xffffffffu, s.lo, off)};
+            s = ff_add(s, o);
+        }
+        if (lane == 0) p.tile_sums[item * 4 + warp] = ff_to_double(s);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+}  // namespace qmccpw

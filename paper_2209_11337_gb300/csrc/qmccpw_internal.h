@@ -30,7 +30,7 @@ std::vector<uint32_t> direction_integers(int ndims);
 // One step of the breadth-first Brownian bridge (Sec. 4.4) on s_i = i*dt:
 // W[m] = wl*W[l] + wr*W[r] + sd*z, z being Sobol' dimension `step`.
 struct BridgeStep {
-    int32_t m, l, r, pad;
+    int32_t m, l, r, m_float_bits;  // the last field holds the bits of float(m)
 };
 struct BridgePlan {
     int n = 0;
@@ -71,6 +71,7 @@ struct ContractDev {
     const int32_t *level_start;
     const double *pca64;                 // n x n row-major
     const float *pcaT32;                 // A^T as float, [k][i], i padded to a multiple of 16 with zeros
+    const void *tc_operand;              // tensor-core PCA: Ahat hi then lo, K-major core-matrix layout
     // market-derived constants
     double S0, K, T, r, sigma;
     double dt;                           // t_1 = T/d: spacing of the separated dates
@@ -87,7 +88,19 @@ struct ContractDev {
     double k_bin_gamma;                  // disc / (S0^2 a)
     double k_call_gamma;                 // disc K / (S0^2 a)
     double inv_sigma;
+    // the same constants as float hi + lo pairs (float-float arithmetic of the mixed path)
+    float ff_disc1_S0[2], ff_disc_K[2], ff_disc1[2], ff_disc_K_sqrt_t1[2], ff_k_call_gamma[2];
+    float ff_disc[2], ff_k_bin_delta[2], ff_k_bin_gamma[2];
 };
+
+// hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)
+inline void split_ff(double x, float out[2]) {
+    out[0] = static_cast<float>(x);
+    out[1] = static_cast<float>(x - static_cast<double>(out[0]));
+}
+
+// Fill the derived constants of a contract from S0, K, T, r, sigma, d (host).
+void contract_constants(ContractDev &c);
 
 // Per-launch parameters of the fused kernel.
 struct LaunchParams {
@@ -103,6 +116,8 @@ struct LaunchParams {
     double *tile_sums;                   // items x 4 partial sums (scratch)
     double *point_out;                   // optional per-point values, point x 4 (diagnostics)
     uint64_t point_k0;                   // index of the contract's point 0 (diagnostics; 0 otherwise)
+    int *error_flag;                     // set to a qmccpw_status by a kernel whose bounded wait expired
+    unsigned long long *work_counter;    // items handed out so far (zeroed before each launch)
 };
 
 // Launchers (kernels.cu).  Return the cudaError_t as int.
@@ -118,5 +133,13 @@ int launch_sobol_dump(const uint32_t *table, const uint32_t *shift, int jstride,
 size_t fused_smem_bytes(int precision, int n, int tile_log2);
 int fused_set_smem_limit(int precision, size_t bytes);
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
+
+// Tensor-core PCA (pca_tc.cu).  kind 0: 3-term bf16 split, 1: 3-term tf32 split.
+size_t pca_tc_smem_bytes(int kind);
+int pca_tc_npad();                                   // largest n supported (dimensions after padding)
+int pca_tc_prepare(int kind, size_t smem_bytes);     // raise the dynamic shared memory limit
+int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks);
+int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, void *stream);
+void pca_tc_operand(int kind, int n, const std::vector<double> &A_unit, std::vector<unsigned char> &out);
 
 }  // namespace qmccpw

@@ -127,8 +127,16 @@ BridgePlan bridge_plan(int n, double dt) {
         bp.level_start = {0};
         return bp;
     }
+    // the fourth field of a step carries the bits of float(m), the date index
+    // as a float, so kernels form s_m = m dt without a conversion
+    auto fbits = [](int m) {
+        const float f = static_cast<float>(m);
+        int32_t b;
+        std::memcpy(&b, &f, sizeof(b));
+        return b;
+    };
     // level 0: the terminal value from W(0) = 0
-    bp.steps.push_back({n, 0, 0, 0});
+    bp.steps.push_back({n, 0, 0, fbits(n)});
     bp.w.insert(bp.w.end(), {0.0, 0.0, std::sqrt(n * dt)});
     bp.level_start = {0, 1};
     std::vector<std::pair<int, int>> level = {{0, n}};
@@ -138,7 +146,7 @@ BridgePlan bridge_plan(int n, double dt) {
             if (r - l < 2) continue;
             const int m = (l + r) / 2;
             const double den = static_cast<double>(r - l);
-            bp.steps.push_back({m, l, r, 0});
+            bp.steps.push_back({m, l, r, fbits(m)});
             bp.w.insert(bp.w.end(), {(r - m) / den, (m - l) / den, std::sqrt(dt * (m - l) * (r - m) / den)});
             next.push_back({l, m});
             next.push_back({m, r});
@@ -165,6 +173,31 @@ std::vector<double> pca_factor(int n, double dt) {
             A[static_cast<size_t>(i - 1) * n + (k - 1)] = norm * std::sin(i * theta) * root_lambda;
     }
     return A;
+}
+
+void contract_constants(ContractDev &c) {
+    c.dt = c.T / c.d;
+    c.a = c.sigma * std::sqrt(c.dt);
+    c.omega = c.r - 0.5 * c.sigma * c.sigma;
+    c.psi0 = std::log(c.K / c.S0) - c.omega * c.dt;
+    c.disc = std::exp(-c.r * c.T);
+    c.disc1 = std::exp(c.r * (c.dt - c.T));
+    c.sqrt_t1 = std::sqrt(c.dt);
+    c.inv_a = 1.0 / c.a;
+    c.disc1_S0 = c.disc1 * c.S0;
+    c.disc_K = c.disc * c.K;
+    c.k_bin_delta = c.disc / (c.S0 * c.a);
+    c.k_bin_gamma = c.disc / (c.S0 * c.S0 * c.a);
+    c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
+    c.inv_sigma = 1.0 / c.sigma;
+    split_ff(c.disc1_S0, c.ff_disc1_S0);
+    split_ff(c.disc_K, c.ff_disc_K);
+    split_ff(c.disc1, c.ff_disc1);
+    split_ff(c.disc_K * c.sqrt_t1, c.ff_disc_K_sqrt_t1);
+    split_ff(c.k_call_gamma, c.ff_k_call_gamma);
+    split_ff(c.disc, c.ff_disc);
+    split_ff(c.k_bin_delta, c.ff_k_bin_delta);
+    split_ff(c.k_bin_gamma, c.ff_k_bin_gamma);
 }
 
 }  // namespace qmccpw
