@@ -145,6 +145,78 @@ def cpu_baseline(contracts, budget_s: float = 12.0) -> dict:
                       f"{dt:.1f} s wall)"}
 
 
+def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5, max_inflight=3):
+    """Poisson arrivals through the continuous-batching service.
+
+    Each request is a book-like contract with a target delta standard error in
+    {1e-3, 1e-4, 1e-5}: a pilot run (N = 2^12, R = 16) gives the delta SE at
+    2^12, N is the smallest power of two in [2^12, 2^22] whose SE, scaled as
+    1/N, meets the target, and the main run uses it.  Latency = completion of
+    the main run - arrival.  Requests arriving in the first `warmup_s` seconds
+    are run but not counted."""
+    import queue
+
+    reqs = W.arrivals(rate_hz=rate_hz, duration_s=warmup_s + duration_s, seed=seed, R=16)
+    q.qmccpw_server_start(plan, precision=precision, max_inflight=max_inflight, max_batch_contracts=4096,
+                          max_batch_bytes=256 << 20)
+    pilots = queue.Queue()
+    mains = queue.Queue()
+    lat, main_elems, Ns = [], [0], []
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, rq in enumerate(reqs):
+            delay = rq.arrival_s - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            pilots.put((i, rq, q.qmccpw_submit(plan, rq.contract)))
+        pilots.put(None)
+
+    def sizer():
+        while True:
+            item = pilots.get()
+            if item is None:
+                mains.put(None)
+                return
+            i, rq, t = item
+            _, se, _ = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
+            ratio = max(se[1], 1e-300) / rq.target_se
+            N = 2 ** 12
+            while N < 2 ** 22 and ratio * (2 ** 12) / N > 1.0:
+                N *= 2
+            c = W.with_size(rq.contract, N=N)
+            mains.put((i, rq, c, q.qmccpw_submit(plan, c)))
+
+    def finisher():
+        while True:
+            item = mains.get()
+            if item is None:
+                return
+            i, rq, c, t = item
+            q.qmccpw_wait(plan, t, c.R, 600000)
+            done = time.perf_counter() - t0
+            if rq.arrival_s >= warmup_s:
+                lat.append(done - rq.arrival_s)
+                main_elems[0] += c.N * c.R * c.d
+                Ns.append(c.N)
+
+    threads = [threading.Thread(target=f) for f in (submitter, sizer, finisher)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    wall = time.perf_counter() - t0
+    stats = q.qmccpw_server_get_stats(plan)
+    q.qmccpw_server_stop(plan)
+    lat_ms = sorted(1e3 * x for x in lat)
+    pct = lambda p: lat_ms[min(len(lat_ms) - 1, int(p * len(lat_ms)))] if lat_ms else None
+    return {"rate_hz": rate_hz, "window_s": duration_s, "requests": len(lat_ms), "p50_ms": pct(0.50),
+            "p99_ms": pct(0.99), "max_ms": lat_ms[-1] if lat_ms else None,
+            "throughput_point_dates_per_s": stats["point_dates"] / wall, "wall_s": wall,
+            "batches": stats["batches"], "mean_N": statistics.mean(Ns) if Ns else None,
+            "precision": "fp64" if precision == 0 else "mixed"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -343,6 +415,10 @@ def run_ours(args):
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
     }
+    if args.serving_s > 0:
+        splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED + rank)
+        line["serving"] = {"mixed": serve(q, splan, q.QMCCPW_MIXED, args.serving_rate, args.serving_s)}
+        q.qmccpw_free(splan)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(contracts)
     elif rank == 0 and world == 1:
@@ -362,6 +438,8 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of Poisson arrivals (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=2000.0)
     ap.add_argument("--errors-out", default=None, help="write the per-contract MIXED vs FP64 table (JSON)")
     ap.add_argument("--case", default=None, help="time one contract only, e.g. arith-bb or lookback-pca")
     ap.add_argument("--case-d", type=int, default=64)

@@ -229,6 +229,45 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
                           uint64_t N, int32_t R, int32_t construction, int32_t precision, double *out,
                           void *stream);
 
+/* ---- serving: continuous batching ------------------------------------------
+ * Sec. 7 proposes wrapping the estimator in a microservice; this is its GPU
+ * side.  Requests (contracts) queue on the host; a worker thread forms
+ * batches from whatever is pending each time one of its `max_inflight`
+ * slots is free, admitting requests in arrival order while the batch's
+ * device scratch (about 32 * R * N / P bytes of tile sums per contract) stays
+ * within `max_batch_bytes`, and runs up to `max_inflight` batches on the GPU
+ * at once, one stream each.  A request's result does not depend on the batch
+ * it ran in (bit-identical to qmccpw_greeks).  While a server runs, the plan
+ * must not be used by the other entry points. */
+typedef struct {
+    int32_t precision;             /* qmccpw_precision of every request */
+    int32_t max_inflight;          /* batches on the GPU at once, 1..8 (0: 2) */
+    int32_t max_batch_contracts;   /* requests per batch (<= 0: 1024) */
+    int32_t reserved;              /* must be 0 */
+    uint64_t max_batch_bytes;      /* device scratch admitted per batch (0: 256 MiB) */
+} qmccpw_server_desc;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches;
+    uint64_t point_dates;          /* sum of N * R * d over completed requests */
+    uint64_t pending;              /* requests waiting for a batch */
+} qmccpw_server_stats;
+
+/* Start the service on a plan (INVALID_ARG if one already runs). */
+int qmccpw_server_start(qmccpw_plan_t plan, const qmccpw_server_desc *desc);
+/* Queue one contract; *ticket identifies it.  Validation as qmccpw_greeks;
+ * OOM if the contract alone exceeds the plan's workspace budget. */
+int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t *ticket);
+/* Non-blocking: OK and the result (per_replicate filled if non-NULL, R*4
+ * doubles) once finished, QMCCPW_NOT_READY before; a collected ticket is
+ * forgotten. */
+int qmccpw_poll(qmccpw_plan_t plan, uint64_t ticket, qmccpw_result *out);
+/* Blocking form of qmccpw_poll, at most timeout_ms milliseconds (TIMEOUT). */
+int qmccpw_wait(qmccpw_plan_t plan, uint64_t ticket, int32_t timeout_ms, qmccpw_result *out);
+int qmccpw_server_get_stats(qmccpw_plan_t plan, qmccpw_server_stats *out);
+/* Finish every queued request, then stop the worker (no-op without a server). */
+int qmccpw_server_stop(qmccpw_plan_t plan);
+
 /* Release a plan after waiting for its work; NULL is accepted (no-op). */
 int qmccpw_free(qmccpw_plan_t plan);
 

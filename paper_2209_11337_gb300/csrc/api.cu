@@ -7,10 +7,16 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "qmccpw_internal.h"
@@ -90,6 +96,8 @@ int tc_kind(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1;
 
 }  // namespace
 
+struct QmcServer;
+
 struct qmccpw_plan_s {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -102,11 +110,12 @@ struct qmccpw_plan_s {
     DevBuf dir;          // unscrambled direction integers, ndims x 32
     DevBuf table;        // [r][b][j]
     DevBuf shift;        // [r][j]
-    // per (d, T) tables, keyed by d and the bit pattern of T
-    std::map<std::pair<int, uint64_t>, std::unique_ptr<DTables>> dtables;
+    // unit-spacing bridge / PCA tables, keyed by d
+    std::map<int, std::unique_ptr<DTables>> dtables;
     // grow-only buffers reused by the one-shot entry points
     BatchBuffers ws;
     std::mutex mu;
+    struct QmcServer *server = nullptr;  // continuous-batching service, when started
 };
 
 struct qmccpw_batch_s {
@@ -129,6 +138,19 @@ struct qmccpw_batch_s {
     // fused-kernel timing: event pairs of the most recent launches
     std::vector<cudaEvent_t> ev_start, ev_stop;
     int32_t timed = 0;  // launches recorded since the last read
+    // forget the previous contracts, keep the device buffers for reuse
+    void reset_meta() {
+        count = 0;
+        host.clear();
+        order.clear();
+        R.clear();
+        items = total_reps = items_bb = 0;
+        smem[0] = smem[1] = 0;
+        grid[0] = grid[1] = 0;
+        point_out = nullptr;
+        point_k0 = 0;
+        rep_offset = 0;
+    }
     ~qmccpw_batch_s() {
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_stop) cudaEventDestroy(e);
@@ -162,19 +184,18 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
     return QMCCPW_OK;
 }
 
-// Bridge / PCA tables for (d, T), built on first use and cached by the plan.
-int get_dtables(qmccpw_plan_s *p, int d, double T, const DTables **out) {
-    uint64_t tbits;
-    std::memcpy(&tbits, &T, sizeof(tbits));
-    auto key = std::make_pair(d, tbits);
-    auto it = p->dtables.find(key);
+// Bridge / PCA tables of d dates for unit spacing (dt = 1), built on first use
+// and cached by the plan: with equal spacing both factors scale exactly as
+// sqrt(dt), which the kernels apply, so one table set serves every maturity.
+int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
+    auto it = p->dtables.find(d);
     if (it != p->dtables.end()) {
         *out = it->second.get();
         return QMCCPW_OK;
     }
     auto t = std::make_unique<DTables>();
     const int n = d - 1;
-    const double dt = T / d;
+    const double dt = 1.0;
     t->n = n;
     BridgePlan bp = bridge_plan(n, dt);
     t->n_levels = static_cast<int>(bp.level_start.size()) - 1;
@@ -210,7 +231,7 @@ int get_dtables(qmccpw_plan_s *p, int d, double T, const DTables **out) {
     QMC_CUDA(cudaMemcpy(t->level_start.ptr, bp.level_start.data(), sizeof(int32_t) * bp.level_start.size(),
                         cudaMemcpyHostToDevice));
     *out = t.get();
-    p->dtables.emplace(key, std::move(t));
+    p->dtables.emplace(d, std::move(t));
     return QMCCPW_OK;
 }
 
@@ -245,6 +266,10 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
     c.groups = kThreads / P;
     c.n_levels = t->n_levels;
     c.row_stride = (c.n + 1) | 1;
+    // the register bridge (float, one thread per point, d = 16 or 64) and PCA read z by
+    // dimension; the shared-memory bridge overwrites z with W~ in place at its date
+    c.z_by_dim = (c.construction == QMCCPW_PCA ||
+                  (precision != QMCCPW_FP64 && c.groups == 1 && (c.n == 63 || c.n == 15))) ? 1 : 0;
     c.N = in.N;
     c.item_base = item_base;
     c.rep_base = rep_base;
@@ -276,7 +301,8 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
 }
 
 int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int32_t precision, bool diagnostic,
-                qmccpw_batch_s *b) {
+                qmccpw_batch_s *b, cudaStream_t stream = nullptr) {
+    cudaStream_t st = stream ? stream : p->stream;
     if (count < 1) return fail(QMCCPW_ERR_INVALID_ARG, "count must be >= 1");
     for (int i = 0; i < count; ++i)
         QMC_TRY(validate_contract(p, cs[i].option, cs[i].market, cs[i].N, cs[i].R, cs[i].construction, precision,
@@ -328,13 +354,10 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     QMC_TRY(B.per_rep.ensure(sizeof(double) * 4 * reps));
     QMC_TRY(B.stats.ensure(sizeof(double) * 8 * count));
     QMC_TRY(B.counters.ensure(2 * sizeof(unsigned long long)));
-    QMC_CUDA(cudaMemcpyAsync(B.contracts.ptr, b->host.data(), sizeof(ContractDev) * count, cudaMemcpyHostToDevice,
-                             p->stream));
-    QMC_CUDA(cudaMemcpyAsync(B.item_base.ptr, item_base.data(), sizeof(uint64_t) * count, cudaMemcpyHostToDevice,
-                             p->stream));
-    QMC_CUDA(cudaMemcpyAsync(B.rep_owner.ptr, rep_owner.data(), sizeof(uint64_t) * reps, cudaMemcpyHostToDevice,
-                             p->stream));
-    QMC_CUDA(cudaStreamSynchronize(p->stream));  // the host vectors go out of scope
+    QMC_CUDA(cudaMemcpyAsync(B.contracts.ptr, b->host.data(), sizeof(ContractDev) * count, cudaMemcpyHostToDevice, st));
+    QMC_CUDA(cudaMemcpyAsync(B.item_base.ptr, item_base.data(), sizeof(uint64_t) * count, cudaMemcpyHostToDevice, st));
+    QMC_CUDA(cudaMemcpyAsync(B.rep_owner.ptr, rep_owner.data(), sizeof(uint64_t) * reps, cudaMemcpyHostToDevice, st));
+    QMC_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
     const uint64_t range[2] = {b->items_bb, items - b->items_bb};
     for (int k = 0; k < 2; ++k) {
         if (range[k] == 0) continue;
@@ -418,6 +441,189 @@ int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
     return QMCCPW_OK;
 }
 
+
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Continuous batching service (qmccpw_server_*): requests queue on the host;
+// a worker forms batches from whatever is pending whenever one of its
+// in-flight slots is free, admitting requests while the batch's device
+// scratch stays within the budget, and keeps up to max_inflight batches on
+// the GPU at once (one stream each), so work that arrives while others run
+// overlaps on the device.  A host callback on each slot's stream wakes the
+// worker when the batch's results have landed in pinned host memory.
+// Each contract's result depends only on the contract (its tiles and their
+// reduction order are fixed), so it is the same alone and in any mix.
+// ---------------------------------------------------------------------------
+struct ServerResult {
+    int status = QMCCPW_OK;
+    double mean[4] = {0, 0, 0, 0}, se[4] = {0, 0, 0, 0};
+    std::vector<double> per_rep;
+};
+
+struct ServerSlot {
+    cudaStream_t stream = nullptr;
+    qmccpw_batch_s batch;
+    std::vector<qmccpw_contract> contracts;
+    std::vector<uint64_t> tickets;
+    double *h_stats = nullptr, *h_per = nullptr;  // pinned
+    size_t h_stats_cap = 0, h_per_cap = 0;
+    bool busy = false;
+    std::atomic<bool> done{false};
+    void *owner = nullptr;  // the QmcServer
+};
+
+struct QmcServer {
+    qmccpw_plan_s *plan = nullptr;
+    qmccpw_server_desc desc{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::pair<uint64_t, qmccpw_contract>> pending;
+    std::unordered_map<uint64_t, ServerResult> results;
+    std::unordered_map<uint64_t, bool> known;  // ticket -> submitted and not yet collected
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    std::vector<std::unique_ptr<ServerSlot>> slots;
+    std::thread worker;
+    qmccpw_server_stats stats{};
+
+    static void CUDART_CB on_done(void *arg) {
+        ServerSlot *sl = static_cast<ServerSlot *>(arg);
+        sl->done.store(true);
+        QmcServer *sv = static_cast<QmcServer *>(sl->owner);
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->cv_work.notify_all();
+    }
+
+    // device scratch one contract needs in a batch (tile sums + replicate sums)
+    uint64_t bytes_of(const qmccpw_contract &c) const {
+        const int n = c.option.d - 1;
+        const int P = 1 << (desc.precision >= QMCCPW_MIXED_TC_BF16X3 ? 7 : choose_tile_log2(desc.precision, n));
+        const uint64_t tiles = (c.N + P - 1) / P;
+        return tiles * static_cast<uint64_t>(c.R) * 32u + static_cast<uint64_t>(c.R) * 40u + sizeof(ContractDev) + 16u;
+    }
+
+    void retire(ServerSlot &sl) {
+        qmccpw_batch_s &b = sl.batch;
+        uint64_t rep = 0;
+        for (int k = 0; k < b.count; ++k) {
+            const int caller = b.order[k];
+            ServerResult r;
+            std::memcpy(r.mean, sl.h_stats + 8 * k, sizeof(r.mean));
+            std::memcpy(r.se, sl.h_stats + 8 * k + 4, sizeof(r.se));
+            r.per_rep.assign(sl.h_per + 4 * rep, sl.h_per + 4 * (rep + b.R[k]));
+            rep += b.R[k];
+            const qmccpw_contract &c = sl.contracts[caller];
+            stats.point_dates += c.N * static_cast<uint64_t>(c.R) * static_cast<uint64_t>(c.option.d);
+            results[sl.tickets[caller]] = std::move(r);
+            ++stats.completed;
+        }
+        sl.busy = false;
+        sl.done.store(false);
+        cv_done.notify_all();
+    }
+
+    void fail_all(ServerSlot &sl, int status) {
+        for (uint64_t t : sl.tickets) {
+            ServerResult r;
+            r.status = status;
+            results[t] = std::move(r);
+            ++stats.failed;
+        }
+        sl.busy = false;
+        cv_done.notify_all();
+    }
+
+    // Build and enqueue one batch on a free slot (called without the lock).
+    int launch(ServerSlot &sl) {
+        const int count = static_cast<int>(sl.contracts.size());
+        sl.batch.reset_meta();
+        QMC_TRY(batch_build(plan, sl.contracts.data(), count, desc.precision, false, &sl.batch, sl.stream));
+        if (sl.h_stats_cap < 8u * count) {
+            if (sl.h_stats) cudaFreeHost(sl.h_stats);
+            sl.h_stats = nullptr;
+            QMC_CUDA(cudaMallocHost(&sl.h_stats, sizeof(double) * 8 * count));
+            sl.h_stats_cap = 8u * count;
+        }
+        if (sl.h_per_cap < 4u * sl.batch.total_reps) {
+            if (sl.h_per) cudaFreeHost(sl.h_per);
+            sl.h_per = nullptr;
+            QMC_CUDA(cudaMallocHost(&sl.h_per, sizeof(double) * 4 * sl.batch.total_reps));
+            sl.h_per_cap = 4u * sl.batch.total_reps;
+        }
+        QMC_TRY(batch_enqueue(&sl.batch, sl.stream));
+        const BatchBuffers &B = *sl.batch.buf;
+        QMC_CUDA(cudaMemcpyAsync(sl.h_stats, B.stats.ptr, sizeof(double) * 8 * count, cudaMemcpyDeviceToHost, sl.stream));
+        QMC_CUDA(cudaMemcpyAsync(sl.h_per, B.per_rep.ptr, sizeof(double) * 4 * sl.batch.total_reps,
+                                 cudaMemcpyDeviceToHost, sl.stream));
+        QMC_CUDA(cudaLaunchHostFunc(sl.stream, &QmcServer::on_done, &sl));
+        return QMCCPW_OK;
+    }
+
+    void run() {
+        cudaSetDevice(plan->device);
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            for (auto &sl : slots)
+                if (sl->busy && sl->done.load()) retire(*sl);
+            for (auto &slp : slots) {
+                ServerSlot &sl = *slp;
+                if (sl.busy || pending.empty()) continue;
+                // admission: requests in arrival order while the batch fits the budget
+                sl.contracts.clear();
+                sl.tickets.clear();
+                uint64_t bytes = 0;
+                while (!pending.empty() && static_cast<int>(sl.contracts.size()) < desc.max_batch_contracts) {
+                    const uint64_t need = bytes_of(pending.front().second);
+                    if (!sl.contracts.empty() && bytes + need > desc.max_batch_bytes) break;
+                    bytes += need;
+                    sl.tickets.push_back(pending.front().first);
+                    sl.contracts.push_back(pending.front().second);
+                    pending.pop_front();
+                }
+                sl.busy = true;
+                ++stats.batches;
+                lk.unlock();
+                const int rc = launch(sl);
+                lk.lock();
+                if (rc != QMCCPW_OK) fail_all(sl, rc);
+            }
+            bool any_busy = false;
+            for (auto &sl : slots) any_busy |= sl->busy;
+            if (stopping && pending.empty() && !any_busy) break;
+            cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] {
+                if (stopping && pending.empty()) return true;
+                for (auto &sl : slots) {
+                    if (sl->busy && sl->done.load()) return true;
+                    if (!sl->busy && !pending.empty()) return true;
+                }
+                return false;
+            });
+        }
+    }
+
+    ~QmcServer() {
+        for (auto &sl : slots) {
+            if (sl->stream) {
+                cudaStreamSynchronize(sl->stream);
+                cudaStreamDestroy(sl->stream);
+            }
+            if (sl->h_stats) cudaFreeHost(sl->h_stats);
+            if (sl->h_per) cudaFreeHost(sl->h_per);
+        }
+    }
+};
+
+namespace {
+
+int fill_result(const ServerResult &r, qmccpw_result *out) {
+    if (r.status != QMCCPW_OK) return fail(r.status, "the request's batch failed");
+    std::memcpy(out->mean, r.mean, sizeof(r.mean));
+    std::memcpy(out->se, r.se, sizeof(r.se));
+    if (out->per_replicate) std::memcpy(out->per_replicate, r.per_rep.data(), sizeof(double) * r.per_rep.size());
+    return QMCCPW_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free form (qmccpw_greeks_noalloc): every per-call device array
@@ -505,6 +711,7 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
 int qmccpw_free(qmccpw_plan_t plan) {
     g_last_error.clear();
     if (!plan) return QMCCPW_OK;
+    qmccpw_server_stop(plan);
     cudaSetDevice(plan->device);
     cudaStreamSynchronize(plan->stream);
     plan->dtables.clear();
@@ -698,11 +905,10 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
 
     // the contract and its bridge / PCA tables, built on the host
     const int d = option->d, n = d - 1;
-    const double dt = option->T / d;
-    BridgePlan bp = bridge_plan(n, dt);
+    BridgePlan bp = bridge_plan(n, 1.0);  // unit spacing: the kernels scale by sqrt(dt)
     const int n_pad = (n + 15) & ~15;
     const bool pca = construction == QMCCPW_PCA;
-    std::vector<double> A = (pca && n > 0) ? pca_factor(n, dt) : std::vector<double>();
+    std::vector<double> A = (pca && n > 0) ? pca_factor(n, 1.0) : std::vector<double>();
 
     ContractDev c{};
     c.type = option->type;
@@ -719,6 +925,8 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.groups = kThreads / P;
     c.n_levels = static_cast<int>(bp.level_start.size()) - 1;
     c.row_stride = (n + 1) | 1;
+    c.z_by_dim = (construction == QMCCPW_PCA ||
+                  (precision != QMCCPW_FP64 && c.groups == 1 && (n == 63 || n == 15))) ? 1 : 0;
     c.N = N;
     c.item_base = 0;
     c.rep_base = 0;
@@ -805,6 +1013,112 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     QMC_CUDA(static_cast<cudaError_t>(launch_reduce(lp.contracts, 1, lp.tile_sums, out, out + 4 * static_cast<size_t>(R),
                                                     static_cast<uint64_t>(R),
                                                     reinterpret_cast<const uint64_t *>(dev + o_rep_owner), s)));
+    return QMCCPW_OK;
+}
+
+
+int qmccpw_server_start(qmccpw_plan_t plan, const qmccpw_server_desc *desc) {
+    g_last_error.clear();
+    if (!plan || !desc) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    if (plan->server) return fail(QMCCPW_ERR_INVALID_ARG, "the plan already runs a server");
+    if (desc->reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "reserved must be 0");
+    if (desc->precision < QMCCPW_FP64 || desc->precision > QMCCPW_MIXED_TC_TF32X3)
+        return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
+    if (desc->max_inflight < 0 || desc->max_inflight > 8) return fail(QMCCPW_ERR_INVALID_ARG, "max_inflight out of 0..8");
+    auto sv = std::make_unique<QmcServer>();
+    sv->plan = plan;
+    sv->desc = *desc;
+    if (sv->desc.max_inflight == 0) sv->desc.max_inflight = 2;
+    if (sv->desc.max_batch_contracts <= 0) sv->desc.max_batch_contracts = 1024;
+    if (sv->desc.max_batch_bytes == 0) sv->desc.max_batch_bytes = uint64_t(256) << 20;
+    QMC_CUDA(cudaSetDevice(plan->device));
+    for (int i = 0; i < sv->desc.max_inflight; ++i) {
+        auto sl = std::make_unique<ServerSlot>();
+        sl->owner = sv.get();
+        QMC_CUDA(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
+        sv->slots.push_back(std::move(sl));
+    }
+    QmcServer *raw = sv.get();
+    sv->worker = std::thread([raw] { raw->run(); });
+    plan->server = sv.release();
+    return QMCCPW_OK;
+}
+
+int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t *ticket) {
+    g_last_error.clear();
+    if (!plan || !contract || !ticket) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    QmcServer *sv = plan->server;
+    if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
+    QMC_TRY(validate_contract(plan, contract->option, contract->market, contract->N, contract->R,
+                              contract->construction, sv->desc.precision, false));
+    if (sv->bytes_of(*contract) > plan->workspace_bytes)
+        return fail(QMCCPW_ERR_OOM, "the request needs more device scratch than the plan's workspace budget");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stopping) return fail(QMCCPW_ERR_INVALID_ARG, "the server is stopping");
+    *ticket = sv->next_ticket++;
+    sv->pending.emplace_back(*ticket, *contract);
+    sv->known[*ticket] = true;
+    ++sv->stats.submitted;
+    sv->cv_work.notify_all();
+    return QMCCPW_OK;
+}
+
+int qmccpw_poll(qmccpw_plan_t plan, uint64_t ticket, qmccpw_result *out) {
+    g_last_error.clear();
+    if (!plan || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    QmcServer *sv = plan->server;
+    if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->known.count(ticket)) return fail(QMCCPW_ERR_INVALID_ARG, "unknown or already collected ticket");
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return QMCCPW_NOT_READY;
+    const int rc = fill_result(it->second, out);
+    sv->results.erase(it);
+    sv->known.erase(ticket);
+    return rc;
+}
+
+int qmccpw_wait(qmccpw_plan_t plan, uint64_t ticket, int32_t timeout_ms, qmccpw_result *out) {
+    g_last_error.clear();
+    if (!plan || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    QmcServer *sv = plan->server;
+    if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (!sv->known.count(ticket)) return fail(QMCCPW_ERR_INVALID_ARG, "unknown or already collected ticket");
+    const bool ready = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                            [&] { return sv->results.count(ticket) > 0; });
+    if (!ready) return fail(QMCCPW_ERR_TIMEOUT, "the request is not finished");
+    auto it = sv->results.find(ticket);
+    const int rc = fill_result(it->second, out);
+    sv->results.erase(it);
+    sv->known.erase(ticket);
+    return rc;
+}
+
+int qmccpw_server_get_stats(qmccpw_plan_t plan, qmccpw_server_stats *out) {
+    g_last_error.clear();
+    if (!plan || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    QmcServer *sv = plan->server;
+    if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->pending = sv->pending.size();
+    return QMCCPW_OK;
+}
+
+int qmccpw_server_stop(qmccpw_plan_t plan) {
+    g_last_error.clear();
+    if (!plan) return fail(QMCCPW_ERR_INVALID_ARG, "NULL plan");
+    QmcServer *sv = plan->server;
+    if (!sv) return QMCCPW_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stopping = true;
+        sv->cv_work.notify_all();
+    }
+    sv->worker.join();
+    plan->server = nullptr;
+    delete sv;
     return QMCCPW_OK;
 }
 

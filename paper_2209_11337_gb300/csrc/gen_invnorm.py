@@ -1,4 +1,6 @@
-"""Fit the float inverse-normal polynomials used by the MIXED fused kernel.
+"""Fit the float polynomials used by the MIXED fused kernel.
+
+1. Inverse normal.
 
 Method (Giles, "Approximating the erfinv function", GPU Computing Gems Jade,
 2011): with x = 1 - 2q (q = min(u, 1-u)) and w = -ln(1 - x^2) = -ln(4q(1-q)),
@@ -7,6 +9,9 @@ and Phi^{-1}(q) = -sqrt(2) erfinv(x).  The polynomials here are this
 project's own least-squares fits (Chebyshev nodes, relative weighting, 80-digit
 reference from mpmath), rebased to a shifted monomial form for Horner
 evaluation in float, with the sqrt(2) folded in.
+
+2. 2^f on [-1/2, 1/2] for the path exponentials e^x = 2^k 2^f (k the
+   nearest integer to x log2 e): a degree-6 relative least-squares fit.
 
     python paper_2209_11337_gb300/csrc/gen_invnorm.py    # rewrites invnorm_coeffs.h
 """
@@ -59,7 +64,23 @@ def check(coef, lo, hi, var, shift):
     return float(np.max(np.abs(approx / ref - 1)))
 
 
+DEG_E = 6
+
+
+def fit_exp2():
+    k = np.arange(200)
+    f = 0.5 * np.cos(np.pi * (k + 0.5) / 200)
+    y = np.array([float(mp.power(2, mp.mpf(x))) for x in f])
+    X = np.vander(f, DEG_E + 1, increasing=True)
+    coef, *_ = np.linalg.lstsq(X / y[:, None], np.ones_like(y), rcond=None)
+    fs = np.linspace(-0.5, 0.5, 4001)
+    ref = np.array([float(mp.power(2, mp.mpf(x))) for x in fs[::4]])
+    approx = horner32(coef, fs[::4].astype(np.float32)).astype(np.float64)
+    return coef, float(np.max(np.abs(approx / ref - 1)))
+
+
 def main():
+    e, ee = fit_exp2()
     c = fit(0.0, W0, DEG_C, "w", SHIFT_C)
     t = fit(np.sqrt(W0), np.sqrt(W_MAX), DEG_T, "s", SHIFT_T)
     ec = check(c, 0.0, W0, "w", SHIFT_C)
@@ -73,7 +94,9 @@ def main():
         f.write(f"#define QMC_INVN_W0 {W0}f\n#define QMC_INVN_SHIFT_C {SHIFT_C}f\n#define QMC_INVN_SHIFT_T {SHIFT_T}f\n")
         f.write("#define QMC_INVN_CENTRAL {" + ", ".join(f"{x:.9e}f" for x in c) + "}\n")
         f.write("#define QMC_INVN_TAIL {" + ", ".join(f"{x:.9e}f" for x in t) + "}\n")
-    print("central max rel err", ec, "tail max rel err", et, "->", out)
+        f.write(f"// 2^f on [-1/2, 1/2], degree {DEG_E}, max rel err {ee:.2e} (float Horner)\n")
+        f.write("#define QMC_EXP2_POLY {" + ", ".join(f"{x:.9e}f" for x in e) + "}\n")
+    print("central max rel err", ec, "tail max rel err", et, "exp2 max rel err", ee, "->", out)
 
 
 if __name__ == "__main__":

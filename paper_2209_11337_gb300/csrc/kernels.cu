@@ -47,16 +47,19 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     const int G = c.groups;
     T *row = zw + pt * stride;
     const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
+    const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
     for (int lvl = 0; lvl < c.n_levels; ++lvl) {
         const int b_end = __ldg(c.level_start + lvl + 1);
         for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += G) {
             const int4 st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
-            const T Wl = row[st.y], Wr = row[st.z], z = row[st.x];
+            const T Wl = row[st.y], Wr = row[st.z];
+            T z = row[st.x];
             T Wm;
             if constexpr (sizeof(T) == 8) {
                 const double *w = c.w64 + 3 * b;
-                Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * z;
+                Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (c.sqrt_t1 * z);
             } else {
+                z = fmaf(z, sdt_hi, z * sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
                 // hi + lo coefficients: the low parts first, then the high parts
                 const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
                 const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
@@ -116,13 +119,14 @@ template <int N, int TYPE>
 __device__ __forceinline__ void bridge_registers(const ContractDev &c, const float *row, PathAcc<float> &acc) {
     constexpr BridgeSchedule S = make_schedule(N);
     static_assert(S.count == N, "bridge schedule size");
-    const float sdt = static_cast<float>(c.sqrt_t1);
+    const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
     const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
     float W[N + 1];
     W[0] = 0.0f;
 #pragma unroll
     for (int b = 0; b < N; ++b) {
-        const float z = row[S.m[b]] * sdt;
+        const float z0 = row[b + 1];  // z of dimension b (stored by dimension)
+        const float z = fmaf(z0, sdt_hi, z0 * sdt_lo);  // z sqrt(dt), sqrt(dt) carried as hi + lo
         const float Wl = W[S.l[b]], Wr = W[S.r[b]];
         const float Wm = fmaf(static_cast<float>(S.c[b]), z, fmaf(static_cast<float>(S.wr[b]), Wr - Wl, Wl));
         W[S.m[b]] = Wm;
@@ -147,9 +151,11 @@ __device__ void pca_rows_phase(const ContractDev &c, const T *zw, int stride, Pa
         if constexpr (sizeof(T) == 8) {
             const double *Ai = c.pca64 + static_cast<size_t>(i - 1) * n;
             for (int k = 0; k < n; ++k) Wi += __ldg(Ai + k) * row[k + 1];
+            Wi *= c.sqrt_t1;
         } else {
             const int n_pad = (n + 15) & ~15;
             for (int k = 0; k < n; ++k) Wi = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k) * n_pad + (i - 1)), row[k + 1], Wi);
+            Wi = fmaf(Wi, c.ff_sqrt_t1[0], Wi * c.ff_sqrt_t1[1]);
         }
         acc.template add<TYPE>(i, Wi, omega, sigma, s_i);
     }
@@ -203,7 +209,10 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
             if (i <= n) {
                 const float s_i = fmaf(static_cast<float>(r), dt, s0);
 #pragma unroll
-                for (int j = 0; j < PB; ++j) acc[j].template add<TYPE>(i, w[j][r], omega, sigma, s_i);
+                for (int j = 0; j < PB; ++j) {
+                    const float Wi = fmaf(w[j][r], c.ff_sqrt_t1[0], w[j][r] * c.ff_sqrt_t1[1]);
+                    acc[j].template add<TYPE>(i, Wi, omega, sigma, s_i);
+                }
             }
         }
     }
@@ -217,7 +226,7 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
     if constexpr (CONS == QMCCPW_BB) {
         acc.init(TYPE, threadIdx.x < P);
         if constexpr (sizeof(T) == 4) {
-            if (c.groups == 1 && (c.n == 63 || c.n == 15)) {
+            if (c.z_by_dim) {  // set exactly when the register bridge applies
                 const float *row = zw + threadIdx.x * stride;
                 if (c.n == 63) bridge_registers<63, TYPE>(c, row, acc);
                 else bridge_registers<15, TYPE>(c, row, acc);
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
             for (int it = threadIdx.x; it < work; it += kThreads) {
                 const int j = it % n;
                 const int ch = it / n;
-                const int slot = (CONS == QMCCPW_BB) ? __ldg(&c.steps[j].m) : j + 1;
+                const int slot = c.z_by_dim ? j + 1 : __ldg(&c.steps[j].m);
                 T *dst = zw + static_cast<size_t>(ch * chunk) * stride + slot;
                 // points at or past N (ragged last tile) are never generated: their
                 // index could pass 2^32; they are zero-filled and left out of the sums

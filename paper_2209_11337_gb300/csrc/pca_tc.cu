@@ -181,7 +181,7 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
     const int warp = threadIdx.x >> 5;
     const int half = warp >> 2;                 // warpgroup: which half of the dates
     const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
-    const float sdt = static_cast<float>(c.sqrt_t1);
+    const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
     const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
     acc.init(TYPE, half == 0);
 #pragma unroll
@@ -193,7 +193,8 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int date = col + i + 1;  // W~ at s_date
-            if (date <= c.n) acc.template add<TYPE>(date, d[i] * sdt, omega, sigma, fmaf(static_cast<float>(i), dt, s0));
+            if (date <= c.n)
+                acc.template add<TYPE>(date, fmaf(d[i], sdt_hi, d[i] * sdt_lo), omega, sigma, fmaf(static_cast<float>(i), dt, s0));
         }
     }
     (void)point;

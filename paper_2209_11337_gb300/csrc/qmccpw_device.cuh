@@ -77,7 +77,22 @@ template <> struct Arith<float> {
         const float z = -x * p;  // <= 0 on the lower half
         return upper ? -z : z;
     }
-    __device__ static float ex(float x) { return expf(x); }
+    // e^x for the path sums (|x| well below 80): 2^k 2^f with k the nearest
+    // integer to x log2 e, read from the low bits of x log2 e + 1.5 2^23
+    // (no conversion instruction), f = x log2 e - k in [-1/2, 1/2] with the
+    // residual of log2 e, and 2^f from the fitted polynomial (8.7e-8).
+    __device__ static float ex(float x) {
+        constexpr float c[] = QMC_EXP2_POLY;
+        const float t = x * 1.44269502f;
+        const float r = t + 12582912.0f;
+        const float kf = r - 12582912.0f;
+        const float f = fmaf(x, 1.44269502f, -kf) + x * 1.92596299e-8f;
+        float p = c[6];
+#pragma unroll
+        for (int i = 5; i >= 0; --i) p = fmaf(p, f, c[i]);
+        const int k = __float_as_int(r) - 0x4B400000;
+        return __int_as_float(__float_as_int(p) + (k << 23));
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -201,58 +216,75 @@ __device__ __forceinline__ ff ff_of_double(double x) {
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
 
-// ln x in double for a positive normal float x: x = 2^e m, m in [1/sqrt2,
-// sqrt2), ln m = 2 atanh(f), f = (m-1)/(m+1), |f| <= 0.172, series to f^15
-// (truncation < 2e-14); f from a float reciprocal and one Newton step.
-__device__ __forceinline__ double ln_of_float(float x) {
+__device__ __forceinline__ ff ff_mul_ff(ff a, ff b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return ff_fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+
+// ln x in float-float for a positive normal float x, absolute error < 1e-9
+// (60x below the float rounding of x itself):
+// x = 2^e m, m in [1/sqrt2, sqrt2), ln m = 2 atanh f with f = (m-1)/(m+1)
+// formed in float-float (|f| <= 0.172); 2f is carried in float-float and the
+// rest of the series, 2f^3 (1/3 + f^2/5 + ... + f^8/11) <= 3.4e-3, in float
+// from f's leading part (truncation < 2e-11, rounding and the dropped low
+// part of f < 1e-9); e ln2 with a 2-part ln2 whose leading part has 16
+// trailing zero bits, so e times it is exact.
+__device__ __forceinline__ ff ln_ff(float x) {
     const uint32_t b = __float_as_uint(x);
-    int e = static_cast<int>((b >> 23) & 0xFFu) - 127;
+    uint32_t eb = (b >> 23) & 0xFFu;
     float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
     if (m > 1.41421356f) {
         m *= 0.5f;
-        e += 1;
+        eb += 1u;
     }
-    const double md = m;
-    const double num = md - 1.0, den = md + 1.0;
-    double r = static_cast<double>(__frcp_rn(static_cast<float>(den)));
-    r = r * fma(-den, r, 2.0);
-    const double f = num * r;
-    const double f2 = f * f;
-    double s = 1.0 / 15.0;
-    s = fma(s, f2, 1.0 / 13.0);
-    s = fma(s, f2, 1.0 / 11.0);
-    s = fma(s, f2, 1.0 / 9.0);
-    s = fma(s, f2, 1.0 / 7.0);
-    s = fma(s, f2, 1.0 / 5.0);
-    s = fma(s, f2, 1.0 / 3.0);
-    s = fma(s, f2, 1.0);
-    const double lnm = 2.0 * f * s;
-    return fma(static_cast<double>(e), 0.69314718055994530942, lnm);
+    const float num = m - 1.0f;                  // exact
+    const ff den = ff_two_sum(m, 1.0f);          // m + 1, exact
+    const float q1 = __fdiv_rn(num, den.hi);
+    const float r = fmaf(-q1, den.hi, num) - q1 * den.lo;
+    const ff f = ff_fast_two_sum(q1, __fdiv_rn(r, den.hi));
+    const float f2 = f.hi * f.hi;
+    float t = fmaf(f2, 1.0f / 11.0f, 1.0f / 9.0f);
+    t = fmaf(t, f2, 1.0f / 7.0f);
+    t = fmaf(t, f2, 1.0f / 5.0f);
+    t = fmaf(t, f2, 1.0f / 3.0f);
+    const ff lnm = ff_add(ff{2.0f * f.hi, 2.0f * f.lo}, ff{2.0f * f.hi * f2 * t, 0.0f});
+    const float e = small_uint_to_float(eb) - 127.0f;  // exponent without a conversion instruction
+    const ff eln2 = ff_fast_two_sum(e * 0.693145751953125f, e * 1.42860676533018e-06f);
+    return ff_add(eln2, lnm);
 }
 
-// Mixed precision: the switch point psi in double; the normal tail and
-// density in float; their combination with the contract constants in
-// float-float.  The price of a call is the difference of two terms of size
-// ~K: a float product there would bias every point by ~2^-24 K, which no
-// averaging removes.  Beyond |psi| = 12 the float density and tail
-// underflow, so those (rare) points take the double formulas.
+// Mixed precision: the switch point psi and every combination with the
+// contract constants in float-float (about 44 significant bits, on the FP32
+// pipe: on this GPU a warp's FP64 instruction holds its sub-partition's FP64
+// unit ~64x longer than an FP32 one, and ~25 of them per point halved the
+// throughput of the whole kernel); the normal tail and density in float.
+// The price of a call is the difference of two terms of size ~K: a float
+// product there would bias every point by ~2^-24 K, which no averaging
+// removes.  Beyond |psi| = 12 the float density and tail underflow, so those
+// (rare) points take the double formulas.
 __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[4]) {
-    const double psi = (c.psi0 - ln_of_float(xhat)) * c.inv_a;
-    if (fabs(psi) > 12.0) {
+    const ff psi = ff_mul_ff(ff_add(ff_of(c.ff_psi0), ff_neg(ln_ff(xhat))), ff_of(c.ff_inv_a));
+    const float p = psi.hi;
+    if (fabsf(p) > 12.0f) {
         double d[4];
         values_fp64(c, static_cast<double>(xhat), static_cast<double>(dhat), d);
         for (int g = 0; g < 4; ++g) v[g] = ff_of_double(d[g]);
         return;
     }
-    const float p = static_cast<float>(psi);
     const float pdf = 0.398942280f * expf(-0.5f * p * p);
     if (c.type == QMCCPW_BINARY_ASIAN) {
         const float sf = 0.5f * erfcf(p * 0.707106781f);
         v[0] = ff_mul(ff_of(c.ff_disc), sf);
         v[1] = ff_mul(ff_of(c.ff_k_bin_delta), pdf);
-        const double bracket = static_cast<double>(dhat / xhat) * c.inv_a + psi * c.inv_sigma - c.sqrt_t1;
-        v[2] = ff_mul(ff_of_double(c.disc * bracket), pdf);
-        v[3] = ff_mul(ff_of_double(c.k_bin_gamma * (psi * c.inv_a - 1.0)), pdf);
+        // D/(a X) + psi/sigma - sqrt(t1), then times e^{-rT} phi(psi)
+        ff br = ff_mul(ff_of(c.ff_inv_a), dhat / xhat);
+        br = ff_add(br, ff_mul_ff(psi, ff_of(c.ff_inv_sigma)));
+        br = ff_add(br, ff_neg(ff_of(c.ff_sqrt_t1)));
+        v[2] = ff_mul_ff(ff_mul(ff_of(c.ff_disc), pdf), br);
+        // e^{-rT} phi(psi) / (S0^2 a) (psi/a - 1)
+        const ff g = ff_add(ff_mul_ff(psi, ff_of(c.ff_inv_a)), ff{-1.0f, 0.0f});
+        v[3] = ff_mul_ff(ff_mul(ff_of(c.ff_k_bin_gamma), pdf), g);
     } else {
         const float a = static_cast<float>(c.a);
         const float sfs = 0.5f * erfcf((p - a) * 0.707106781f);

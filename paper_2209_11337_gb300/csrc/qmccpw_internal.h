@@ -60,13 +60,13 @@ struct ContractDev {
     int32_t groups;                      // kThreads / P threads per point in the path phase
     int32_t n_levels;                    // bridge levels
     int32_t row_stride;                  // shared-memory row (point) stride in elements, odd
-    int32_t pad0;
+    int32_t z_by_dim;                    // 1: z of dimension j at column j+1; 0: at the date it drives
     uint64_t N;
     uint64_t item_base;                  // first work item of this contract
     uint64_t rep_base;                   // first replicate slot of this contract (in per-replicate arrays)
-    // per-d tables (device pointers)
+    // per-d tables for unit spacing (device pointers); kernels scale by sqrt(dt)
     const BridgeStep *steps;
-    const double *w64;                   // 3 per step: wl, wr, sd
+    const double *w64;                   // 3 per step: wl, wr, c (sd = c sqrt(dt))
     const float *w32;                    // (hi, lo) float pairs of wl, wr, sd + 2 pad: 8 per step
     const int32_t *level_start;
     const double *pca64;                 // n x n row-major
@@ -91,6 +91,8 @@ struct ContractDev {
     // the same constants as float hi + lo pairs (float-float arithmetic of the mixed path)
     float ff_disc1_S0[2], ff_disc_K[2], ff_disc1[2], ff_disc_K_sqrt_t1[2], ff_k_call_gamma[2];
     float ff_disc[2], ff_k_bin_delta[2], ff_k_bin_gamma[2];
+    float ff_sqrt_t1[2];                 // sqrt(dt) as hi + lo: the scale of every path increment
+    float ff_psi0[2], ff_inv_a[2], ff_inv_sigma[2];
 };
 
 // hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)

@@ -198,6 +198,10 @@ void contract_constants(ContractDev &c) {
     split_ff(c.disc, c.ff_disc);
     split_ff(c.k_bin_delta, c.ff_k_bin_delta);
     split_ff(c.k_bin_gamma, c.ff_k_bin_gamma);
+    split_ff(c.sqrt_t1, c.ff_sqrt_t1);
+    split_ff(c.psi0, c.ff_psi0);
+    split_ff(c.inv_a, c.ff_inv_a);
+    split_ff(c.inv_sigma, c.ff_inv_sigma);
 }
 
 }  // namespace qmccpw

@@ -53,7 +53,9 @@ EXPORTS = (
     "qmccpw_batch_launch", "qmccpw_batch_results", "qmccpw_batch_device_results",
     "qmccpw_batch_launch_count", "qmccpw_batch_set_timing", "qmccpw_batch_timing",
     "qmccpw_batch_free", "qmccpw_sobol_points",
-    "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_free", "qmccpw_last_error", "qmccpw_version",
+    "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_server_start", "qmccpw_submit", "qmccpw_poll",
+    "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_free", "qmccpw_last_error",
+    "qmccpw_version",
 )
 
 
@@ -88,6 +90,17 @@ class qmccpw_contract(ctypes.Structure):
                 ("R", ctypes.c_int32), ("construction", ctypes.c_int32)]
 
 
+class qmccpw_server_desc(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("max_batch_contracts", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_batch_bytes", ctypes.c_uint64)]
+
+
+class qmccpw_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("point_dates", ctypes.c_uint64), ("pending", ctypes.c_uint64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -119,6 +132,12 @@ def library() -> ctypes.CDLL:
                                               P(ctypes.c_double)]
             L.qmccpw_greeks_noalloc.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), u64, i32, i32, i32,
                                                  ctypes.c_void_p, vp]
+            L.qmccpw_server_start.argtypes = [vp, P(qmccpw_server_desc)]
+            L.qmccpw_submit.argtypes = [vp, P(qmccpw_contract), P(u64)]
+            L.qmccpw_poll.argtypes = [vp, u64, P(qmccpw_result)]
+            L.qmccpw_wait.argtypes = [vp, u64, i32, P(qmccpw_result)]
+            L.qmccpw_server_get_stats.argtypes = [vp, P(qmccpw_server_stats)]
+            L.qmccpw_server_stop.argtypes = [vp]
             L.qmccpw_free.argtypes = [vp]
             L.qmccpw_last_error.restype = ctypes.c_char_p
             L.qmccpw_version.restype = ctypes.c_char_p
@@ -267,6 +286,52 @@ def qmccpw_greeks_noalloc(plan, type: int, d: int, K: float, T: float, S0: float
     _check(library().qmccpw_greeks_noalloc(plan, ctypes.byref(qmccpw_option(type, d, K, T)),
                                            ctypes.byref(qmccpw_market(S0, r, sigma)), N, R, construction,
                                            precision, ctypes.c_void_p(out_device_ptr), stream))
+
+
+def qmccpw_server_start(plan, precision: int = QMCCPW_MIXED, max_inflight: int = 2,
+                        max_batch_contracts: int = 1024, max_batch_bytes: int = 0) -> None:
+    desc = qmccpw_server_desc(precision, max_inflight, max_batch_contracts, 0, max_batch_bytes)
+    _check(library().qmccpw_server_start(plan, ctypes.byref(desc)))
+
+
+def qmccpw_submit(plan, c) -> int:
+    """Queue a contract (object with type, d, K, T, S0, r, sigma, N, R, construction); returns its ticket."""
+    arr = contract_array([c])
+    t = ctypes.c_uint64()
+    _check(library().qmccpw_submit(plan, arr, ctypes.byref(t)))
+    return t.value
+
+
+def _server_result(R):
+    per = np.zeros((R, 4))
+    res = qmccpw_result()
+    res.per_replicate = per.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return res, per
+
+
+def qmccpw_poll(plan, ticket: int, R: int):
+    """(mean, se, per_replicate) when finished, None while not ready."""
+    res, per = _server_result(R)
+    rc = _check(library().qmccpw_poll(plan, ticket, ctypes.byref(res)))
+    if rc == QMCCPW_NOT_READY:
+        return None
+    return np.array(res.mean[:]), np.array(res.se[:]), per
+
+
+def qmccpw_wait(plan, ticket: int, R: int, timeout_ms: int = 60000):
+    res, per = _server_result(R)
+    _check(library().qmccpw_wait(plan, ticket, timeout_ms, ctypes.byref(res)))
+    return np.array(res.mean[:]), np.array(res.se[:]), per
+
+
+def qmccpw_server_get_stats(plan) -> dict:
+    st = qmccpw_server_stats()
+    _check(library().qmccpw_server_get_stats(plan, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in qmccpw_server_stats._fields_}
+
+
+def qmccpw_server_stop(plan) -> None:
+    _check(library().qmccpw_server_stop(plan))
 
 
 def qmccpw_last_error() -> str:
