@@ -344,7 +344,9 @@ def run_ours(args):
         q.qmccpw_free(plan)
         return
 
-    mixed = timed(q.QMCCPW_MIXED, args.steps, args.warmup, with_clocks=True)
+    grid_prec = {"mixed": q.QMCCPW_MIXED, "tc-bf16": q.QMCCPW_MIXED_TC_BF16X3,
+                 "tc-tf32": q.QMCCPW_MIXED_TC_TF32X3}[args.grid_precision]
+    mixed = timed(grid_prec, args.steps, args.warmup, with_clocks=True)
     fp64 = timed(q.QMCCPW_FP64, args.fp64_steps, 1) if args.fp64_steps > 0 else None
 
     # end to end through the public API with host buffers: contracts in, results out
@@ -415,6 +417,45 @@ def run_ours(args):
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
     }
+    if args.book_steps > 0:
+        # the 4096-contract book: one batched launch sequence per step, MIXED, plus an FP64 sample
+        bplan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED + rank,
+                              stream=stream.cuda_stream, workspace_bytes=8 << 30)
+        bk = W.book(4096, seed=4, R=16)
+        bel = elements(bk)
+        bb = q.Batch(bplan, bk, q.QMCCPW_MIXED)
+        bb.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        bb.set_timing(args.book_steps)
+        t0 = time.perf_counter()
+        ev = []
+        for _ in range(args.book_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bb.launch(stream.cuda_stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        bms = sum(a.elapsed_time(b) for a, b in ev) / args.book_steps
+        bb.free()
+        sample = bk[:64]
+        sb = q.Batch(bplan, sample, q.QMCCPW_FP64)
+        sb.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sb.launch(stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f64ms = e0.elapsed_time(e1)
+        sb.free()
+        q.qmccpw_free(bplan)
+        line["book"] = {"workload": "4096 contracts (seed 4): type U{3}, d U{12..365}, K U(80,120), sigma U(0.1,0.5), "
+                                    "T U(0.25,2), r U(0,0.08), N=2^U{12..18}, R=16, bridge",
+                        "point_dates": bel, "mixed": {"value": world * bel / (max_over_ranks(bms) / 1e3), "unit": UNIT,
+                                                      "ms_per_step": max_over_ranks(bms), "steps": args.book_steps},
+                        "fp64_sample": {"contracts": 64, "value": elements(sample) / (f64ms / 1e3), "unit": UNIT,
+                                        "ms": f64ms}}
     if args.serving_s > 0:
         splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED + rank)
         line["serving"] = {"mixed": serve(q, splan, q.QMCCPW_MIXED, args.serving_rate, args.serving_s)}
@@ -438,6 +479,9 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid-precision", choices=["mixed", "tc-bf16", "tc-tf32"], default="mixed",
+                    help="precision of the timed grid (tc-*: PCA contracts on tensor cores)")
+    ap.add_argument("--book-steps", type=int, default=1, help="timed steps of the 4096-contract book (0: skip)")
     ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of Poisson arrivals (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0)
     ap.add_argument("--errors-out", default=None, help="write the per-contract MIXED vs FP64 table (JSON)")

@@ -69,8 +69,10 @@ typedef enum {
     QMCCPW_FP64 = 0,                 /* every step in double precision */
     QMCCPW_MIXED = 1,                /* inverse normal, path and payoff in float; switch point psi in
                                         double; per-point values summed in double */
-    QMCCPW_MIXED_TC_BF16X3 = 2,      /* MIXED with the PCA product on tensor cores, 3-term bf16 split */
-    QMCCPW_MIXED_TC_TF32X3 = 3       /* MIXED with the PCA product on tensor cores, 3-term tf32 split */
+    QMCCPW_MIXED_TC_BF16X3 = 2,      /* MIXED with the PCA product on tensor cores, 3-term bf16 split
+                                        (d <= 65); bridge contracts run as MIXED */
+    QMCCPW_MIXED_TC_TF32X3 = 3       /* MIXED with the PCA product on tensor cores, 3-term tf32 split
+                                        (d <= 65); bridge contracts run as MIXED */
 } qmccpw_precision;
 
 typedef struct qmccpw_plan_s *qmccpw_plan_t;
@@ -132,7 +134,8 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc);
  * Estimate price, delta, vega and gamma of one contract with N points per
  * replicate and R replicates.  Synchronous: the result is in *out when the
  * call returns.  Path construction per `construction`, arithmetic per
- * `precision` (tensor-core precisions require QMCCPW_PCA).
+ * `precision` (a tensor-core precision applies to PCA contracts with d <= 65
+ * and runs bridge contracts as MIXED).
  * Errors: INVALID_ARG (d, R outside the plan; N = 0 or > 2^32; S0, K, T,
  * sigma not positive and finite; r not finite), UNSUPPORTED, OOM (workspace
  * budget), CUDA.
@@ -228,6 +231,22 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
 int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
                           uint64_t N, int32_t R, int32_t construction, int32_t precision, double *out,
                           void *stream);
+
+/* ---- tile tuning (a deployment aid; the paper has a fixed 64-thread block)
+ * The CUDA-core kernels (FP64, MIXED) process tiles of P points per CTA; by
+ * default P is the largest power of two <= 256 whose z/W tile fits 65 KiB of
+ * shared memory (three CTAs per SM).  qmccpw_autotune times the fused kernel
+ * with CUDA events on a workload of about 2^24 point-dates (2^21 in FP64)
+ * for every distinct (construction, d) of `sample`, over P from twice the
+ * default down to a quarter of it (>= 32), and keeps the fastest in the
+ * plan; every later call on the plan uses it.  qmccpw_tuning_get reads the
+ * P in use; qmccpw_tuning_set stores one (a power of two in 32..256; 0
+ * restores the default), so a caller can persist and reload a tuning.
+ * Different tiles regroup the per-tile partial sums, so FP64 results can
+ * differ from the untuned ones in the last bits. */
+int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t count, int32_t precision);
+int qmccpw_tuning_get(qmccpw_plan_t plan, int32_t precision, int32_t construction, int32_t d, int32_t *points_per_tile);
+int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t construction, int32_t d, int32_t points_per_tile);
 
 /* ---- serving: continuous batching ------------------------------------------
  * Sec. 7 proposes wrapping the estimator in a microservice; this is its GPU

@@ -12,6 +12,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -92,6 +93,11 @@ struct DTables {
 };
 
 bool is_tc(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 || precision == QMCCPW_MIXED_TC_TF32X3; }
+// Kernel precision of one contract: a tensor-core precision applies to the PCA
+// product only; bridge contracts under it run as MIXED.
+int contract_precision(int precision, int construction) {
+    return (is_tc(precision) && construction == QMCCPW_BB) ? QMCCPW_MIXED : precision;
+}
 int tc_kind(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1; }
 
 }  // namespace
@@ -114,6 +120,8 @@ struct qmccpw_plan_s {
     std::map<int, std::unique_ptr<DTables>> dtables;
     // grow-only buffers reused by the one-shot entry points
     BatchBuffers ws;
+    // tile sizes chosen by qmccpw_autotune / qmccpw_tuning_set: (precision, construction, d) -> log2 P
+    std::map<std::tuple<int, int, int>, int> tuned_tile;
     std::mutex mu;
     struct QmcServer *server = nullptr;  // continuous-batching service, when started
 };
@@ -177,9 +185,7 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
         return fail(QMCCPW_ERR_INVALID_ARG, "construction out of range");
     if (precision < QMCCPW_FP64 || precision > QMCCPW_MIXED_TC_TF32X3)
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
-    if (precision >= QMCCPW_MIXED_TC_BF16X3 && construction != QMCCPW_PCA)
-        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core precisions apply to the PCA construction only");
-    if (precision >= QMCCPW_MIXED_TC_BF16X3 && o.d - 1 > pca_tc_npad())
+    if (precision >= QMCCPW_MIXED_TC_BF16X3 && construction == QMCCPW_PCA && o.d - 1 > pca_tc_npad())
         return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA supports d <= " + std::to_string(pca_tc_npad() + 1));
     return QMCCPW_OK;
 }
@@ -247,8 +253,23 @@ int choose_tile_log2(int precision, int n) {
     return lg;
 }
 
-int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, uint64_t item_base,
+// Gray-code run length of the Sobol' phase: with n >= 32 a warp takes whole
+// runs, so aim for one run per warp (8 per tile); with small n, (run, dim)
+// items, at least two per thread.
+int chunk_log2_for(int n, int tile_log2) {
+    const int P = 1 << tile_log2;
+    int lg = tile_log2;
+    if (n >= 32) {
+        while (lg > 2 && (P >> lg) < kThreads / 32) --lg;
+    } else {
+        while (lg > 0 && static_cast<long>(n) * (P >> lg) < 2L * kThreads) --lg;
+    }
+    return lg;
+}
+
+int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precision, uint64_t item_base,
                    uint64_t rep_base, ContractDev *out) {
+    const int precision = contract_precision(batch_precision, in.construction);
     const DTables *t = nullptr;
     QMC_TRY(get_dtables(p, in.option.d, in.option.T, &t));
     ContractDev c{};
@@ -256,11 +277,14 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int precision, u
     c.d = in.option.d;
     c.n = in.option.d - 1;
     c.construction = in.construction;
-    c.tile_log2 = is_tc(precision) ? 7 : choose_tile_log2(precision, c.n);
+    if (is_tc(precision)) {
+        c.tile_log2 = 7;
+    } else {
+        auto tt = p->tuned_tile.find(std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, in.construction, c.d));
+        c.tile_log2 = tt != p->tuned_tile.end() ? tt->second : choose_tile_log2(precision, c.n);
+    }
     const int P = 1 << c.tile_log2;
-    int chunk_log2 = c.tile_log2;
-    while (chunk_log2 > 0 && static_cast<long>(c.n) * (P >> chunk_log2) < 2L * kThreads) --chunk_log2;
-    c.chunk_log2 = chunk_log2;
+    c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2);
     c.R = in.R;
     c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
     c.groups = kThreads / P;
@@ -337,8 +361,8 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         reps += c.R;
         b->R[k] = c.R;
         size_t &sm = b->smem[in.construction == QMCCPW_BB ? 0 : 1];
-        sm = std::max(sm, is_tc(precision) ? pca_tc_smem_bytes(tc_kind(precision))
-                                           : fused_smem_bytes(precision, c.n, c.tile_log2));
+        const int kp = contract_precision(precision, in.construction);
+        sm = std::max(sm, is_tc(kp) ? pca_tc_smem_bytes(tc_kind(kp)) : fused_smem_bytes(kp, c.n, c.tile_log2));
     }
     b->items = items;
     b->total_reps = reps;
@@ -362,10 +386,11 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     for (int k = 0; k < 2; ++k) {
         if (range[k] == 0) continue;
         int per_sm = 0;
-        if (is_tc(precision))
-            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(precision), b->smem[k], &per_sm)));
+        const int kp = contract_precision(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA);
+        if (is_tc(kp))
+            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp), b->smem[k], &per_sm)));
         else
-            QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
+            QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(kp, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
         if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
         const uint64_t slots = static_cast<uint64_t>(per_sm) * p->sm_count;
         b->grid[k] = static_cast<int>(std::min<uint64_t>(range[k], slots));
@@ -398,11 +423,12 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
         lp.item_end = bounds[k + 1];
         lp.work_counter = B.counters.as<unsigned long long>() + k;
         QMC_CUDA(cudaMemsetAsync(lp.work_counter, 0, sizeof(unsigned long long), s));
-        if (is_tc(b->precision))
-            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(b->precision), b->smem[k], b->grid[k], s)));
+        const int kp = contract_precision(b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA);
+        if (is_tc(kp))
+            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(kp), b->smem[k], b->grid[k], s)));
         else
             QMC_CUDA(static_cast<cudaError_t>(
-                launch_fused(lp, b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
+                launch_fused(lp, kp, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
     }
     if (cap) {
         QMC_CUDA(cudaEventRecord(b->ev_stop[slot], s));
@@ -499,7 +525,8 @@ struct QmcServer {
     // device scratch one contract needs in a batch (tile sums + replicate sums)
     uint64_t bytes_of(const qmccpw_contract &c) const {
         const int n = c.option.d - 1;
-        const int P = 1 << (desc.precision >= QMCCPW_MIXED_TC_BF16X3 ? 7 : choose_tile_log2(desc.precision, n));
+        const int kp = contract_precision(desc.precision, c.construction);
+        const int P = 1 << (is_tc(kp) ? 7 : choose_tile_log2(kp, n));
         const uint64_t tiles = (c.N + P - 1) / P;
         return tiles * static_cast<uint64_t>(c.R) * 32u + static_cast<uint64_t>(c.R) * 40u + sizeof(ContractDev) + 16u;
     }
@@ -917,9 +944,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.construction = construction;
     c.tile_log2 = choose_tile_log2(precision, n);
     const int P = 1 << c.tile_log2;
-    int chunk_log2 = c.tile_log2;
-    while (chunk_log2 > 0 && static_cast<long>(n) * (P >> chunk_log2) < 2L * kThreads) --chunk_log2;
-    c.chunk_log2 = chunk_log2;
+    c.chunk_log2 = chunk_log2_for(n, c.tile_log2);
     c.R = R;
     c.tiles = static_cast<int32_t>((N + P - 1) / P);
     c.groups = kThreads / P;
@@ -1120,6 +1145,104 @@ int qmccpw_server_stop(qmccpw_plan_t plan) {
     plan->server = nullptr;
     delete sv;
     return QMCCPW_OK;
+}
+
+
+int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t construction, int32_t d, int32_t points_per_tile) {
+    g_last_error.clear();
+    if (!plan) return fail(QMCCPW_ERR_INVALID_ARG, "NULL plan");
+    if (precision != QMCCPW_FP64 && precision != QMCCPW_MIXED)
+        return fail(QMCCPW_ERR_INVALID_ARG, "tuning applies to the FP64 and MIXED CUDA-core kernels");
+    if (construction != QMCCPW_BB && construction != QMCCPW_PCA) return fail(QMCCPW_ERR_INVALID_ARG, "construction");
+    if (d < 1 || d > plan->d_max) return fail(QMCCPW_ERR_INVALID_ARG, "d outside the plan");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    const auto key = std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, construction, d);
+    if (points_per_tile == 0) {
+        plan->tuned_tile.erase(key);
+        return QMCCPW_OK;
+    }
+    int lg = 0;
+    while (lg < kMaxTileLog2 && (1 << lg) < points_per_tile) ++lg;
+    if ((1 << lg) != points_per_tile || points_per_tile < 32)
+        return fail(QMCCPW_ERR_INVALID_ARG, "points_per_tile must be a power of two in 32..256");
+    if (fused_smem_bytes(precision, d - 1, lg) > 200u * 1024u)
+        return fail(QMCCPW_ERR_INVALID_ARG, "tile too large for shared memory");
+    plan->tuned_tile[key] = lg;
+    return QMCCPW_OK;
+}
+
+int qmccpw_tuning_get(qmccpw_plan_t plan, int32_t precision, int32_t construction, int32_t d, int32_t *points_per_tile) {
+    g_last_error.clear();
+    if (!plan || !points_per_tile) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    if (d < 1 || d > plan->d_max) return fail(QMCCPW_ERR_INVALID_ARG, "d outside the plan");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    if (is_tc(precision)) {
+        *points_per_tile = 128;
+        return QMCCPW_OK;
+    }
+    auto it = plan->tuned_tile.find(std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, construction, d));
+    *points_per_tile = 1 << (it != plan->tuned_tile.end() ? it->second : choose_tile_log2(precision, d - 1));
+    return QMCCPW_OK;
+}
+
+int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t count, int32_t precision) {
+    g_last_error.clear();
+    if (!plan || !sample || count < 1) return fail(QMCCPW_ERR_INVALID_ARG, "NULL or empty sample");
+    if (precision != QMCCPW_FP64 && precision != QMCCPW_MIXED)
+        return fail(QMCCPW_ERR_INVALID_ARG, "tuning applies to the FP64 and MIXED CUDA-core kernels");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    QMC_CUDA(cudaSetDevice(plan->device));
+    cudaEvent_t e0, e1;
+    QMC_CUDA(cudaEventCreate(&e0));
+    QMC_CUDA(cudaEventCreate(&e1));
+    int rc = QMCCPW_OK;
+    std::map<std::pair<int, int>, bool> seen;
+    for (int i = 0; i < count && rc == QMCCPW_OK; ++i) {
+        const qmccpw_contract &src = sample[i];
+        rc = validate_contract(plan, src.option, src.market, src.N, src.R, src.construction, precision, false);
+        if (rc != QMCCPW_OK) break;
+        if (seen[std::make_pair(src.construction, src.option.d)]) continue;
+        seen[std::make_pair(src.construction, src.option.d)] = true;
+        const auto key = std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, src.construction, src.option.d);
+        plan->tuned_tile.erase(key);
+        const int base = choose_tile_log2(precision, src.option.d - 1);
+        // a workload of its own size: about 2^24 point-dates (2^21 in FP64)
+        qmccpw_contract c = src;
+        c.R = 4;
+        const uint64_t target = precision == QMCCPW_FP64 ? (1ull << 21) : (1ull << 24);
+        c.N = std::max<uint64_t>(1024, target / (4ull * static_cast<uint64_t>(c.option.d)));
+        int best = base;
+        float best_ms = 1e30f;
+        for (int lg = std::min(kMaxTileLog2, base + 1); lg >= std::max(5, base - 2) && rc == QMCCPW_OK; --lg) {
+            if (fused_smem_bytes(precision, c.option.d - 1, lg) > 200u * 1024u) continue;
+            plan->tuned_tile[key] = lg;
+            qmccpw_batch_s b;
+            b.buf = &plan->ws;
+            rc = batch_build(plan, &c, 1, precision, false, &b);
+            if (rc != QMCCPW_OK) break;
+            float times[3];
+            for (int rep = 0; rep < 4 && rc == QMCCPW_OK; ++rep) {
+                if (rep > 0) cudaEventRecord(e0, plan->stream);
+                rc = batch_enqueue(&b, plan->stream);
+                if (rep > 0) {
+                    cudaEventRecord(e1, plan->stream);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&times[rep - 1], e0, e1);
+                }
+            }
+            if (rc != QMCCPW_OK) break;
+            std::sort(times, times + 3);
+            if (times[1] < best_ms) {
+                best_ms = times[1];
+                best = lg;
+            }
+        }
+        plan->tuned_tile[key] = best;
+    }
+    cudaStreamSynchronize(plan->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 }  // extern "C"

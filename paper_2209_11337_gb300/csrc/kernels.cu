@@ -309,10 +309,24 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
             const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
             const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
             const int chunk = 1 << c.chunk_log2;
-            const int work = (P >> c.chunk_log2) * n;
-            for (int it = threadIdx.x; it < work; it += kThreads) {
-                const int j = it % n;
-                const int ch = it / n;
+            const int nchunks = P >> c.chunk_log2;
+            // n >= 32: a warp takes whole chunks, its lanes consecutive dimensions
+            // (stores to one row: no bank conflicts); smaller n: (chunk, dim) items
+            const bool by_warp = n >= 32;
+            const int step = by_warp ? kThreads / 32 : kThreads;
+            const int first = by_warp ? (threadIdx.x >> 5) : threadIdx.x;
+            const int work = by_warp ? nchunks * ((n + 31) >> 5) : nchunks * n;
+            for (int it = first; it < work; it += step) {
+                int j, ch;
+                if (by_warp) {
+                    const int per = (n + 31) >> 5;            // 32-wide dimension blocks per chunk
+                    ch = it / per;
+                    j = (it - ch * per) * 32 + (threadIdx.x & 31);
+                    if (j >= n) continue;
+                } else {
+                    j = it % n;
+                    ch = it / n;
+                }
                 const int slot = c.z_by_dim ? j + 1 : __ldg(&c.steps[j].m);
                 T *dst = zw + static_cast<size_t>(ch * chunk) * stride + slot;
                 // points at or past N (ragged last tile) are never generated: their

@@ -108,8 +108,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 
 // Instruction descriptor: FP32 accumulate, A and B of format `fmt`
 // (kind::f16: 1 = bf16; kind::tf32: 2 = tf32), both K-major, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(kNpad >> 3) << 17) |
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int n = kNpad) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
            (static_cast<uint32_t>(kM >> 4) << 24);
 }
 
@@ -150,10 +150,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // ---- operand element addressing ----------------------------------------------
 // Element (row, k) of a K-major operand with kNpad columns of ESIZE bytes:
 // core matrix (row/8, k/T) of 128 bytes, T = 16/ESIZE elements per row.
-template <int ESIZE>
+template <int ESIZE, int NPAD = kNpad>
 __device__ __forceinline__ uint32_t operand_offset(int row, int k) {
     constexpr int T = 16 / ESIZE;
-    return static_cast<uint32_t>(((row >> 3) * (kNpad / T) + k / T) * 128 + (row & 7) * 16 + (k % T) * ESIZE);
+    return static_cast<uint32_t>(((row >> 3) * (NPAD / T) + k / T) * 128 + (row & 7) * 16 + (k % T) * ESIZE);
 }
 
 // hi + lo split of a float for the 3-term product
@@ -176,7 +176,7 @@ __device__ __forceinline__ void split_store(unsigned char *hi_base, unsigned cha
     }
 }
 
-template <int KIND, int TYPE>
+template <int KIND, int TYPE, int NPAD = kNpad>
 __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float> &acc, int point) {
     const int warp = threadIdx.x >> 5;
     const int half = warp >> 2;                 // warpgroup: which half of the dates
@@ -185,8 +185,8 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
     const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
     acc.init(TYPE, half == 0);
 #pragma unroll
-    for (int blk = 0; blk < kNpad / 32; ++blk) {
-        const int col = half * (kNpad / 2) + blk * 16;
+    for (int blk = 0; blk < NPAD / 32; ++blk) {
+        const int col = half * (NPAD / 2) + blk * 16;
         float d[16];
         tmem_ld16(tmem + lane_base + static_cast<uint32_t>(col), d);
         const float s0 = static_cast<float>(col + 1) * dt;
@@ -208,7 +208,7 @@ struct TcShared {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 1) pca_tc_kernel(const __grid_constant__ LaunchParams p) {
+__global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_constant__ LaunchParams p) {
     constexpr int ES = KIND == 0 ? 2 : 4;                  // element bytes
     constexpr uint32_t kOpBytesZ = kM * kNpad * ES;        // one split part of Z
     constexpr uint32_t kOpBytesB = kNpad * kNpad * ES;     // one split part of Ahat
@@ -273,10 +273,22 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tc_kernel(const __grid_consta
         const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
         const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
         const int chunk = 1 << c.chunk_log2;
-        const int work = (kM >> c.chunk_log2) * n;
-        for (int it = threadIdx.x; it < work; it += kThreads) {
-            const int j = it % n;
-            const int ch = it / n;
+        const int nchunks = kM >> c.chunk_log2;
+        const bool by_warp = n >= 32;
+        const int step = by_warp ? kThreads / 32 : kThreads;
+        const int first = by_warp ? (threadIdx.x >> 5) : static_cast<int>(threadIdx.x);
+        const int work = by_warp ? nchunks * ((n + 31) >> 5) : nchunks * n;
+        for (int it = first; it < work; it += step) {
+            int j, ch;
+            if (by_warp) {
+                const int per = (n + 31) >> 5;
+                ch = it / per;
+                j = (it - ch * per) * 32 + (threadIdx.x & 31);
+                if (j >= n) continue;
+            } else {
+                j = it % n;
+                ch = it / n;
+            }
             const uint64_t first_local = tile * kM + static_cast<uint64_t>(ch) * chunk;
             const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
             const int row0 = ch * chunk;

@@ -216,6 +216,14 @@ __device__ __forceinline__ ff ff_of_double(double x) {
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
 
+// 1/x to ~1 ulp for positive normal x: the SFU approximation and one Newton
+// step (IEEE division expands to a longer sequence)
+__device__ __forceinline__ float rcp_f32(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * fmaf(-x, r, 2.0f);
+}
+
 __device__ __forceinline__ ff ff_mul_ff(ff a, ff b) {
     const float p = a.hi * b.hi;
     const float e = fmaf(a.hi, b.hi, -p);
@@ -240,9 +248,10 @@ __device__ __forceinline__ ff ln_ff(float x) {
     }
     const float num = m - 1.0f;                  // exact
     const ff den = ff_two_sum(m, 1.0f);          // m + 1, exact
-    const float q1 = __fdiv_rn(num, den.hi);
-    const float r = fmaf(-q1, den.hi, num) - q1 * den.lo;
-    const ff f = ff_fast_two_sum(q1, __fdiv_rn(r, den.hi));
+    const float inv = rcp_f32(den.hi);
+    const float q1 = num * inv;
+    const float r = fmaf(-q1, den.hi, num) - q1 * den.lo;  // the remainder corrects q1's rounding
+    const ff f = ff_fast_two_sum(q1, r * inv);
     const float f2 = f.hi * f.hi;
     float t = fmaf(f2, 1.0f / 11.0f, 1.0f / 9.0f);
     t = fmaf(t, f2, 1.0f / 7.0f);
@@ -278,7 +287,7 @@ __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[
         v[0] = ff_mul(ff_of(c.ff_disc), sf);
         v[1] = ff_mul(ff_of(c.ff_k_bin_delta), pdf);
         // D/(a X) + psi/sigma - sqrt(t1), then times e^{-rT} phi(psi)
-        ff br = ff_mul(ff_of(c.ff_inv_a), dhat / xhat);
+        ff br = ff_mul(ff_of(c.ff_inv_a), dhat * rcp_f32(xhat));
         br = ff_add(br, ff_mul_ff(psi, ff_of(c.ff_inv_sigma)));
         br = ff_add(br, ff_neg(ff_of(c.ff_sqrt_t1)));
         v[2] = ff_mul_ff(ff_mul(ff_of(c.ff_disc), pdf), br);
@@ -361,11 +370,11 @@ __device__ __forceinline__ void finish_functional(const ContractDev &c, const Pa
         xhat = acc.x;
         dhat = acc.dsum;
     } else if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-        const T inv_d = T(1) / static_cast<T>(c.d);
+        const T inv_d = static_cast<T>(c.inv_d);
         xhat = Arith<T>::ex(acc.x * inv_d);
         dhat = xhat * acc.dsum * inv_d;
     } else {
-        const T inv_d = T(1) / static_cast<T>(c.d);
+        const T inv_d = static_cast<T>(c.inv_d);
         xhat = acc.x * inv_d;
         dhat = acc.dsum * inv_d;
     }

@@ -88,6 +88,7 @@ struct ContractDev {
     double k_bin_gamma;                  // disc / (S0^2 a)
     double k_call_gamma;                 // disc K / (S0^2 a)
     double inv_sigma;
+    double inv_d;                        // 1/d
     // the same constants as float hi + lo pairs (float-float arithmetic of the mixed path)
     float ff_disc1_S0[2], ff_disc_K[2], ff_disc1[2], ff_disc_K_sqrt_t1[2], ff_k_call_gamma[2];
     float ff_disc[2], ff_k_bin_delta[2], ff_k_bin_gamma[2];

@@ -190,6 +190,7 @@ void contract_constants(ContractDev &c) {
     c.k_bin_gamma = c.disc / (c.S0 * c.S0 * c.a);
     c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
     c.inv_sigma = 1.0 / c.sigma;
+    c.inv_d = 1.0 / c.d;
     split_ff(c.disc1_S0, c.ff_disc1_S0);
     split_ff(c.disc_K, c.ff_disc_K);
     split_ff(c.disc1, c.ff_disc1);

@@ -54,7 +54,8 @@ EXPORTS = (
     "qmccpw_batch_launch_count", "qmccpw_batch_set_timing", "qmccpw_batch_timing",
     "qmccpw_batch_free", "qmccpw_sobol_points",
     "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_server_start", "qmccpw_submit", "qmccpw_poll",
-    "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_free", "qmccpw_last_error",
+    "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_autotune", "qmccpw_tuning_get",
+    "qmccpw_tuning_set", "qmccpw_free", "qmccpw_last_error",
     "qmccpw_version",
 )
 
@@ -138,6 +139,9 @@ def library() -> ctypes.CDLL:
             L.qmccpw_wait.argtypes = [vp, u64, i32, P(qmccpw_result)]
             L.qmccpw_server_get_stats.argtypes = [vp, P(qmccpw_server_stats)]
             L.qmccpw_server_stop.argtypes = [vp]
+            L.qmccpw_autotune.argtypes = [vp, P(qmccpw_contract), i32, i32]
+            L.qmccpw_tuning_get.argtypes = [vp, i32, i32, i32, P(i32)]
+            L.qmccpw_tuning_set.argtypes = [vp, i32, i32, i32, i32]
             L.qmccpw_free.argtypes = [vp]
             L.qmccpw_last_error.restype = ctypes.c_char_p
             L.qmccpw_version.restype = ctypes.c_char_p
@@ -332,6 +336,21 @@ def qmccpw_server_get_stats(plan) -> dict:
 
 def qmccpw_server_stop(plan) -> None:
     _check(library().qmccpw_server_stop(plan))
+
+
+def qmccpw_autotune(plan, sample: Sequence, precision: int = QMCCPW_MIXED) -> None:
+    arr = contract_array(sample)
+    _check(library().qmccpw_autotune(plan, arr, len(sample), precision))
+
+
+def qmccpw_tuning_get(plan, precision: int, construction: int, d: int) -> int:
+    out = ctypes.c_int32()
+    _check(library().qmccpw_tuning_get(plan, precision, construction, d, ctypes.byref(out)))
+    return out.value
+
+
+def qmccpw_tuning_set(plan, precision: int, construction: int, d: int, points_per_tile: int) -> None:
+    _check(library().qmccpw_tuning_set(plan, precision, construction, d, points_per_tile))
 
 
 def qmccpw_last_error() -> str:

@@ -70,7 +70,15 @@ def test_tc_repeatable_and_batch_equals_single(q, plan):
             assert np.array_equal(p0, p1)
 
 
-def test_tc_rejects_bridge_and_large_d(q, plan):
-    with pytest.raises(q.QmcCpwError) as e:
-        q.qmccpw_greeks(plan, 0, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 2, W.BB, 2)
-    assert e.value.code == q.QMCCPW_ERR_UNSUPPORTED
+def test_tc_precision_runs_bridge_contracts_as_mixed_and_rejects_large_d(q, plan):
+    c = W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 2, W.BB)
+    tc = q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, W.BB, 2)
+    mixed = q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, W.BB, q.QMCCPW_MIXED)
+    assert np.array_equal(tc[2], mixed[2])
+    big = q.qmccpw_plan(device=0, d_max=100, r_max=4, seed=SEED)
+    try:
+        with pytest.raises(q.QmcCpwError) as e:
+            q.qmccpw_greeks(big, 0, 100, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 2, W.PCA, 2)
+        assert e.value.code == q.QMCCPW_ERR_UNSUPPORTED
+    finally:
+        q.qmccpw_free(big)
