@@ -217,6 +217,80 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5, max_inf
             "precision": "fp64" if precision == 0 else "mixed"}
 
 
+def latency_small(q, plan, stream, calls: int) -> dict:
+    """The small case (arith, d=16, bridge, N=2^14, R=8, FP64): wall time of
+    one synchronous public call, of a prepared batch launch + wait, of its
+    CUDA-graph replay + wait, and the device time of one replay."""
+    import torch
+    c = W.small_arith()
+
+    def quantiles(ts):
+        ts = sorted(ts)
+        return {"p50_us": 1e6 * ts[len(ts) // 2], "p99_us": 1e6 * ts[min(len(ts) - 1, int(0.99 * len(ts)))]}
+
+    warm = 10
+    ts = []
+    for i in range(calls + warm):
+        t0 = time.perf_counter()
+        q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, c.construction, q.QMCCPW_FP64)
+        ts.append(time.perf_counter() - t0)
+    out = {"workload": "arith Asian call, d=16, bridge, N=2^14, R=8, FP64 (one contract)",
+           "sync_call": quantiles(ts[warm:])}
+    for mode in ("launch", "graph"):
+        b = q.Batch(plan, [c], q.QMCCPW_FP64)
+        if mode == "graph":
+            b.use_graph(True)
+        ts = []
+        for i in range(calls + warm):
+            t0 = time.perf_counter()
+            b.launch(stream.cuda_stream)
+            stream.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out[mode + "_and_wait"] = quantiles(ts[warm:])
+        b.set_timing(calls)
+        for _ in range(calls):
+            b.launch(stream.cuda_stream)
+        ms, n = b.timing()
+        out[mode + "_device_us"] = 1e3 * ms / max(1, n)
+        out[mode + "_kernels"] = b.launch_count()
+        b.free()
+    return out
+
+
+def pca_stress(q, local, rank, stream, steps: int) -> dict:
+    """d = 256 PCA (three products, N = 2^22, R = 16): CUDA-core MIXED and the
+    tensor-core precisions, device time per step; error against FP64 at
+    N = 2^16 (the same estimator on fewer points) in units of its SE."""
+    import torch
+    plan = q.qmccpw_plan(device=local, d_max=257, r_max=16, seed=W.SCRAMBLE_SEED + rank, stream=stream.cuda_stream)
+    full = W.pca_stress()
+    small = W.pca_stress(N=2 ** 16)
+    el = elements(full)
+    out = {"workload": "PCA d=256 (n=255), {arith,binary,lookback}, S0=K=100 sigma=0.2 r=0.05 T=1, N=2^22, R=16",
+           "point_dates": el}
+    ref = q.qmccpw_greeks_batch(plan, small, q.QMCCPW_FP64)
+    for name, prec in (("mixed", q.QMCCPW_MIXED), ("tc-bf16", q.QMCCPW_MIXED_TC_BF16X3),
+                       ("tc-tf32", q.QMCCPW_MIXED_TC_TF32X3)):
+        try:
+            b = q.Batch(plan, full, prec)
+        except q.QmcCpwError as e:
+            out[name] = {"unsupported": str(e)}
+            continue
+        b.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        b.set_timing(steps)
+        for _ in range(steps):
+            b.launch(stream.cuda_stream)
+        ms, n = b.timing()
+        b.free()
+        res = q.qmccpw_greeks_batch(plan, small, prec)
+        worst = max(abs(m[g] - m64[g]) / s64[g] for (m, _, _), (m64, s64, _) in zip(res, ref) for g in range(4))
+        out[name] = {"value": el / (ms / n / 1e3), "unit": UNIT, "fused_ms": ms / n,
+                     "max_err_in_se_vs_fp64_at_N_2^16": worst}
+    q.qmccpw_free(plan)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -351,7 +425,7 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: contracts in, results out
     def e2e_once():
-        return q.qmccpw_greeks_batch(plan, contracts, q.QMCCPW_MIXED)
+        return q.qmccpw_greeks_batch(plan, contracts, grid_prec)
 
     e2e_once()
     torch.cuda.synchronize()
@@ -399,7 +473,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "contracts": len(contracts), "d": 64, "N": 2 ** 20, "R": 32,
-                   "precision": "MIXED: inverse normal, path and payoff in f32; switch point and reductions in f64",
+                   "precision": {"mixed": "MIXED", "tc-bf16": "MIXED_TC_BF16X3",
+                                 "tc-tf32": "MIXED_TC_TF32X3"}[args.grid_precision] +
+                                ": inverse normal and path in f32; switch point and per-point values in "
+                                "float-float; tile and replicate sums in f64",
                    "point_dates_per_step": elems, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"dp{world} (independent contracts per GPU)"},
         "fp64": None if fp64 is None else {
@@ -456,6 +533,10 @@ def run_ours(args):
                                                       "ms_per_step": max_over_ranks(bms), "steps": args.book_steps},
                         "fp64_sample": {"contracts": 64, "value": elements(sample) / (f64ms / 1e3), "unit": UNIT,
                                         "ms": f64ms}}
+    if args.latency_calls > 0:
+        line["latency_small"] = latency_small(q, plan, stream, args.latency_calls)
+    if args.stress_steps > 0:
+        line["pca_stress"] = pca_stress(q, local, rank, stream, args.stress_steps)
     if args.serving_s > 0:
         splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED + rank)
         line["serving"] = {"mixed": serve(q, splan, q.QMCCPW_MIXED, args.serving_rate, args.serving_s)}
@@ -483,6 +564,8 @@ def main(argv=None):
                     help="precision of the timed grid (tc-*: PCA contracts on tensor cores)")
     ap.add_argument("--book-steps", type=int, default=1, help="timed steps of the 4096-contract book (0: skip)")
     ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of Poisson arrivals (0: skip)")
+    ap.add_argument("--latency-calls", type=int, default=200, help="calls timed in the small-case latency section")
+    ap.add_argument("--stress-steps", type=int, default=1, help="timed steps of the d=256 PCA case (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0)
     ap.add_argument("--errors-out", default=None, help="write the per-contract MIXED vs FP64 table (JSON)")
     ap.add_argument("--case", default=None, help="time one contract only, e.g. arith-bb or lookback-pca")

@@ -67,12 +67,15 @@ typedef enum {
 /* ---- arithmetic precision ----------------------------------------------- */
 typedef enum {
     QMCCPW_FP64 = 0,                 /* every step in double precision */
-    QMCCPW_MIXED = 1,                /* inverse normal, path and payoff in float; switch point psi in
-                                        double; per-point values summed in double */
-    QMCCPW_MIXED_TC_BF16X3 = 2,      /* MIXED with the PCA product on tensor cores, 3-term bf16 split
-                                        (d <= 65); bridge contracts run as MIXED */
-    QMCCPW_MIXED_TC_TF32X3 = 3       /* MIXED with the PCA product on tensor cores, 3-term tf32 split
-                                        (d <= 65); bridge contracts run as MIXED */
+    QMCCPW_MIXED = 1,                /* inverse normal and path in float; switch point psi and the
+                                        per-point values in float-float (about 44 bits); tile and
+                                        replicate sums in double */
+    QMCCPW_MIXED_TC_BF16X3 = 2,      /* MIXED with the PCA product on tensor cores in bf16: z in two
+                                        parts, Ahat in three, the leading parts on fixed grids
+                                        (exact hi x hi accumulation), five products (d <= 257);
+                                        bridge contracts run as MIXED */
+    QMCCPW_MIXED_TC_TF32X3 = 3       /* the same in tf32: z and Ahat in two parts, three products
+                                        (d <= 257); bridge contracts run as MIXED */
 } qmccpw_precision;
 
 typedef struct qmccpw_plan_s *qmccpw_plan_t;
@@ -134,8 +137,8 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc);
  * Estimate price, delta, vega and gamma of one contract with N points per
  * replicate and R replicates.  Synchronous: the result is in *out when the
  * call returns.  Path construction per `construction`, arithmetic per
- * `precision` (a tensor-core precision applies to PCA contracts with d <= 65
- * and runs bridge contracts as MIXED).
+ * `precision` (a tensor-core precision applies to PCA contracts with
+ * d <= 257 and runs bridge contracts as MIXED).
  * Errors: INVALID_ARG (d, R outside the plan; N = 0 or > 2^32; S0, K, T,
  * sigma not positive and finite; r not finite), UNSUPPORTED, OOM (workspace
  * budget), CUDA.
@@ -180,6 +183,17 @@ int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches);
  */
 int qmccpw_batch_set_timing(qmccpw_batch_t batch, int32_t capacity);
 int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches);
+/*
+ * CUDA-graph replay (launch-bound small batches; no counterpart in the
+ * paper): with enable != 0 the next qmccpw_batch_launch captures the batch's
+ * launch sequence (counter resets, fused grids, reduction, statistics) into
+ * a CUDA graph on a private stream, and every launch then replays it with
+ * one graph launch on the caller's stream.  The work and its results are
+ * the same as without the graph; timing events, if on, bracket the whole
+ * replay.  enable = 0 waits for the device and drops the graph.
+ * Errors: INVALID_ARG (NULL batch), CUDA (capture or instantiation failed).
+ */
+int qmccpw_batch_use_graph(qmccpw_batch_t batch, int32_t enable);
 int qmccpw_batch_free(qmccpw_batch_t batch);
 
 /*

@@ -266,6 +266,21 @@ int oracle_bridge(int n, double dt, const double *z, double *W)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Standard construction: the path the paper's simulation listing builds     */
+/* (Sec. 4.1-4.2), one independent increment per step,                       */
+/*   W~(s_i) = W~(s_{i-1}) + sqrt(dt) z_i,  i = 1..n,  W~(s_0) = 0,            */
+/* so Sobol' dimension i drives the increment of step i.                      */
+/* ------------------------------------------------------------------------ */
+int oracle_forward(int n, double dt, const double *z, double *W)
+{
+    if (n < 0 || !(dt > 0.0) || !W || (n > 0 && !z)) return -1;
+    const double h = sqrt(dt);
+    W[0] = 0.0;
+    for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + h * z[i - 1];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* PCA construction (named as future work in Sec. 6 / 7): W~ = A z with      */
 /* A A^T = Sigma, Sigma_ik = dt*min(i,k) (eq. WboldTilde with equal steps).   */
 /* For this matrix the eigenpairs are known in closed form:                   */
@@ -319,7 +334,7 @@ static int check_contract(const contract_t *c, int construction)
     if (c->d < 1 || c->d > MAX_DIMS) return -1;
     if (!(c->K > 0.0) || !(c->T > 0.0) || !(c->S0 > 0.0) || !(c->sigma > 0.0)) return -1;
     if (!isfinite(c->K) || !isfinite(c->T) || !isfinite(c->S0) || !isfinite(c->sigma) || !isfinite(c->r)) return -1;
-    if (construction != 0 && construction != 1) return -1;
+    if (construction < 0 || construction > 2) return -1;
     return 0;
 }
 
@@ -394,6 +409,7 @@ static int build_path(const contract_t *c, int construction, const double *A, co
     const int n = c->d - 1;
     const double t1 = c->T / c->d;
     if (construction == 0) return oracle_bridge(n, t1, z, W);
+    if (construction == 2) return oracle_forward(n, t1, z, W);
     return pca_apply(n, A, z, W);
 }
 

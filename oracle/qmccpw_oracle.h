@@ -15,7 +15,7 @@
  *   - option type: 0 arithmetic-Asian call, 1 binary-Asian (pays 1 if the
  *     arithmetic average exceeds K), 2 fixed-strike lookback call,
  *     3 geometric-Asian call (test-only product with a closed form).
- *   - construction: 0 Brownian bridge, 1 PCA.
+ *   - construction: 0 Brownian bridge, 1 PCA, 2 standard (forward increments).
  *   - value order of every 4-vector: price, delta, vega, gamma.
  *   - every int-returning function returns 0 on success, -1 on bad arguments.
  */
@@ -52,6 +52,9 @@ double oracle_inv_normal(double u);
 
 /* Brownian bridge: W[0..n] at s_i = i*dt from z[0..n-1] (z[0] drives s_n). */
 int oracle_bridge(int n, double dt, const double *z, double *W);
+
+/* Standard construction (Sec. 4.1-4.2 listing): W~(s_i) = W~(s_{i-1}) + sqrt(dt) z[i-1]. */
+int oracle_forward(int n, double dt, const double *z, double *W);
 
 /* PCA factor A (n x n, row-major) of Sigma_ik = dt*min(i,k): A = V diag(sqrt(lambda)). */
 int oracle_pca_matrix(int n, double dt, double *A);

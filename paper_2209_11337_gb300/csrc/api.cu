@@ -89,7 +89,7 @@ struct DTables {
     int n = 0;
     int n_levels = 0;
     DevBuf steps, w64, w32, level_start, pca64, pca32;
-    DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32), built on first use
+    DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32; resident or streamed form by n), built on first use
 };
 
 bool is_tc(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 || precision == QMCCPW_MIXED_TC_TF32X3; }
@@ -98,7 +98,19 @@ bool is_tc(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 || precis
 int contract_precision(int precision, int construction) {
     return (is_tc(precision) && construction == QMCCPW_BB) ? QMCCPW_MIXED : precision;
 }
-int tc_kind(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1; }
+// tensor-core kernel of a PCA contract with n dimensions: resident (n <= 64)
+// bf16 0 / tf32 1, streamed (n <= 256) bf16 2 / tf32 3
+int tc_kind(int precision, int n) {
+    const int base = precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1;
+    return n > pca_tc_max_n(base) ? base + 2 : base;
+}
+int tc_slot(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1; }
+// launch segment of a contract (kernel precision kp): 0 bridge, 1 PCA on the
+// streamed tensor-core kernel, 2 other PCA
+int segment_of(int kp, int construction, int n) {
+    if (construction == QMCCPW_BB) return 0;
+    return (is_tc(kp) && tc_kind(kp, n) >= 2) ? 1 : 2;
+}
 
 }  // namespace
 
@@ -134,9 +146,12 @@ struct qmccpw_batch_s {
     std::vector<int32_t> order;      // order[i] = caller's index of host[i]
     std::vector<int32_t> R;
     uint64_t items = 0, total_reps = 0;
-    uint64_t items_bb = 0;           // items [0, items_bb) use the bridge, the rest PCA
-    size_t smem[2] = {0, 0};         // per construction
-    int grid[2] = {0, 0};
+    // launch segments: items [0, items_bb) bridge, [items_bb, items_big) PCA
+    // on the streamed d <= 257 tensor-core kernel, the rest PCA on the kernel
+    // of the batch precision
+    uint64_t items_bb = 0, items_big = 0;
+    size_t smem[3] = {0, 0, 0};
+    int grid[3] = {0, 0, 0};
     BatchBuffers own;          // used by prepared batches
     BatchBuffers *buf = &own;  // one-shot calls point this at the plan's workspace
     // diagnostics
@@ -146,15 +161,24 @@ struct qmccpw_batch_s {
     // fused-kernel timing: event pairs of the most recent launches
     std::vector<cudaEvent_t> ev_start, ev_stop;
     int32_t timed = 0;  // launches recorded since the last read
+    // CUDA-graph replay (qmccpw_batch_use_graph): the launch sequence captured
+    // once on a private stream, then one graph launch per call
+    bool use_graph = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        graph_exec = nullptr;
+    }
     // forget the previous contracts, keep the device buffers for reuse
     void reset_meta() {
         count = 0;
         host.clear();
         order.clear();
         R.clear();
-        items = total_reps = items_bb = 0;
-        smem[0] = smem[1] = 0;
-        grid[0] = grid[1] = 0;
+        items = total_reps = items_bb = items_big = 0;
+        smem[0] = smem[1] = smem[2] = 0;
+        grid[0] = grid[1] = grid[2] = 0;
         point_out = nullptr;
         point_k0 = 0;
         rep_offset = 0;
@@ -162,6 +186,8 @@ struct qmccpw_batch_s {
     ~qmccpw_batch_s() {
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_stop) cudaEventDestroy(e);
+        drop_graph();
+        if (capture_stream) cudaStreamDestroy(capture_stream);
     }
 };
 
@@ -185,8 +211,12 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
         return fail(QMCCPW_ERR_INVALID_ARG, "construction out of range");
     if (precision < QMCCPW_FP64 || precision > QMCCPW_MIXED_TC_TF32X3)
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
-    if (precision >= QMCCPW_MIXED_TC_BF16X3 && construction == QMCCPW_PCA && o.d - 1 > pca_tc_npad())
-        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA supports d <= " + std::to_string(pca_tc_npad() + 1));
+    if (is_tc(precision) && construction == QMCCPW_PCA) {
+        const int kind = tc_kind(precision, o.d - 1);
+        if (o.d - 1 > pca_tc_max_n(kind))
+            return fail(QMCCPW_ERR_UNSUPPORTED,
+                        "tensor-core PCA supports d <= " + std::to_string(pca_tc_max_n(kind) + 1));
+    }
     return QMCCPW_OK;
 }
 
@@ -305,10 +335,10 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.pcaT32 = t->pca32.as<float>();
     if (is_tc(precision)) {
         DTables *mt = const_cast<DTables *>(t);
-        DevBuf &op = mt->tc[tc_kind(precision)];
+        DevBuf &op = mt->tc[tc_slot(precision)];
         if (!op.ptr) {
             std::vector<unsigned char> bytes;
-            pca_tc_operand(tc_kind(precision), c.n, pca_factor(c.n, 1.0), bytes);
+            pca_tc_operand(tc_kind(precision, c.n), c.n, pca_factor(c.n, 1.0), bytes);
             QMC_TRY(op.alloc(bytes.size()));
             QMC_CUDA(cudaMemcpy(op.ptr, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
         }
@@ -356,13 +386,15 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         const ContractDev &c = b->host[k];
         item_base[k] = items;
         items += static_cast<uint64_t>(c.R) * c.tiles;
-        if (in.construction == QMCCPW_BB) b->items_bb = items;
+        const int kp = contract_precision(precision, in.construction);
+        const int seg = segment_of(kp, in.construction, c.n);
+        if (seg == 0) b->items_bb = items;
+        if (seg <= 1) b->items_big = items;
         for (int r = 0; r < c.R; ++r) rep_owner.push_back(static_cast<uint64_t>(k));
         reps += c.R;
         b->R[k] = c.R;
-        size_t &sm = b->smem[in.construction == QMCCPW_BB ? 0 : 1];
-        const int kp = contract_precision(precision, in.construction);
-        sm = std::max(sm, is_tc(kp) ? pca_tc_smem_bytes(tc_kind(kp)) : fused_smem_bytes(kp, c.n, c.tile_log2));
+        size_t &sm = b->smem[seg];
+        sm = std::max(sm, is_tc(kp) ? pca_tc_smem_bytes(tc_kind(kp, c.n)) : fused_smem_bytes(kp, c.n, c.tile_log2));
     }
     b->items = items;
     b->total_reps = reps;
@@ -377,18 +409,20 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     QMC_TRY(B.tile_sums.ensure(scratch));
     QMC_TRY(B.per_rep.ensure(sizeof(double) * 4 * reps));
     QMC_TRY(B.stats.ensure(sizeof(double) * 8 * count));
-    QMC_TRY(B.counters.ensure(2 * sizeof(unsigned long long)));
+    QMC_TRY(B.counters.ensure(3 * sizeof(unsigned long long)));
     QMC_CUDA(cudaMemcpyAsync(B.contracts.ptr, b->host.data(), sizeof(ContractDev) * count, cudaMemcpyHostToDevice, st));
     QMC_CUDA(cudaMemcpyAsync(B.item_base.ptr, item_base.data(), sizeof(uint64_t) * count, cudaMemcpyHostToDevice, st));
     QMC_CUDA(cudaMemcpyAsync(B.rep_owner.ptr, rep_owner.data(), sizeof(uint64_t) * reps, cudaMemcpyHostToDevice, st));
     QMC_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
-    const uint64_t range[2] = {b->items_bb, items - b->items_bb};
-    for (int k = 0; k < 2; ++k) {
+    const uint64_t range[3] = {b->items_bb, b->items_big - b->items_bb, items - b->items_big};
+    for (int k = 0; k < 3; ++k) {
         if (range[k] == 0) continue;
         int per_sm = 0;
         const int kp = contract_precision(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA);
-        if (is_tc(kp))
-            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp), b->smem[k], &per_sm)));
+        if (k == 1)
+            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp, 256), b->smem[k], &per_sm)));
+        else if (is_tc(kp))
+            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp, 0), b->smem[k], &per_sm)));
         else
             QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(kp, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
         if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
@@ -398,7 +432,7 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     return QMCCPW_OK;
 }
 
-int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
+int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s, bool record_events = true) {
     qmccpw_plan_s *p = b->plan;
     const BatchBuffers &B = *b->buf;
     LaunchParams lp{};
@@ -413,19 +447,21 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s) {
     lp.point_out = b->point_out;
     lp.point_k0 = b->point_k0;
     lp.error_flag = p->err.as<int>();
-    const size_t cap = b->ev_start.size();
+    const size_t cap = record_events ? b->ev_start.size() : 0;
     const size_t slot = cap ? static_cast<size_t>(b->timed) % cap : 0;
     if (cap) QMC_CUDA(cudaEventRecord(b->ev_start[slot], s));
-    const uint64_t bounds[3] = {0, b->items_bb, b->items};
-    for (int k = 0; k < 2; ++k) {
+    const uint64_t bounds[4] = {0, b->items_bb, b->items_big, b->items};
+    for (int k = 0; k < 3; ++k) {
         if (bounds[k + 1] == bounds[k]) continue;
         lp.item_begin = bounds[k];
         lp.item_end = bounds[k + 1];
         lp.work_counter = B.counters.as<unsigned long long>() + k;
         QMC_CUDA(cudaMemsetAsync(lp.work_counter, 0, sizeof(unsigned long long), s));
         const int kp = contract_precision(b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA);
-        if (is_tc(kp))
-            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(kp), b->smem[k], b->grid[k], s)));
+        if (k == 1)
+            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(kp, 256), b->smem[k], b->grid[k], s)));
+        else if (is_tc(kp))
+            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(kp, 0), b->smem[k], b->grid[k], s)));
         else
             QMC_CUDA(static_cast<cudaError_t>(
                 launch_fused(lp, kp, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
@@ -716,7 +752,7 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
         QMC_CUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
         p->own_stream = true;
     }
-    for (int kind : {0, 1})
+    for (int kind : {0, 1, 2, 3})
         QMC_CUDA(static_cast<cudaError_t>(pca_tc_prepare(kind, pca_tc_smem_bytes(kind))));
     QMC_TRY(p->err.alloc(sizeof(int)));
     QMC_CUDA(cudaMemset(p->err.ptr, 0, sizeof(int)));
@@ -767,7 +803,44 @@ int qmccpw_batch_launch(qmccpw_batch_t batch, void *stream) {
     g_last_error.clear();
     if (!batch) return fail(QMCCPW_ERR_INVALID_ARG, "NULL batch");
     QMC_CUDA(cudaSetDevice(batch->plan->device));
-    return batch_enqueue(batch, stream ? static_cast<cudaStream_t>(stream) : batch->plan->stream);
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : batch->plan->stream;
+    if (!batch->use_graph) return batch_enqueue(batch, s);
+    if (!batch->graph_exec) {
+        if (!batch->capture_stream) QMC_CUDA(cudaStreamCreateWithFlags(&batch->capture_stream, cudaStreamNonBlocking));
+        QMC_CUDA(cudaStreamBeginCapture(batch->capture_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = batch_enqueue(batch, batch->capture_stream, false);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(batch->capture_stream, &g);
+        if (rc != QMCCPW_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        QMC_CUDA(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&batch->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        QMC_CUDA(ei);
+    }
+    const size_t cap = batch->ev_start.size();
+    const size_t slot = cap ? static_cast<size_t>(batch->timed) % cap : 0;
+    if (cap) QMC_CUDA(cudaEventRecord(batch->ev_start[slot], s));
+    QMC_CUDA(cudaGraphLaunch(batch->graph_exec, s));
+    if (cap) {
+        QMC_CUDA(cudaEventRecord(batch->ev_stop[slot], s));
+        ++batch->timed;
+    }
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_use_graph(qmccpw_batch_t batch, int32_t enable) {
+    g_last_error.clear();
+    if (!batch) return fail(QMCCPW_ERR_INVALID_ARG, "NULL batch");
+    QMC_CUDA(cudaSetDevice(batch->plan->device));
+    if (!enable) {
+        QMC_CUDA(cudaDeviceSynchronize());
+        batch->drop_graph();
+    }
+    batch->use_graph = enable != 0;
+    return QMCCPW_OK;
 }
 
 int qmccpw_batch_results(qmccpw_batch_t batch, qmccpw_result *out) {
@@ -789,8 +862,9 @@ int qmccpw_batch_device_results(qmccpw_batch_t batch, const double **per_replica
 int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches) {
     g_last_error.clear();
     if (!batch || !launches) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
-    // one fused grid per construction present, the per-replicate reduction, the statistics
-    *launches = (batch->items_bb > 0 ? 1 : 0) + (batch->items > batch->items_bb ? 1 : 0) + 2;
+    // one grid per launch segment present, the per-replicate reduction, the statistics
+    *launches = (batch->items_bb > 0 ? 1 : 0) + (batch->items_big > batch->items_bb ? 1 : 0) +
+                (batch->items > batch->items_big ? 1 : 0) + 2;
     return QMCCPW_OK;
 }
 

@@ -335,12 +335,8 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
                 const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
                 if (len > 0) {
                     const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
-                    uint32_t y = sobol_first(tab, p.jstride, j, __ldg(shf + j), k0);
-                    dst[0] = Arith<T>::inv_normal(y);
-                    for (int s = 1; s < len; ++s) {
-                        y ^= __ldg(tab + (__ffs(k0 + s) - 1) * p.jstride + j);
-                        dst[s * stride] = Arith<T>::inv_normal(y);
-                    }
+                    sobol_points(tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2,
+                                 [&](int s, uint32_t y) { dst[s * stride] = Arith<T>::inv_normal(y); });
                 }
                 for (int s = len; s < chunk; ++s) dst[s * stride] = T(0);
             }

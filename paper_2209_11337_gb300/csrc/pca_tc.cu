@@ -3,22 +3,48 @@
 // W~ = A z with A A^T = Sigma (eq. WboldTilde); for equal spacing
 // A = sqrt(dt) * Ahat where Ahat (the factor for dt = 1) depends on n only.
 // One CTA (256 threads) per work item of 128 points:
-//   1. Sobol' + inverse normal as in the CUDA-core kernel, but z is split
-//      into hi + lo parts (bf16 or tf32) written straight into the K-major
-//      canonical operand layout (8-row x 16-byte core matrices).
-//   2. One thread issues D = Z_hi Ahat_hi^T + Z_lo Ahat_hi^T + Z_hi Ahat_lo^T
-//      (the 3-term split product, FP32 accumulation in tensor memory),
-//      M = 128 points, N = 64 dates, K = 64 dimensions; Ahat hi/lo stays
-//      resident in shared memory (staged by a bulk TMA copy).
-//   3. The epilogue reads D with tcgen05.ld (warp w owns TMEM lanes
+//   1. Sobol' + inverse normal as in the CUDA-core kernel; z is split into
+//      hi + lo parts (bf16 or tf32) written straight into the operand layout
+//      (K-major, 128-byte swizzle, so a warp's stores hit distinct banks).
+//   2. One thread issues the split product with FP32 accumulation in tensor
+//      memory, M = 128 points, N = dates, K = dimensions: D1 = Z_hi Ahat_hi^T
+//      and D2 = the small products (tf32: Z_lo Ahat_hi^T + Z_hi Ahat_lo^T;
+//      bf16, Ahat in three parts: Z_lo Ahat_hi^T + Z_hi Ahat_mid^T +
+//      Z_lo Ahat_mid^T + Z_hi Ahat_lo^T).
+//   3. The epilogue reads D1 + D2 with tcgen05.ld (warp w owns TMEM lanes
 //      32(w%4)..+31, warpgroup w/4 one half of the columns), scales by
 //      sqrt(dt) and forms the path sums; then the conditional step and the
 //      tile sum exactly as in the CUDA-core kernel.
+// Exact leading product: the tensor core's FP32 accumulation does not round
+// to nearest, and a bias of ~1 ulp of |D| per instruction shifts every path
+// the same way (averaging over points does not remove it).  So the hi parts
+// lie on fixed grids (z: 2^-5 for bf16, 2^-8 for tf32, with |z| < 6.4 from
+// u >= 2^-33; Ahat: 2^-e with e the largest that keeps max|Ahat| 2^e within
+// the 8 or 11 significant bits), every product and partial sum of D1 is then
+// a multiple of one quantum and far below 2^24 quanta, and D1 is exact.  The
+// small terms go to their own accumulator D2, where the same ulp errors are
+// 2^-9 (tf32) to 2^-4 (bf16) of |W~| smaller.
+// Fixed matrix, random points: rounding z costs every point an independent,
+// zero-mean error that the average over points removes, but rounding Ahat
+// is one fixed perturbation of the factor, hence of the covariance of every
+// simulated path, and no number of points removes it.  A bf16 hi + lo pair
+// leaves Ahat off by up to 2^-15 (~2e-6 relative bias of the estimates at
+// d = 16..64, about ten standard errors on the d = 64 benchmark); so bf16
+// carries Ahat in three parts (hi on its grid, mid and lo each the bf16 of
+// what remains, ~2^-23), while tf32 keeps two (off by <= 2^-20, at the
+// float floor).  z keeps two parts in both: its rounding is new for every
+// point, and so is the product z_lo x Ahat_lo that tf32 leaves out (at most
+// 2^-18, zero-mean).
+// Two variants, each for bf16 and tf32: d <= 65 (N = K = 64; Ahat resident,
+// staged by one bulk TMA copy per contract) and d <= 257 (N = K = 256; Ahat
+// streamed from L2 in K-chunks, see pca_tcs_kernel).
 // Every wait on an mbarrier is bounded: on expiry the kernel records an
 // error code, releases its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -106,6 +132,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;  // base offset 0, relative LBO mode, no swizzle
 }
 
+// The same for a K-major operand with the 128-byte swizzle: rows of 128
+// bytes, 8-row atoms of 1024 bytes (1024-byte aligned), atoms of one K
+// column SBO = 1024 apart; layout type 2 in bits 61-63; LBO unused.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1) << 16;
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(2) << 61;
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulate, A and B of format `fmt`
 // (kind::f16: 1 = bf16; kind::tf32: 2 = tf32), both K-major, M = 128, N = 64.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int n = kNpad) {
@@ -135,69 +174,160 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 columns of D1 and of D2 for this warp's 32 lanes, one wait for both.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
+    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+        "[%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[16 + i]);
+    }
 }
 
 // ---- operand element addressing ----------------------------------------------
-// Element (row, k) of a K-major operand with kNpad columns of ESIZE bytes:
-// core matrix (row/8, k/T) of 128 bytes, T = 16/ESIZE elements per row.
+// Element (row, k) of a K-major operand without swizzle, NPAD columns of
+// ESIZE bytes: core matrix (row/8, k/T) of 128 bytes, T = 16/ESIZE.
 template <int ESIZE, int NPAD = kNpad>
 __device__ __forceinline__ uint32_t operand_offset(int row, int k) {
     constexpr int T = 16 / ESIZE;
     return static_cast<uint32_t>(((row >> 3) * (NPAD / T) + k / T) * 128 + (row & 7) * 16 + (k % T) * ESIZE);
 }
 
-// hi + lo split of a float for the 3-term product
+// Element (row, k) of Z (kM rows), K-major with the 128-byte swizzle: K
+// columns of 128 bytes each hold kM rows of 128 bytes; the 16-byte unit u of
+// row r sits at u ^ (r % 8).  With lanes over k a warp's stores cover whole
+// 128-byte rows, so they fall in distinct banks.
+template <int ESIZE>
+__device__ __forceinline__ uint32_t z_offset(int row, int k) {
+    const uint32_t kb = static_cast<uint32_t>(k) * ESIZE;
+    return (kb >> 7) * (kM * 128u) + static_cast<uint32_t>(row) * 128u +
+           ((((kb >> 4) & 7u) ^ (static_cast<uint32_t>(row) & 7u)) << 4) + (kb & 15u);
+}
+// Start of the K slice [kb, kb + 32 bytes) of Z for one instruction.
+__device__ __forceinline__ uint32_t z_slice(uint32_t base, uint32_t kb) { return base + (kb >> 7) * (kM * 128u) + (kb & 127u); }
+
+// hi + lo split of z: hi on the fixed grid (2^-5 bf16, 2^-8 tf32; rounding
+// by the add-and-subtract of 1.5 2^23, exact for |z| 2^8 < 2^22), so it is
+// exact in the operand type; lo = z - hi is exact in float, then rounded.
 template <int KIND>
 __device__ __forceinline__ void split_store(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, float z) {
+    constexpr float kScale = KIND == 0 ? 32.0f : 256.0f;
+    const float h = __fadd_rn(__fadd_rn(z * kScale, 12582912.0f), -12582912.0f) * (1.0f / kScale);
+    const float l = z - h;
     if constexpr (KIND == 0) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(z);
-        const __nv_bfloat16 l = __float2bfloat16_rn(z - __bfloat162float(h));
-        *reinterpret_cast<__nv_bfloat16 *>(hi_base + off) = h;
-        *reinterpret_cast<__nv_bfloat16 *>(lo_base + off) = l;
+        *reinterpret_cast<__nv_bfloat16 *>(hi_base + off) = __float2bfloat16_rn(h);
+        *reinterpret_cast<__nv_bfloat16 *>(lo_base + off) = __float2bfloat16_rn(l);
     } else {
         // tf32 keeps 10 explicit mantissa bits: round to nearest at bit 13
-        const uint32_t b = __float_as_uint(z);
-        const uint32_t hb = (b + 0x1000u) & 0xFFFFE000u;
-        const float h = __uint_as_float(hb);
-        const float l = z - h;
-        const uint32_t lb = (__float_as_uint(l) + 0x1000u) & 0xFFFFE000u;
-        *reinterpret_cast<uint32_t *>(hi_base + off) = hb;
-        *reinterpret_cast<uint32_t *>(lo_base + off) = lb;
+        *reinterpret_cast<uint32_t *>(hi_base + off) = __float_as_uint(h);
+        *reinterpret_cast<uint32_t *>(lo_base + off) = (__float_as_uint(l) + 0x1000u) & 0xFFFFE000u;
     }
 }
 
-template <int KIND, int TYPE, int NPAD = kNpad>
-__device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float> &acc, int point) {
+// Path sums of this thread's point over its warpgroup's half of the dates:
+// W~ = sqrt(dt) (D1 + D2), D2 at column offset NPAD.
+template <int TYPE, int NPAD>
+__device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float> &acc) {
     const int warp = threadIdx.x >> 5;
     const int half = warp >> 2;                 // warpgroup: which half of the dates
     const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
     const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
     const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
     acc.init(TYPE, half == 0);
-#pragma unroll
-    for (int blk = 0; blk < NPAD / 32; ++blk) {
-        const int col = half * (NPAD / 2) + blk * 16;
-        float d[16];
-        tmem_ld16(tmem + lane_base + static_cast<uint32_t>(col), d);
+    const int last = min(c.n, (half + 1) * (NPAD / 2));  // dates beyond n are padding
+#pragma unroll 1
+    for (int col = half * (NPAD / 2); col < last; col += 16) {
+        float d1[16], d2[16];
+        tmem_ld16x2(tmem + lane_base + static_cast<uint32_t>(col), tmem + lane_base + static_cast<uint32_t>(col + NPAD),
+                    d1, d2);
         const float s0 = static_cast<float>(col + 1) * dt;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int date = col + i + 1;  // W~ at s_date
+            const float w = d1[i] + d2[i];
             if (date <= c.n)
-                acc.template add<TYPE>(date, fmaf(d[i], sdt_hi, d[i] * sdt_lo), omega, sigma, fmaf(static_cast<float>(i), dt, s0));
+                acc.template add<TYPE>(date, fmaf(w, sdt_hi, w * sdt_lo), omega, sigma, fmaf(static_cast<float>(i), dt, s0));
         }
     }
-    (void)point;
+}
+
+template <int NPAD>
+__device__ __forceinline__ void epilogue_dispatch(const ContractDev &c, uint32_t tmem, PathAcc<float> &acc) {
+    switch (c.type) {
+        case QMCCPW_ARITH_ASIAN_CALL: epilogue_sums<QMCCPW_ARITH_ASIAN_CALL, NPAD>(c, tmem, acc); break;
+        case QMCCPW_BINARY_ASIAN: epilogue_sums<QMCCPW_BINARY_ASIAN, NPAD>(c, tmem, acc); break;
+        case QMCCPW_LOOKBACK_FIXED_CALL: epilogue_sums<QMCCPW_LOOKBACK_FIXED_CALL, NPAD>(c, tmem, acc); break;
+        default: epilogue_sums<QMCCPW_GEOMETRIC_ASIAN_CALL, NPAD>(c, tmem, acc); break;
+    }
+}
+
+// Merge the two warpgroups' partial sums of each point, the conditional step
+// and the tile sum (shared by both variants).
+__device__ __forceinline__ void finish_tile(const LaunchParams &p, const ContractDev &c, uint64_t item, uint64_t tile,
+                                           PathAcc<float> &acc, unsigned char *scratch) {
+    const int warp = threadIdx.x >> 5;
+    const int point = 32 * (warp & 3) + (threadIdx.x & 31);
+    stage_partial<float>(scratch, kM, warp >> 2, point, acc);
+    __syncthreads();
+    ff v[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    const uint64_t local_point = tile * kM + point;
+    if (warp < 4) {
+        merge_partials<float>(scratch, kM, 2, point, c.type, acc);
+        if (local_point < c.N) {
+            float xhat, dhat;
+            finish_functional(c, acc, xhat, dhat);
+            values_mixed(c, xhat, dhat, v);
+            if (p.point_out) {
+                double *o = p.point_out + local_point * 4;
+                for (int g = 0; g < 4; ++g) o[g] = ff_to_double(v[g]);
+            }
+        }
+    }
+    tile_sum(p, item, v, scratch);
+}
+
+// Phase 1 of both variants: Sobol' + inverse normal of the tile's points for
+// dimensions j0 <= j < j1, split and stored into Z at column j - j0.  A warp
+// takes a chunk of consecutive points and 32 dimensions (lanes over k);
+// points past N are 0.  Columns of Z at or beyond n are never rewritten: the
+// matching columns of Ahat are zero, so whatever finite z they hold adds 0.
+template <int KIND>
+__device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const ContractDev &c, uint32_t rep, uint64_t tile,
+                                           unsigned char *z_hi, unsigned char *z_lo, int j0, int j1) {
+    constexpr int ES = KIND == 0 ? 2 : 4;
+    const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
+    const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
+    const int chunk = 1 << c.chunk_log2;
+    const int nchunks = kM >> c.chunk_log2;
+    const int per = (j1 - j0 + 31) >> 5;
+    const int work = nchunks * per;
+    for (int it = threadIdx.x >> 5; it < work; it += kThreads / 32) {
+        const int ch = it / per;
+        const int j = j0 + (it - ch * per) * 32 + (threadIdx.x & 31);
+        if (j >= j1) continue;
+        const int col = j - j0;
+        const uint64_t first_local = tile * kM + static_cast<uint64_t>(ch) * chunk;
+        const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
+        const int row0 = ch * chunk;
+        if (len > 0) {
+            const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
+            sobol_points(tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2, [&](int s, uint32_t y) {
+                split_store<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), Arith<float>::inv_normal(y));
+            });
+        }
+        for (int s = len; s < chunk; ++s) split_store<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), 0.0f);
+    }
 }
 
 struct TcShared {
@@ -207,20 +337,27 @@ struct TcShared {
     int32_t abort;
 };
 
+// dynamic shared memory rounded up to the 1024-byte alignment of swizzled operands
+__device__ __forceinline__ unsigned char *aligned_smem(unsigned char *raw) {
+    const uint32_t a = smem_u32(raw);
+    return raw + (((a + 1023u) & ~1023u) - a);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_constant__ LaunchParams p) {
     constexpr int ES = KIND == 0 ? 2 : 4;                  // element bytes
     constexpr uint32_t kOpBytesZ = kM * kNpad * ES;        // one split part of Z
     constexpr uint32_t kOpBytesB = kNpad * kNpad * ES;     // one split part of Ahat
+    constexpr int kPartsB = KIND == 0 ? 3 : 2;             // Ahat parts: bf16 hi/mid/lo, tf32 hi/lo
     constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 1u : 2u);
     constexpr uint32_t kLbo = 128, kSbo = (kNpad / (16 / ES)) * 128;
+    constexpr uint32_t kCols = 2 * kNpad;                  // D1 and D2
 
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *z_hi = smem;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *z_hi = aligned_smem(smem_raw);
     unsigned char *z_lo = z_hi + kOpBytesZ;
-    unsigned char *b_hi = z_lo + kOpBytesZ;                // b_lo follows b_hi (one bulk copy)
-    unsigned char *b_lo = b_hi + kOpBytesB;
-    unsigned char *scratch = b_lo + kOpBytesB;             // partial sums, tile values
+    unsigned char *b_hi = z_lo + kOpBytesZ;                // the other parts follow (one bulk copy)
+    unsigned char *scratch = b_hi + kPartsB * kOpBytesB;   // partial sums, tile values
     __shared__ TcShared sh;
 
     const int warp = threadIdx.x >> 5;
@@ -231,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_consta
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(&sh.tmem_addr, kNpad);
+    if (warp == 0) tmem_alloc(&sh.tmem_addr, kCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -259,8 +396,8 @@ __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_consta
         __syncthreads();
         if (sh.loaded_n != n) {
             if (threadIdx.x == 0) {
-                mbar_expect_tx(&sh.bar_b, 2 * kOpBytesB);
-                bulk_copy_g2s(b_hi, c.tc_operand, 2 * kOpBytesB, &sh.bar_b);
+                mbar_expect_tx(&sh.bar_b, kPartsB * kOpBytesB);
+                bulk_copy_g2s(b_hi, c.tc_operand, kPartsB * kOpBytesB, &sh.bar_b);
             }
             if (!mbar_wait(&sh.bar_b, b_phase & 1u)) atomicExch(&sh.abort, 1);
             ++b_phase;
@@ -270,39 +407,7 @@ __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_consta
         if (sh.abort) break;
 
         // ---- phase 1: Sobol' + inverse normal -> split operand
-        const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
-        const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
-        const int chunk = 1 << c.chunk_log2;
-        const int nchunks = kM >> c.chunk_log2;
-        const bool by_warp = n >= 32;
-        const int step = by_warp ? kThreads / 32 : kThreads;
-        const int first = by_warp ? (threadIdx.x >> 5) : static_cast<int>(threadIdx.x);
-        const int work = by_warp ? nchunks * ((n + 31) >> 5) : nchunks * n;
-        for (int it = first; it < work; it += step) {
-            int j, ch;
-            if (by_warp) {
-                const int per = (n + 31) >> 5;
-                ch = it / per;
-                j = (it - ch * per) * 32 + (threadIdx.x & 31);
-                if (j >= n) continue;
-            } else {
-                j = it % n;
-                ch = it / n;
-            }
-            const uint64_t first_local = tile * kM + static_cast<uint64_t>(ch) * chunk;
-            const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
-            const int row0 = ch * chunk;
-            if (len > 0) {
-                const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
-                uint32_t y = sobol_first(tab, p.jstride, j, __ldg(shf + j), k0);
-                split_store<KIND>(z_hi, z_lo, operand_offset<ES>(row0, j), Arith<float>::inv_normal(y));
-                for (int s = 1; s < len; ++s) {
-                    y ^= __ldg(tab + (__ffs(k0 + s) - 1) * p.jstride + j);
-                    split_store<KIND>(z_hi, z_lo, operand_offset<ES>(row0 + s, j), Arith<float>::inv_normal(y));
-                }
-            }
-            for (int s = len; s < chunk; ++s) split_store<KIND>(z_hi, z_lo, operand_offset<ES>(row0 + s, j), 0.0f);
-        }
+        sobol_to_z<KIND>(p, c, rep, tile, z_hi, z_lo, 0, n);
         fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
         tc_fence_before();
         __syncthreads();
@@ -310,19 +415,22 @@ __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_consta
 
         // ---- phase 2: the split product into tensor memory
         if (threadIdx.x == 0) {
-            const uint32_t za[2] = {smem_u32(z_hi), smem_u32(z_lo)};
-            const uint32_t ba[2] = {smem_u32(b_hi), smem_u32(b_lo)};
-            const int pa[3] = {0, 1, 0}, pb[3] = {0, 0, 1};  // (hi,hi), (lo,hi), (hi,lo)
-            uint32_t accum = 0;
+            const uint32_t bh = smem_u32(b_hi), b2 = bh + kOpBytesB, b3 = b2 + kOpBytesB;
 #pragma unroll
-            for (int t = 0; t < 3; ++t)
-#pragma unroll
-                for (int ks = 0; ks < kNpad / (32 / ES); ++ks) {  // K per instruction: 16 bf16 or 8 tf32 = 32 bytes
-                    const uint32_t koff = static_cast<uint32_t>(ks) * 256u;
-                    mma<KIND>(tmem, smem_desc(za[pa[t]] + koff, kLbo, kSbo), smem_desc(ba[pb[t]] + koff, kLbo, kSbo),
-                              kIdesc, accum);
-                    accum = 1;
+            for (int ks = 0; ks < kNpad / (32 / ES); ++ks) {  // K per instruction: 16 bf16 or 8 tf32 = 32 bytes
+                const uint32_t kb = static_cast<uint32_t>(ks) * 32u;     // Z: byte offset along K
+                const uint32_t koff = static_cast<uint32_t>(ks) * 256u;  // Ahat: two core matrices along K
+                const uint64_t zh = smem_desc_sw128(z_slice(smem_u32(z_hi), kb));
+                const uint64_t zl = smem_desc_sw128(z_slice(smem_u32(z_lo), kb));
+                const uint32_t acc = ks > 0 ? 1u : 0u;
+                mma<KIND>(tmem, zh, smem_desc(bh + koff, kLbo, kSbo), kIdesc, acc);
+                mma<KIND>(tmem + kNpad, zl, smem_desc(bh + koff, kLbo, kSbo), kIdesc, acc);
+                mma<KIND>(tmem + kNpad, zh, smem_desc(b2 + koff, kLbo, kSbo), kIdesc, 1u);
+                if constexpr (KIND == 0) {  // bf16: Ahat mid is b2, lo is b3
+                    mma<KIND>(tmem + kNpad, zl, smem_desc(b2 + koff, kLbo, kSbo), kIdesc, 1u);
+                    mma<KIND>(tmem + kNpad, zh, smem_desc(b3 + koff, kLbo, kSbo), kIdesc, 1u);
                 }
+            }
             mma_commit(&sh.bar_mma);
         }
         if (!mbar_wait(&sh.bar_mma, mma_phase & 1u)) atomicExch(&sh.abort, 1);
@@ -331,31 +439,9 @@ __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_consta
 
         // ---- phase 3: path sums from D, merged across the two warpgroups
         PathAcc<float> acc;
-        const int point = 32 * (warp & 3) + (threadIdx.x & 31);
-        switch (c.type) {
-            case QMCCPW_ARITH_ASIAN_CALL: epilogue_sums<KIND, QMCCPW_ARITH_ASIAN_CALL>(c, tmem, acc, point); break;
-            case QMCCPW_BINARY_ASIAN: epilogue_sums<KIND, QMCCPW_BINARY_ASIAN>(c, tmem, acc, point); break;
-            case QMCCPW_LOOKBACK_FIXED_CALL: epilogue_sums<KIND, QMCCPW_LOOKBACK_FIXED_CALL>(c, tmem, acc, point); break;
-            default: epilogue_sums<KIND, QMCCPW_GEOMETRIC_ASIAN_CALL>(c, tmem, acc, point); break;
-        }
+        epilogue_dispatch<kNpad>(c, tmem, acc);
         tc_fence_before();
-        stage_partial<float>(scratch, kM, warp >> 2, point, acc);
-        __syncthreads();
-        ff v[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-        const uint64_t local_point = tile * kM + point;
-        if (warp < 4) {
-            merge_partials<float>(scratch, kM, 2, point, c.type, acc);
-            if (local_point < c.N) {
-                float xhat, dhat;
-                finish_functional(c, acc, xhat, dhat);
-                values_mixed(c, xhat, dhat, v);
-                if (p.point_out) {
-                    double *o = p.point_out + local_point * 4;
-                    for (int g = 0; g < 4; ++g) o[g] = ff_to_double(v[g]);
-                }
-            }
-        }
-        tile_sum(p, item, v, scratch);
+        finish_tile(p, c, item, tile, acc, scratch);
     }
 
     // release tensor memory (also after an abort)
@@ -364,76 +450,320 @@ __global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_consta
     if (sh.abort && threadIdx.x == 0 && p.error_flag) atomicExch(p.error_flag, QMCCPW_ERR_TIMEOUT);
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, kNpad);
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// d up to 257 (N = K = 256), Ahat streamed.  Ahat (384 KB bf16 in three
+// parts, 512 KB tf32 in two) does not fit beside Z, so it comes from L2 in
+// K-chunks of 16 dimensions (all parts of a chunk in one bulk TMA copy, 24 or
+// 32 KB) through two buffers.
+// A buffer is refilled once the products that read it have completed
+// (tcgen05.commit to its release barrier), one chunk behind the issue front,
+// and the first two chunks of the next tile are fetched while the epilogue
+// of this one runs; only the chunks that hold dimensions below n are used.
+// Z hi/lo stays resident: all 256 columns for bf16 (128 KB); for tf32 the
+// same 128 KB holds 128 columns, so Z is generated in two K-halves, the
+// second after the products of the first are done.  D1 and D2 take all 512
+// TMEM columns: one CTA per SM.
+constexpr int kNbig = 256;
+
+template <int KIND> struct Streamed {
+    static constexpr int ES = KIND == 0 ? 2 : 4;
+    static constexpr int Kc = 16;                          // K per chunk
+    static constexpr int Kz = KIND == 0 ? 256 : 128;       // Z columns resident at a time
+    static constexpr int Parts = KIND == 0 ? 3 : 2;        // Ahat parts
+    static constexpr uint32_t ZPart = kM * Kz * ES;        // one split part of Z
+    static constexpr uint32_t ChunkPart = kNbig * Kc * ES; // one part of one chunk (8 or 16 KB)
+    static constexpr uint32_t ChunkBytes = Parts * ChunkPart;  // 24 KB bf16, 32 KB tf32
+};
+
+struct TcSharedS {
+    uint64_t bar_b[2], bar_f[2], bar_mma;
+    uint32_t tmem_addr;
+    int32_t abort;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_constant__ LaunchParams p) {
+    using S = Streamed<KIND>;
+    constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 1u : 2u, kNbig);
+    constexpr uint32_t kLbo = 128;
+    constexpr uint32_t kSboB = (S::Kc * S::ES / 16) * 128;  // 8-row groups of a chunk
+    constexpr uint32_t kCols = 2 * kNbig;
+    constexpr int kSteps = S::Kc * S::ES / 32;             // instructions (32 bytes of K) per chunk
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *z_hi = aligned_smem(smem_raw);
+    unsigned char *z_lo = z_hi + S::ZPart;
+    unsigned char *bbuf = z_lo + S::ZPart;                 // two chunk buffers
+    unsigned char *scratch = bbuf + 2 * S::ChunkBytes;
+    __shared__ TcSharedS sh;
+    __shared__ uint64_t next_item;
+
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sh.bar_b[i], 1);
+            mbar_init(&sh.bar_f[i], 1);
+        }
+        mbar_init(&sh.bar_mma, 1);
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&sh.tmem_addr, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh.tmem_addr;
+    for (uint32_t i = threadIdx.x; i < 2 * S::ZPart / 4; i += kThreads) reinterpret_cast<uint32_t *>(z_hi)[i] = 0u;
+
+    // barrier phases and the chunk pipeline are thread 0's alone; chunk q of
+    // the CTA's running sequence uses buffer q & 1
+    uint32_t b_ph[2] = {0, 0}, f_ph[2] = {0, 0}, mma_ph = 0;
+    uint64_t q = 0;                // running index of the next chunk to consume
+    const void *loaded = nullptr;  // operand whose next two chunks are in flight or resident
+    bool ok = true;                // thread 0: no wait has expired
+    auto fetch = [&](const void *op, int chunk, int buf) {
+        mbar_expect_tx(&sh.bar_b[buf], S::ChunkBytes);
+        bulk_copy_g2s(bbuf + buf * S::ChunkBytes, static_cast<const unsigned char *>(op) + chunk * S::ChunkBytes,
+                      S::ChunkBytes, &sh.bar_b[buf]);
+    };
+    auto wait_b = [&](int buf) {
+        ok = ok && mbar_wait(&sh.bar_b[buf], b_ph[buf] & 1u);
+        ++b_ph[buf];
+    };
+    auto wait_f = [&](int buf) {
+        ok = ok && mbar_wait(&sh.bar_f[buf], f_ph[buf] & 1u);
+        ++f_ph[buf];
+    };
+
+    while (true) {
+        // the stop decision travels with the item: written by thread 0 only
+        // here, read by all after the barrier (an expired wait stops the loop)
+        if (threadIdx.x == 0) next_item = sh.abort ? p.item_end : p.item_begin + atomicAdd(p.work_counter, 1ull);
+        __syncthreads();
+        const uint64_t item = next_item;
+        if (item >= p.item_end) break;
+        const int ci = find_contract(p.item_base, p.count, item);
+        const ContractDev &c = p.contracts[ci];
+        const uint64_t local = item - c.item_base;
+        const uint32_t rep = static_cast<uint32_t>(local / static_cast<uint64_t>(c.tiles)) + p.rep_offset;
+        const uint64_t tile = local % static_cast<uint64_t>(c.tiles);
+        const int nch = (c.n + S::Kc - 1) / S::Kc;        // chunks holding dimensions below n (>= 5)
+        if (threadIdx.x == 0 && ok && loaded != c.tc_operand) {
+            // first tile, or a contract with another d: let the prefetch of
+            // the previous operand land, then fetch this one's chunks 0 and 1
+            if (loaded != nullptr) {
+                wait_b(q & 1);
+                wait_b((q + 1) & 1);
+            }
+            if (ok) {
+                fetch(c.tc_operand, 0, q & 1);
+                fetch(c.tc_operand, 1, (q + 1) & 1);
+                loaded = c.tc_operand;
+            } else {
+                sh.abort = 1;
+            }
+        }
+
+        for (int j0 = 0; j0 < c.n; j0 += S::Kz) {
+            if (j0 > 0) {
+                // Z is rewritten: the products of the previous half must be done
+                if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 1);
+                ++mma_ph;
+                tc_fence_after();
+                __syncthreads();
+            }
+            // ---- phase 1: Sobol' + inverse normal -> split Z, columns j0..
+            sobol_to_z<KIND>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+
+            // ---- phase 2: the chunks of this half; 3 (tf32) or 4 (bf16) products per k-step
+            if (threadIdx.x == 0) {
+                const int c_end = min(nch, (j0 + S::Kz) / S::Kc);
+                for (int cc = j0 / S::Kc; cc < c_end && ok; ++cc, ++q) {
+                    const int buf = static_cast<int>(q & 1);
+                    wait_b(buf);
+                    if (!ok) break;
+                    const uint32_t bh = smem_u32(bbuf + buf * S::ChunkBytes), b2 = bh + S::ChunkPart,
+                                   b3 = b2 + S::ChunkPart;
+#pragma unroll
+                    for (int ks = 0; ks < kSteps; ++ks) {
+                        const uint32_t kb = static_cast<uint32_t>((cc * S::Kc - j0) * S::ES + ks * 32);  // Z byte offset
+                        const uint32_t koff = static_cast<uint32_t>(ks) * 256u;                       // chunk: two core matrices
+                        const uint64_t zh = smem_desc_sw128(z_slice(smem_u32(z_hi), kb));
+                        const uint64_t zl = smem_desc_sw128(z_slice(smem_u32(z_lo), kb));
+                        const uint32_t acc = (cc | ks) ? 1u : 0u;
+                        mma<KIND>(tmem, zh, smem_desc(bh + koff, kLbo, kSboB), kIdesc, acc);
+                        mma<KIND>(tmem + kNbig, zl, smem_desc(bh + koff, kLbo, kSboB), kIdesc, acc);
+                        mma<KIND>(tmem + kNbig, zh, smem_desc(b2 + koff, kLbo, kSboB), kIdesc, 1u);
+                        if constexpr (KIND == 0) {  // bf16: Ahat mid is b2, lo is b3
+                            mma<KIND>(tmem + kNbig, zl, smem_desc(b2 + koff, kLbo, kSboB), kIdesc, 1u);
+                            mma<KIND>(tmem + kNbig, zh, smem_desc(b3 + koff, kLbo, kSboB), kIdesc, 1u);
+                        }
+                    }
+                    mma_commit(&sh.bar_f[buf]);
+                    if (cc >= 1) {
+                        // chunk cc-1's products are done with their buffer: refill it
+                        // with chunk cc+1 (chunk 0 of the next tile after the last)
+                        wait_f(buf ^ 1);
+                        if (ok) fetch(c.tc_operand, (cc + 1) % nch, buf ^ 1);
+                    }
+                }
+                if (ok && c_end == nch) {
+                    wait_f(static_cast<int>((q - 1) & 1));  // the last chunk's products: then chunk 1 of the next tile
+                    if (ok) fetch(c.tc_operand, 1, static_cast<int>((q + 1) & 1));
+                }
+                mma_commit(&sh.bar_mma);  // arrives when every product issued above is done
+                if (!ok) sh.abort = 1;
+            }
+        }
+        if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 1);
+        ++mma_ph;
+        tc_fence_after();
+
+        // ---- phase 3: path sums from D1 + D2, then values and the tile sum
+        PathAcc<float> acc;
+        epilogue_dispatch<kNbig>(c, tmem, acc);
+        tc_fence_before();
+        finish_tile(p, c, item, tile, acc, scratch);
+    }
+
+    // the prefetched chunks must land before the CTA exits
+    if (threadIdx.x == 0 && ok && loaded != nullptr) {
+        wait_b(q & 1);
+        wait_b((q + 1) & 1);
+        if (!ok) sh.abort = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (sh.abort && threadIdx.x == 0 && p.error_flag) atomicExch(p.error_flag, QMCCPW_ERR_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
     }
 }
 
 }  // namespace
 
 size_t pca_tc_smem_bytes(int kind) {
-    const size_t es = kind == 0 ? 2 : 4;
-    const size_t ops = 2 * kM * kNpad * es + 2 * kNpad * kNpad * es;
     const size_t scratch = 4 * kThreads * sizeof(double) > 4 * kThreads * 12 ? 4 * kThreads * sizeof(double)
                                                                             : 4 * kThreads * 12;
-    return ops + scratch;
+    if (kind == 2) return 1024 + 2 * static_cast<size_t>(Streamed<0>::ZPart) + 2 * Streamed<0>::ChunkBytes + scratch;
+    if (kind == 3) return 1024 + 2 * static_cast<size_t>(Streamed<1>::ZPart) + 2 * Streamed<1>::ChunkBytes + scratch;
+    const size_t es = kind == 0 ? 2 : 4, parts = kind == 0 ? 3 : 2;
+    return 1024 + 2 * kM * kNpad * es + parts * kNpad * kNpad * es + scratch;
 }
 
-int pca_tc_npad() { return kNpad; }
+int pca_tc_max_n(int kind) { return kind >= 2 ? kNbig : kNpad; }
 
 int pca_tc_prepare(int kind, size_t smem_bytes) {
-    cudaError_t e = kind == 0 ? cudaFuncSetAttribute(pca_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     static_cast<int>(smem_bytes))
-                              : cudaFuncSetAttribute(pca_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     static_cast<int>(smem_bytes));
+    const int b = static_cast<int>(smem_bytes);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = kind == 0   ? cudaFuncSetAttribute(pca_tc_kernel<0>, a, b)
+                    : kind == 1 ? cudaFuncSetAttribute(pca_tc_kernel<1>, a, b)
+                    : kind == 2 ? cudaFuncSetAttribute(pca_tcs_kernel<0>, a, b)
+                                : cudaFuncSetAttribute(pca_tcs_kernel<1>, a, b);
     return static_cast<int>(e);
 }
 
+// Resident CTAs per SM from the kernel's resources: shared memory (dynamic,
+// static and the per-block reservation), registers (allocated per warp in
+// units of 256), threads and tensor-memory columns (D1 + D2 of every
+// resident CTA within the SM's 512).  The runtime's occupancy query gave one
+// CTA per SM for these kernels (a 152-CTA grid on 152 SMs) where the
+// profiler's launch statistics show room for three, so the count is formed
+// here; a grid larger than fits would only queue, the work list is dynamic.
 int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks) {
-    cudaError_t e = kind == 0
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pca_tc_kernel<0>, kThreads, smem_bytes)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pca_tc_kernel<1>, kThreads, smem_bytes);
-    return static_cast<int>(e);
+    cudaFuncAttributes fa{};
+    cudaError_t e = kind == 0   ? cudaFuncGetAttributes(&fa, pca_tc_kernel<0>)
+                    : kind == 1 ? cudaFuncGetAttributes(&fa, pca_tc_kernel<1>)
+                    : kind == 2 ? cudaFuncGetAttributes(&fa, pca_tcs_kernel<0>)
+                                : cudaFuncGetAttributes(&fa, pca_tcs_kernel<1>);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return static_cast<int>(e);
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+        return static_cast<int>(e);
+    const size_t per_block = smem_bytes + fa.sharedSizeBytes + static_cast<size_t>(reserved);
+    const int by_smem = static_cast<int>(static_cast<size_t>(smem_sm) / per_block);
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_warp > 0 ? (regs_sm / regs_warp) / (kThreads / 32) : 0;
+    const int by_threads = threads_sm / kThreads;
+    const int by_tmem = 512 / (kind >= 2 ? 2 * kNbig : 2 * kNpad);
+    *blocks = std::max(0, std::min(std::min(by_smem, by_regs), std::min(by_threads, by_tmem)));
+    return 0;
 }
 
 int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (kind == 0) pca_tc_kernel<0><<<grid, kThreads, smem_bytes, s>>>(p);
-    else pca_tc_kernel<1><<<grid, kThreads, smem_bytes, s>>>(p);
+    else if (kind == 1) pca_tc_kernel<1><<<grid, kThreads, smem_bytes, s>>>(p);
+    else if (kind == 2) pca_tcs_kernel<0><<<grid, kThreads, smem_bytes, s>>>(p);
+    else pca_tcs_kernel<1><<<grid, kThreads, smem_bytes, s>>>(p);
     return static_cast<int>(cudaGetLastError());
 }
 
-// Host: Ahat = A / sqrt(dt) (the factor for unit spacing), split into hi + lo
-// of the operand type and laid out K-major in 8 x 16-byte core matrices.
+// Host: Ahat = A / sqrt(dt) (the factor for unit spacing) split into parts
+// of the operand type: hi = Ahat rounded to the grid 2^-e, e the largest
+// with max|Ahat| 2^e <= 2^8 - 1/2 (bf16) or 2^11 - 1/2 (tf32), so hi is exact
+// in the operand type and hi x z_hi products accumulate exactly; tf32: lo =
+// the rest, rounded; bf16: mid = the rest rounded to bf16, lo = what mid
+// leaves, rounded.  Layout K-major without swizzle in 8 x 16-byte core
+// matrices: kinds 0 and 1 one 64 x 64 block per part, parts in order; kinds
+// 2 and 3 K-chunks of 16 dimensions, each chunk all parts (256 x 16 each) in
+// order, so one bulk copy brings a whole chunk.
 void pca_tc_operand(int kind, int n, const std::vector<double> &A_unit, std::vector<unsigned char> &out) {
-    const int es = kind == 0 ? 2 : 4;
+    const bool tf32 = kind == 1 || kind == 3;
+    const int es = tf32 ? 4 : 2;
+    const int parts = tf32 ? 2 : 3;
     const int T = 16 / es;
-    const size_t part = static_cast<size_t>(kNpad) * kNpad * es;
-    out.assign(2 * part, 0);
-    auto offset = [&](int row, int k) {
-        return static_cast<size_t>(((row >> 3) * (kNpad / T) + k / T) * 128 + (row & 7) * 16 + (k % T) * es);
+    const int npad = pca_tc_max_n(kind);
+    const int kc = Streamed<0>::Kc;
+    const size_t part_bytes = kind >= 2 ? static_cast<size_t>(npad) * kc * es : static_cast<size_t>(npad) * npad * es;
+    out.assign(static_cast<size_t>(parts) * npad * npad * es, 0);
+    double amax = 0.0;
+    for (double a : A_unit) amax = std::max(amax, std::fabs(a));
+    const double lim = tf32 ? 2047.5 : 255.5;
+    const int e = amax > 0.0 ? static_cast<int>(std::floor(std::log2(lim / amax))) : 0;
+    const double scale = std::ldexp(1.0, e);
+    auto offset = [&](int row, int k, int part) -> size_t {
+        if (kind >= 2) {
+            const int c = k / kc, kk = k % kc;
+            return (static_cast<size_t>(c) * parts + part) * part_bytes +
+                   static_cast<size_t>(((row >> 3) * (kc / T) + kk / T) * 128 + (row & 7) * 16 + (kk % T) * es);
+        }
+        return part * part_bytes +
+               static_cast<size_t>(((row >> 3) * (npad / T) + k / T) * 128 + (row & 7) * 16 + (k % T) * es);
     };
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < n; ++k) {
             const double a = A_unit[static_cast<size_t>(i) * n + k];
-            const size_t off = offset(i, k);
-            if (kind == 0) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(static_cast<float>(a));
-                const __nv_bfloat16 l = __float2bfloat16_rn(static_cast<float>(a - static_cast<double>(__bfloat162float(h))));
-                std::memcpy(&out[off], &h, 2);
-                std::memcpy(&out[part + off], &l, 2);
+            const double h = std::nearbyint(a * scale) / scale;  // exact in 8 (11) significant bits
+            if (!tf32) {
+                const __nv_bfloat16 hb = __float2bfloat16_rn(static_cast<float>(h));
+                const __nv_bfloat16 mb = __float2bfloat16_rn(static_cast<float>(a - h));
+                const __nv_bfloat16 lb =
+                    __float2bfloat16_rn(static_cast<float>(a - h - static_cast<double>(__bfloat162float(mb))));
+                std::memcpy(&out[offset(i, k, 0)], &hb, 2);
+                std::memcpy(&out[offset(i, k, 1)], &mb, 2);
+                std::memcpy(&out[offset(i, k, 2)], &lb, 2);
             } else {
-                const float af = static_cast<float>(a);
-                uint32_t b;
-                std::memcpy(&b, &af, 4);
-                const uint32_t hb = (b + 0x1000u) & 0xFFFFE000u;
-                float h;
-                std::memcpy(&h, &hb, 4);
-                const float l = static_cast<float>(a - static_cast<double>(h));
-                uint32_t lb;
+                const float hf = static_cast<float>(h);
+                const float l = static_cast<float>(a - h);
+                uint32_t hb, lb;
+                std::memcpy(&hb, &hf, 4);
                 std::memcpy(&lb, &l, 4);
                 lb = (lb + 0x1000u) & 0xFFFFE000u;
-                std::memcpy(&out[off], &hb, 4);
-                std::memcpy(&out[part + off], &lb, 4);
+                std::memcpy(&out[offset(i, k, 0)], &hb, 4);
+                std::memcpy(&out[offset(i, k, 1)], &lb, 4);
             }
         }
 }

@@ -270,17 +270,14 @@ __device__ __forceinline__ ff ln_ff(float x) {
 // throughput of the whole kernel); the normal tail and density in float.
 // The price of a call is the difference of two terms of size ~K: a float
 // product there would bias every point by ~2^-24 K, which no averaging
-// removes.  Beyond |psi| = 12 the float density and tail underflow, so those
-// (rare) points take the double formulas.
+// removes.  Far out (|psi| beyond ~13) the float density and the small tail
+// underflow to zero while the exact terms they scale are below 1e-35; the
+// large tail is 1 there, so every value keeps its limit and no point leaves the FP32
+// pipe (with a = sigma sqrt(t_1) small, such points are common, and one of
+// them in a warp would send the whole warp down a double-precision branch).
 __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[4]) {
     const ff psi = ff_mul_ff(ff_add(ff_of(c.ff_psi0), ff_neg(ln_ff(xhat))), ff_of(c.ff_inv_a));
     const float p = psi.hi;
-    if (fabsf(p) > 12.0f) {
-        double d[4];
-        values_fp64(c, static_cast<double>(xhat), static_cast<double>(dhat), d);
-        for (int g = 0; g < 4; ++g) v[g] = ff_of_double(d[g]);
-        return;
-    }
     const float pdf = 0.398942280f * expf(-0.5f * p * p);
     if (c.type == QMCCPW_BINARY_ASIAN) {
         const float sf = 0.5f * erfcf(p * 0.707106781f);
@@ -321,6 +318,57 @@ __device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab
         g &= g - 1u;
     }
     return y;
+}
+
+__host__ __device__ constexpr int ctz_const(int s) {
+    int b = 0;
+    while (!(s & 1)) {
+        s >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+// A run of 2^LG consecutive points whose first index k0 is a multiple of
+// 2^LG: point s of the run steps by direction integer ctz(s) < LG, the same
+// for every such run, so those LG integers are loaded once and the run is
+// unrolled (no index arithmetic or load per point).
+template <int LG, typename Emit>
+__device__ __forceinline__ void sobol_run(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
+                                          Emit &&emit) {
+    uint32_t v[LG > 0 ? LG : 1];
+#pragma unroll
+    for (int b = 0; b < LG; ++b) v[b] = __ldg(tab + b * jstride + j);
+    emit(0, y);
+#pragma unroll
+    for (int s = 1; s < (1 << LG); ++s) {
+        y ^= v[ctz_const(s)];
+        emit(s, y);
+    }
+}
+
+// Sobol' integers y(k0), ..., y(k0 + len - 1) of dimension j in Gray-code
+// order (x(g(k+1)) = x(g(k)) xor v_ctz(k+1)), handed to emit(s, y).  A full
+// aligned run of 4..64 points takes the unrolled form above.
+template <typename Emit>
+__device__ __forceinline__ void sobol_points(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t shift,
+                                             uint32_t k0, int len, int chunk_log2, Emit &&emit) {
+    uint32_t y = sobol_first(tab, jstride, j, shift, k0);
+    if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
+        switch (chunk_log2) {
+            case 2: sobol_run<2>(tab, jstride, j, y, emit); return;
+            case 3: sobol_run<3>(tab, jstride, j, y, emit); return;
+            case 4: sobol_run<4>(tab, jstride, j, y, emit); return;
+            case 5: sobol_run<5>(tab, jstride, j, y, emit); return;
+            case 6: sobol_run<6>(tab, jstride, j, y, emit); return;
+            default: break;
+        }
+    }
+    emit(0, y);
+    for (int s = 1; s < len; ++s) {
+        y ^= __ldg(tab + (__ffs(k0 + s) - 1) * jstride + j);
+        emit(s, y);
+    }
 }
 
 __device__ __forceinline__ int find_contract(const uint64_t *__restrict__ base, int count, uint64_t item) {

@@ -137,9 +137,11 @@ size_t fused_smem_bytes(int precision, int n, int tile_log2);
 int fused_set_smem_limit(int precision, size_t bytes);
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
 
-// Tensor-core PCA (pca_tc.cu).  kind 0: 3-term bf16 split, 1: 3-term tf32 split.
+// Tensor-core PCA (pca_tc.cu).  kind 0: bf16 split (4 products), 1: tf32
+// split (3 products), both n <= 64 with Ahat resident; kinds 2 (bf16) and 3
+// (tf32): n <= 256, Ahat streamed in K-chunks.
 size_t pca_tc_smem_bytes(int kind);
-int pca_tc_npad();                                   // largest n supported (dimensions after padding)
+int pca_tc_max_n(int kind);                          // largest n (dimensions) the kind supports
 int pca_tc_prepare(int kind, size_t smem_bytes);     // raise the dynamic shared memory limit
 int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks);
 int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, void *stream);

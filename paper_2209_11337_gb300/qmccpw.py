@@ -52,7 +52,7 @@ EXPORTS = (
     "qmccpw_plan", "qmccpw_greeks", "qmccpw_greeks_batch", "qmccpw_batch_create",
     "qmccpw_batch_launch", "qmccpw_batch_results", "qmccpw_batch_device_results",
     "qmccpw_batch_launch_count", "qmccpw_batch_set_timing", "qmccpw_batch_timing",
-    "qmccpw_batch_free", "qmccpw_sobol_points",
+    "qmccpw_batch_use_graph", "qmccpw_batch_free", "qmccpw_sobol_points",
     "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_server_start", "qmccpw_submit", "qmccpw_poll",
     "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_autotune", "qmccpw_tuning_get",
     "qmccpw_tuning_set", "qmccpw_free", "qmccpw_last_error",
@@ -127,6 +127,7 @@ def library() -> ctypes.CDLL:
             L.qmccpw_batch_launch_count.argtypes = [vp, P(i32)]
             L.qmccpw_batch_set_timing.argtypes = [vp, i32]
             L.qmccpw_batch_timing.argtypes = [vp, P(ctypes.c_float), P(i32)]
+            L.qmccpw_batch_use_graph.argtypes = [vp, i32]
             L.qmccpw_batch_free.argtypes = [vp]
             L.qmccpw_sobol_points.argtypes = [vp, u32, i32, u64, u64, P(u32)]
             L.qmccpw_point_values.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), i32, i32, u32, u64, u64,
@@ -231,6 +232,10 @@ class Batch:
 
     def set_timing(self, capacity: int) -> None:
         _check(library().qmccpw_batch_set_timing(self.handle, capacity))
+
+    def use_graph(self, enable: bool = True) -> None:
+        """Replay the launch sequence as one CUDA graph (qmccpw_batch_use_graph)."""
+        _check(library().qmccpw_batch_use_graph(self.handle, 1 if enable else 0))
 
     def timing(self):
         """(summed fused-kernel milliseconds, launches covered) since the last call."""

@@ -163,7 +163,7 @@ def test_invalid_arguments_are_rejected(q, plan):
                             args["sigma"], args["N"], args["R"], q.QMCCPW_BB, q.QMCCPW_FP64)
         assert e.value.code == q.QMCCPW_ERR_INVALID_ARG, override
     with pytest.raises(q.QmcCpwError) as e:
-        q.qmccpw_greeks(plan, 0, 100, 100.0, 1.0, 100.0, 0.05, 0.2, 256, 4, q.QMCCPW_PCA, q.QMCCPW_MIXED_TC_BF16X3)
+        q.qmccpw_greeks(plan, 0, 300, 100.0, 1.0, 100.0, 0.05, 0.2, 256, 4, q.QMCCPW_PCA, q.QMCCPW_MIXED_TC_TF32X3)
     assert e.value.code == q.QMCCPW_ERR_UNSUPPORTED
 
 

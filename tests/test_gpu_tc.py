@@ -1,9 +1,13 @@
-"""Tensor-core PCA (tcgen05, 3-term bf16 / tf32 split) against the oracle and
+"""Tensor-core PCA (tcgen05, bf16 / tf32 hi + lo split) against the oracle and
 the FP64 GPU path.
 
-The split product carries the PCA factor to about 2^-17 (bf16: 8 + 8 bits)
-or 2^-22 (tf32: 11 + 11 bits) relative, and z likewise; the bars below are
-derived from those widths.  Results are stated per Greek by the bench.
+The leading product z_hi Ahat_hi is exact (hi parts on fixed grids), so the
+split only adds rounding noise of the lo parts: |z - z_hi - z_lo| <= 2^-15
+(bf16: |z_lo| <= 2^-6, 8 significant bits) or 2^-21 (tf32: |z_lo| <= 2^-9,
+11 bits).  Ahat is one fixed matrix whose rounding no averaging removes: bf16
+carries it in three parts (~2^-23), tf32 in two (<= 2^-20).  The per-point
+bars below are derived from the z widths; the estimator must show no bias
+beyond the float floor the MIXED path has.
 """
 import numpy as np
 import pytest
@@ -13,7 +17,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 SEED = W.SCRAMBLE_SEED
-SPLIT_EPS = {2: 2.0 ** -16, 3: 2.0 ** -21}  # precision code -> relative width of the 3-term split
+SPLIT_EPS = {2: 2.0 ** -15, 3: 2.0 ** -21}  # precision code -> absolute width of the lo rounding
 
 
 @pytest.fixture(scope="module")
@@ -26,35 +30,80 @@ def q():
 
 @pytest.fixture(scope="module")
 def plan(q):
-    h = q.qmccpw_plan(device=0, d_max=65, r_max=32, seed=SEED)
+    h = q.qmccpw_plan(device=0, d_max=258, r_max=32, seed=SEED)
     yield h
     q.qmccpw_free(h)
 
 
+def point_bar(eps):
+    # a point's W~ carries sqrt(n) lo errors of ~eps times entries of Ahat; its
+    # values amplify by up to ~1/a: the median over points stays far below this
+    return 50 * eps + 1e-6
+
+
 @pytest.mark.parametrize("prec", [2, 3])
-@pytest.mark.parametrize("typ,d", [(0, 64), (1, 64), (2, 64), (3, 33), (0, 2), (2, 17)])
+@pytest.mark.parametrize("typ,d", [(0, 64), (1, 64), (2, 64), (3, 33), (0, 2), (2, 17), (1, 65)])
 def test_tc_point_values_against_oracle(q, plan, prec, typ, d):
     k0, count, rep = 1000, 300, 3     # 300 points: three tiles of 128, the last one ragged
     ref = oracle.point_values(SEED, typ, d, 100.0, 1.0, 100.0, 0.05, 0.25, W.PCA, rep, k0, count)
     got = q.qmccpw_point_values(plan, typ, d, 100.0, 1.0, 100.0, 0.05, 0.25, W.PCA, prec, rep, k0, count)
     scale = np.mean(np.abs(ref), axis=0)
     err = np.abs(got - ref) / np.maximum(np.abs(ref), scale)
-    eps = SPLIT_EPS[prec]
-    # a point's path mixes d terms of relative error ~eps; its values amplify by up to ~1/a
-    assert np.median(err) < 50 * eps + 1e-6, (np.median(err, axis=0), np.max(err, axis=0))
+    assert np.median(err) < point_bar(SPLIT_EPS[prec]), (np.median(err, axis=0), np.max(err, axis=0))
     assert np.all(np.isfinite(got))
 
 
 @pytest.mark.parametrize("prec", [2, 3])
-def test_tc_estimator_against_fp64(q, plan, prec):
-    cs = [c for c in W.grid_d64(N=2 ** 16, R=8) if c.construction == W.PCA][::3]
+@pytest.mark.parametrize("typ,d", [(0, 66), (1, 100), (2, 129), (3, 130), (3, 200), (0, 257), (2, 257)])
+def test_tc_streamed_point_values_against_oracle(q, plan, prec, typ, d):
+    """d > 65: Ahat streamed in K-chunks (N = K = 256); tf32 beyond d = 129
+    builds Z in two K-halves."""
+    k0, count, rep = 77, 200, 1       # two tiles, the second ragged
+    ref = oracle.point_values(SEED, typ, d, 100.0, 1.0, 100.0, 0.05, 0.25, W.PCA, rep, k0, count)
+    got = q.qmccpw_point_values(plan, typ, d, 100.0, 1.0, 100.0, 0.05, 0.25, W.PCA, prec, rep, k0, count)
+    scale = np.mean(np.abs(ref), axis=0)
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), scale)
+    assert np.median(err) < point_bar(SPLIT_EPS[prec]), (np.median(err, axis=0), np.max(err, axis=0))
+    assert np.all(np.isfinite(got))
+
+
+def greek_scale(c):
+    pts = oracle.point_values(SEED, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, W.PCA, 0, 0, 1024)
+    return np.mean(np.abs(pts), axis=0)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tc_estimator_unbiased_against_fp64(q, plan, prec):
+    """The PCA contracts of the d=64, N=2^20, R=32 grid against FP64: every
+    Greek within 0.1 SE + 2^-21 mean |per-point value| (the MIXED bar) and
+    within 1 SE, and at least half within 0.1 SE.  On these contracts the
+    RQMC standard error sits at the float floor (PCA at sigma = 0.1: 1-4e-8
+    relative), so the CUDA-core MIXED path itself has 57% within 0.1 SE, not
+    the two thirds it shows over the whole grid.  A tensor-core accumulation
+    bias of ~1 ulp of |W~| per instruction showed here as 6-13 SE before the
+    leading product was made exact, and a two-part bf16 Ahat (off by up to
+    2^-15) as up to 11 SE."""
+    cs = [c for c in W.grid_d64() if c.construction == W.PCA]
     tc = q.qmccpw_greeks_batch(plan, cs, prec)
     f64 = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_FP64)
-    eps = SPLIT_EPS[prec]
-    for c, (m, s, p), (m64, s64, p64) in zip(cs, tc, f64):
-        scale = np.mean(np.abs(oracle.point_values(SEED, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, W.PCA, 0, 0, 512)),
-                        axis=0)
-        bound = 0.1 * s64 + 20 * eps * scale
+    bad, met, total = [], 0, 0
+    for c, (m, _, _), (m64, s64, _) in zip(cs, tc, f64):
+        err = np.abs(m - m64)
+        met += int(np.sum(err <= 0.1 * s64))
+        total += 4
+        if np.any(err > 0.1 * s64 + 2.0 ** -21 * greek_scale(c)) or np.any(err > s64):
+            bad.append((c.label(), (err / s64).tolist()))
+    assert not bad, bad[:5]
+    assert met / total >= 0.5, met / total
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tc_streamed_estimator_against_fp64(q, plan, prec):
+    cs = W.pca_stress(N=2 ** 16, R=8) + [W.Contract(W.GEOMETRIC, 100, 100.0, 1.0, 100.0, 0.05, 0.3, 2 ** 16, 8, W.PCA)]
+    tc = q.qmccpw_greeks_batch(plan, cs, prec)
+    f64 = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_FP64)
+    for c, (m, _, _), (m64, s64, _) in zip(cs, tc, f64):
+        bound = 0.1 * s64 + 2.0 ** -21 * greek_scale(c)
         assert np.all(np.abs(m - m64) <= bound), (c.label(), (np.abs(m - m64) / s64).tolist())
 
 
@@ -70,15 +119,31 @@ def test_tc_repeatable_and_batch_equals_single(q, plan):
             assert np.array_equal(p0, p1)
 
 
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tc_three_segments_batch_equals_single(q, plan, prec):
+    """A batch holding bridge, streamed (d > 65) and resident (d <= 65) PCA
+    contracts: three launches, each result the same as alone."""
+    cs = [W.Contract(W.ARITH, 257, 100.0, 1.0, 100.0, 0.05, 0.2, 3000, 2, W.PCA),
+          W.Contract(W.BINARY, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 2000, 3, W.BB),
+          W.Contract(W.LOOKBACK, 100, 105.0, 1.0, 100.0, 0.05, 0.3, 1000, 2, W.PCA),
+          W.Contract(W.ARITH, 33, 95.0, 0.5, 100.0, 0.02, 0.2, 4096, 2, W.PCA)]
+    batch = q.qmccpw_greeks_batch(plan, cs, prec)
+    for c, (_, _, p) in zip(cs, batch):
+        _, _, p0 = q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, c.construction, prec)
+        assert np.array_equal(p0, p)
+    b = q.Batch(plan, cs, prec)
+    try:
+        assert b.launch_count() == 5  # three fused grids, the reduction, the statistics
+    finally:
+        b.free()
+
+
 def test_tc_precision_runs_bridge_contracts_as_mixed_and_rejects_large_d(q, plan):
     c = W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 2, W.BB)
     tc = q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, W.BB, 2)
     mixed = q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, W.BB, q.QMCCPW_MIXED)
     assert np.array_equal(tc[2], mixed[2])
-    big = q.qmccpw_plan(device=0, d_max=100, r_max=4, seed=SEED)
-    try:
+    for prec, d in ((3, 258), (2, 258)):  # both splits: d <= 257
         with pytest.raises(q.QmcCpwError) as e:
-            q.qmccpw_greeks(big, 0, 100, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 2, W.PCA, 2)
+            q.qmccpw_greeks(plan, 0, d, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 2, W.PCA, prec)
         assert e.value.code == q.QMCCPW_ERR_UNSUPPORTED
-    finally:
-        q.qmccpw_free(big)
