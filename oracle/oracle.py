@@ -16,14 +16,14 @@ import threading
 import numpy as np
 
 __all__ = [
-    "ARITH", "BINARY", "LOOKBACK", "GEOMETRIC", "BB", "PCA",
+    "ARITH", "BINARY", "LOOKBACK", "GEOMETRIC", "BB", "PCA", "STD", "forward",
     "build", "lib", "primitive_polys", "direction_numbers", "scramble",
     "sobol", "inv_normal", "bridge", "pca_matrix", "point", "point_values",
     "greeks", "partial_sums", "using_library", "compile_source",
 ]
 
 ARITH, BINARY, LOOKBACK, GEOMETRIC = 0, 1, 2, 3
-BB, PCA = 0, 1
+BB, PCA, STD = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qmccpw_oracle.c")
@@ -67,6 +67,7 @@ def _load(path: str) -> ctypes.CDLL:
     L.oracle_inv_normal.restype = d
     L.oracle_bridge.argtypes = [i, d, dp, dp]
     L.oracle_pca_matrix.argtypes = [i, d, dp]
+    L.oracle_forward.argtypes = [i, d, dp, dp]
     L.oracle_point.argtypes = [i, i, d, d, d, d, d, i, dp, dp, dp]
     L.oracle_point_values.argtypes = [u64, i, i, d, d, d, d, d, i, u32, u64, u64, dp]
     L.oracle_greeks.argtypes = [u64, i, i, d, d, d, d, d, i, u64, i, i, dp, dp, dp]
@@ -149,6 +150,15 @@ def bridge(n: int, dt: float, z) -> np.ndarray:
     W = np.zeros(n + 1)
     zz = z if n > 0 else np.zeros(1)
     _check(lib().oracle_bridge(n, dt, _f64(zz), _f64(W)), "bridge")
+    return W
+
+
+def forward(n: int, dt: float, z) -> np.ndarray:
+    """Standard construction: W~(s_i) = W~(s_{i-1}) + sqrt(dt) z_i."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    W = np.zeros(n + 1)
+    zz = z if n > 0 else np.zeros(1)
+    _check(lib().oracle_forward(n, dt, _f64(zz), _f64(W)), "forward")
     return W
 
 

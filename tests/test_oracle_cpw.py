@@ -60,7 +60,7 @@ def conditional_by_quadrature(opt, K, T, S0, r, sigma, stilde):
     return disc * val
 
 
-CASES = [(opt, d, cons) for opt in (0, 1, 2, 3) for d, cons in ((2, 0), (5, 0), (8, 0), (8, 1), (13, 1))]
+CASES = [(opt, d, cons) for opt in (0, 1, 2, 3) for d, cons in ((2, 0), (5, 0), (8, 0), (8, 1), (13, 1), (6, 2))]
 
 
 @pytest.mark.parametrize("opt,d,cons", CASES)
@@ -150,7 +150,7 @@ def geometric_vega(S0, K, r, sig, T, d):
     return richardson(f, sig, 1e-3, 1)
 
 
-@pytest.mark.parametrize("cons", [0, 1])
+@pytest.mark.parametrize("cons", [0, 1, 2])
 @pytest.mark.parametrize("K", [90.0, 100.0, 110.0])
 def test_estimator_matches_geometric_asian_closed_form(oracle_lib, cons, K):
     S0, r, sig, T, d = 100.0, 0.05, 0.2, 1.0, 16

@@ -64,6 +64,14 @@ MUTANTS = {
     "geometric mean missing the drift": (
         "lsum += omega * s + c->sigma * W[i];", "lsum += c->sigma * W[i];",
         lambda o: cpw.test_estimator_matches_geometric_asian_closed_form(o, 1, 90.0)),
+    "standard construction increments scaled by dt instead of sqrt(dt)": (
+        "for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + h * z[i - 1];",
+        "for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + dt * z[i - 1];",
+        lambda o: paths.test_forward_covariance_and_structure(o, 15)),
+    "standard construction driven by the dimensions in reverse": (
+        "for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + h * z[i - 1];",
+        "for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + h * z[n - i];",
+        lambda o: paths.test_forward_covariance_and_structure(o, 15)),
     "inverse normal Halley step with the wrong sign": (
         "z -= step;", "z += step;",
         lambda o: paths.test_inverse_normal_published_quantiles(o)),

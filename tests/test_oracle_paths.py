@@ -88,6 +88,25 @@ def test_bridge_order_terminal_then_midpoints(oracle_lib):
     assert np.argmax(A5[:, 1]) == 1  # s_2
 
 
+def forward_matrix(oracle_lib, n, dt):
+    cols = []
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        cols.append(oracle_lib.forward(n, dt, e)[1:])
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("n", [1, 2, 15, 64, 255])
+def test_forward_covariance_and_structure(oracle_lib, n):
+    # the standard construction's factor is sqrt(dt) times the lower-triangular
+    # matrix of ones: dimension k drives the increment of step k alone
+    dt = 1.0 / (n + 1)
+    A = forward_matrix(oracle_lib, n, dt)
+    assert np.max(np.abs(A @ A.T - sigma_matrix(n, dt))) <= 1e-14 * n * dt
+    assert np.allclose(A, math.sqrt(dt) * np.tril(np.ones((n, n))), rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("n", [1, 2, 15, 63, 255])
 def test_pca_factor(oracle_lib, n):
     dt = 1.0 / (n + 1)
@@ -107,7 +126,7 @@ def test_pca_factor(oracle_lib, n):
     assert np.max(np.abs(G - np.diag(np.diag(G)))) < 1e-12 * np.max(lam)
 
 
-@pytest.mark.parametrize("opt,d,cons", [(0, 16, 0), (1, 9, 1), (2, 33, 0), (3, 5, 1)])
+@pytest.mark.parametrize("opt,d,cons", [(0, 16, 0), (1, 9, 1), (2, 33, 0), (3, 5, 1), (0, 12, 2), (2, 7, 2)])
 def test_estimator_points_use_the_pinned_pieces(oracle_lib, opt, d, cons):
     # The estimator's point k of replicate r is: scrambled Sobol integers at
     # Gray index g(k), u = (y + 1/2) 2^-32, z = Phi^{-1}(u), then the path and
