@@ -64,6 +64,70 @@ def fp32_peak_tflops() -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# the kernel each launch segment of a batch runs, by grid precision
+SEGMENT_KERNELS = {
+    "mixed": ("fused_kernel<float, bridge>", "fused_kernel<float, standard>", "pca_tcs_kernel",
+              "fused_kernel<float, pca>"),
+    "tc-bf16": ("fused_kernel<float, bridge>", "fused_kernel<float, standard>", "pca_tcs_kernel<bf16>",
+                "pca_tc_kernel<bf16>"),
+    "tc-tf32": ("fused_kernel<float, bridge>", "fused_kernel<float, standard>", "pca_tcs_kernel<tf32>",
+                "pca_tc_kernel<tf32>"),
+}
+FLOPS_TC_FP32 = FLOPS_BRIDGE - 5  # FP32 work of the tensor-core kernels: the product runs on the tensor pipe
+FLOPS_STD = FLOPS_BRIDGE - 2      # standard construction: a running sum and the sqrt(dt) scale instead of the bridge
+# DRAM read + write bytes of one full-size launch of the grid's kernels, from
+# one ncu capture (profiles/dram_bytes_grid_d64_tcbf16.md); None for a kernel
+# that changed since
+GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 3272192 + 100472576, "fused_kernel<float, bridge>": 1055232 + 25592320}
+
+
+def roofline(grid_precision: str, contracts, segment_ms) -> dict:
+    """Roofline of the launch segment that takes the most time (its kernel
+    is the dominant one of the step): algorithmic FP32 flops of its
+    contracts / its event-timed duration against the FP32 pipe peak; for a
+    tensor-core segment also the useful PCA product (2 n flops per
+    point-date) against the measured dense bf16 peak."""
+    seg = max(range(4), key=lambda k: segment_ms[k])
+    ms = segment_ms[seg]
+    if seg == 0:
+        mine = [c for c in contracts if c.construction == W.BB]
+    elif seg == 1:
+        mine = [c for c in contracts if c.construction == W.STD]
+    else:
+        mine = [c for c in contracts if c.construction == W.PCA and ((c.d - 1 > 64) == (seg == 2))]
+    tc = grid_precision != "mixed" and seg >= 2
+    flops = 0.0
+    for c in mine:
+        per = FLOPS_BRIDGE if seg == 0 else FLOPS_STD if seg == 1 else (
+            FLOPS_TC_FP32 if tc else FLOPS_BRIDGE - 5 + 2 * (c.d - 1))
+        flops += float(c.N) * c.R * c.d * per
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": GRID_TRAFFIC.get(SEGMENT_KERNELS[grid_precision][seg]),
+           "kernel": SEGMENT_KERNELS[grid_precision][seg], "ms_per_launch": ms,
+           "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flops x 2070 MHz (unit counts, max clock)",
+           "flops_note": "FP32 flops per point-date: bridge 32; standard 30; PCA on CUDA cores 27 + 2(d-1); "
+                         "tensor-core PCA 27 (the product is on the tensor pipe)"}
+    if tc:
+        gemm = sum(float(c.N) * c.R * c.d * 2 * (c.d - 1) for c in mine)
+        bf16 = measured_peaks().get("bf16_tflops_sustained")
+        t_ach = gemm / (ms / 1e3) / 1e12
+        out["tensor"] = {"achieved": t_ach, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": (t_ach / bf16) if bf16 else None,
+                         "note": "useful product W = A z, 2 n flops per point-date, against the measured "
+                                 "sustained dense bf16 peak (of measured)"}
+    return out
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
@@ -387,19 +451,21 @@ def run_ours(args):
         wall = time.perf_counter() - t0
         clocks = sampler.stop() if sampler else None
         step_ms = [a.elapsed_time(b) for a, b in events]
+        seg_ms, _ = batch.segment_timing()
         fused_ms, nl = batch.timing()
         launches = batch.launch_count() * steps
         res = batch.results()
         batch.free()
         return {"ms_per_step": sum(step_ms) / steps, "wall_s": wall, "fused_ms": fused_ms / max(1, nl),
-                "clocks": clocks, "launches": launches, "results": res}
+                "segment_ms": [x / max(1, nl) for x in seg_ms], "clocks": clocks, "launches": launches,
+                "results": res}
 
     if args.case:
         # single-contract run for profiling: no JSON line
         typ, cons = args.case.split("-")
         tmap = {"arith": W.ARITH, "binary": W.BINARY, "lookback": W.LOOKBACK, "geometric": W.GEOMETRIC}
         one = [W.Contract(tmap[typ], args.case_d, 100.0, 1.0, 100.0, 0.05, 0.2, args.case_N, args.case_R,
-                          W.BB if cons == "bb" else W.PCA)]
+                          {"bb": W.BB, "pca": W.PCA, "std": W.STD}[cons])]
         prec = {"fp64": q.QMCCPW_FP64, "mixed": q.QMCCPW_MIXED, "tc-bf16": q.QMCCPW_MIXED_TC_BF16X3,
                 "tc-tf32": q.QMCCPW_MIXED_TC_TF32X3}[args.case_precision]
         batch = q.Batch(plan, one, prec)
@@ -421,6 +487,8 @@ def run_ours(args):
     grid_prec = {"mixed": q.QMCCPW_MIXED, "tc-bf16": q.QMCCPW_MIXED_TC_BF16X3,
                  "tc-tf32": q.QMCCPW_MIXED_TC_TF32X3}[args.grid_precision]
     mixed = timed(grid_prec, args.steps, args.warmup, with_clocks=True)
+    # the same grid with PCA on the CUDA cores (MIXED), beside the headline
+    cuda_core = timed(q.QMCCPW_MIXED, args.steps, 1) if args.grid_precision != "mixed" else None
     fp64 = timed(q.QMCCPW_FP64, args.fp64_steps, 1) if args.fp64_steps > 0 else None
 
     # end to end through the public API with host buffers: contracts in, results out
@@ -438,11 +506,8 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
 
     ms = max_over_ranks(mixed["ms_per_step"])
-    fused_ms = max_over_ranks(mixed["fused_ms"])
     value = world * elems / (ms / 1e3)
-    flops = algorithmic_flops(contracts)
-    achieved = flops / (fused_ms / 1e3) / 1e12
-    peak = fp32_peak_tflops()
+    seg_ms = [max_over_ranks(x) for x in mixed["segment_ms"]]
 
     # MIXED against FP64 on the same points, in units of the FP64 standard error
     err_se = None
@@ -484,11 +549,12 @@ def run_ours(args):
             "ms_per_step": max_over_ranks(fp64["ms_per_step"]), "steps": args.fp64_steps},
         "mixed_vs_fp64_max_err_in_se": err_se,
         "mixed_vs_fp64_share_within_0p1_se": err_frac,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "fused_kernel<float>", "fused_ms_per_launch": fused_ms,
-                     "note": "FP32 pipe peak from 152 SMs x 128 lanes x 2 flops x 2070 MHz (unit counts and "
-                             "max clock); algorithmic flops: 32 per point-date (bridge), 27+2(d-1) (PCA)"},
+        "roofline": roofline(args.grid_precision, contracts, seg_ms),
+        "segment_ms": {"bridge": seg_ms[0], "standard": seg_ms[1], "pca_streamed": seg_ms[2], "pca": seg_ms[3]},
+        "mixed_cuda_core": None if cuda_core is None else {
+            "value": world * elems / (max_over_ranks(cuda_core["ms_per_step"]) / 1e3), "unit": UNIT,
+            "ms_per_step": max_over_ranks(cuda_core["ms_per_step"]),
+            "note": "the same grid in MIXED precision with the PCA product on the CUDA cores"},
         "e2e": {"value": world * elems / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": mixed["launches"],
@@ -560,8 +626,8 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--grid-precision", choices=["mixed", "tc-bf16", "tc-tf32"], default="mixed",
-                    help="precision of the timed grid (tc-*: PCA contracts on tensor cores)")
+    ap.add_argument("--grid-precision", choices=["mixed", "tc-bf16", "tc-tf32"], default="tc-bf16",
+                    help="precision of the timed grid (tc-*: float path with the PCA product on tensor cores)")
     ap.add_argument("--book-steps", type=int, default=1, help="timed steps of the 4096-contract book (0: skip)")
     ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of Poisson arrivals (0: skip)")
     ap.add_argument("--latency-calls", type=int, default=200, help="calls timed in the small-case latency section")

@@ -61,7 +61,9 @@ typedef enum {
 /* ---- path construction of W~ = A z with A A^T = Sigma (eq. WboldTilde) -- */
 typedef enum {
     QMCCPW_BB = 0,                   /* Brownian bridge, Sec. 4.4: terminal value, then midpoints breadth first */
-    QMCCPW_PCA = 1                   /* principal components of Sigma (named in Sec. 6 as the next reduction) */
+    QMCCPW_PCA = 1,                  /* principal components of Sigma (named in Sec. 6 as the next reduction) */
+    QMCCPW_STD = 2                   /* standard construction, one increment per step (the path of the
+                                        simulation listing, Sec. 4.1-4.2): W~(s_i) = W~(s_{i-1}) + sqrt(dt) z_i */
 } qmccpw_construction;
 
 /* ---- arithmetic precision ----------------------------------------------- */
@@ -184,6 +186,16 @@ int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches);
 int qmccpw_batch_set_timing(qmccpw_batch_t batch, int32_t capacity);
 int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches);
 /*
+ * The same record split by launch segment, without clearing it (call before
+ * qmccpw_batch_timing): segment_ms[0] bridge contracts, [1] standard
+ * construction, [2] PCA on the streamed tensor-core kernel (d > 65), [3] the
+ * other PCA contracts, each the summed milliseconds from the end of the
+ * previous segment (a segment a batch does not have reads about 0).  Graph
+ * replays record no segments (*launches = 0).  segment_ms has 4 entries.
+ * Errors: INVALID_ARG (NULL argument), CUDA.
+ */
+int qmccpw_batch_segment_timing(qmccpw_batch_t batch, float *segment_ms, int32_t *launches);
+/*
  * CUDA-graph replay (launch-bound small batches; no counterpart in the
  * paper): with enable != 0 the next qmccpw_batch_launch captures the batch's
  * launch sequence (counter resets, fused grids, reduction, statistics) into
@@ -195,6 +207,18 @@ int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches
  */
 int qmccpw_batch_use_graph(qmccpw_batch_t batch, int32_t enable);
 int qmccpw_batch_free(qmccpw_batch_t batch);
+
+/*
+ * Self-test of the failure path of the tensor-core kernels' waits (no
+ * counterpart in the paper): launches on `device` one CTA that waits, with
+ * the kernels' own bounded poll loop and a limit of `limit_us`
+ * microseconds, on an mbarrier that nothing arrives at.  The wait must give
+ * up and the kernel exit normally: *kernel_status = QMCCPW_ERR_TIMEOUT (what
+ * the kernels record on expiry), QMCCPW_OK if the barrier completed (a
+ * defect).  The context stays usable.  Errors: INVALID_ARG (NULL status,
+ * limit outside 1..1e6), OOM, CUDA.
+ */
+int qmccpw_selftest_bounded_wait(int32_t device, int32_t limit_us, int32_t *kernel_status);
 
 /*
  * Diagnostics for bit-exact checks.  qmccpw_sobol_points writes the 32-bit

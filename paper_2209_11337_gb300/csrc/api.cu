@@ -93,10 +93,11 @@ struct DTables {
 };
 
 bool is_tc(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 || precision == QMCCPW_MIXED_TC_TF32X3; }
+constexpr int kSegments = 4;  // launch segments of a batch (segment_of)
 // Kernel precision of one contract: a tensor-core precision applies to the PCA
 // product only; bridge contracts under it run as MIXED.
 int contract_precision(int precision, int construction) {
-    return (is_tc(precision) && construction == QMCCPW_BB) ? QMCCPW_MIXED : precision;
+    return (is_tc(precision) && construction != QMCCPW_PCA) ? QMCCPW_MIXED : precision;
 }
 // tensor-core kernel of a PCA contract with n dimensions: resident (n <= 64)
 // bf16 0 / tf32 1, streamed (n <= 256) bf16 2 / tf32 3
@@ -105,12 +106,15 @@ int tc_kind(int precision, int n) {
     return n > pca_tc_max_n(base) ? base + 2 : base;
 }
 int tc_slot(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1; }
-// launch segment of a contract (kernel precision kp): 0 bridge, 1 PCA on the
-// streamed tensor-core kernel, 2 other PCA
+// launch segment of a contract (kernel precision kp): 0 bridge, 1 standard
+// construction, 2 PCA on the streamed tensor-core kernel, 3 other PCA; one
+// grid per segment present, in this order
 int segment_of(int kp, int construction, int n) {
     if (construction == QMCCPW_BB) return 0;
-    return (is_tc(kp) && tc_kind(kp, n) >= 2) ? 1 : 2;
+    if (construction == QMCCPW_STD) return 1;
+    return (is_tc(kp) && tc_kind(kp, n) >= 2) ? 2 : 3;
 }
+int segment_construction(int seg) { return seg == 0 ? QMCCPW_BB : seg == 1 ? QMCCPW_STD : QMCCPW_PCA; }
 
 }  // namespace
 
@@ -146,12 +150,10 @@ struct qmccpw_batch_s {
     std::vector<int32_t> order;      // order[i] = caller's index of host[i]
     std::vector<int32_t> R;
     uint64_t items = 0, total_reps = 0;
-    // launch segments: items [0, items_bb) bridge, [items_bb, items_big) PCA
-    // on the streamed d <= 257 tensor-core kernel, the rest PCA on the kernel
-    // of the batch precision
-    uint64_t items_bb = 0, items_big = 0;
-    size_t smem[3] = {0, 0, 0};
-    int grid[3] = {0, 0, 0};
+    // launch segments (segment_of): items [seg_begin[k], seg_begin[k + 1])
+    uint64_t seg_begin[kSegments + 1] = {0, 0, 0, 0, 0};
+    size_t smem[kSegments] = {0, 0, 0, 0};
+    int grid[kSegments] = {0, 0, 0, 0};
     BatchBuffers own;          // used by prepared batches
     BatchBuffers *buf = &own;  // one-shot calls point this at the plan's workspace
     // diagnostics
@@ -160,6 +162,7 @@ struct qmccpw_batch_s {
     uint32_t rep_offset = 0;
     // fused-kernel timing: event pairs of the most recent launches
     std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<cudaEvent_t> ev_seg;  // kSegments per slot: the end of each launch segment
     int32_t timed = 0;  // launches recorded since the last read
     // CUDA-graph replay (qmccpw_batch_use_graph): the launch sequence captured
     // once on a private stream, then one graph launch per call
@@ -176,9 +179,12 @@ struct qmccpw_batch_s {
         host.clear();
         order.clear();
         R.clear();
-        items = total_reps = items_bb = items_big = 0;
-        smem[0] = smem[1] = smem[2] = 0;
-        grid[0] = grid[1] = grid[2] = 0;
+        items = total_reps = 0;
+        for (int k = 0; k <= kSegments; ++k) seg_begin[k] = 0;
+        for (int k = 0; k < kSegments; ++k) {
+            smem[k] = 0;
+            grid[k] = 0;
+        }
         point_out = nullptr;
         point_k0 = 0;
         rep_offset = 0;
@@ -186,6 +192,7 @@ struct qmccpw_batch_s {
     ~qmccpw_batch_s() {
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_stop) cudaEventDestroy(e);
+        for (auto e : ev_seg) cudaEventDestroy(e);
         drop_graph();
         if (capture_stream) cudaStreamDestroy(capture_stream);
     }
@@ -207,7 +214,7 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
     if (N < 1 || N > (1ull << 32)) return fail(QMCCPW_ERR_INVALID_ARG, "N must be in 1..2^32");
     if (!diagnostic && (R < 2 || R > p->r_max))
         return fail(QMCCPW_ERR_INVALID_ARG, "R " + std::to_string(R) + " outside 2..r_max=" + std::to_string(p->r_max));
-    if (construction != QMCCPW_BB && construction != QMCCPW_PCA)
+    if (construction != QMCCPW_BB && construction != QMCCPW_PCA && construction != QMCCPW_STD)
         return fail(QMCCPW_ERR_INVALID_ARG, "construction out of range");
     if (precision < QMCCPW_FP64 || precision > QMCCPW_MIXED_TC_TF32X3)
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
@@ -322,7 +329,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.row_stride = (c.n + 1) | 1;
     // the register bridge (float, one thread per point, d = 16 or 64) and PCA read z by
     // dimension; the shared-memory bridge overwrites z with W~ in place at its date
-    c.z_by_dim = (c.construction == QMCCPW_PCA ||
+    c.z_by_dim = (c.construction != QMCCPW_BB ||
                   (precision != QMCCPW_FP64 && c.groups == 1 && (c.n == 63 || c.n == 15))) ? 1 : 0;
     c.N = in.N;
     c.item_base = item_base;
@@ -367,14 +374,18 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     b->precision = precision;
     b->host.resize(count);
     b->R.resize(count);
-    // launch order: bridge contracts, then PCA; within each, larger d first
-    // (their items are the costliest, and the dynamic schedule hands items
-    // out in order, so the tail of the launch holds the cheap ones)
+    // launch order: by segment (bridge, standard, streamed tensor-core PCA,
+    // other PCA); within each, larger d first (their items are the costliest,
+    // and the dynamic schedule hands items out in order, so the tail of the
+    // launch holds the cheap ones)
     b->order.clear();
-    for (int cons : {QMCCPW_BB, QMCCPW_PCA}) {
+    auto seg_of = [&](int i) {
+        return segment_of(contract_precision(precision, cs[i].construction), cs[i].construction, cs[i].option.d - 1);
+    };
+    for (int seg = 0; seg < kSegments; ++seg) {
         const size_t first = b->order.size();
         for (int i = 0; i < count; ++i)
-            if (cs[i].construction == cons) b->order.push_back(i);
+            if (seg_of(i) == seg) b->order.push_back(i);
         std::stable_sort(b->order.begin() + first, b->order.end(),
                          [&](int x, int y) { return cs[x].option.d > cs[y].option.d; });
     }
@@ -388,8 +399,7 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         items += static_cast<uint64_t>(c.R) * c.tiles;
         const int kp = contract_precision(precision, in.construction);
         const int seg = segment_of(kp, in.construction, c.n);
-        if (seg == 0) b->items_bb = items;
-        if (seg <= 1) b->items_big = items;
+        for (int k = seg + 1; k <= kSegments; ++k) b->seg_begin[k] = items;
         for (int r = 0; r < c.R; ++r) rep_owner.push_back(static_cast<uint64_t>(k));
         reps += c.R;
         b->R[k] = c.R;
@@ -409,25 +419,24 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     QMC_TRY(B.tile_sums.ensure(scratch));
     QMC_TRY(B.per_rep.ensure(sizeof(double) * 4 * reps));
     QMC_TRY(B.stats.ensure(sizeof(double) * 8 * count));
-    QMC_TRY(B.counters.ensure(3 * sizeof(unsigned long long)));
+    QMC_TRY(B.counters.ensure(kSegments * sizeof(unsigned long long)));
     QMC_CUDA(cudaMemcpyAsync(B.contracts.ptr, b->host.data(), sizeof(ContractDev) * count, cudaMemcpyHostToDevice, st));
     QMC_CUDA(cudaMemcpyAsync(B.item_base.ptr, item_base.data(), sizeof(uint64_t) * count, cudaMemcpyHostToDevice, st));
     QMC_CUDA(cudaMemcpyAsync(B.rep_owner.ptr, rep_owner.data(), sizeof(uint64_t) * reps, cudaMemcpyHostToDevice, st));
     QMC_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
-    const uint64_t range[3] = {b->items_bb, b->items_big - b->items_bb, items - b->items_big};
-    for (int k = 0; k < 3; ++k) {
-        if (range[k] == 0) continue;
+    for (int k = 0; k < kSegments; ++k) {
+        const uint64_t range = b->seg_begin[k + 1] - b->seg_begin[k];
+        if (range == 0) continue;
         int per_sm = 0;
-        const int kp = contract_precision(precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA);
-        if (k == 1)
-            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp, 256), b->smem[k], &per_sm)));
-        else if (is_tc(kp))
-            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp, 0), b->smem[k], &per_sm)));
+        const int cons = segment_construction(k);
+        const int kp = contract_precision(precision, cons);
+        if (is_tc(kp))
+            QMC_CUDA(static_cast<cudaError_t>(pca_tc_occupancy(tc_kind(kp, k == 2 ? 256 : 0), b->smem[k], &per_sm)));
         else
-            QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(kp, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], &per_sm)));
+            QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(kp, cons, b->smem[k], &per_sm)));
         if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
         const uint64_t slots = static_cast<uint64_t>(per_sm) * p->sm_count;
-        b->grid[k] = static_cast<int>(std::min<uint64_t>(range[k], slots));
+        b->grid[k] = static_cast<int>(std::min<uint64_t>(range, slots));
     }
     return QMCCPW_OK;
 }
@@ -450,21 +459,21 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s, bool record_events = true) 
     const size_t cap = record_events ? b->ev_start.size() : 0;
     const size_t slot = cap ? static_cast<size_t>(b->timed) % cap : 0;
     if (cap) QMC_CUDA(cudaEventRecord(b->ev_start[slot], s));
-    const uint64_t bounds[4] = {0, b->items_bb, b->items_big, b->items};
-    for (int k = 0; k < 3; ++k) {
-        if (bounds[k + 1] == bounds[k]) continue;
-        lp.item_begin = bounds[k];
-        lp.item_end = bounds[k + 1];
-        lp.work_counter = B.counters.as<unsigned long long>() + k;
-        QMC_CUDA(cudaMemsetAsync(lp.work_counter, 0, sizeof(unsigned long long), s));
-        const int kp = contract_precision(b->precision, k == 0 ? QMCCPW_BB : QMCCPW_PCA);
-        if (k == 1)
-            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(kp, 256), b->smem[k], b->grid[k], s)));
-        else if (is_tc(kp))
-            QMC_CUDA(static_cast<cudaError_t>(launch_pca_tc(lp, tc_kind(kp, 0), b->smem[k], b->grid[k], s)));
-        else
-            QMC_CUDA(static_cast<cudaError_t>(
-                launch_fused(lp, kp, k == 0 ? QMCCPW_BB : QMCCPW_PCA, b->smem[k], b->grid[k], s)));
+    for (int k = 0; k < kSegments; ++k) {
+        if (b->seg_begin[k + 1] > b->seg_begin[k]) {
+            lp.item_begin = b->seg_begin[k];
+            lp.item_end = b->seg_begin[k + 1];
+            lp.work_counter = B.counters.as<unsigned long long>() + k;
+            QMC_CUDA(cudaMemsetAsync(lp.work_counter, 0, sizeof(unsigned long long), s));
+            const int cons = segment_construction(k);
+            const int kp = contract_precision(b->precision, cons);
+            if (is_tc(kp))
+                QMC_CUDA(static_cast<cudaError_t>(
+                    launch_pca_tc(lp, tc_kind(kp, k == 2 ? 256 : 0), b->smem[k], b->grid[k], s)));
+            else
+                QMC_CUDA(static_cast<cudaError_t>(launch_fused(lp, kp, cons, b->smem[k], b->grid[k], s)));
+        }
+        if (cap) QMC_CUDA(cudaEventRecord(b->ev_seg[slot * kSegments + k], s));
     }
     if (cap) {
         QMC_CUDA(cudaEventRecord(b->ev_stop[slot], s));
@@ -739,7 +748,7 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
     QMC_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     // allow every tile size up front (occupancy follows the bytes each launch asks for)
     for (int prec : {QMCCPW_FP64, QMCCPW_MIXED})
-        QMC_CUDA(static_cast<cudaError_t>(fused_set_smem_limit(prec, static_cast<size_t>(smem_optin) - 1024)));
+        QMC_CUDA(static_cast<cudaError_t>(fused_set_smem_limit(prec, static_cast<size_t>(smem_optin))));
     p->seed = desc->seed;
     p->d_max = desc->d_max;
     p->r_max = desc->r_max;
@@ -863,8 +872,9 @@ int qmccpw_batch_launch_count(qmccpw_batch_t batch, int32_t *launches) {
     g_last_error.clear();
     if (!batch || !launches) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
     // one grid per launch segment present, the per-replicate reduction, the statistics
-    *launches = (batch->items_bb > 0 ? 1 : 0) + (batch->items_big > batch->items_bb ? 1 : 0) +
-                (batch->items > batch->items_big ? 1 : 0) + 2;
+    int n = 2;
+    for (int k = 0; k < kSegments; ++k) n += batch->seg_begin[k + 1] > batch->seg_begin[k] ? 1 : 0;
+    *launches = n;
     return QMCCPW_OK;
 }
 
@@ -875,8 +885,10 @@ int qmccpw_batch_set_timing(qmccpw_batch_t batch, int32_t capacity) {
     QMC_CUDA(cudaStreamSynchronize(batch->plan->stream));
     for (auto e : batch->ev_start) cudaEventDestroy(e);
     for (auto e : batch->ev_stop) cudaEventDestroy(e);
+    for (auto e : batch->ev_seg) cudaEventDestroy(e);
     batch->ev_start.clear();
     batch->ev_stop.clear();
+    batch->ev_seg.clear();
     batch->timed = 0;
     for (int i = 0; i < capacity; ++i) {
         cudaEvent_t a, b;
@@ -884,6 +896,10 @@ int qmccpw_batch_set_timing(qmccpw_batch_t batch, int32_t capacity) {
         QMC_CUDA(cudaEventCreate(&b));
         batch->ev_start.push_back(a);
         batch->ev_stop.push_back(b);
+        for (int k = 0; k < kSegments; ++k) {
+            QMC_CUDA(cudaEventCreate(&a));
+            batch->ev_seg.push_back(a);
+        }
     }
     return QMCCPW_OK;
 }
@@ -904,6 +920,55 @@ int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches
     *launches = n;
     batch->timed = 0;
     return QMCCPW_OK;
+}
+
+int qmccpw_batch_segment_timing(qmccpw_batch_t batch, float *segment_ms, int32_t *launches) {
+    g_last_error.clear();
+    if (!batch || !segment_ms || !launches) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    const int cap = static_cast<int>(batch->ev_start.size());
+    const int n = std::min(batch->timed, cap);
+    for (int k = 0; k < kSegments; ++k) segment_ms[k] = 0.0f;
+    if (batch->use_graph) {  // a replay records no segment boundaries
+        *launches = 0;
+        return QMCCPW_OK;
+    }
+    for (int i = 0; i < n; ++i) {
+        QMC_CUDA(cudaEventSynchronize(batch->ev_stop[i]));
+        cudaEvent_t prev = batch->ev_start[i];
+        for (int k = 0; k < kSegments; ++k) {
+            float ms = 0.0f;
+            QMC_CUDA(cudaEventElapsedTime(&ms, prev, batch->ev_seg[i * kSegments + k]));
+            segment_ms[k] += ms;
+            prev = batch->ev_seg[i * kSegments + k];
+        }
+    }
+    *launches = n;
+    return QMCCPW_OK;
+}
+
+int qmccpw_selftest_bounded_wait(int32_t device, int32_t limit_us, int32_t *kernel_status) {
+    g_last_error.clear();
+    if (!kernel_status || limit_us < 1 || limit_us > 1000000)
+        return fail(QMCCPW_ERR_INVALID_ARG, "NULL status or limit outside 1..1e6 us");
+    QMC_CUDA(cudaSetDevice(device));
+    cudaStream_t st = nullptr;
+    QMC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    DevBuf flag;
+    int rc = flag.alloc(sizeof(int));
+    int host = -1;
+    if (rc == QMCCPW_OK) {
+        cudaError_t e = cudaMemsetAsync(flag.ptr, 0xff, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = static_cast<cudaError_t>(launch_bounded_wait_probe(static_cast<uint64_t>(limit_us) * 1000u,
+                                                                   flag.as<int>(), st));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&host, flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(QMCCPW_ERR_CUDA, cudaGetErrorString(e));
+    }
+    flag.release();
+    cudaStreamDestroy(st);
+    *kernel_status = host;
+    return rc;
 }
 
 int qmccpw_batch_free(qmccpw_batch_t batch) {
@@ -1024,7 +1089,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.groups = kThreads / P;
     c.n_levels = static_cast<int>(bp.level_start.size()) - 1;
     c.row_stride = (n + 1) | 1;
-    c.z_by_dim = (construction == QMCCPW_PCA ||
+    c.z_by_dim = (construction != QMCCPW_BB ||
                   (precision != QMCCPW_FP64 && c.groups == 1 && (n == 63 || n == 15))) ? 1 : 0;
     c.N = N;
     c.item_base = 0;
@@ -1227,7 +1292,8 @@ int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t constructio
     if (!plan) return fail(QMCCPW_ERR_INVALID_ARG, "NULL plan");
     if (precision != QMCCPW_FP64 && precision != QMCCPW_MIXED)
         return fail(QMCCPW_ERR_INVALID_ARG, "tuning applies to the FP64 and MIXED CUDA-core kernels");
-    if (construction != QMCCPW_BB && construction != QMCCPW_PCA) return fail(QMCCPW_ERR_INVALID_ARG, "construction");
+    if (construction != QMCCPW_BB && construction != QMCCPW_PCA && construction != QMCCPW_STD)
+        return fail(QMCCPW_ERR_INVALID_ARG, "construction");
     if (d < 1 || d > plan->d_max) return fail(QMCCPW_ERR_INVALID_ARG, "d outside the plan");
     std::lock_guard<std::mutex> lock(plan->mu);
     const auto key = std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, construction, d);

@@ -218,6 +218,45 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
     }
 }
 
+// Standard construction: W~(s_i) = sqrt(dt) (z_1 + ... + z_i).  The G
+// threads of a point split its dates into G contiguous blocks: each sums its
+// block's z, the sums of the earlier blocks (through shared memory, added in
+// block order) give its starting value, and it walks its block again adding
+// every date to its accumulator.
+template <typename T> __device__ __forceinline__ T small_int_to(int i);
+template <> __device__ __forceinline__ float small_int_to<float>(int i) { return small_uint_to_float(static_cast<uint32_t>(i)); }
+template <> __device__ __forceinline__ double small_int_to<double>(int i) { return static_cast<double>(i); }
+
+__shared__ double forward_block_sums[kThreads];  // one per thread, shared by the product types' instances
+
+template <typename T, int TYPE>
+__device__ void forward_phase(const ContractDev &c, const T *zw, int stride, PathAcc<T> &acc) {
+    T *block_sum = reinterpret_cast<T *>(forward_block_sums);
+    const int P = 1 << c.tile_log2;
+    const int pt = threadIdx.x & (P - 1);
+    const int g = threadIdx.x >> c.tile_log2;
+    const int n = c.n;
+    const int per = (n + c.groups - 1) / c.groups;
+    const int i0 = 1 + g * per, i1 = min(n, (g + 1) * per);  // this thread's dates (may be none)
+    const T *row = zw + pt * stride;                          // row[i] = z of dimension i - 1
+    T w = T(0);
+    if (c.groups > 1) {
+        for (int i = i0; i <= i1; ++i) w += row[i];
+        block_sum[threadIdx.x] = w;
+        __syncthreads();
+        w = T(0);
+        for (int h = 0; h < g; ++h) w += block_sum[h * P + pt];
+    }
+    const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
+    for (int i = i0; i <= i1; ++i) {
+        w += row[i];
+        T Wi;
+        if constexpr (sizeof(T) == 8) Wi = w * c.sqrt_t1;
+        else Wi = fmaf(w, c.ff_sqrt_t1[0], w * c.ff_sqrt_t1[1]);
+        acc.template add<TYPE>(i, Wi, omega, sigma, small_int_to<T>(i) * dt);
+    }
+}
+
 // Phase 2 for one product type: returns, for threads t < P, the merged
 // accumulator of point t in `acc` (other threads' acc is unspecified).
 template <typename T, int CONS, int TYPE>
@@ -234,6 +273,15 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
             }
         }
         bridge_phase<T, TYPE>(c, zw, stride, acc);
+        if (c.groups == 1) return;
+        __syncthreads();
+        stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
+        __syncthreads();
+        if (threadIdx.x < P) merge_partials<T>(zw, P, c.groups, threadIdx.x, TYPE, acc);
+        return;
+    } else if constexpr (CONS == QMCCPW_STD) {
+        acc.init(TYPE, threadIdx.x < P);
+        forward_phase<T, TYPE>(c, zw, stride, acc);
         if (c.groups == 1) return;
         __syncthreads();
         stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
@@ -504,40 +552,47 @@ size_t fused_smem_bytes(int precision, int n, int tile_log2) {
     return ((zw > red ? zw : red) + 15) & ~size_t(15);
 }
 
+// Raise each kernel's dynamic shared-memory limit to what the per-block
+// opt-in maximum leaves beside that kernel's static shared memory.
 template <typename T>
-static cudaError_t set_limit_all(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<T, QMCCPW_BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static cudaError_t set_limit(void (*kernel)(LaunchParams), int optin) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fused_kernel<T, QMCCPW_PCA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - static_cast<int>(fa.sharedSizeBytes));
 }
 
-int fused_set_smem_limit(int precision, size_t bytes) {
-    const int b = static_cast<int>(bytes);
+template <typename T>
+static cudaError_t set_limit_all(int optin) {
+    cudaError_t e = set_limit<T>(fused_kernel<T, QMCCPW_BB>, optin);
+    if (e == cudaSuccess) e = set_limit<T>(fused_kernel<T, QMCCPW_PCA>, optin);
+    if (e == cudaSuccess) e = set_limit<T>(fused_kernel<T, QMCCPW_STD>, optin);
+    return e;
+}
+
+template <typename T>
+static auto fused_for(int construction) -> void (*)(LaunchParams) {
+    return construction == QMCCPW_BB ? fused_kernel<T, QMCCPW_BB>
+           : construction == QMCCPW_STD ? fused_kernel<T, QMCCPW_STD>
+                                        : fused_kernel<T, QMCCPW_PCA>;
+}
+
+int fused_set_smem_limit(int precision, size_t optin_bytes) {
+    const int b = static_cast<int>(optin_bytes);
     return static_cast<int>(precision == QMCCPW_FP64 ? set_limit_all<double>(b) : set_limit_all<float>(b));
 }
 
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm) {
-    cudaError_t e;
-    if (precision == QMCCPW_FP64)
-        e = construction == QMCCPW_BB
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<double, QMCCPW_BB>, kThreads, smem_bytes)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<double, QMCCPW_PCA>, kThreads, smem_bytes);
-    else
-        e = construction == QMCCPW_BB
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<float, QMCCPW_BB>, kThreads, smem_bytes)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_kernel<float, QMCCPW_PCA>, kThreads, smem_bytes);
-    return static_cast<int>(e);
+    const void *f = precision == QMCCPW_FP64 ? reinterpret_cast<const void *>(fused_for<double>(construction))
+                                             : reinterpret_cast<const void *>(fused_for<float>(construction));
+    return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem_bytes));
 }
 
 int launch_fused(const LaunchParams &p, int precision, int construction, size_t smem_bytes, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (precision == QMCCPW_FP64) {
-        if (construction == QMCCPW_BB) fused_kernel<double, QMCCPW_BB><<<grid, kThreads, smem_bytes, s>>>(p);
-        else fused_kernel<double, QMCCPW_PCA><<<grid, kThreads, smem_bytes, s>>>(p);
-    } else {
-        if (construction == QMCCPW_BB) fused_kernel<float, QMCCPW_BB><<<grid, kThreads, smem_bytes, s>>>(p);
-        else fused_kernel<float, QMCCPW_PCA><<<grid, kThreads, smem_bytes, s>>>(p);
-    }
+    if (precision == QMCCPW_FP64) fused_for<double>(construction)<<<grid, kThreads, smem_bytes, s>>>(p);
+    else fused_for<float>(construction)<<<grid, kThreads, smem_bytes, s>>>(p);
     return static_cast<int>(cudaGetLastError());
 }
 

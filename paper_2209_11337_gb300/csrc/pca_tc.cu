@@ -79,8 +79,8 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Poll the barrier for the given phase parity; false if kWaitLimitNs passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Poll the barrier for the given phase parity; false if limit_ns passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
     const uint32_t addr = smem_u32(bar);
     const uint64_t start = global_ns();
     while (true) {
@@ -93,7 +93,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (global_ns() - start > kWaitLimitNs) return false;
+        if (global_ns() - start > limit_ns) return false;
     }
 }
 
@@ -648,7 +648,27 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_const
     }
 }
 
+// Failure-path check of the bounded wait: an mbarrier that nothing arrives at
+// (count 1, no arrive, no copy), waited on with the kernels' own poll loop and
+// a short limit; the wait must give up and the kernel exit normally.
+__global__ void bounded_wait_probe_kernel(uint64_t limit_ns, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool done = mbar_wait(&bar, 0u, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0) *status = done ? QMCCPW_OK : QMCCPW_ERR_TIMEOUT;
+}
+
 }  // namespace
+
+int launch_bounded_wait_probe(uint64_t limit_ns, int *status, void *stream) {
+    bounded_wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(limit_ns, status);
+    return static_cast<int>(cudaGetLastError());
+}
 
 size_t pca_tc_smem_bytes(int kind) {
     const size_t scratch = 4 * kThreads * sizeof(double) > 4 * kThreads * 12 ? 4 * kThreads * sizeof(double)

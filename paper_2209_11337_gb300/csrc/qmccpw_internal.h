@@ -134,13 +134,14 @@ int launch_sobol_dump(const uint32_t *table, const uint32_t *shift, int jstride,
                       uint64_t k0, uint64_t count, uint32_t *out, void *stream);
 // dynamic shared memory of one CTA for a contract with n dims and 2^tile_log2 points
 size_t fused_smem_bytes(int precision, int n, int tile_log2);
-int fused_set_smem_limit(int precision, size_t bytes);
+int fused_set_smem_limit(int precision, size_t optin_bytes);  // optin_bytes: the device's per-block opt-in maximum
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
 
 // Tensor-core PCA (pca_tc.cu).  kind 0: bf16 split (4 products), 1: tf32
 // split (3 products), both n <= 64 with Ahat resident; kinds 2 (bf16) and 3
 // (tf32): n <= 256, Ahat streamed in K-chunks.
 size_t pca_tc_smem_bytes(int kind);
+int launch_bounded_wait_probe(uint64_t limit_ns, int *status, void *stream);
 int pca_tc_max_n(int kind);                          // largest n (dimensions) the kind supports
 int pca_tc_prepare(int kind, size_t smem_bytes);     // raise the dynamic shared memory limit
 int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks);

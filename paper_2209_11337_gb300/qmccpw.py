@@ -41,6 +41,7 @@ QMCCPW_GEOMETRIC_ASIAN_CALL = 3
 
 QMCCPW_BB = 0
 QMCCPW_PCA = 1
+QMCCPW_STD = 2
 
 QMCCPW_FP64 = 0
 QMCCPW_MIXED = 1
@@ -52,7 +53,8 @@ EXPORTS = (
     "qmccpw_plan", "qmccpw_greeks", "qmccpw_greeks_batch", "qmccpw_batch_create",
     "qmccpw_batch_launch", "qmccpw_batch_results", "qmccpw_batch_device_results",
     "qmccpw_batch_launch_count", "qmccpw_batch_set_timing", "qmccpw_batch_timing",
-    "qmccpw_batch_use_graph", "qmccpw_batch_free", "qmccpw_sobol_points",
+    "qmccpw_batch_use_graph", "qmccpw_batch_segment_timing", "qmccpw_batch_free",
+    "qmccpw_selftest_bounded_wait", "qmccpw_sobol_points",
     "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_server_start", "qmccpw_submit", "qmccpw_poll",
     "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_autotune", "qmccpw_tuning_get",
     "qmccpw_tuning_set", "qmccpw_free", "qmccpw_last_error",
@@ -128,6 +130,8 @@ def library() -> ctypes.CDLL:
             L.qmccpw_batch_set_timing.argtypes = [vp, i32]
             L.qmccpw_batch_timing.argtypes = [vp, P(ctypes.c_float), P(i32)]
             L.qmccpw_batch_use_graph.argtypes = [vp, i32]
+            L.qmccpw_selftest_bounded_wait.argtypes = [i32, i32, P(i32)]
+            L.qmccpw_batch_segment_timing.argtypes = [vp, P(ctypes.c_float), P(i32)]
             L.qmccpw_batch_free.argtypes = [vp]
             L.qmccpw_sobol_points.argtypes = [vp, u32, i32, u64, u64, P(u32)]
             L.qmccpw_point_values.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), i32, i32, u32, u64, u64,
@@ -233,6 +237,12 @@ class Batch:
     def set_timing(self, capacity: int) -> None:
         _check(library().qmccpw_batch_set_timing(self.handle, capacity))
 
+    def segment_timing(self):
+        """([bridge, standard, streamed tensor-core PCA, other PCA] milliseconds, launches), record kept."""
+        ms, n = (ctypes.c_float * 4)(), ctypes.c_int32()
+        _check(library().qmccpw_batch_segment_timing(self.handle, ms, ctypes.byref(n)))
+        return list(ms), n.value
+
     def use_graph(self, enable: bool = True) -> None:
         """Replay the launch sequence as one CUDA graph (qmccpw_batch_use_graph)."""
         _check(library().qmccpw_batch_use_graph(self.handle, 1 if enable else 0))
@@ -276,6 +286,13 @@ def qmccpw_sobol_points(plan, replicate: int, ndims: int, k0: int, count: int) -
     _check(library().qmccpw_sobol_points(plan, replicate, ndims, k0, count,
                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
     return out
+
+
+def qmccpw_selftest_bounded_wait(device: int = 0, limit_us: int = 10000) -> int:
+    """Status the probe kernel recorded (QMCCPW_ERR_TIMEOUT when the bounded wait gave up)."""
+    st = ctypes.c_int32()
+    _check(library().qmccpw_selftest_bounded_wait(device, limit_us, ctypes.byref(st)))
+    return st.value
 
 
 def qmccpw_point_values(plan, type: int, d: int, K: float, T: float, S0: float, r: float, sigma: float,
