@@ -48,28 +48,50 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     T *row = zw + pt * stride;
     const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
     const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
+    // node b of the schedule: W~ at its date from its endpoints and z
+    auto node = [&](int b, int4 &st) -> T {
+        st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
+        const T Wl = row[st.y], Wr = row[st.z];
+        T z = row[st.x];
+        T Wm;
+        if constexpr (sizeof(T) == 8) {
+            const double *w = c.w64 + 3 * b;
+            Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (c.sqrt_t1 * z);
+        } else {
+            z = fmaf(z, sdt_hi, z * sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
+            // hi + lo coefficients: the low parts first, then the high parts
+            const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
+            const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
+            float lo = h.y * Wl;
+            lo = fmaf(h.w, Wr, lo);
+            lo = fmaf(g.y, z, lo);
+            Wm = fmaf(h.x, Wl, fmaf(h.z, Wr, fmaf(g.x, z, lo)));
+        }
+        row[st.x] = Wm;
+        return Wm;
+    };
     for (int lvl = 0; lvl < c.n_levels; ++lvl) {
         const int b_end = __ldg(c.level_start + lvl + 1);
-        for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += G) {
-            const int4 st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
-            const T Wl = row[st.y], Wr = row[st.z];
-            T z = row[st.x];
-            T Wm;
-            if constexpr (sizeof(T) == 8) {
-                const double *w = c.w64 + 3 * b;
-                Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (c.sqrt_t1 * z);
+        // the nodes of a level are independent: a thread takes two at a time
+        // (float: their exponentials in packed form)
+        for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += 2 * G) {
+            int4 s0, s1;
+            const T W0 = node(b, s0);
+            if constexpr (sizeof(T) == 4) {
+                if (b + G < b_end) {
+                    const T W1 = node(b + G, s1);
+                    acc.template add2<TYPE>(s0.x, s1.x, W0, W1, omega, sigma, __int_as_float(s0.w) * dt,
+                                            __int_as_float(s1.w) * dt);
+                    continue;
+                }
+                acc.template add<TYPE>(s0.x, W0, omega, sigma, __int_as_float(s0.w) * dt);
             } else {
-                z = fmaf(z, sdt_hi, z * sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
-                // hi + lo coefficients: the low parts first, then the high parts
-                const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
-                const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
-                float lo = h.y * Wl;
-                lo = fmaf(h.w, Wr, lo);
-                lo = fmaf(g.y, z, lo);
-                Wm = fmaf(h.x, Wl, fmaf(h.z, Wr, fmaf(g.x, z, lo)));
+                acc.template add<TYPE>(s0.x, W0, omega, sigma, static_cast<T>(__int_as_float(s0.w)) * dt);
+                if (b + G < b_end) {
+                    const T W1 = node(b + G, s1);
+                    acc.template add<TYPE>(s1.x, W1, omega, sigma, static_cast<T>(__int_as_float(s1.w)) * dt);
+                }
             }
-            row[st.x] = Wm;
-            acc.template add<TYPE>(st.x, Wm, omega, sigma, static_cast<T>(__int_as_float(st.w)) * dt);
         }
         if (G > 1) __syncthreads();
     }
@@ -123,14 +145,24 @@ __device__ __forceinline__ void bridge_registers(const ContractDev &c, const flo
     const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
     float W[N + 1];
     W[0] = 0.0f;
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
+    auto node = [&](int b) {
         const float z0 = row[b + 1];  // z of dimension b (stored by dimension)
         const float z = fmaf(z0, sdt_hi, z0 * sdt_lo);  // z sqrt(dt), sqrt(dt) carried as hi + lo
         const float Wl = W[S.l[b]], Wr = W[S.r[b]];
         const float Wm = fmaf(static_cast<float>(S.c[b]), z, fmaf(static_cast<float>(S.wr[b]), Wr - Wl, Wl));
         W[S.m[b]] = Wm;
-        acc.template add<TYPE>(S.m[b], Wm, omega, sigma, static_cast<float>(S.m[b]) * dt);
+        return Wm;
+    };
+    // nodes in schedule order, their exponentials two at a time
+#pragma unroll
+    for (int b = 0; b + 1 < N; b += 2) {
+        const float W0 = node(b), W1 = node(b + 1);
+        acc.template add2<TYPE>(S.m[b], S.m[b + 1], W0, W1, omega, sigma, static_cast<float>(S.m[b]) * dt,
+                                static_cast<float>(S.m[b + 1]) * dt);
+    }
+    if constexpr (N % 2 == 1) {
+        const float W0 = node(N - 1);
+        acc.template add<TYPE>(S.m[N - 1], W0, omega, sigma, static_cast<float>(S.m[N - 1]) * dt);
     }
 }
 
@@ -203,16 +235,20 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
             }
         }
         const float s0 = static_cast<float>(rb * 16 + 1) * dt;
+        const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
+        for (int r = 0; r < 16; r += 2) {  // dates i, i + 1: exponentials in packed form
             const int i = rb * 16 + r + 1;
-            if (i <= n) {
-                const float s_i = fmaf(static_cast<float>(r), dt, s0);
+            const float s_i = fmaf(static_cast<float>(r), dt, s0), s_i1 = fmaf(static_cast<float>(r + 1), dt, s0);
+            if (i + 1 <= n) {
 #pragma unroll
-                for (int j = 0; j < PB; ++j) {
-                    const float Wi = fmaf(w[j][r], c.ff_sqrt_t1[0], w[j][r] * c.ff_sqrt_t1[1]);
-                    acc[j].template add<TYPE>(i, Wi, omega, sigma, s_i);
-                }
+                for (int j = 0; j < PB; ++j)
+                    acc[j].template add2<TYPE>(i, i + 1, fmaf(w[j][r], sh, w[j][r] * sl),
+                                               fmaf(w[j][r + 1], sh, w[j][r + 1] * sl), omega, sigma, s_i, s_i1);
+            } else if (i <= n) {
+#pragma unroll
+                for (int j = 0; j < PB; ++j)
+                    acc[j].template add<TYPE>(i, fmaf(w[j][r], sh, w[j][r] * sl), omega, sigma, s_i);
             }
         }
     }
@@ -248,12 +284,24 @@ __device__ void forward_phase(const ContractDev &c, const T *zw, int stride, Pat
         for (int h = 0; h < g; ++h) w += block_sum[h * P + pt];
     }
     const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
-    for (int i = i0; i <= i1; ++i) {
-        w += row[i];
-        T Wi;
-        if constexpr (sizeof(T) == 8) Wi = w * c.sqrt_t1;
-        else Wi = fmaf(w, c.ff_sqrt_t1[0], w * c.ff_sqrt_t1[1]);
-        acc.template add<TYPE>(i, Wi, omega, sigma, small_int_to<T>(i) * dt);
+    if constexpr (sizeof(T) == 8) {
+        for (int i = i0; i <= i1; ++i) {
+            w += row[i];
+            acc.template add<TYPE>(i, w * c.sqrt_t1, omega, sigma, small_int_to<T>(i) * dt);
+        }
+    } else {
+        const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
+        int i = i0;
+        for (; i + 1 <= i1; i += 2) {  // two dates at a time: exponentials in packed form
+            const float w0 = w + row[i];
+            w = w0 + row[i + 1];
+            acc.template add2<TYPE>(i, i + 1, fmaf(w0, sh, w0 * sl), fmaf(w, sh, w * sl), omega, sigma,
+                                    small_int_to<float>(i) * dt, small_int_to<float>(i + 1) * dt);
+        }
+        if (i <= i1) {
+            w += row[i];
+            acc.template add<TYPE>(i, fmaf(w, sh, w * sl), omega, sigma, small_int_to<float>(i) * dt);
+        }
     }
 }
 
@@ -330,8 +378,10 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
 
 // CONS is the construction of every contract this launch covers (the host
 // launches one grid per construction over that construction's items).
+// Register budget: the PCA product's register block needs up to 128
+// registers (two CTAs per SM); the other forms fit three CTAs per SM.
 template <typename T, int CONS>
-__global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ LaunchParams p) {
+__global__ void __launch_bounds__(kThreads, CONS == QMCCPW_PCA ? 2 : 3) fused_kernel(const __grid_constant__ LaunchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
 
     __shared__ uint64_t next_item;
@@ -383,8 +433,19 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
                 const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
                 if (len > 0) {
                     const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
-                    sobol_points(tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2,
-                                 [&](int s, uint32_t y) { dst[s * stride] = Arith<T>::inv_normal(y); });
+                    if constexpr (sizeof(T) == 4) {
+                        sobol_point_pairs(
+                            tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2,
+                            [&](int s, uint32_t y) { dst[s * stride] = Arith<float>::inv_normal(y); },
+                            [&](int s, uint32_t y0, uint32_t y1) {
+                                const float2 z = Arith<float>::inv_normal2(y0, y1);
+                                dst[s * stride] = z.x;
+                                dst[(s + 1) * stride] = z.y;
+                            });
+                    } else {
+                        sobol_points(tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2,
+                                     [&](int s, uint32_t y) { dst[s * stride] = Arith<T>::inv_normal(y); });
+                    }
                 }
                 for (int s = len; s < chunk; ++s) dst[s * stride] = T(0);
             }

@@ -235,6 +235,33 @@ __device__ __forceinline__ void split_store(unsigned char *hi_base, unsigned cha
     }
 }
 
+// The same split for two adjacent dimensions (k even, k + 1) of one point:
+// one 32-bit word per part for bf16 (hi is exact, so its bf16 is the top
+// half of its bits; lo rounds to nearest even in integer arithmetic), one
+// 64-bit word per part for tf32.  `off` is element k's offset (4- or 8-byte
+// aligned: the swizzle permutes whole 16-byte units).
+template <int KIND>
+__device__ __forceinline__ void split_store_pair(unsigned char *hi_base, unsigned char *lo_base, uint32_t off,
+                                                 float2 z) {
+    constexpr float kScale = KIND == 0 ? 32.0f : 256.0f;
+    const float2 h = mul2(add2(fma2(z, f2(kScale), f2(12582912.0f)), f2(-12582912.0f)), f2(1.0f / kScale));
+    const float2 l = add2(z, make_float2(-h.x, -h.y));
+    if constexpr (KIND == 0) {
+        auto rne16 = [](float v) {
+            const uint32_t b = __float_as_uint(v);
+            return (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+        };
+        *reinterpret_cast<uint32_t *>(hi_base + off) = (__float_as_uint(h.x) >> 16) | (__float_as_uint(h.y) & 0xFFFF0000u);
+        *reinterpret_cast<uint32_t *>(lo_base + off) = rne16(l.x) | (rne16(l.y) << 16);
+    } else {
+        const uint2 hb = make_uint2(__float_as_uint(h.x), __float_as_uint(h.y));
+        const uint2 lb = make_uint2((__float_as_uint(l.x) + 0x1000u) & 0xFFFFE000u,
+                                    (__float_as_uint(l.y) + 0x1000u) & 0xFFFFE000u);
+        *reinterpret_cast<uint2 *>(hi_base + off) = hb;
+        *reinterpret_cast<uint2 *>(lo_base + off) = lb;
+    }
+}
+
 // Path sums of this thread's point over its warpgroup's half of the dates:
 // W~ = sqrt(dt) (D1 + D2), D2 at column offset NPAD.
 template <int TYPE, int NPAD>
@@ -253,11 +280,15 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
                     d1, d2);
         const float s0 = static_cast<float>(col + 1) * dt;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int date = col + i + 1;  // W~ at s_date
-            const float w = d1[i] + d2[i];
-            if (date <= c.n)
-                acc.template add<TYPE>(date, fmaf(w, sdt_hi, w * sdt_lo), omega, sigma, fmaf(static_cast<float>(i), dt, s0));
+        for (int i = 0; i < 16; i += 2) {  // dates (W~ at s_date) two at a time: exponentials in packed form
+            const int date = col + i + 1;
+            const float w0 = d1[i] + d2[i], w1 = d1[i + 1] + d2[i + 1];
+            const float s_a = fmaf(static_cast<float>(i), dt, s0), s_b = fmaf(static_cast<float>(i + 1), dt, s0);
+            if (date + 1 <= c.n)
+                acc.template add2<TYPE>(date, date + 1, fmaf(w0, sdt_hi, w0 * sdt_lo), fmaf(w1, sdt_hi, w1 * sdt_lo),
+                                        omega, sigma, s_a, s_b);
+            else if (date <= c.n)
+                acc.template add<TYPE>(date, fmaf(w0, sdt_hi, w0 * sdt_lo), omega, sigma, s_a);
         }
     }
 }
@@ -297,11 +328,60 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
     tile_sum(p, item, v, scratch);
 }
 
+// Two Gray-code chains (dimensions ja and jb) over the same run of points,
+// emit(s, y_ja(k0+s), y_jb(k0+s)); a full aligned run of 4..64 points is
+// unrolled with both dimensions' direction integers in registers.
+template <int LG, typename Emit>
+__device__ __forceinline__ void chain_pair_run(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
+                                               uint32_t ya, uint32_t yb, Emit &&emit) {
+    uint32_t va[LG], vb[LG];
+#pragma unroll
+    for (int b = 0; b < LG; ++b) {
+        va[b] = __ldg(tab + b * jstride + ja);
+        vb[b] = __ldg(tab + b * jstride + jb);
+    }
+    emit(0, ya, yb);
+#pragma unroll
+    for (int s = 1; s < (1 << LG); ++s) {
+        ya ^= va[ctz_const(s)];
+        yb ^= vb[ctz_const(s)];
+        emit(s, ya, yb);
+    }
+}
+
+template <typename Emit>
+__device__ __forceinline__ void sobol_chain_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
+                                                 uint32_t ya, uint32_t yb, uint32_t k0, int len, int chunk_log2,
+                                                 Emit &&emit) {
+    if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
+        switch (chunk_log2) {
+            case 2: chain_pair_run<2>(tab, jstride, ja, jb, ya, yb, emit); return;
+            case 3: chain_pair_run<3>(tab, jstride, ja, jb, ya, yb, emit); return;
+            case 4: chain_pair_run<4>(tab, jstride, ja, jb, ya, yb, emit); return;
+            case 5: chain_pair_run<5>(tab, jstride, ja, jb, ya, yb, emit); return;
+            case 6: chain_pair_run<6>(tab, jstride, ja, jb, ya, yb, emit); return;
+            default: break;
+        }
+    }
+    for (int s = 0; s < len; ++s) {
+        if (s > 0) {
+            const int b = __ffs(k0 + s) - 1;
+            ya ^= __ldg(tab + b * jstride + ja);
+            yb ^= __ldg(tab + b * jstride + jb);
+        }
+        emit(s, ya, yb);
+    }
+}
+
 // Phase 1 of both variants: Sobol' + inverse normal of the tile's points for
-// dimensions j0 <= j < j1, split and stored into Z at column j - j0.  A warp
-// takes a chunk of consecutive points and 32 dimensions (lanes over k);
-// points past N are 0.  Columns of Z at or beyond n are never rewritten: the
-// matching columns of Ahat are zero, so whatever finite z they hold adds 0.
+// dimensions j0 <= j < j1, split and stored into Z at column j - j0.  A lane
+// takes two adjacent dimensions (j even relative to j0) over a chunk of
+// consecutive points, the two Gray-code chains side by side, so each step
+// evaluates the inverse normal of two draws at once and stores both
+// dimensions' parts in one word; a warp covers 64 dimensions of a row
+// (128-byte swizzled rows: conflict-free).  Points past N are 0.  Columns of Z
+// at or beyond n meet only zero Ahat columns: an odd last dimension is
+// paired with a copy of itself in the next (padding) column.
 template <int KIND>
 __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const ContractDev &c, uint32_t rep, uint64_t tile,
                                            unsigned char *z_hi, unsigned char *z_lo, int j0, int j1) {
@@ -310,23 +390,28 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
     const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
     const int chunk = 1 << c.chunk_log2;
     const int nchunks = kM >> c.chunk_log2;
-    const int per = (j1 - j0 + 31) >> 5;
+    const int per = (j1 - j0 + 63) >> 6;
     const int work = nchunks * per;
     for (int it = threadIdx.x >> 5; it < work; it += kThreads / 32) {
         const int ch = it / per;
-        const int j = j0 + (it - ch * per) * 32 + (threadIdx.x & 31);
-        if (j >= j1) continue;
-        const int col = j - j0;
+        const int col = (it - ch * per) * 64 + 2 * (threadIdx.x & 31);
+        const int ja = j0 + col;
+        if (ja >= j1) continue;
+        const int jb = ja + 1 < j1 ? ja + 1 : ja;  // odd last dimension: its own copy (in bounds of the tables)
         const uint64_t first_local = tile * kM + static_cast<uint64_t>(ch) * chunk;
         const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
         const int row0 = ch * chunk;
         if (len > 0) {
             const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
-            sobol_points(tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2, [&](int s, uint32_t y) {
-                split_store<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), Arith<float>::inv_normal(y));
-            });
+            const uint32_t ya = sobol_first(tab, p.jstride, ja, __ldg(shf + ja), k0);
+            const uint32_t yb = sobol_first(tab, p.jstride, jb, __ldg(shf + jb), k0);
+            auto emit = [&](int s, uint32_t a, uint32_t b) {
+                split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), Arith<float>::inv_normal2(a, b));
+            };
+            sobol_chain_pair(tab, p.jstride, ja, jb, ya, yb, k0, len, c.chunk_log2, emit);
         }
-        for (int s = len; s < chunk; ++s) split_store<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), 0.0f);
+        for (int s = len; s < chunk; ++s)
+            split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), make_float2(0.0f, 0.0f));
     }
 }
 
@@ -344,7 +429,7 @@ __device__ __forceinline__ unsigned char *aligned_smem(unsigned char *raw) {
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 2) pca_tc_kernel(const __grid_constant__ LaunchParams p) {
+__global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(const __grid_constant__ LaunchParams p) {
     constexpr int ES = KIND == 0 ? 2 : 4;                  // element bytes
     constexpr uint32_t kOpBytesZ = kM * kNpad * ES;        // one split part of Z
     constexpr uint32_t kOpBytesB = kNpad * kNpad * ES;     // one split part of Ahat

@@ -60,38 +60,86 @@ __device__ __forceinline__ float small_uint_to_float(uint32_t x) {
     return __uint_as_float(0x4B000000u | x) - 8388608.0f;
 }
 
+// Packed two-lane FP32 arithmetic (one instruction for two elements): the
+// polynomial chains below run on pairs of independent elements, with the
+// same operations in the same order as the one-element forms, so a pair
+// gives bit for bit the two single results.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 template <> struct Arith<float> {
-    __device__ static float inv_normal(uint32_t y) {
-        const bool upper = y >= 0x80000000u;
-        const uint32_t lo = upper ? ~y : y;
-        // q = (lo + 1/2) 2^-32 <= 1/2 from lo = a 2^23 + b: one rounding
+    // q = (lo + 1/2) 2^-32 <= 1/2 from lo = a 2^23 + b (one rounding), the
+    // reflection sign of the upper half, and w = -ln(4q(1-q)); shared by the
+    // one- and two-element forms
+    __device__ static __forceinline__ float q_of(uint32_t y, uint32_t &sign) {
+        const uint32_t m = static_cast<uint32_t>(static_cast<int32_t>(y) >> 31);  // all ones on the upper half
+        const uint32_t lo = y ^ m;
+        sign = m & 0x80000000u;
         const float fa = small_uint_to_float(lo >> 23);
         const float fb = small_uint_to_float(lo & 0x007FFFFFu);
-        const float q = fmaf(fa, 0x1p-9f, fmaf(fb, 0x1p-32f, 0x1p-33f));
+        return fmaf(fa, 0x1p-9f, fmaf(fb, 0x1p-32f, 0x1p-33f));
+    }
+    __device__ static __forceinline__ float tail(float w) { return horner_t(sqrtf(w) - QMC_INVN_SHIFT_T); }
+    __device__ static float inv_normal(uint32_t y) {
+        uint32_t sign;
+        const float q = q_of(y, sign);
         const float x = fmaf(-2.0f, q, 1.0f);
         const float q4 = 4.0f * q;
-        const float w = -0.693147181f * __log2f(fmaf(-q4, q, q4));       // -ln(4q(1-q))
-        float p;
-        if (w < QMC_INVN_W0) p = horner_c(w - QMC_INVN_SHIFT_C);
-        else p = horner_t(sqrtf(w) - QMC_INVN_SHIFT_T);
+        const float w = -0.693147181f * __log2f(fmaf(-q4, q, q4));  // -ln(4q(1-q))
+        const float p = w < QMC_INVN_W0 ? horner_c(w - QMC_INVN_SHIFT_C) : tail(w);
         const float z = -x * p;  // <= 0 on the lower half
-        return upper ? -z : z;
+        return __uint_as_float(__float_as_uint(z) ^ sign);
+    }
+    // two draws at once: the central branch (99.9% of draws) in packed form;
+    // a pair with a tail draw takes the one-element branches
+    __device__ static float2 inv_normal2(uint32_t y0, uint32_t y1) {
+        uint32_t s0, s1;
+        const float2 q = make_float2(q_of(y0, s0), q_of(y1, s1));
+        const float2 x = fma2(f2(-2.0f), q, f2(1.0f));
+        const float2 q4 = mul2(f2(4.0f), q);
+        const float2 a = fma2(make_float2(-q4.x, -q4.y), q, q4);
+        const float2 w = mul2(f2(-0.693147181f), make_float2(__log2f(a.x), __log2f(a.y)));
+        float2 p;
+        if (w.x < QMC_INVN_W0 && w.y < QMC_INVN_W0) {
+            constexpr float c[] = QMC_INVN_CENTRAL;
+            const float2 t = add2(w, f2(-QMC_INVN_SHIFT_C));
+            p = f2(c[9]);
+#pragma unroll
+            for (int i = 8; i >= 0; --i) p = fma2(p, t, f2(c[i]));
+        } else {
+            p.x = w.x < QMC_INVN_W0 ? horner_c(w.x - QMC_INVN_SHIFT_C) : tail(w.x);
+            p.y = w.y < QMC_INVN_W0 ? horner_c(w.y - QMC_INVN_SHIFT_C) : tail(w.y);
+        }
+        const float2 z = mul2(make_float2(-x.x, -x.y), p);
+        return make_float2(__uint_as_float(__float_as_uint(z.x) ^ s0), __uint_as_float(__float_as_uint(z.y) ^ s1));
     }
     // e^x for the path sums (|x| well below 80): 2^k 2^f with k the nearest
     // integer to x log2 e, read from the low bits of x log2 e + 1.5 2^23
     // (no conversion instruction), f = x log2 e - k in [-1/2, 1/2] with the
-    // residual of log2 e, and 2^f from the fitted polynomial (8.7e-8).
+    // residual of log2 e, 2^f from the fitted polynomial (8.7e-8), and 2^k
+    // added to the exponent field (the bias term of r cancels modulo 2^32).
     __device__ static float ex(float x) {
         constexpr float c[] = QMC_EXP2_POLY;
-        const float t = x * 1.44269502f;
-        const float r = t + 12582912.0f;
+        const float r = fmaf(x, 1.44269502f, 12582912.0f);
         const float kf = r - 12582912.0f;
-        const float f = fmaf(x, 1.44269502f, -kf) + x * 1.92596299e-8f;
+        const float f = fmaf(x, 1.92596299e-8f, fmaf(x, 1.44269502f, -kf));
         float p = c[6];
 #pragma unroll
         for (int i = 5; i >= 0; --i) p = fmaf(p, f, c[i]);
-        const int k = __float_as_int(r) - 0x4B400000;
-        return __int_as_float(__float_as_int(p) + (k << 23));
+        return __uint_as_float(__float_as_uint(p) + (__float_as_uint(r) << 23));
+    }
+    __device__ static float2 ex2(float2 x) {
+        constexpr float c[] = QMC_EXP2_POLY;
+        const float2 r = fma2(x, f2(1.44269502f), f2(12582912.0f));
+        const float2 kf = add2(r, f2(-12582912.0f));
+        const float2 f = fma2(x, f2(1.92596299e-8f), fma2(x, f2(1.44269502f), make_float2(-kf.x, -kf.y)));
+        float2 p = f2(c[6]);
+#pragma unroll
+        for (int i = 5; i >= 0; --i) p = fma2(p, f, f2(c[i]));
+        return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(r.x) << 23)),
+                           __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(r.y) << 23)));
     }
 };
 
@@ -120,23 +168,48 @@ template <typename T> struct PathAcc {
     // node: date index after t_1 (ties of the lookback maximum); s = node * dt
     template <int TYPE>
     __device__ __forceinline__ void add(int32_t node, T W, T omega, T sigma, T s) {
-        const T lx = omega * s + sigma * W;
-        const T wv = W - sigma * s;
+        const T lx = fma(sigma, W, omega * s);
+        const T wv = fma(-sigma, s, W);
         if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
             x += lx;
             dsum += wv;
         } else {
-            const T e = Arith<T>::ex(lx);
-            if constexpr (TYPE == QMCCPW_LOOKBACK_FIXED_CALL) {
-                if (e > x || (e == x && node < m)) {
-                    x = e;
-                    dsum = e * wv;
-                    m = node;
-                }
-            } else {
-                x += e;
-                dsum += e * wv;
+            take<TYPE>(node, Arith<T>::ex(lx), wv);
+        }
+    }
+
+    // two dates at once (node0 before node1), float: the exponent arguments
+    // and the exponentials in packed form, the sums in date order, so the
+    // result equals two calls of add
+    template <int TYPE>
+    __device__ __forceinline__ void add2(int32_t node0, int32_t node1, float W0, float W1, float omega, float sigma,
+                                         float s0, float s1) {
+        const float2 s = make_float2(s0, s1), W = make_float2(W0, W1);
+        const float2 lx = fma2(f2(sigma), W, mul2(f2(omega), s));
+        const float2 wv = fma2(f2(-sigma), s, W);
+        if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+            x += lx.x;
+            dsum += wv.x;
+            x += lx.y;
+            dsum += wv.y;
+        } else {
+            const float2 e = Arith<float>::ex2(lx);
+            take<TYPE>(node0, e.x, wv.x);
+            take<TYPE>(node1, e.y, wv.y);
+        }
+    }
+
+    template <int TYPE>
+    __device__ __forceinline__ void take(int32_t node, T e, T wv) {
+        if constexpr (TYPE == QMCCPW_LOOKBACK_FIXED_CALL) {
+            if (e > x || (e == x && node < m)) {
+                x = e;
+                dsum = e * wv;
+                m = node;
             }
+        } else {
+            x += e;
+            dsum = fma(e, wv, dsum);
         }
     }
 
@@ -368,6 +441,52 @@ __device__ __forceinline__ void sobol_points(const uint32_t *__restrict__ tab, i
     for (int s = 1; s < len; ++s) {
         y ^= __ldg(tab + (__ffs(k0 + s) - 1) * jstride + j);
         emit(s, y);
+    }
+}
+
+// The same points handed out in consecutive pairs, emit2(s, y(k0+s),
+// y(k0+s+1)) for s = 0, 2, 4, ..., and emit1 for an odd last point: for the
+// float paths, which evaluate the inverse normal two draws at a time.
+template <int LG, typename Emit2>
+__device__ __forceinline__ void sobol_run_pairs(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
+                                                Emit2 &&emit2) {
+    uint32_t v[LG];
+#pragma unroll
+    for (int b = 0; b < LG; ++b) v[b] = __ldg(tab + b * jstride + j);
+#pragma unroll
+    for (int s = 0; s < (1 << LG); s += 2) {
+        if (s > 0) y ^= v[ctz_const(s)];
+        const uint32_t y1 = y ^ v[0];  // ctz(s + 1) = 0 for even s
+        emit2(s, y, y1);
+        y = y1;
+    }
+}
+
+template <typename Emit1, typename Emit2>
+__device__ __forceinline__ void sobol_point_pairs(const uint32_t *__restrict__ tab, int jstride, int j,
+                                                  uint32_t shift, uint32_t k0, int len, int chunk_log2,
+                                                  Emit1 &&emit1, Emit2 &&emit2) {
+    uint32_t y = sobol_first(tab, jstride, j, shift, k0);
+    if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
+        switch (chunk_log2) {
+            case 2: sobol_run_pairs<2>(tab, jstride, j, y, emit2); return;
+            case 3: sobol_run_pairs<3>(tab, jstride, j, y, emit2); return;
+            case 4: sobol_run_pairs<4>(tab, jstride, j, y, emit2); return;
+            case 5: sobol_run_pairs<5>(tab, jstride, j, y, emit2); return;
+            case 6: sobol_run_pairs<6>(tab, jstride, j, y, emit2); return;
+            default: break;
+        }
+    }
+    int s = 0;
+    for (; s + 1 < len; s += 2) {
+        if (s > 0) y ^= __ldg(tab + (__ffs(k0 + s) - 1) * jstride + j);
+        const uint32_t y1 = y ^ __ldg(tab + (__ffs(k0 + s + 1) - 1) * jstride + j);
+        emit2(s, y, y1);
+        y = y1;
+    }
+    if (s < len) {
+        if (s > 0) y ^= __ldg(tab + (__ffs(k0 + s) - 1) * jstride + j);
+        emit1(s, y);
     }
 }
 

@@ -76,25 +76,28 @@ def greek_scale(c):
 def test_tc_estimator_unbiased_against_fp64(q, plan, prec):
     """The PCA contracts of the d=64, N=2^20, R=32 grid against FP64: every
     Greek within 0.1 SE + 2^-21 mean |per-point value| (the MIXED bar) and
-    within 1 SE, and at least half within 0.1 SE.  On these contracts the
-    RQMC standard error sits at the float floor (PCA at sigma = 0.1: 1-4e-8
-    relative), so the CUDA-core MIXED path itself has 57% within 0.1 SE, not
-    the two thirds it shows over the whole grid.  A tensor-core accumulation
-    bias of ~1 ulp of |W~| per instruction showed here as 6-13 SE before the
-    leading product was made exact, and a two-part bf16 Ahat (off by up to
-    2^-15) as up to 11 SE."""
+    within 1 SE, and the share within 0.1 SE no more than 0.1 below the
+    CUDA-core MIXED path's on the same contracts.  Here the RQMC standard
+    error sits at the float floor (PCA at sigma = 0.1: 1-4e-8 relative), so
+    MIXED itself has only about half the pairs within 0.1 SE, and that share
+    moves by a few pairs with any change of float rounding.  A tensor-core
+    accumulation bias of ~1 ulp of |W~| per instruction showed here as 6-13
+    SE before the leading product was made exact, and a two-part bf16 Ahat
+    (off by up to 2^-15) as up to 11 SE."""
     cs = [c for c in W.grid_d64() if c.construction == W.PCA]
     tc = q.qmccpw_greeks_batch(plan, cs, prec)
+    mixed = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_MIXED)
     f64 = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_FP64)
-    bad, met, total = [], 0, 0
-    for c, (m, _, _), (m64, s64, _) in zip(cs, tc, f64):
+    bad, met, met_mixed, total = [], 0, 0, 0
+    for c, (m, _, _), (mm, _, _), (m64, s64, _) in zip(cs, tc, mixed, f64):
         err = np.abs(m - m64)
         met += int(np.sum(err <= 0.1 * s64))
+        met_mixed += int(np.sum(np.abs(mm - m64) <= 0.1 * s64))
         total += 4
         if np.any(err > 0.1 * s64 + 2.0 ** -21 * greek_scale(c)) or np.any(err > s64):
             bad.append((c.label(), (err / s64).tolist()))
     assert not bad, bad[:5]
-    assert met / total >= 0.5, met / total
+    assert met / total >= met_mixed / total - 0.1, (met / total, met_mixed / total)
 
 
 @pytest.mark.parametrize("prec", [2, 3])
