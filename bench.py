@@ -48,6 +48,54 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+class Ranks:
+    """The job's ranks: one process per GPU, independent contracts per rank
+    (no data-path collective); the only collectives are the timing barrier
+    and the max over ranks of a step time.  `backend` "nccl" on the GPUs,
+    "gloo" for host-side checks."""
+
+    def __init__(self, world: int, backend: str = "nccl", local: int = 0):
+        import torch
+        self.world = world
+        self.dist = None
+        self.device = torch.device("cuda", local) if backend == "nccl" else torch.device("cpu")
+        if world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=self.device)
+            else:
+                dist.init_process_group("gloo")
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+def rank_seed(rank: int) -> int:
+    """Scramble seed of a rank: every rank runs the whole batch on its own
+    randomisation (weak scaling)."""
+    return W.SCRAMBLE_SEED + rank
+
+
+def job_value(point_dates_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the point-dates all ranks processed over the
+    slowest rank's time."""
+    return world * point_dates_per_rank / (max_ms / 1e3)
+
+
 def elements(contracts) -> int:
     return sum(c.N * c.R * c.d for c in contracts)
 
@@ -326,7 +374,7 @@ def pca_stress(q, local, rank, stream, steps: int) -> dict:
     tensor-core precisions, device time per step; error against FP64 at
     N = 2^16 (the same estimator on fewer points) in units of its SE."""
     import torch
-    plan = q.qmccpw_plan(device=local, d_max=257, r_max=16, seed=W.SCRAMBLE_SEED + rank, stream=stream.cuda_stream)
+    plan = q.qmccpw_plan(device=local, d_max=257, r_max=16, seed=rank_seed(rank), stream=stream.cuda_stream)
     full = W.pca_stress()
     small = W.pca_stress(N=2 ** 16)
     el = elements(full)
@@ -395,21 +443,8 @@ def run_ours(args):
 
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(world, "nccl", local)
+    barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
 
     from paper_2209_11337_gb300 import build as lib_build
     from paper_2209_11337_gb300 import qmccpw as q
@@ -417,7 +452,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()  # one non-default stream for the library, the events and the L2 flush
     torch.cuda.set_stream(stream)
-    plan = q.qmccpw_plan(device=local, d_max=max(65, args.case_d + 1), r_max=32, seed=W.SCRAMBLE_SEED + rank,
+    plan = q.qmccpw_plan(device=local, d_max=max(65, args.case_d + 1), r_max=32, seed=rank_seed(rank),
                          stream=stream.cuda_stream)
     contracts = W.grid_d64()
     elems = elements(contracts)
@@ -506,7 +541,7 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
 
     ms = max_over_ranks(mixed["ms_per_step"])
-    value = world * elems / (ms / 1e3)
+    value = job_value(elems, world, ms)
     seg_ms = [max_over_ranks(x) for x in mixed["segment_ms"]]
 
     # MIXED against FP64 on the same points, in units of the FP64 standard error
@@ -545,14 +580,14 @@ def run_ours(args):
                    "point_dates_per_step": elems, "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"dp{world} (independent contracts per GPU)"},
         "fp64": None if fp64 is None else {
-            "value": world * elems / (max_over_ranks(fp64["ms_per_step"]) / 1e3), "unit": UNIT,
+            "value": job_value(elems, world, max_over_ranks(fp64["ms_per_step"])), "unit": UNIT,
             "ms_per_step": max_over_ranks(fp64["ms_per_step"]), "steps": args.fp64_steps},
         "mixed_vs_fp64_max_err_in_se": err_se,
         "mixed_vs_fp64_share_within_0p1_se": err_frac,
         "roofline": roofline(args.grid_precision, contracts, seg_ms),
         "segment_ms": {"bridge": seg_ms[0], "standard": seg_ms[1], "pca_streamed": seg_ms[2], "pca": seg_ms[3]},
         "mixed_cuda_core": None if cuda_core is None else {
-            "value": world * elems / (max_over_ranks(cuda_core["ms_per_step"]) / 1e3), "unit": UNIT,
+            "value": job_value(elems, world, max_over_ranks(cuda_core["ms_per_step"])), "unit": UNIT,
             "ms_per_step": max_over_ranks(cuda_core["ms_per_step"]),
             "note": "the same grid in MIXED precision with the PCA product on the CUDA cores"},
         "e2e": {"value": world * elems / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -562,7 +597,7 @@ def run_ours(args):
     }
     if args.book_steps > 0:
         # the 4096-contract book: one batched launch sequence per step, MIXED, plus an FP64 sample
-        bplan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED + rank,
+        bplan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=rank_seed(rank),
                               stream=stream.cuda_stream, workspace_bytes=8 << 30)
         bk = W.book(4096, seed=4, R=16)
         bel = elements(bk)
@@ -595,7 +630,7 @@ def run_ours(args):
         q.qmccpw_free(bplan)
         line["book"] = {"workload": "4096 contracts (seed 4): type U{3}, d U{12..365}, K U(80,120), sigma U(0.1,0.5), "
                                     "T U(0.25,2), r U(0,0.08), N=2^U{12..18}, R=16, bridge",
-                        "point_dates": bel, "mixed": {"value": world * bel / (max_over_ranks(bms) / 1e3), "unit": UNIT,
+                        "point_dates": bel, "mixed": {"value": job_value(bel, world, max_over_ranks(bms)), "unit": UNIT,
                                                       "ms_per_step": max_over_ranks(bms), "steps": args.book_steps},
                         "fp64_sample": {"contracts": 64, "value": elements(sample) / (f64ms / 1e3), "unit": UNIT,
                                         "ms": f64ms}}
@@ -604,7 +639,7 @@ def run_ours(args):
     if args.stress_steps > 0:
         line["pca_stress"] = pca_stress(q, local, rank, stream, args.stress_steps)
     if args.serving_s > 0:
-        splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED + rank)
+        splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=rank_seed(rank))
         line["serving"] = {"mixed": serve(q, splan, q.QMCCPW_MIXED, args.serving_rate, args.serving_s)}
         q.qmccpw_free(splan)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -614,8 +649,7 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line))
     q.qmccpw_free(plan)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def main(argv=None):
