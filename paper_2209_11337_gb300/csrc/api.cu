@@ -399,7 +399,7 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         items += static_cast<uint64_t>(c.R) * c.tiles;
         const int kp = contract_precision(precision, in.construction);
         const int seg = segment_of(kp, in.construction, c.n);
-        for (int k = seg + 1; k <= kSegments; ++k) b->seg_begin[k] = items;
+        for (int g = seg + 1; g <= kSegments; ++g) b->seg_begin[g] = items;
         for (int r = 0; r < c.R; ++r) rep_owner.push_back(static_cast<uint64_t>(k));
         reps += c.R;
         b->R[k] = c.R;

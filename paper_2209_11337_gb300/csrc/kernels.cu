@@ -384,22 +384,17 @@ template <typename T, int CONS>
 __global__ void __launch_bounds__(kThreads, CONS == QMCCPW_PCA ? 2 : 3) fused_kernel(const __grid_constant__ LaunchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
 
-    __shared__ uint64_t next_item;
+    __shared__ WorkItem work;
     while (true) {
-        // dynamic schedule: CTAs take the next item as they finish one (the
-        // result of an item never depends on which CTA ran it)
-        if (threadIdx.x == 0) next_item = p.item_begin + atomicAdd(p.work_counter, 1ull);
-        __syncthreads();
-        const uint64_t item = next_item;
+        next_work(p, work);
+        const uint64_t item = work.item;
         if (item >= p.item_end) break;
-        const int ci = find_contract(p.item_base, p.count, item);
-        const ContractDev &c = p.contracts[ci];
+        const ContractDev &c = p.contracts[work.ci];
         const int P = 1 << c.tile_log2;
         const int n = c.n;
         const int stride = c.row_stride;
-        const uint64_t local = item - c.item_base;
-        const uint32_t rep = static_cast<uint32_t>(local / static_cast<uint64_t>(c.tiles)) + p.rep_offset;
-        const uint64_t tile = local % static_cast<uint64_t>(c.tiles);
+        const uint32_t rep = work.rep;
+        const uint64_t tile = work.tile;
         T *zw = reinterpret_cast<T *>(smem);
 
         // ---- phase 1: Sobol' + inverse normal -> zw[point][slot]

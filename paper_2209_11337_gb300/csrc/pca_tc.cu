@@ -462,20 +462,15 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
     for (uint32_t i = threadIdx.x; i < 2 * kOpBytesZ / 4; i += kThreads) reinterpret_cast<uint32_t *>(z_hi)[i] = 0u;
 
     uint32_t b_phase = 0, mma_phase = 0;
-    __shared__ uint64_t next_item;
+    __shared__ WorkItem work;
     while (true) {
-        // dynamic schedule: CTAs take the next item as they finish one (the
-        // result of an item never depends on which CTA ran it)
-        if (threadIdx.x == 0) next_item = p.item_begin + atomicAdd(p.work_counter, 1ull);
-        __syncthreads();
-        const uint64_t item = next_item;
+        next_work(p, work);
+        const uint64_t item = work.item;
         if (item >= p.item_end) break;
-        const int ci = find_contract(p.item_base, p.count, item);
-        const ContractDev &c = p.contracts[ci];
+        const ContractDev &c = p.contracts[work.ci];
         const int n = c.n;
-        const uint64_t local = item - c.item_base;
-        const uint32_t rep = static_cast<uint32_t>(local / static_cast<uint64_t>(c.tiles)) + p.rep_offset;
-        const uint64_t tile = local % static_cast<uint64_t>(c.tiles);
+        const uint32_t rep = work.rep;
+        const uint64_t tile = work.tile;
 
         // ---- Ahat (hi, lo) for this n: one bulk copy when n changes
         __syncthreads();
@@ -584,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_const
     unsigned char *bbuf = z_lo + S::ZPart;                 // two chunk buffers
     unsigned char *scratch = bbuf + 2 * S::ChunkBytes;
     __shared__ TcSharedS sh;
-    __shared__ uint64_t next_item;
+    __shared__ WorkItem work;
 
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
@@ -624,17 +619,14 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_const
     };
 
     while (true) {
-        // the stop decision travels with the item: written by thread 0 only
-        // here, read by all after the barrier (an expired wait stops the loop)
-        if (threadIdx.x == 0) next_item = sh.abort ? p.item_end : p.item_begin + atomicAdd(p.work_counter, 1ull);
-        __syncthreads();
-        const uint64_t item = next_item;
+        // the stop decision travels with the item: thread 0 reads the abort
+        // flag here and ends the loop for all (an expired wait stops it)
+        next_work(p, work, threadIdx.x == 0 && sh.abort);
+        const uint64_t item = work.item;
         if (item >= p.item_end) break;
-        const int ci = find_contract(p.item_base, p.count, item);
-        const ContractDev &c = p.contracts[ci];
-        const uint64_t local = item - c.item_base;
-        const uint32_t rep = static_cast<uint32_t>(local / static_cast<uint64_t>(c.tiles)) + p.rep_offset;
-        const uint64_t tile = local % static_cast<uint64_t>(c.tiles);
+        const ContractDev &c = p.contracts[work.ci];
+        const uint32_t rep = work.rep;
+        const uint64_t tile = work.tile;
         const int nch = (c.n + S::Kc - 1) / S::Kc;        // chunks holding dimensions below n (>= 5)
         if (threadIdx.x == 0 && ok && loaded != c.tc_operand) {
             // first tile, or a contract with another d: let the prefetch of

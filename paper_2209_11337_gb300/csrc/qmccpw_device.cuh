@@ -500,6 +500,34 @@ __device__ __forceinline__ int find_contract(const uint64_t *__restrict__ base, 
     return lo;
 }
 
+// The next work item of the dynamic schedule (CTAs take items as they finish
+// one; an item's result never depends on which CTA ran it), decoded once by
+// thread 0 and handed to the CTA through shared memory: contract, replicate
+// and tile.  `stop` ends the loop for every thread.  Ends with a barrier;
+// the caller's loop must pass another barrier before the next call.
+struct WorkItem {
+    uint64_t item, tile;
+    int32_t ci;
+    uint32_t rep;
+};
+
+__device__ __forceinline__ void next_work(const LaunchParams &p, WorkItem &w, bool stop = false) {
+    if (threadIdx.x == 0) {
+        const uint64_t item = stop ? p.item_end : p.item_begin + atomicAdd(p.work_counter, 1ull);
+        w.item = item;
+        if (item < p.item_end) {
+            const int ci = find_contract(p.item_base, p.count, item);
+            const uint64_t local = item - p.contracts[ci].item_base;
+            const uint64_t tiles = static_cast<uint64_t>(p.contracts[ci].tiles);
+            const uint64_t r = local / tiles;
+            w.ci = ci;
+            w.rep = static_cast<uint32_t>(r) + p.rep_offset;
+            w.tile = local - r * tiles;
+        }
+    }
+    __syncthreads();
+}
+
 // Partial accumulators of a point live in several threads; they are staged
 // in shared memory as slot-major arrays and merged by one thread per point in
 // slot order (a fixed order, so the result does not depend on scheduling).
