@@ -334,7 +334,8 @@ static int check_contract(const contract_t *c, int construction)
     if (c->d < 1 || c->d > MAX_DIMS) return -1;
     if (!(c->K > 0.0) || !(c->T > 0.0) || !(c->S0 > 0.0) || !(c->sigma > 0.0)) return -1;
     if (!isfinite(c->K) || !isfinite(c->T) || !isfinite(c->S0) || !isfinite(c->sigma) || !isfinite(c->r)) return -1;
-    if (construction < 0 || construction > 2) return -1;
+    if (construction < 0 || construction > 4) return -1;
+    if (construction >= 3 && c->type == 2) return -1;  /* leading-coordinate conditioning: no lookback */
     return 0;
 }
 
@@ -404,6 +405,130 @@ static void greeks_from_path(const contract_t *c, const double *W, double out[4]
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Conditioning on the leading coordinate of the full-path construction     */
+/* (constructions 3: bridge, 4: PCA; the next reduction the paper names in  */
+/* Sec. 6-7, GPCA-style).  The whole path W(t_1..t_d), t_j = j dt, is built */
+/* from d Gaussians by the bridge or PCA of d dates; W(t_j) = a_j x + R_j    */
+/* with x the leading Gaussian (bridge: the terminal value; PCA: the first   */
+/* component), a_j > 0 its loading, R_j the rest built from the n = d-1      */
+/* sampled Gaussians.  With c_j = (S0/d) exp(omega t_j + sigma R_j) and     */
+/* b_j = sigma a_j the average is X(x) = sum_j c_j exp(b_j x), increasing    */
+/* in x; the payoff switches at the root x* of X(x*) = K, found by Newton's  */
+/* method on ln X(x) - ln K (convex and increasing, so the iteration        */
+/* converges from any start), and integrating x out gives, with             */
+/* E[e^{b x}; x > x*] = e^{b^2/2} Phi(b - x*):                                */
+/*   call:   e^{-rT} [ sum_j c_j e^{b_j^2/2} Phi(b_j - x*) - K Phi(-x*) ]      */
+/*   binary: e^{-rT} Phi(-x*)                                                */
+/* and the pathwise Greeks by differentiating these at fixed R (the terms  */
+/* from moving x* cancel in the call price, since X(x*) = K).  The          */
+/* geometric mean is log-linear in x: X(x) = G e^{b x}, b = sigma mean(a),  */
+/* and x* is explicit.  The lookback maximum is not offered here.           */
+/* ------------------------------------------------------------------------ */
+static double phi_bar(double y) { return norm_sf(y); }  /* P(x > y) */
+
+/* R_j and a_j, j = 1..d (index j-1), from the n = d-1 sampled z. */
+static int lead_path(const contract_t *c, int construction, const double *A, const double *z, double *R, double *a)
+{
+    const int d = c->d;
+    const double dt = c->T / d;
+    if (construction == 3) {
+        double *zz = (double *)calloc((size_t)d + 1, sizeof(double));
+        double *W = (double *)malloc(sizeof(double) * ((size_t)d + 1));
+        if (!zz || !W) { free(zz); free(W); return -1; }
+        for (int k = 1; k < d; ++k) zz[k] = z[k - 1];       /* the leading Gaussian set to 0 */
+        int rc = oracle_bridge(d, dt, zz, W);
+        for (int j = 1; j <= d && rc == 0; ++j) R[j - 1] = W[j];
+        for (int k = 0; k < d; ++k) zz[k] = 0.0;
+        zz[0] = 1.0;                                          /* the loading of the leading one */
+        if (rc == 0) rc = oracle_bridge(d, dt, zz, W);
+        for (int j = 1; j <= d && rc == 0; ++j) a[j - 1] = W[j];
+        free(zz); free(W);
+        return rc;
+    }
+    for (int j = 0; j < d; ++j) {
+        double acc = 0.0;
+        for (int k = 1; k < d; ++k) acc += A[(size_t)j * (size_t)d + (size_t)k] * z[k - 1];
+        R[j] = acc;
+        a[j] = A[(size_t)j * (size_t)d];
+    }
+    return 0;
+}
+
+static void lead_values(const contract_t *c, const double *R, const double *a, double out[4])
+{
+    const int d = c->d;
+    const double dt = c->T / d, sig = c->sigma, K = c->K, S0 = c->S0;
+    const double omega = c->r - 0.5 * sig * sig;
+    const double disc = exp(-c->r * c->T);
+    if (c->type == 3) {                              /* geometric: log-linear in x */
+        double lmean = 0.0, amean = 0.0, bmean = 0.0;
+        for (int j = 0; j < d; ++j) {
+            const double t = (j + 1) * dt;
+            lmean += omega * t + sig * R[j];
+            amean += a[j];
+            bmean += R[j] - sig * t;
+        }
+        lmean /= d; amean /= d; bmean /= d;
+        const double G = S0 * exp(lmean), b = sig * amean;
+        const double xs = (log(K) - log(G)) / b;
+        const double eb = G * exp(0.5 * b * b);
+        out[0] = disc * (eb * phi_bar(xs - b) - K * phi_bar(xs));
+        out[1] = disc * eb * phi_bar(xs - b) / S0;
+        out[2] = disc * eb * ((amean * b + bmean) * phi_bar(xs - b) + amean * norm_pdf(xs - b));
+        out[3] = disc * norm_pdf(xs) * K / (S0 * S0 * b);
+        return;
+    }
+    /* log c_j and b_j; Newton on g(x) = ln X(x) - ln K from x = 0 */
+    double *lc = (double *)malloc(sizeof(double) * (size_t)d);
+    double *b = (double *)malloc(sizeof(double) * (size_t)d);
+    if (!lc || !b) { free(lc); free(b); for (int g = 0; g < 4; ++g) out[g] = NAN; return; }
+    for (int j = 0; j < d; ++j) {
+        const double t = (j + 1) * dt;
+        lc[j] = log(S0 / d) + omega * t + sig * R[j];
+        b[j] = sig * a[j];
+    }
+    double x = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        double m = -INFINITY;
+        for (int j = 0; j < d; ++j) m = fmax(m, lc[j] + b[j] * x);
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < d; ++j) {
+            const double e = exp(lc[j] + b[j] * x - m);
+            s0 += e;
+            s1 += b[j] * e;
+        }
+        const double g = m + log(s0) - log(K);
+        const double step = g / (s1 / s0);
+        x -= step;
+        if (fabs(step) <= 1e-15 * (1.0 + fabs(x))) break;
+    }
+    double X1 = 0.0, X2 = 0.0, F0 = 0.0, V = 0.0, B = 0.0;
+    for (int j = 0; j < d; ++j) {
+        const double t = (j + 1) * dt;
+        const double e = exp(lc[j] + b[j] * x);               /* c_j e^{b_j x*} */
+        const double eh = exp(lc[j] + 0.5 * b[j] * b[j]);      /* c_j e^{b_j^2/2} */
+        X1 += b[j] * e;
+        X2 += b[j] * b[j] * e;
+        F0 += eh * phi_bar(x - b[j]);
+        V += eh * ((sig * a[j] * a[j] + R[j] - sig * t) * phi_bar(x - b[j]) + a[j] * norm_pdf(x - b[j]));
+        B += e * (a[j] * x + R[j] - sig * t);
+    }
+    const double pdf = norm_pdf(x);
+    if (c->type == 0) {
+        out[0] = disc * (F0 - K * phi_bar(x));
+        out[1] = disc * F0 / S0;
+        out[2] = disc * V;
+        out[3] = disc * pdf * K * K / (S0 * S0 * X1);
+    } else {
+        out[0] = disc * phi_bar(x);
+        out[1] = disc * pdf * K / (S0 * X1);
+        out[2] = disc * pdf * B / X1;
+        out[3] = disc * K * pdf * (x * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1));
+    }
+    free(lc); free(b);
+}
+
 static int build_path(const contract_t *c, int construction, const double *A, const double *z, double *W)
 {
     const int n = c->d - 1;
@@ -419,6 +544,24 @@ int oracle_point(int type, int d, double K, double T, double S0, double r, doubl
     contract_t c = {type, d, K, T, S0, r, sigma};
     if (check_contract(&c, construction) != 0 || !out || (d > 1 && !z)) return -1;
     const int n = d - 1;
+    if (construction >= 3) {
+        /* stilde (if given) receives R_j, j = 1..d; the loadings a_j are not returned */
+        double *R = (double *)malloc(sizeof(double) * (size_t)d);
+        double *a = (double *)malloc(sizeof(double) * (size_t)d);
+        double *A = NULL;
+        int rc = (R && a) ? 0 : -1;
+        if (rc == 0 && construction == 4) {
+            A = (double *)malloc(sizeof(double) * (size_t)d * (size_t)d);
+            rc = (A && oracle_pca_matrix(d, T / d, A) == 0) ? 0 : -1;
+        }
+        if (rc == 0) rc = lead_path(&c, construction, A, z, R, a);
+        if (rc == 0) {
+            lead_values(&c, R, a, out);
+            if (stilde) for (int j = 0; j < d; ++j) stilde[j] = R[j];
+        }
+        free(R); free(a); free(A);
+        return rc;
+    }
     double *W = (double *)malloc(sizeof(double) * (size_t)(n + 1));
     double *A = NULL;
     if (!W) return -1;
@@ -468,12 +611,20 @@ static int problem_init(problem_t *p, uint64_t seed, const contract_t *c, int co
     p->construction = construction;
     p->seed = seed;
     const int n = c->d - 1;
-    if (n == 0) return 0;
+    if (n == 0 && construction != 4) return 0;
+    if (n == 0) {
+        p->A = (double *)malloc(sizeof(double));
+        return (p->A && oracle_pca_matrix(1, c->T, p->A) == 0) ? 0 : -1;
+    }
     p->v = (uint32_t *)malloc(sizeof(uint32_t) * 32u * (size_t)n);
     if (!p->v || oracle_direction_numbers(n, p->v) != 0) return -1;
     if (construction == 1) {
         p->A = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
         if (!p->A || oracle_pca_matrix(n, c->T / c->d, p->A) != 0) return -1;
+    }
+    if (construction == 4) {  /* the full-path factor, d x d */
+        p->A = (double *)malloc(sizeof(double) * (size_t)c->d * (size_t)c->d);
+        if (!p->A || oracle_pca_matrix(c->d, c->T / c->d, p->A) != 0) return -1;
     }
     return 0;
 }
@@ -487,9 +638,10 @@ static int replicate_sums(const problem_t *p, uint32_t rep, uint64_t k0, uint64_
     const int n = p->c.d - 1;
     uint32_t *rows = NULL, *shift = NULL;
     double *z = (double *)malloc(sizeof(double) * (size_t)(n + 1));
-    double *W = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *W = (double *)malloc(sizeof(double) * (size_t)(n + 2));
+    double *a = (double *)malloc(sizeof(double) * (size_t)(n + 2));
     int rc = 0;
-    if (!z || !W) rc = -1;
+    if (!z || !W || !a) rc = -1;
     if (rc == 0 && n > 0) {
         rows = (uint32_t *)malloc(sizeof(uint32_t) * 32u * (size_t)n);
         shift = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
@@ -505,15 +657,21 @@ static int replicate_sums(const problem_t *p, uint32_t rep, uint64_t k0, uint64_
             double u = ((double)y + 0.5) * 0x1p-32;
             z[j] = oracle_inv_normal(u);
         }
-        rc = build_path(&p->c, p->construction, p->A, z, W);
-        if (rc != 0) break;
         double val[4];
-        greeks_from_path(&p->c, W, val, NULL);
+        if (p->construction >= 3) {
+            rc = lead_path(&p->c, p->construction, p->A, z, W, a);
+            if (rc != 0) break;
+            lead_values(&p->c, W, a, val);
+        } else {
+            rc = build_path(&p->c, p->construction, p->A, z, W);
+            if (rc != 0) break;
+            greeks_from_path(&p->c, W, val, NULL);
+        }
         for (int g = 0; g < 4; ++g) neumaier_add(&acc[g], val[g]);
         if (per_point) for (int g = 0; g < 4; ++g) per_point[t * 4 + (uint64_t)g] = val[g];
     }
     for (int g = 0; g < 4; ++g) sums[g] = neumaier_value(&acc[g]);
-    free(z); free(W); free(rows); free(shift);
+    free(z); free(W); free(a); free(rows); free(shift);
     return rc;
 }
 

@@ -15,7 +15,12 @@
  *   - option type: 0 arithmetic-Asian call, 1 binary-Asian (pays 1 if the
  *     arithmetic average exceeds K), 2 fixed-strike lookback call,
  *     3 geometric-Asian call (test-only product with a closed form).
- *   - construction: 0 Brownian bridge, 1 PCA, 2 standard (forward increments).
+ *   - construction: 0 Brownian bridge, 1 PCA, 2 standard (forward increments),
+ *     all with x_1 (the first Brownian increment) integrated out; 3 and 4:
+ *     the leading coordinate of the full-path bridge (3) or PCA (4) of the d
+ *     dates integrated out instead, its switch point x* found by Newton's
+ *     method (no lookback).  For 3 and 4, oracle_point's stilde (if given)
+ *     receives the rest of the path R_j, j = 1..d.
  *   - value order of every 4-vector: price, delta, vega, gamma.
  *   - every int-returning function returns 0 on success, -1 on bad arguments.
  */

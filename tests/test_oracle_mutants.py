@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import test_oracle_cpw as cpw
+import test_oracle_lead as lead
 import test_oracle_paths as paths
 import test_oracle_sobol as sob
 
@@ -72,6 +73,15 @@ MUTANTS = {
         "for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + h * z[i - 1];",
         "for (int i = 1; i <= n; ++i) W[i] = W[i - 1] + h * z[n - i];",
         lambda o: paths.test_forward_covariance_and_structure(o, 15)),
+    "leading-coordinate call vega without its density term": (
+        "* phi_bar(x - b[j]) + a[j] * norm_pdf(x - b[j]));", "* phi_bar(x - b[j]));",
+        lambda o: lead.test_lead_greeks_equal_finite_differences(o, 0, 5, 3)),
+    "leading-coordinate binary gamma without the curvature term": (
+        "(x * K - 2.0 * X1 + K * X2 / X1)", "(x * K - 2.0 * X1)",
+        lambda o: lead.test_lead_greeks_equal_finite_differences(o, 1, 7, 4)),
+    "leading-coordinate loading read from the second PCA column": (
+        "a[j] = A[(size_t)j * (size_t)d];", "a[j] = A[(size_t)j * (size_t)d + 1];",
+        lambda o: lead.test_lead_value_equals_quadrature_over_the_leading_coordinate(o, 0, 7, 4)),
     "inverse normal Halley step with the wrong sign": (
         "z -= step;", "z += step;",
         lambda o: paths.test_inverse_normal_published_quantiles(o)),
