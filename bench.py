@@ -143,7 +143,7 @@ def roofline(grid_precision: str, contracts, segment_ms) -> dict:
     contracts / its event-timed duration against the FP32 pipe peak; for a
     tensor-core segment also the useful PCA product (2 n flops per
     point-date) against the measured dense bf16 peak."""
-    seg = max(range(4), key=lambda k: segment_ms[k])
+    seg = max(range(len(segment_ms)), key=lambda k: segment_ms[k])
     ms = segment_ms[seg]
     if seg == 0:
         mine = [c for c in contracts if c.construction == W.BB]
@@ -503,7 +503,8 @@ def run_ours(args):
         typ, cons = args.case.split("-")
         tmap = {"arith": W.ARITH, "binary": W.BINARY, "lookback": W.LOOKBACK, "geometric": W.GEOMETRIC}
         one = [W.Contract(tmap[typ], args.case_d, 100.0, 1.0, 100.0, 0.05, 0.2, args.case_N, args.case_R,
-                          {"bb": W.BB, "pca": W.PCA, "std": W.STD}[cons])]
+                          {"bb": W.BB, "pca": W.PCA, "std": W.STD, "bblead": W.BB_LEAD,
+                           "pcalead": W.PCA_LEAD}[cons])]
         prec = {"fp64": q.QMCCPW_FP64, "mixed": q.QMCCPW_MIXED, "tc-bf16": q.QMCCPW_MIXED_TC_BF16X3,
                 "tc-tf32": q.QMCCPW_MIXED_TC_TF32X3}[args.case_precision]
         batch = q.Batch(plan, one, prec)

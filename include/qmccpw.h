@@ -62,8 +62,13 @@ typedef enum {
 typedef enum {
     QMCCPW_BB = 0,                   /* Brownian bridge, Sec. 4.4: terminal value, then midpoints breadth first */
     QMCCPW_PCA = 1,                  /* principal components of Sigma (named in Sec. 6 as the next reduction) */
-    QMCCPW_STD = 2                   /* standard construction, one increment per step (the path of the
+    QMCCPW_STD = 2,                  /* standard construction, one increment per step (the path of the
                                         simulation listing, Sec. 4.1-4.2): W~(s_i) = W~(s_{i-1}) + sqrt(dt) z_i */
+    QMCCPW_BB_LEAD = 3,              /* the whole path of the d dates by the bridge, its leading coordinate
+                                        (the terminal value) integrated out instead of the first increment;
+                                        switch point by Newton's method (Sec. 6-7 name this reduction);
+                                        arithmetic, binary and geometric Asians (no lookback) */
+    QMCCPW_PCA_LEAD = 4              /* the same with the PCA of the d dates, its first component integrated out */
 } qmccpw_construction;
 
 /* ---- arithmetic precision ----------------------------------------------- */
@@ -189,9 +194,10 @@ int qmccpw_batch_timing(qmccpw_batch_t batch, float *fused_ms, int32_t *launches
  * The same record split by launch segment, without clearing it (call before
  * qmccpw_batch_timing): segment_ms[0] bridge contracts, [1] standard
  * construction, [2] PCA on the streamed tensor-core kernel (d > 65), [3] the
- * other PCA contracts, each the summed milliseconds from the end of the
- * previous segment (a segment a batch does not have reads about 0).  Graph
- * replays record no segments (*launches = 0).  segment_ms has 4 entries.
+ * other PCA contracts, [4] and [5] the leading-coordinate bridge and PCA,
+ * each the summed milliseconds from the end of the previous segment (a
+ * segment a batch does not have reads about 0).  Graph replays record no
+ * segments (*launches = 0).  segment_ms has 6 entries.
  * Errors: INVALID_ARG (NULL argument), CUDA.
  */
 int qmccpw_batch_segment_timing(qmccpw_batch_t batch, float *segment_ms, int32_t *launches);
@@ -264,7 +270,7 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
  * Errors: as qmccpw_greeks; OOM when the work of this call (about
  * 32 * R * N / P bytes of tile sums, P = 256 for d <= 65 in MIXED, plus the
  * d-dependent tables) exceeds the 16 MiB array; UNSUPPORTED for the
- * tensor-core precisions.
+ * tensor-core precisions and the leading-coordinate constructions.
  */
 int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
                           uint64_t N, int32_t R, int32_t construction, int32_t precision, double *out,

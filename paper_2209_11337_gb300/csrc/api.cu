@@ -89,11 +89,12 @@ struct DTables {
     int n = 0;
     int n_levels = 0;
     DevBuf steps, w64, w32, level_start, pca64, pca32;
+    DevBuf lead64, lead32;  // loadings of the leading coordinate, dates 1..n: bridge (j/sqrt(n)) then PCA (first column)
     DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32; resident or streamed form by n), built on first use
 };
 
 bool is_tc(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 || precision == QMCCPW_MIXED_TC_TF32X3; }
-constexpr int kSegments = 4;  // launch segments of a batch (segment_of)
+constexpr int kSegments = 6;  // launch segments of a batch (segment_of)
 // Kernel precision of one contract: a tensor-core precision applies to the PCA
 // product only; bridge contracts under it run as MIXED.
 int contract_precision(int precision, int construction) {
@@ -107,14 +108,21 @@ int tc_kind(int precision, int n) {
 }
 int tc_slot(int precision) { return precision == QMCCPW_MIXED_TC_BF16X3 ? 0 : 1; }
 // launch segment of a contract (kernel precision kp): 0 bridge, 1 standard
-// construction, 2 PCA on the streamed tensor-core kernel, 3 other PCA; one
-// grid per segment present, in this order
+// construction, 2 PCA on the streamed tensor-core kernel, 3 other PCA, 4 and
+// 5 the leading-coordinate bridge and PCA; one grid per segment present, in
+// this order
 int segment_of(int kp, int construction, int n) {
     if (construction == QMCCPW_BB) return 0;
     if (construction == QMCCPW_STD) return 1;
+    if (construction == QMCCPW_BB_LEAD) return 4;
+    if (construction == QMCCPW_PCA_LEAD) return 5;
     return (is_tc(kp) && tc_kind(kp, n) >= 2) ? 2 : 3;
 }
-int segment_construction(int seg) { return seg == 0 ? QMCCPW_BB : seg == 1 ? QMCCPW_STD : QMCCPW_PCA; }
+int segment_construction(int seg) {
+    static const int cons[kSegments] = {QMCCPW_BB, QMCCPW_STD, QMCCPW_PCA, QMCCPW_PCA, QMCCPW_BB_LEAD, QMCCPW_PCA_LEAD};
+    return cons[seg];
+}
+bool is_lead(int construction) { return construction == QMCCPW_BB_LEAD || construction == QMCCPW_PCA_LEAD; }
 
 }  // namespace
 
@@ -151,9 +159,9 @@ struct qmccpw_batch_s {
     std::vector<int32_t> R;
     uint64_t items = 0, total_reps = 0;
     // launch segments (segment_of): items [seg_begin[k], seg_begin[k + 1])
-    uint64_t seg_begin[kSegments + 1] = {0, 0, 0, 0, 0};
-    size_t smem[kSegments] = {0, 0, 0, 0};
-    int grid[kSegments] = {0, 0, 0, 0};
+    uint64_t seg_begin[kSegments + 1] = {};
+    size_t smem[kSegments] = {};
+    int grid[kSegments] = {};
     BatchBuffers own;          // used by prepared batches
     BatchBuffers *buf = &own;  // one-shot calls point this at the plan's workspace
     // diagnostics
@@ -214,8 +222,12 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
     if (N < 1 || N > (1ull << 32)) return fail(QMCCPW_ERR_INVALID_ARG, "N must be in 1..2^32");
     if (!diagnostic && (R < 2 || R > p->r_max))
         return fail(QMCCPW_ERR_INVALID_ARG, "R " + std::to_string(R) + " outside 2..r_max=" + std::to_string(p->r_max));
-    if (construction != QMCCPW_BB && construction != QMCCPW_PCA && construction != QMCCPW_STD)
+    if (construction < QMCCPW_BB || construction > QMCCPW_PCA_LEAD)
         return fail(QMCCPW_ERR_INVALID_ARG, "construction out of range");
+    if (is_lead(construction) && o.type == QMCCPW_LOOKBACK_FIXED_CALL)
+        return fail(QMCCPW_ERR_UNSUPPORTED, "the leading-coordinate constructions do not offer the lookback");
+    if (is_lead(construction) && o.d + 1 > QMCCPW_D_LIMIT)
+        return fail(QMCCPW_ERR_INVALID_ARG, "d too large for the full-path construction");
     if (precision < QMCCPW_FP64 || precision > QMCCPW_MIXED_TC_TF32X3)
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
     if (is_tc(precision) && construction == QMCCPW_PCA) {
@@ -264,6 +276,19 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
     QMC_TRY(t->level_start.alloc(sizeof(int32_t) * bp.level_start.size()));
     QMC_TRY(t->pca64.alloc(sizeof(double) * std::max<size_t>(1, A.size())));
     QMC_TRY(t->pca32.alloc(sizeof(float) * std::max<size_t>(1, A32.size())));
+    // the leading coordinate's loading when these n dates are a whole path: the bridge's
+    // terminal value (W~(s_i) = (i/n) sqrt(n) z), then the first principal component
+    const int nl = std::max(1, n);
+    std::vector<double> lead(2 * static_cast<size_t>(nl), 0.0);
+    for (int i = 1; i <= n; ++i) {
+        lead[i - 1] = static_cast<double>(i) / std::sqrt(static_cast<double>(n));
+        lead[nl + i - 1] = A[static_cast<size_t>(i - 1) * n];
+    }
+    std::vector<float> lead32(lead.begin(), lead.end());
+    QMC_TRY(t->lead64.alloc(sizeof(double) * lead.size()));
+    QMC_TRY(t->lead32.alloc(sizeof(float) * lead32.size()));
+    QMC_CUDA(cudaMemcpy(t->lead64.ptr, lead.data(), sizeof(double) * lead.size(), cudaMemcpyHostToDevice));
+    QMC_CUDA(cudaMemcpy(t->lead32.ptr, lead32.data(), sizeof(float) * lead32.size(), cudaMemcpyHostToDevice));
     if (n > 0) {
         QMC_CUDA(cudaMemcpy(t->steps.ptr, bp.steps.data(), sizeof(BridgeStep) * bp.steps.size(), cudaMemcpyHostToDevice));
         QMC_CUDA(cudaMemcpy(t->w64.ptr, bp.w.data(), sizeof(double) * bp.w.size(), cudaMemcpyHostToDevice));
@@ -282,11 +307,11 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
 // share an SM (228 KiB) with room for the static reduction scratch.
 constexpr size_t kTileBudget = 66560;
 
-int choose_tile_log2(int precision, int n) {
+int choose_tile_log2(int precision, int n, int construction = QMCCPW_BB) {
     const size_t elem = precision == QMCCPW_FP64 ? 8 : 4;
-    const int stride = (n + 1) | 1;
+    const int row = tile_row_elems(construction, n);
     int lg = kMaxTileLog2;
-    while (lg > 0 && (static_cast<size_t>(1u << lg) * stride * elem) > kTileBudget) --lg;
+    while (lg > 0 && (static_cast<size_t>(1u << lg) * row * elem) > kTileBudget) --lg;
     return lg;
 }
 
@@ -308,7 +333,9 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
                    uint64_t rep_base, ContractDev *out) {
     const int precision = contract_precision(batch_precision, in.construction);
     const DTables *t = nullptr;
-    QMC_TRY(get_dtables(p, in.option.d, in.option.T, &t));
+    // the leading-coordinate constructions build the whole path of the d dates: the tables of d + 1
+    const bool lead = is_lead(in.construction);
+    QMC_TRY(get_dtables(p, in.option.d + (lead ? 1 : 0), in.option.T, &t));
     ContractDev c{};
     c.type = in.option.type;
     c.d = in.option.d;
@@ -318,7 +345,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
         c.tile_log2 = 7;
     } else {
         auto tt = p->tuned_tile.find(std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, in.construction, c.d));
-        c.tile_log2 = tt != p->tuned_tile.end() ? tt->second : choose_tile_log2(precision, c.n);
+        c.tile_log2 = tt != p->tuned_tile.end() ? tt->second : choose_tile_log2(precision, c.n, c.construction);
     }
     const int P = 1 << c.tile_log2;
     c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2);
@@ -326,11 +353,19 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
     c.groups = kThreads / P;
     c.n_levels = t->n_levels;
-    c.row_stride = (c.n + 1) | 1;
+    c.row_stride = lead ? (c.n + 2) | 1 : (c.n + 1) | 1;
     // the register bridge (float, one thread per point, d = 16 or 64) and PCA read z by
     // dimension; the shared-memory bridge overwrites z with W~ in place at its date
-    c.z_by_dim = (c.construction != QMCCPW_BB ||
-                  (precision != QMCCPW_FP64 && c.groups == 1 && (c.n == 63 || c.n == 15))) ? 1 : 0;
+    c.z_by_dim = (c.construction != QMCCPW_BB && c.construction != QMCCPW_BB_LEAD) ||
+                         (c.construction == QMCCPW_BB && precision != QMCCPW_FP64 && c.groups == 1 &&
+                          (c.n == 63 || c.n == 15))
+                     ? 1 : 0;
+    c.slot_shift = lead ? 1 : 0;
+    if (lead) {
+        const size_t off = c.construction == QMCCPW_PCA_LEAD ? static_cast<size_t>(std::max(1, c.d)) : 0;
+        c.lead_a64 = t->lead64.as<double>() + off;
+        c.lead_a32 = t->lead32.as<float>() + off;
+    }
     c.N = in.N;
     c.item_base = item_base;
     c.rep_base = rep_base;
@@ -404,7 +439,8 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         reps += c.R;
         b->R[k] = c.R;
         size_t &sm = b->smem[seg];
-        sm = std::max(sm, is_tc(kp) ? pca_tc_smem_bytes(tc_kind(kp, c.n)) : fused_smem_bytes(kp, c.n, c.tile_log2));
+        sm = std::max(sm, is_tc(kp) ? pca_tc_smem_bytes(tc_kind(kp, c.n))
+                                    : fused_smem_bytes(kp, in.construction, c.n, c.tile_log2));
     }
     b->items = items;
     b->total_reps = reps;
@@ -571,7 +607,7 @@ struct QmcServer {
     uint64_t bytes_of(const qmccpw_contract &c) const {
         const int n = c.option.d - 1;
         const int kp = contract_precision(desc.precision, c.construction);
-        const int P = 1 << (is_tc(kp) ? 7 : choose_tile_log2(kp, n));
+        const int P = 1 << (is_tc(kp) ? 7 : choose_tile_log2(kp, n, c.construction));
         const uint64_t tiles = (c.N + P - 1) / P;
         return tiles * static_cast<uint64_t>(c.R) * 32u + static_cast<uint64_t>(c.R) * 40u + sizeof(ContractDev) + 16u;
     }
@@ -1062,7 +1098,9 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     if (!plan || !option || !market || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
     QMC_TRY(validate_contract(plan, *option, *market, N, R, construction, precision, false));
     if (precision >= QMCCPW_MIXED_TC_BF16X3)
-        return fail(QMCCPW_ERR_UNSUPPORTED, "tensor-core PCA precisions are not built in this library version");
+        return fail(QMCCPW_ERR_UNSUPPORTED, "the allocation-free entry point offers FP64 and MIXED only");
+    if (is_lead(construction))
+        return fail(QMCCPW_ERR_UNSUPPORTED, "the allocation-free entry point offers the bridge, PCA and standard constructions");
     std::lock_guard<std::mutex> lock(plan->mu);
     QMC_CUDA(cudaSetDevice(plan->device));
     unsigned char *scratch = nullptr;
@@ -1081,7 +1119,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.d = d;
     c.n = n;
     c.construction = construction;
-    c.tile_log2 = choose_tile_log2(precision, n);
+    c.tile_log2 = choose_tile_log2(precision, n, construction);
     const int P = 1 << c.tile_log2;
     c.chunk_log2 = chunk_log2_for(n, c.tile_log2);
     c.R = R;
@@ -1156,7 +1194,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     QMC_CUDA(cudaMemcpyAsync(dev, host.data(), staged, cudaMemcpyHostToDevice, s));
 
     int per_sm = 0;
-    const size_t smem = fused_smem_bytes(precision, n, c.tile_log2);
+    const size_t smem = fused_smem_bytes(precision, construction, n, c.tile_log2);
     QMC_CUDA(static_cast<cudaError_t>(fused_occupancy(precision, construction, smem, &per_sm)));
     if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "fused kernel does not fit on an SM");
     const int grid = static_cast<int>(std::min<uint64_t>(items, static_cast<uint64_t>(per_sm) * plan->sm_count));
@@ -1292,8 +1330,7 @@ int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t constructio
     if (!plan) return fail(QMCCPW_ERR_INVALID_ARG, "NULL plan");
     if (precision != QMCCPW_FP64 && precision != QMCCPW_MIXED)
         return fail(QMCCPW_ERR_INVALID_ARG, "tuning applies to the FP64 and MIXED CUDA-core kernels");
-    if (construction != QMCCPW_BB && construction != QMCCPW_PCA && construction != QMCCPW_STD)
-        return fail(QMCCPW_ERR_INVALID_ARG, "construction");
+    if (construction < QMCCPW_BB || construction > QMCCPW_PCA_LEAD) return fail(QMCCPW_ERR_INVALID_ARG, "construction");
     if (d < 1 || d > plan->d_max) return fail(QMCCPW_ERR_INVALID_ARG, "d outside the plan");
     std::lock_guard<std::mutex> lock(plan->mu);
     const auto key = std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, construction, d);
@@ -1305,7 +1342,7 @@ int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t constructio
     while (lg < kMaxTileLog2 && (1 << lg) < points_per_tile) ++lg;
     if ((1 << lg) != points_per_tile || points_per_tile < 32)
         return fail(QMCCPW_ERR_INVALID_ARG, "points_per_tile must be a power of two in 32..256");
-    if (fused_smem_bytes(precision, d - 1, lg) > 200u * 1024u)
+    if (fused_smem_bytes(precision, construction, d - 1, lg) > 200u * 1024u)
         return fail(QMCCPW_ERR_INVALID_ARG, "tile too large for shared memory");
     plan->tuned_tile[key] = lg;
     return QMCCPW_OK;
@@ -1321,7 +1358,8 @@ int qmccpw_tuning_get(qmccpw_plan_t plan, int32_t precision, int32_t constructio
         return QMCCPW_OK;
     }
     auto it = plan->tuned_tile.find(std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, construction, d));
-    *points_per_tile = 1 << (it != plan->tuned_tile.end() ? it->second : choose_tile_log2(precision, d - 1));
+    *points_per_tile =
+        1 << (it != plan->tuned_tile.end() ? it->second : choose_tile_log2(precision, d - 1, construction));
     return QMCCPW_OK;
 }
 
@@ -1345,7 +1383,7 @@ int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t c
         seen[std::make_pair(src.construction, src.option.d)] = true;
         const auto key = std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, src.construction, src.option.d);
         plan->tuned_tile.erase(key);
-        const int base = choose_tile_log2(precision, src.option.d - 1);
+        const int base = choose_tile_log2(precision, src.option.d - 1, src.construction);
         // a workload of its own size: about 2^24 point-dates (2^21 in FP64)
         qmccpw_contract c = src;
         c.R = 4;
@@ -1354,7 +1392,7 @@ int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t c
         int best = base;
         float best_ms = 1e30f;
         for (int lg = std::min(kMaxTileLog2, base + 1); lg >= std::max(5, base - 2) && rc == QMCCPW_OK; --lg) {
-            if (fused_smem_bytes(precision, c.option.d - 1, lg) > 200u * 1024u) continue;
+            if (fused_smem_bytes(precision, c.construction, c.option.d - 1, lg) > 200u * 1024u) continue;
             plan->tuned_tile[key] = lg;
             qmccpw_batch_s b;
             b.buf = &plan->ws;

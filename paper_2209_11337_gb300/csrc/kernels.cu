@@ -37,6 +37,73 @@ namespace {
 // ---------------------------------------------------------------------------
 // the fused kernel
 // ---------------------------------------------------------------------------
+// Node b of a bridge schedule in a point's row: W~ at its date from its
+// endpoints and z (unit-spacing weights, z scaled by sqrt(dt)), written in
+// place of z.
+template <typename T>
+__device__ __forceinline__ T bridge_node(const ContractDev &c, T *row, int b, int4 &st) {
+    st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
+    const T Wl = row[st.y], Wr = row[st.z];
+    T z = row[st.x];
+    T Wm;
+    if constexpr (sizeof(T) == 8) {
+        const double *w = c.w64 + 3 * b;
+        Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (c.sqrt_t1 * z);
+    } else {
+        z = fmaf(z, c.ff_sqrt_t1[0], z * c.ff_sqrt_t1[1]);  // z sqrt(dt): the tables hold unit-spacing weights
+        // hi + lo coefficients: the low parts first, then the high parts
+        const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
+        const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
+        float lo = h.y * Wl;
+        lo = fmaf(h.w, Wr, lo);
+        lo = fmaf(g.y, z, lo);
+        Wm = fmaf(h.x, Wl, fmaf(h.z, Wr, fmaf(g.x, z, lo)));
+    }
+    row[st.x] = Wm;
+    return Wm;
+}
+
+// The whole bridge of the leading-coordinate construction, levels breadth
+// first, W~ left in the rows (no running sums: the values need the whole
+// path first).
+template <typename T>
+__device__ void bridge_store(const ContractDev &c, T *zw, int stride) {
+    const int P = 1 << c.tile_log2;
+    T *row = zw + (threadIdx.x & (P - 1)) * stride;
+    const int grp = threadIdx.x >> c.tile_log2;
+    for (int lvl = 0; lvl < c.n_levels; ++lvl) {
+        const int b_end = __ldg(c.level_start + lvl + 1);
+        for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += c.groups) {
+            int4 st;
+            bridge_node<T>(c, row, b, st);
+        }
+        if (c.groups > 1) __syncthreads();
+    }
+}
+
+// The rest of the PCA path of the leading-coordinate construction: R_i =
+// sqrt(dt) sum_k Ahat[i][k] z_k over the d components (z_1 = 0 in slot 1),
+// into the second row; the G threads of a point take every G-th date.
+template <typename T>
+__device__ void lead_pca_store(const ContractDev &c, const T *zw, T *rbuf, int stride) {
+    const int P = 1 << c.tile_log2;
+    const int pt = threadIdx.x & (P - 1);
+    const int nd = c.d;  // whole-path dimension
+    const T *row = zw + pt * stride;
+    T *out = rbuf + pt * stride;
+    for (int i = 1 + (threadIdx.x >> c.tile_log2); i <= nd; i += c.groups) {
+        T w = T(0);
+        if constexpr (sizeof(T) == 8) {
+            const double *Ai = c.pca64 + static_cast<size_t>(i - 1) * nd;
+            for (int k = 2; k <= nd; ++k) w = fma(__ldg(Ai + k - 1), row[k], w);
+            out[i] = w * c.sqrt_t1;
+        } else {
+            const int n_pad = (nd + 15) & ~15;
+            for (int k = 2; k <= nd; ++k) w = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k - 1) * n_pad + (i - 1)), row[k], w);
+            out[i] = fmaf(w, c.ff_sqrt_t1[0], w * c.ff_sqrt_t1[1]);
+        }
+    }
+}
 // Bridge (Sec. 4.4): levels breadth first; within a level the nodes of a
 // point are spread over its G threads; W~ overwrites z in the point's row.
 template <typename T, int TYPE>
@@ -47,29 +114,7 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     const int G = c.groups;
     T *row = zw + pt * stride;
     const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
-    const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
-    // node b of the schedule: W~ at its date from its endpoints and z
-    auto node = [&](int b, int4 &st) -> T {
-        st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
-        const T Wl = row[st.y], Wr = row[st.z];
-        T z = row[st.x];
-        T Wm;
-        if constexpr (sizeof(T) == 8) {
-            const double *w = c.w64 + 3 * b;
-            Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (c.sqrt_t1 * z);
-        } else {
-            z = fmaf(z, sdt_hi, z * sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
-            // hi + lo coefficients: the low parts first, then the high parts
-            const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
-            const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
-            float lo = h.y * Wl;
-            lo = fmaf(h.w, Wr, lo);
-            lo = fmaf(g.y, z, lo);
-            Wm = fmaf(h.x, Wl, fmaf(h.z, Wr, fmaf(g.x, z, lo)));
-        }
-        row[st.x] = Wm;
-        return Wm;
-    };
+    auto node = [&](int b, int4 &st) -> T { return bridge_node<T>(c, row, b, st); };
     for (int lvl = 0; lvl < c.n_levels; ++lvl) {
         const int b_end = __ldg(c.level_start + lvl + 1);
         // the nodes of a level are independent: a thread takes two at a time
@@ -378,10 +423,12 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
 
 // CONS is the construction of every contract this launch covers (the host
 // launches one grid per construction over that construction's items).
-// Register budget: the PCA product's register block needs up to 128
-// registers (two CTAs per SM); the other forms fit three CTAs per SM.
+// Register budget: the float PCA product's register block needs up to 128
+// registers and the double forms more than 80 (two CTAs per SM); the other
+// float forms fit three CTAs per SM.
 template <typename T, int CONS>
-__global__ void __launch_bounds__(kThreads, CONS == QMCCPW_PCA ? 2 : 3) fused_kernel(const __grid_constant__ LaunchParams p) {
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CONS != QMCCPW_PCA) ? 3 : 2)
+    fused_kernel(const __grid_constant__ LaunchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
 
     __shared__ WorkItem work;
@@ -420,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, CONS == QMCCPW_PCA ? 2 : 3) fused_ke
                     j = it % n;
                     ch = it / n;
                 }
-                const int slot = c.z_by_dim ? j + 1 : __ldg(&c.steps[j].m);
+                const int slot = c.z_by_dim ? j + 1 + c.slot_shift : __ldg(&c.steps[j + c.slot_shift].m);
                 T *dst = zw + static_cast<size_t>(ch * chunk) * stride + slot;
                 // points at or past N (ragged last tile) are never generated: their
                 // index could pass 2^32; they are zero-filled and left out of the sums
@@ -446,33 +493,59 @@ __global__ void __launch_bounds__(kThreads, CONS == QMCCPW_PCA ? 2 : 3) fused_ke
             }
         }
         for (int pt = threadIdx.x; pt < P; pt += kThreads) zw[pt * stride] = T(0);
+        if (c.slot_shift) {  // the leading coordinate is integrated out: its slot holds 0
+            const int lead_slot = c.z_by_dim ? 1 : __ldg(&c.steps[0].m);
+            for (int pt = threadIdx.x; pt < P; pt += kThreads) zw[pt * stride + lead_slot] = T(0);
+        }
         __syncthreads();
 
-        // ---- phase 2: path construction and running sums, merged per point
-        PathAcc<T> acc;
-        switch (c.type) {
-            case QMCCPW_ARITH_ASIAN_CALL: path_phase<T, CONS, QMCCPW_ARITH_ASIAN_CALL>(c, zw, stride, acc); break;
-            case QMCCPW_BINARY_ASIAN: path_phase<T, CONS, QMCCPW_BINARY_ASIAN>(c, zw, stride, acc); break;
-            case QMCCPW_LOOKBACK_FIXED_CALL: path_phase<T, CONS, QMCCPW_LOOKBACK_FIXED_CALL>(c, zw, stride, acc); break;
-            default: path_phase<T, CONS, QMCCPW_GEOMETRIC_ASIAN_CALL>(c, zw, stride, acc); break;
-        }
-        const int pt = threadIdx.x;
-
-        // ---- phase 3: conditional values of the point, tile sum
         using V = typename std::conditional<sizeof(T) == 8, double, ff>::type;
+        const int pt = threadIdx.x;
+        const uint64_t local_point = tile * P + pt;
         V v[4];
         for (int g = 0; g < 4; ++g) v[g] = V{};
-        const uint64_t local_point = tile * P + pt;
-        if (pt < P && local_point < c.N) {
-            T xhat, dhat;
-            finish_functional(c, acc, xhat, dhat);
-            if constexpr (sizeof(T) == 8) values_fp64(c, xhat, dhat, v);
-            else values_mixed(c, xhat, dhat, v);
-            if (p.point_out) {
-                double *o = p.point_out + local_point * 4;
+        if constexpr (CONS == QMCCPW_BB_LEAD || CONS == QMCCPW_PCA_LEAD) {
+            // ---- phase 2: the rest of the whole path R_1..R_d (leading Gaussian 0)
+            T *rbuf = zw;
+            if constexpr (CONS == QMCCPW_BB_LEAD) {
+                bridge_store<T>(c, zw, stride);
+            } else {
+                rbuf = zw + static_cast<size_t>(P) * stride;
+                lead_pca_store<T>(c, zw, rbuf, stride);
+            }
+            __syncthreads();
+            // ---- phase 3: the switch point and the values of the point, tile sum
+            if (pt < P && local_point < c.N) {
+                T o[4];
+                lead_values<T>(c, rbuf + pt * stride, o);
                 for (int g = 0; g < 4; ++g) {
-                    if constexpr (sizeof(T) == 8) o[g] = v[g];
-                    else o[g] = ff_to_double(v[g]);
+                    if constexpr (sizeof(T) == 8) v[g] = o[g];
+                    else v[g] = ff{o[g], 0.0f};
+                }
+                if (p.point_out)
+                    for (int g = 0; g < 4; ++g) p.point_out[local_point * 4 + g] = static_cast<double>(o[g]);
+            }
+        } else {
+            // ---- phase 2: path construction and running sums, merged per point
+            PathAcc<T> acc;
+            switch (c.type) {
+                case QMCCPW_ARITH_ASIAN_CALL: path_phase<T, CONS, QMCCPW_ARITH_ASIAN_CALL>(c, zw, stride, acc); break;
+                case QMCCPW_BINARY_ASIAN: path_phase<T, CONS, QMCCPW_BINARY_ASIAN>(c, zw, stride, acc); break;
+                case QMCCPW_LOOKBACK_FIXED_CALL: path_phase<T, CONS, QMCCPW_LOOKBACK_FIXED_CALL>(c, zw, stride, acc); break;
+                default: path_phase<T, CONS, QMCCPW_GEOMETRIC_ASIAN_CALL>(c, zw, stride, acc); break;
+            }
+            // ---- phase 3: conditional values of the point, tile sum
+            if (pt < P && local_point < c.N) {
+                T xhat, dhat;
+                finish_functional(c, acc, xhat, dhat);
+                if constexpr (sizeof(T) == 8) values_fp64(c, xhat, dhat, v);
+                else values_mixed(c, xhat, dhat, v);
+                if (p.point_out) {
+                    double *o = p.point_out + local_point * 4;
+                    for (int g = 0; g < 4; ++g) {
+                        if constexpr (sizeof(T) == 8) o[g] = v[g];
+                        else o[g] = ff_to_double(v[g]);
+                    }
                 }
             }
         }
@@ -599,10 +672,9 @@ __global__ void sobol_dump_kernel(const uint32_t *__restrict__ tab, const uint32
 
 }  // namespace
 
-size_t fused_smem_bytes(int precision, int n, int tile_log2) {
+size_t fused_smem_bytes(int precision, int construction, int n, int tile_log2) {
     const size_t elem = (precision == QMCCPW_FP64) ? 8 : 4;
-    const int stride = (n + 1) | 1;
-    const size_t zw = static_cast<size_t>(1u << tile_log2) * stride * elem;
+    const size_t zw = static_cast<size_t>(1u << tile_log2) * tile_row_elems(construction, n) * elem;
     // staging of partial accumulators: up to 4 * kThreads (slot, point) entries of (x, dsum, m)
     const size_t red = 4 * kThreads * (2 * elem + sizeof(int32_t));  // >= 4 * kThreads doubles for the tile sum
     return ((zw > red ? zw : red) + 15) & ~size_t(15);
@@ -624,14 +696,20 @@ static cudaError_t set_limit_all(int optin) {
     cudaError_t e = set_limit<T>(fused_kernel<T, QMCCPW_BB>, optin);
     if (e == cudaSuccess) e = set_limit<T>(fused_kernel<T, QMCCPW_PCA>, optin);
     if (e == cudaSuccess) e = set_limit<T>(fused_kernel<T, QMCCPW_STD>, optin);
+    if (e == cudaSuccess) e = set_limit<T>(fused_kernel<T, QMCCPW_BB_LEAD>, optin);
+    if (e == cudaSuccess) e = set_limit<T>(fused_kernel<T, QMCCPW_PCA_LEAD>, optin);
     return e;
 }
 
 template <typename T>
 static auto fused_for(int construction) -> void (*)(LaunchParams) {
-    return construction == QMCCPW_BB ? fused_kernel<T, QMCCPW_BB>
-           : construction == QMCCPW_STD ? fused_kernel<T, QMCCPW_STD>
-                                        : fused_kernel<T, QMCCPW_PCA>;
+    switch (construction) {
+        case QMCCPW_BB: return fused_kernel<T, QMCCPW_BB>;
+        case QMCCPW_STD: return fused_kernel<T, QMCCPW_STD>;
+        case QMCCPW_BB_LEAD: return fused_kernel<T, QMCCPW_BB_LEAD>;
+        case QMCCPW_PCA_LEAD: return fused_kernel<T, QMCCPW_PCA_LEAD>;
+        default: return fused_kernel<T, QMCCPW_PCA>;
+    }
 }
 
 int fused_set_smem_limit(int precision, size_t optin_bytes) {

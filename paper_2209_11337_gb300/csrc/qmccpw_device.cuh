@@ -377,6 +377,250 @@ __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[
 }
 
 // ---------------------------------------------------------------------------
+// conditioning on the leading coordinate of the whole path (constructions
+// BB_LEAD, PCA_LEAD; the next reduction Sec. 6-7 name): the path of the d
+// dates is W(t_j) = a_j x + R_j, x the leading Gaussian, so the average is
+// X(x) = sum_j c_j e^{b_j x} with c_j = (S0/d) e^{omega t_j + sigma R_j},
+// b_j = sigma a_j > 0.  The switch point x* solves X(x*) = K: Newton's method
+// on ln X(x) - ln K, convex and increasing in x, converges from x = 0.  Then
+// with E[e^{bx}; x > x*] = e^{b^2/2} Phi(b - x*) the conditional values are
+// closed forms: call e^{-rT}[sum_j c_j e^{b_j^2/2} Phi(b_j - x*) - K Phi(-x*)],
+// binary e^{-rT} Phi(-x*), and their derivatives at fixed R.  The geometric
+// mean is log-linear in x, so its x* is explicit.  R[1..d] is the rest of the
+// path (unit spacing of the tables already scaled), a from the contract's
+// loading table times sqrt(dt).
+// ---------------------------------------------------------------------------
+template <typename T> struct LeadMath;
+template <> struct LeadMath<double> {
+    __device__ static double ex(double x) { return exp(x); }
+    __device__ static double ln(double x) { return log(x); }
+    __device__ static double sf(double x) { return 0.5 * erfc(x * 0.70710678118654752440); }
+    __device__ static double pdf(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
+    static constexpr double tol = 1e-15;
+    static constexpr int iters = 200;
+};
+template <> struct LeadMath<float> {
+    __device__ static float ex(float x) { return Arith<float>::ex(x); }
+    __device__ static float ln(float x) { return logf(x); }
+    __device__ static float sf(float x) { return 0.5f * erfcf(x * 0.707106781f); }
+    __device__ static float pdf(float x) { return 0.398942280f * expf(-0.5f * x * x); }
+    static constexpr float tol = 2e-7f;
+    static constexpr int iters = 24;
+};
+
+template <typename T>
+__device__ __forceinline__ T lead_loading(const ContractDev &c, int j) {  // a_{j+1}, 0-based j
+    if constexpr (sizeof(T) == 8) return __ldg(c.lead_a64 + j) * c.sqrt_t1;
+    else return __ldg(c.lead_a32 + j) * (c.ff_sqrt_t1[0] + c.ff_sqrt_t1[1]);
+}
+
+// values of one point: out = price, delta, vega, gamma (before the tile sum)
+template <typename T>
+__device__ void lead_values(const ContractDev &c, const T *R, T out[4]);
+
+// FP64: the formulas as they stand
+template <>
+__device__ void lead_values<double>(const ContractDev &c, const double *R, double out[4]) {
+    using M = LeadMath<double>;
+    const int d = c.d;
+    const double dt = c.dt, sig = c.sigma, omega = c.omega, K = c.K, S0 = c.S0, disc = c.disc;
+    if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+        double lmean = 0, amean = 0, bmean = 0;
+        for (int j = 0; j < d; ++j) {
+            const double t = (j + 1) * dt, Rj = R[j + 1];
+            lmean += omega * t + sig * Rj;
+            amean += lead_loading<double>(c, j);
+            bmean += Rj - sig * t;
+        }
+        lmean *= c.inv_d;
+        amean *= c.inv_d;
+        bmean *= c.inv_d;
+        const double b = sig * amean;
+        const double xs = (c.psi0 + c.omega * c.dt - lmean) / b;  // (ln(K/S0) - lmean) / b, G = S0 e^{lmean}
+        const double eb = S0 * exp(lmean + 0.5 * b * b);
+        out[0] = disc * (eb * M::sf(xs - b) - K * M::sf(xs));
+        out[1] = disc * eb * M::sf(xs - b) / S0;
+        out[2] = disc * eb * ((amean * b + bmean) * M::sf(xs - b) + amean * M::pdf(xs - b));
+        out[3] = disc * M::pdf(xs) * K / (S0 * S0 * b);
+        return;
+    }
+    // Newton on g(x) = ln X(x) - ln K from x = 0; stop on a step below the
+    // tolerance or (from the third step) one that no longer shrinks
+    double x = 0, last = 1e300;
+    for (int it = 0; it < M::iters; ++it) {
+        double s0 = 0, s1 = 0;
+        for (int j = 0; j < d; ++j) {
+            const double b = sig * lead_loading<double>(c, j);
+            const double e = exp(c.ln_lead_c0 + omega * ((j + 1) * dt) + sig * R[j + 1] + b * x);
+            s0 += e;
+            s1 += b * e;
+        }
+        const double step = (log(s0) - c.ln_K) * (s0 / s1);
+        x -= step;
+        const double mag = fabs(step);
+        if (mag <= M::tol * (1.0 + fabs(x)) || (it >= 2 && mag >= last)) break;
+        last = mag;
+    }
+    double X1 = 0, X2 = 0, F0 = 0, V = 0, B = 0;
+    const double pdf = M::pdf(x);
+    for (int j = 0; j < d; ++j) {
+        const double t = (j + 1) * dt, a = lead_loading<double>(c, j), b = sig * a, Rj = R[j + 1];
+        const double lc = c.ln_lead_c0 + omega * t + sig * Rj;
+        const double e = exp(lc + b * x);               // c_j e^{b_j x*}
+        const double eh = exp(lc + 0.5 * b * b);        // c_j e^{b_j^2/2}
+        const double sfj = M::sf(x - b);
+        X1 += b * e;
+        X2 += b * b * e;
+        F0 += eh * sfj;
+        V += eh * (sig * a * a + Rj - sig * t) * sfj + a * e * pdf;  // e^{b^2/2} phi(x*-b) = e^{b x*} phi(x*)
+        B += e * (a * x + Rj - sig * t);
+    }
+    if (c.type == QMCCPW_ARITH_ASIAN_CALL) {
+        out[0] = disc * (F0 - K * M::sf(x));
+        out[1] = disc * F0 / S0;
+        out[2] = disc * V;
+        out[3] = disc * pdf * K * K / (S0 * S0 * X1);
+    } else {
+        out[0] = disc * M::sf(x);
+        out[1] = disc * pdf * K / (S0 * X1);
+        out[2] = disc * pdf * B / X1;
+        out[3] = disc * K * pdf * (x * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1));
+    }
+}
+
+// Mixed: two places where float would bias every point the same way are
+// moved out of float.
+// (1) The switch point: X(x) = (S0/d) sum_j e^{omega t_j + sigma R_j + b_j x};
+//     the constant ln(S0/(d K)) of g(x) = ln X(x) - ln K enters as a
+//     float-float pair (its float rounding alone would shift x* by ~1e-7/b),
+//     the sum is accumulated and its logarithm taken in float-float.
+// (2) The call price F0 - K Phi(-x*) is a difference of two nearly equal
+//     terms.  With K = sum_j e_j (e_j = c_j e^{b_j x*}) and the Mills ratio
+//     M(y) = Phi(-y)/phi(y), each term is c_j e^{b_j^2/2} Phi(b_j - x*) -
+//     e_j Phi(-x*) = e_j phi(x*) [M(x* - b_j) - M(x*)], and the bracket is the
+//     power series sum_k m_k b_j^k with m_k = (-1)^k M^(k)(x*)/k! >= 0 (M is
+//     completely monotone), so it sums positive terms.  M(x*) and the m_k come
+//     from the recurrence M' = xM - 1, M^(k+1) = x M^(k) + k M^(k-1) in double,
+//     once per point.  The residual X(x*) - K of the float switch point is
+//     added back at first order.
+constexpr int kMillsTerms = 20;
+
+template <>
+__device__ void lead_values<float>(const ContractDev &c, const float *R, float out[4]) {
+    const int d = c.d;
+    const float dt = static_cast<float>(c.dt), sig = static_cast<float>(c.sigma);
+    const float omega = static_cast<float>(c.omega);
+    const double K = c.K, S0 = c.S0, disc = c.disc;
+    const float S0d = static_cast<float>(c.S0 * c.inv_d);
+    if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+        // log-linear in x: the double formulas from float sums of the path
+        float lmean = 0, amean = 0, bmean = 0;
+        for (int j = 0; j < d; ++j) {
+            const float t = static_cast<float>(j + 1) * dt, Rj = R[j + 1];
+            lmean += omega * t + sig * Rj;
+            amean += lead_loading<float>(c, j);
+            bmean += Rj - sig * t;
+        }
+        double o[4];
+        const double lm = lmean * c.inv_d, am = amean * c.inv_d, bm = bmean * c.inv_d;
+        const double b = c.sigma * am;
+        const double xs = (c.psi0 + c.omega * c.dt - lm) / b;
+        const double eb = S0 * exp(lm + 0.5 * b * b);
+        const double sfb = 0.5 * erfc((xs - b) * 0.70710678118654752440), sfx = 0.5 * erfc(xs * 0.70710678118654752440);
+        const double pb = 0.39894228040143267794 * exp(-0.5 * (xs - b) * (xs - b));
+        const double px = 0.39894228040143267794 * exp(-0.5 * xs * xs);
+        o[0] = disc * (eb * sfb - K * sfx);
+        o[1] = disc * eb * sfb / S0;
+        o[2] = disc * eb * ((am * b + bm) * sfb + am * pb);
+        o[3] = disc * px * K / (S0 * S0 * b);
+        for (int g = 0; g < 4; ++g) out[g] = static_cast<float>(o[g]);
+        return;
+    }
+    // (1) switch point
+    float cst[2];
+    cst[0] = static_cast<float>(c.ln_lead_c0 - c.ln_K);
+    cst[1] = static_cast<float>((c.ln_lead_c0 - c.ln_K) - static_cast<double>(cst[0]));
+    // float Newton steps to the rounding floor, then one step with the sum in
+    // float-float and g in float-float
+    float x = 0, last = 1e30f;
+    for (int it = 0; it <= LeadMath<float>::iters; ++it) {
+        const bool polish = it == LeadMath<float>::iters;
+        ff s0{0.0f, 0.0f};
+        float s1 = 0;
+        for (int j = 0; j < d; ++j) {
+            const float b = sig * lead_loading<float>(c, j);
+            const float e = Arith<float>::ex(fmaf(omega, static_cast<float>(j + 1) * dt, fmaf(sig, R[j + 1], b * x)));
+            if (polish) s0 = ff_add(s0, ff{e, 0.0f});
+            else s0.hi += e;
+            s1 = fmaf(b, e, s1);
+        }
+        float gv;
+        if (polish) {
+            const ff g = ff_add(ln_ff(s0.hi), ff{cst[0], cst[1] + s0.lo / s0.hi});  // {hi, lo}
+            gv = g.hi + g.lo;
+        } else {
+            gv = logf(s0.hi) + (cst[0] + cst[1]);
+        }
+        const float step = gv * (s0.hi / s1);
+        x -= step;
+        if (polish) break;
+        const float mag = fabsf(step);
+        if (mag <= LeadMath<float>::tol * (1.0f + fabsf(x)) || (it >= 2 && mag >= last)) it = LeadMath<float>::iters - 1;
+        last = mag;
+    }
+    // (2) the Mills ratio at x* and its series coefficients, in double
+    const double xd = x;
+    const double Mx = 0.5 * erfc(xd * 0.70710678118654752440) / (0.39894228040143267794 * exp(-0.5 * xd * xd));
+    const double pdf = 0.39894228040143267794 * exp(-0.5 * xd * xd);
+    float mk[kMillsTerms];
+    {
+        double m_prev = Mx, m_cur = xd * Mx - 1.0;  // M, M'
+        double fact = 1.0, sign = -1.0;
+        for (int k = 1; k <= kMillsTerms; ++k) {
+            fact *= k;
+            mk[k - 1] = static_cast<float>(sign * m_cur / fact);
+            const double m_next = xd * m_cur + k * m_prev;
+            m_prev = m_cur;
+            m_cur = m_next;
+            sign = -sign;
+        }
+    }
+    float X1 = 0, X2 = 0, SP = 0, SA = 0, V1 = 0, B = 0;
+    ff Xs{0.0f, 0.0f}, W0{0.0f, 0.0f};
+    for (int j = 0; j < d; ++j) {
+        const float t = static_cast<float>(j + 1) * dt, a = lead_loading<float>(c, j), b = sig * a, Rj = R[j + 1];
+        const float e = S0d * Arith<float>::ex(fmaf(omega, t, fmaf(sig, Rj, b * x)));  // c_j e^{b_j x*}
+        float P = mk[kMillsTerms - 1];
+#pragma unroll
+        for (int k = kMillsTerms - 2; k >= 0; --k) P = fmaf(P, b, mk[k]);
+        P *= b;                                    // M(x* - b) - M(x*)
+        const float w = fmaf(sig, a * a, Rj - sig * t);
+        Xs = ff_add(Xs, ff{e, 0.0f});
+        X1 = fmaf(b, e, X1);
+        X2 = fmaf(b * b, e, X2);
+        SP = fmaf(e, P, SP);                       // sum e_j [M(x*-b_j) - M(x*)]
+        SA = fmaf(a, e, SA);
+        V1 = fmaf(e * w, P, V1);
+        W0 = ff_add(W0, ff{e * w, 0.0f});          // sum e_j w_j: signs mixed, kept in float-float
+        B = fmaf(e, fmaf(a, x, Rj - sig * t), B);
+    }
+    // X(x*) - K of the float switch point
+    const double resid = (static_cast<double>(Xs.hi) + Xs.lo) - K;
+    const double sfx = Mx * pdf;  // Phi(-x*)
+    if (c.type == QMCCPW_ARITH_ASIAN_CALL) {
+        out[0] = static_cast<float>(disc * (pdf * SP + resid * sfx));
+        out[1] = static_cast<float>(disc * (pdf * SP + (K + resid) * sfx) / S0);
+        out[2] = static_cast<float>(disc * pdf * (Mx * (static_cast<double>(W0.hi) + W0.lo) + V1 + SA));
+        out[3] = static_cast<float>(disc * pdf * K * K / (S0 * S0 * X1));
+    } else {
+        out[0] = static_cast<float>(disc * sfx);
+        out[1] = static_cast<float>(disc * pdf * K / (S0 * X1));
+        out[2] = static_cast<float>(disc * pdf * B / X1);
+        out[3] = static_cast<float>(disc * K * pdf * (xd * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1)));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Sobol' integers of one dimension over a run of consecutive points
 // ---------------------------------------------------------------------------
 // First point k0: XOR of the direction integers of the set bits of g(k0),

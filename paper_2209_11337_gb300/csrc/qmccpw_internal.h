@@ -60,7 +60,8 @@ struct ContractDev {
     int32_t groups;                      // kThreads / P threads per point in the path phase
     int32_t n_levels;                    // bridge levels
     int32_t row_stride;                  // shared-memory row (point) stride in elements, odd
-    int32_t z_by_dim;                    // 1: z of dimension j at column j+1; 0: at the date it drives
+    int32_t z_by_dim;                    // 1: z of dimension j at column j+1+slot_shift; 0: at the date node j+slot_shift drives
+    int32_t slot_shift;                  // 1 for the leading-coordinate constructions (dimension j drives node j+1), else 0
     uint64_t N;
     uint64_t item_base;                  // first work item of this contract
     uint64_t rep_base;                   // first replicate slot of this contract (in per-replicate arrays)
@@ -72,6 +73,8 @@ struct ContractDev {
     const double *pca64;                 // n x n row-major
     const float *pcaT32;                 // A^T as float, [k][i], i padded to a multiple of 16 with zeros
     const void *tc_operand;              // tensor-core PCA: Ahat hi then lo, K-major core-matrix layout
+    const double *lead_a64;              // leading-coordinate constructions: its loading on dates 1..d, unit spacing
+    const float *lead_a32;
     // market-derived constants
     double S0, K, T, r, sigma;
     double dt;                           // t_1 = T/d: spacing of the separated dates
@@ -89,6 +92,8 @@ struct ContractDev {
     double k_call_gamma;                 // disc K / (S0^2 a)
     double inv_sigma;
     double inv_d;                        // 1/d
+    double ln_lead_c0;                   // ln(S0/d): leading-coordinate constructions
+    double ln_K;
     // the same constants as float hi + lo pairs (float-float arithmetic of the mixed path)
     float ff_disc1_S0[2], ff_disc_K[2], ff_disc1[2], ff_disc_K_sqrt_t1[2], ff_k_call_gamma[2];
     float ff_disc[2], ff_k_bin_delta[2], ff_k_bin_gamma[2];
@@ -133,7 +138,15 @@ int launch_scramble(uint64_t seed, const uint32_t *v, int ndims, int jstride, in
 int launch_sobol_dump(const uint32_t *table, const uint32_t *shift, int jstride, int ndims,
                       uint64_t k0, uint64_t count, uint32_t *out, void *stream);
 // dynamic shared memory of one CTA for a contract with n dims and 2^tile_log2 points
-size_t fused_smem_bytes(int precision, int n, int tile_log2);
+// Shared-memory elements per point of the fused kernel's tile: z / W~ in
+// slots 0..n (odd stride); the leading-coordinate constructions build the
+// whole path, slots 0..n+1, and the PCA one keeps its rest R in a second row.
+inline int tile_row_elems(int construction, int n) {
+    if (construction == QMCCPW_BB_LEAD) return (n + 2) | 1;
+    if (construction == QMCCPW_PCA_LEAD) return 2 * ((n + 2) | 1);
+    return (n + 1) | 1;
+}
+size_t fused_smem_bytes(int precision, int construction, int n, int tile_log2);
 int fused_set_smem_limit(int precision, size_t optin_bytes);  // optin_bytes: the device's per-block opt-in maximum
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
 

@@ -42,6 +42,8 @@ QMCCPW_GEOMETRIC_ASIAN_CALL = 3
 QMCCPW_BB = 0
 QMCCPW_PCA = 1
 QMCCPW_STD = 2
+QMCCPW_BB_LEAD = 3
+QMCCPW_PCA_LEAD = 4
 
 QMCCPW_FP64 = 0
 QMCCPW_MIXED = 1
@@ -238,8 +240,9 @@ class Batch:
         _check(library().qmccpw_batch_set_timing(self.handle, capacity))
 
     def segment_timing(self):
-        """([bridge, standard, streamed tensor-core PCA, other PCA] milliseconds, launches), record kept."""
-        ms, n = (ctypes.c_float * 4)(), ctypes.c_int32()
+        """([bridge, standard, streamed tensor-core PCA, other PCA, leading-coordinate bridge,
+        leading-coordinate PCA] milliseconds, launches), record kept."""
+        ms, n = (ctypes.c_float * 6)(), ctypes.c_int32()
         _check(library().qmccpw_batch_segment_timing(self.handle, ms, ctypes.byref(n)))
         return list(ms), n.value
 

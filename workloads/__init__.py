@@ -15,10 +15,10 @@ from dataclasses import dataclass, replace
 from typing import List
 
 ARITH, BINARY, LOOKBACK, GEOMETRIC = 0, 1, 2, 3
-BB, PCA, STD = 0, 1, 2
+BB, PCA, STD, BB_LEAD, PCA_LEAD = 0, 1, 2, 3, 4
 FP64, MIXED, MIXED_TC_BF16X3, MIXED_TC_TF32X3 = 0, 1, 2, 3
 TYPE_NAMES = {ARITH: "arith", BINARY: "binary", LOOKBACK: "lookback", GEOMETRIC: "geometric"}
-CONS_NAMES = {BB: "bb", PCA: "pca", STD: "std"}
+CONS_NAMES = {BB: "bb", PCA: "pca", STD: "std", BB_LEAD: "bblead", PCA_LEAD: "pcalead"}
 
 #: key of the random linear scrambles and digital shifts
 SCRAMBLE_SEED = 0x220911337
