@@ -237,22 +237,22 @@ __device__ __forceinline__ void split_store(unsigned char *hi_base, unsigned cha
 
 // The same split for two adjacent dimensions (k even, k + 1) of one point:
 // one 32-bit word per part for bf16 (hi is exact, so its bf16 is the top
-// half of its bits; lo rounds to nearest even in integer arithmetic), one
-// 64-bit word per part for tf32.  `off` is element k's offset (4- or 8-byte
-// aligned: the swizzle permutes whole 16-byte units).
+// half of its bits, gathered by one byte permutation; lo is rounded to
+// nearest even by the packed conversion), one 64-bit word per part for tf32.
+// hs = z kScale rounded to an integer; lo = z - hs / kScale is exact, so one
+// FMA forms it.  `off` is element k's offset (4- or 8-byte aligned: the
+// swizzle permutes whole 16-byte units).
 template <int KIND>
 __device__ __forceinline__ void split_store_pair(unsigned char *hi_base, unsigned char *lo_base, uint32_t off,
                                                  float2 z) {
     constexpr float kScale = KIND == 0 ? 32.0f : 256.0f;
-    const float2 h = mul2(add2(fma2(z, f2(kScale), f2(12582912.0f)), f2(-12582912.0f)), f2(1.0f / kScale));
-    const float2 l = add2(z, make_float2(-h.x, -h.y));
+    const float2 hs = add2(fma2(z, f2(kScale), f2(12582912.0f)), f2(-12582912.0f));
+    const float2 h = mul2(hs, f2(1.0f / kScale));
+    const float2 l = fma2(hs, f2(-1.0f / kScale), z);
     if constexpr (KIND == 0) {
-        auto rne16 = [](float v) {
-            const uint32_t b = __float_as_uint(v);
-            return (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
-        };
-        *reinterpret_cast<uint32_t *>(hi_base + off) = (__float_as_uint(h.x) >> 16) | (__float_as_uint(h.y) & 0xFFFF0000u);
-        *reinterpret_cast<uint32_t *>(lo_base + off) = rne16(l.x) | (rne16(l.y) << 16);
+        const __nv_bfloat162 lw = __floats2bfloat162_rn(l.x, l.y);  // .x (element k) in the low half
+        *reinterpret_cast<uint32_t *>(hi_base + off) = __byte_perm(__float_as_uint(h.x), __float_as_uint(h.y), 0x7632);
+        *reinterpret_cast<__nv_bfloat162 *>(lo_base + off) = lw;
     } else {
         const uint2 hb = make_uint2(__float_as_uint(h.x), __float_as_uint(h.y));
         const uint2 lb = make_uint2((__float_as_uint(l.x) + 0x1000u) & 0xFFFFE000u,
@@ -280,15 +280,15 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
                     d1, d2);
         const float s0 = static_cast<float>(col + 1) * dt;
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {  // dates (W~ at s_date) two at a time: exponentials in packed form
+        for (int i = 0; i < 16; i += 2) {  // dates (W~ at s_date) two at a time, in packed form
             const int date = col + i + 1;
-            const float w0 = d1[i] + d2[i], w1 = d1[i + 1] + d2[i + 1];
-            const float s_a = fmaf(static_cast<float>(i), dt, s0), s_b = fmaf(static_cast<float>(i + 1), dt, s0);
+            const float2 w = add2(make_float2(d1[i], d1[i + 1]), make_float2(d2[i], d2[i + 1]));
+            const float2 W = fma2(w, f2(sdt_hi), mul2(w, f2(sdt_lo)));
+            const float2 sd = fma2(make_float2(static_cast<float>(i), static_cast<float>(i + 1)), f2(dt), f2(s0));
             if (date + 1 <= c.n)
-                acc.template add2<TYPE>(date, date + 1, fmaf(w0, sdt_hi, w0 * sdt_lo), fmaf(w1, sdt_hi, w1 * sdt_lo),
-                                        omega, sigma, s_a, s_b);
+                acc.template add2<TYPE>(date, date + 1, W.x, W.y, omega, sigma, sd.x, sd.y);
             else if (date <= c.n)
-                acc.template add<TYPE>(date, fmaf(w0, sdt_hi, w0 * sdt_lo), omega, sigma, s_a);
+                acc.template add<TYPE>(date, W.x, omega, sigma, sd.x);
         }
     }
 }
@@ -403,8 +403,8 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
         const int row0 = ch * chunk;
         if (len > 0) {
             const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
-            const uint32_t ya = sobol_first(tab, p.jstride, ja, __ldg(shf + ja), k0);
-            const uint32_t yb = sobol_first(tab, p.jstride, jb, __ldg(shf + jb), k0);
+            uint32_t ya, yb;
+            sobol_first_pair(tab, p.jstride, ja, jb, __ldg(shf + ja), __ldg(shf + jb), k0, ya, yb);
             auto emit = [&](int s, uint32_t a, uint32_t b) {
                 split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), Arith<float>::inv_normal2(a, b));
             };

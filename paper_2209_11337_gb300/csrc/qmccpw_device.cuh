@@ -72,14 +72,31 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 template <> struct Arith<float> {
     // q = (lo + 1/2) 2^-32 <= 1/2 from lo = a 2^23 + b (one rounding), the
     // reflection sign of the upper half, and w = -ln(4q(1-q)); shared by the
-    // one- and two-element forms
+    // one- and two-element forms.  With B = 2^23 + b (b placed in the
+    // mantissa of 2^23), B 2^-32 - (2^-9 - 2^-33) = (2b + 1) 2^-33 exactly
+    // (2b + 1 < 2^24), so one FMA gives the low part and one more q.
+    static constexpr float kQLow = -(0x1p-9f - 0x1p-33f);  // exact: 24 significant bits
     __device__ static __forceinline__ float q_of(uint32_t y, uint32_t &sign) {
         const uint32_t m = static_cast<uint32_t>(static_cast<int32_t>(y) >> 31);  // all ones on the upper half
         const uint32_t lo = y ^ m;
-        sign = m & 0x80000000u;
+        sign = y & 0x80000000u;
         const float fa = small_uint_to_float(lo >> 23);
-        const float fb = small_uint_to_float(lo & 0x007FFFFFu);
-        return fmaf(fa, 0x1p-9f, fmaf(fb, 0x1p-32f, 0x1p-33f));
+        const float t = fmaf(__uint_as_float(0x4B000000u | (lo & 0x007FFFFFu)), 0x1p-32f, kQLow);
+        return fmaf(fa, 0x1p-9f, t);
+    }
+    // -q for two draws, the floating-point steps in packed form (the
+    // negated constants give exactly -q; the packed form then needs no
+    // negated operands below)
+    __device__ static __forceinline__ float2 neg_q_of2(uint32_t y0, uint32_t y1, uint32_t &s0, uint32_t &s1) {
+        const uint32_t lo0 = y0 ^ static_cast<uint32_t>(static_cast<int32_t>(y0) >> 31);
+        const uint32_t lo1 = y1 ^ static_cast<uint32_t>(static_cast<int32_t>(y1) >> 31);
+        s0 = y0 & 0x80000000u;
+        s1 = y1 & 0x80000000u;
+        const float2 fa = add2(make_float2(__uint_as_float(0x4B000000u | (lo0 >> 23)),
+                                           __uint_as_float(0x4B000000u | (lo1 >> 23))), f2(-8388608.0f));
+        const float2 fb = make_float2(__uint_as_float(0x4B000000u | (lo0 & 0x007FFFFFu)),
+                                      __uint_as_float(0x4B000000u | (lo1 & 0x007FFFFFu)));
+        return fma2(fa, f2(-0x1p-9f), fma2(fb, f2(-0x1p-32f), f2(-kQLow)));
     }
     __device__ static __forceinline__ float tail(float w) { return horner_t(sqrtf(w) - QMC_INVN_SHIFT_T); }
     __device__ static float inv_normal(uint32_t y) {
@@ -96,10 +113,10 @@ template <> struct Arith<float> {
     // a pair with a tail draw takes the one-element branches
     __device__ static float2 inv_normal2(uint32_t y0, uint32_t y1) {
         uint32_t s0, s1;
-        const float2 q = make_float2(q_of(y0, s0), q_of(y1, s1));
-        const float2 x = fma2(f2(-2.0f), q, f2(1.0f));
-        const float2 q4 = mul2(f2(4.0f), q);
-        const float2 a = fma2(make_float2(-q4.x, -q4.y), q, q4);
+        const float2 nq = neg_q_of2(y0, y1, s0, s1);
+        const float2 xm = fma2(f2(-2.0f), nq, f2(-1.0f));  // 2q - 1 = -x
+        const float2 q4 = mul2(f2(-4.0f), nq);
+        const float2 a = fma2(q4, nq, q4);                 // 4q(1 - q), one rounding
         const float2 w = mul2(f2(-0.693147181f), make_float2(__log2f(a.x), __log2f(a.y)));
         float2 p;
         if (w.x < QMC_INVN_W0 && w.y < QMC_INVN_W0) {
@@ -112,7 +129,7 @@ template <> struct Arith<float> {
             p.x = w.x < QMC_INVN_W0 ? horner_c(w.x - QMC_INVN_SHIFT_C) : tail(w.x);
             p.y = w.y < QMC_INVN_W0 ? horner_c(w.y - QMC_INVN_SHIFT_C) : tail(w.y);
         }
-        const float2 z = mul2(make_float2(-x.x, -x.y), p);
+        const float2 z = mul2(xm, p);
         return make_float2(__uint_as_float(__float_as_uint(z.x) ^ s0), __uint_as_float(__float_as_uint(z.y) ^ s1));
     }
     // e^x for the path sums (|x| well below 80): 2^k 2^f with k the nearest
@@ -133,8 +150,8 @@ template <> struct Arith<float> {
     __device__ static float2 ex2(float2 x) {
         constexpr float c[] = QMC_EXP2_POLY;
         const float2 r = fma2(x, f2(1.44269502f), f2(12582912.0f));
-        const float2 kf = add2(r, f2(-12582912.0f));
-        const float2 f = fma2(x, f2(1.92596299e-8f), fma2(x, f2(1.44269502f), make_float2(-kf.x, -kf.y)));
+        const float2 nkf = fma2(r, f2(-1.0f), f2(12582912.0f));  // -k, exact
+        const float2 f = fma2(x, f2(1.92596299e-8f), fma2(x, f2(1.44269502f), nkf));
         float2 p = f2(c[6]);
 #pragma unroll
         for (int i = 5; i >= 0; --i) p = fma2(p, f, f2(c[i]));
@@ -635,6 +652,22 @@ __device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab
         g &= g - 1u;
     }
     return y;
+}
+
+// The first point of two dimensions at once (one walk over the set bits of
+// g(k0), two loads per bit).
+__device__ __forceinline__ void sobol_first_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
+                                                 uint32_t shift_a, uint32_t shift_b, uint32_t k0, uint32_t &ya,
+                                                 uint32_t &yb) {
+    uint32_t g = k0 ^ (k0 >> 1);
+    ya = shift_a;
+    yb = shift_b;
+    while (g) {
+        const uint32_t *row = tab + (__ffs(g) - 1) * jstride;
+        ya ^= __ldg(row + ja);
+        yb ^= __ldg(row + jb);
+        g &= g - 1u;
+    }
 }
 
 __host__ __device__ constexpr int ctz_const(int s) {
