@@ -37,6 +37,11 @@ namespace {
 // ---------------------------------------------------------------------------
 // the fused kernel
 // ---------------------------------------------------------------------------
+// small non-negative int as T (float: without a conversion instruction)
+template <typename T> __device__ __forceinline__ T small_int_to(int i);
+template <> __device__ __forceinline__ float small_int_to<float>(int i) { return small_uint_to_float(static_cast<uint32_t>(i)); }
+template <> __device__ __forceinline__ double small_int_to<double>(int i) { return static_cast<double>(i); }
+
 // Node b of a bridge schedule in a point's row: W~ at its date from its
 // endpoints and z (unit-spacing weights, z scaled by sqrt(dt)), written in
 // place of z.
@@ -113,7 +118,8 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     const int grp = threadIdx.x >> c.tile_log2;
     const int G = c.groups;
     T *row = zw + pt * stride;
-    const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
+    T omega, sigma, dt;
+    market_of(c, omega, sigma, dt);
     auto node = [&](int b, int4 &st) -> T { return bridge_node<T>(c, row, b, st); };
     for (int lvl = 0; lvl < c.n_levels; ++lvl) {
         const int b_end = __ldg(c.level_start + lvl + 1);
@@ -187,7 +193,7 @@ __device__ __forceinline__ void bridge_registers(const ContractDev &c, const flo
     constexpr BridgeSchedule S = make_schedule(N);
     static_assert(S.count == N, "bridge schedule size");
     const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
-    const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
+    const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
     float W[N + 1];
     W[0] = 0.0f;
     auto node = [&](int b) {
@@ -219,10 +225,11 @@ __device__ void pca_rows_phase(const ContractDev &c, const T *zw, int stride, Pa
     const int pt = threadIdx.x & (P - 1);
     const int grp = threadIdx.x >> c.tile_log2;
     const T *row = zw + pt * stride;
-    const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
+    T omega, sigma, dt;
+    market_of(c, omega, sigma, dt);
     const int n = c.n;
-    T s_i = static_cast<T>(1 + grp) * dt;
-    const T ds = static_cast<T>(c.groups) * dt;
+    T s_i = small_int_to<T>(1 + grp) * dt;
+    const T ds = small_int_to<T>(c.groups) * dt;
     for (int i = 1 + grp; i <= n; i += c.groups, s_i += ds) {
         T Wi = T(0);
         if constexpr (sizeof(T) == 8) {
@@ -252,7 +259,7 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
     const int g = warp % groups;
     slot = warp / groups;
     const int n = c.n, n4 = ((n + 15) & ~15) >> 2;
-    const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
+    const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
     const float *zr[PB];
 #pragma unroll
     for (int j = 0; j < PB; ++j) {
@@ -279,7 +286,7 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
                 for (int r = 0; r < 16; ++r) w[j][r] = fmaf(av[r], z, w[j][r]);
             }
         }
-        const float s0 = static_cast<float>(rb * 16 + 1) * dt;
+        const float s0 = small_uint_to_float(static_cast<uint32_t>(rb * 16 + 1)) * dt;
         const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
 #pragma unroll
         for (int r = 0; r < 16; r += 2) {  // dates i, i + 1: exponentials in packed form
@@ -304,9 +311,6 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
 // block's z, the sums of the earlier blocks (through shared memory, added in
 // block order) give its starting value, and it walks its block again adding
 // every date to its accumulator.
-template <typename T> __device__ __forceinline__ T small_int_to(int i);
-template <> __device__ __forceinline__ float small_int_to<float>(int i) { return small_uint_to_float(static_cast<uint32_t>(i)); }
-template <> __device__ __forceinline__ double small_int_to<double>(int i) { return static_cast<double>(i); }
 
 __shared__ double forward_block_sums[kThreads];  // one per thread, shared by the product types' instances
 
@@ -328,7 +332,8 @@ __device__ void forward_phase(const ContractDev &c, const T *zw, int stride, Pat
         w = T(0);
         for (int h = 0; h < g; ++h) w += block_sum[h * P + pt];
     }
-    const T omega = static_cast<T>(c.omega), sigma = static_cast<T>(c.sigma), dt = static_cast<T>(c.dt);
+    T omega, sigma, dt;
+    market_of(c, omega, sigma, dt);
     if constexpr (sizeof(T) == 8) {
         for (int i = i0; i <= i1; ++i) {
             w += row[i];

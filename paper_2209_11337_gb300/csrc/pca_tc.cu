@@ -270,7 +270,7 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
     const int half = warp >> 2;                 // warpgroup: which half of the dates
     const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
     const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
-    const float omega = static_cast<float>(c.omega), sigma = static_cast<float>(c.sigma), dt = static_cast<float>(c.dt);
+    const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
     acc.init(TYPE, half == 0);
     const int last = min(c.n, (half + 1) * (NPAD / 2));  // dates beyond n are padding
 #pragma unroll 1
@@ -278,7 +278,7 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
         float d1[16], d2[16];
         tmem_ld16x2(tmem + lane_base + static_cast<uint32_t>(col), tmem + lane_base + static_cast<uint32_t>(col + NPAD),
                     d1, d2);
-        const float s0 = static_cast<float>(col + 1) * dt;
+        const float s0 = small_uint_to_float(static_cast<uint32_t>(col + 1)) * dt;
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {  // dates (W~ at s_date) two at a time, in packed form
             const int date = col + i + 1;
@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
         const uint32_t rep = work.rep;
         const uint64_t tile = work.tile;
 
-        // ---- Ahat (hi, lo) for this n: one bulk copy when n changes
-        __syncthreads();
+        // ---- Ahat (hi, lo) for this n: one bulk copy when n changes (the
+        // barrier that ends next_work orders this after the previous tile)
         if (sh.loaded_n != n) {
             if (threadIdx.x == 0) {
                 mbar_expect_tx(&sh.bar_b, kPartsB * kOpBytesB);

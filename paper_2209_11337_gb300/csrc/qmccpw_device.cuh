@@ -382,7 +382,7 @@ __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[
         const ff g = ff_add(ff_mul_ff(psi, ff_of(c.ff_inv_a)), ff{-1.0f, 0.0f});
         v[3] = ff_mul_ff(ff_mul(ff_of(c.ff_k_bin_gamma), pdf), g);
     } else {
-        const float a = static_cast<float>(c.a);
+        const float a = c.f_a;
         const float sfs = 0.5f * erfcf((p - a) * 0.707106781f);
         const float sf = 0.5f * erfcf(p * 0.707106781f);
         const ff cx = ff_mul(ff_of(c.ff_disc1_S0), xhat);
@@ -525,15 +525,15 @@ constexpr int kMillsTerms = 20;
 template <>
 __device__ void lead_values<float>(const ContractDev &c, const float *R, float out[4]) {
     const int d = c.d;
-    const float dt = static_cast<float>(c.dt), sig = static_cast<float>(c.sigma);
-    const float omega = static_cast<float>(c.omega);
+    const float dt = c.f_dt, sig = c.f_sigma;
+    const float omega = c.f_omega;
     const double K = c.K, S0 = c.S0, disc = c.disc;
     const float S0d = static_cast<float>(c.S0 * c.inv_d);
     if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
         // log-linear in x: the double formulas from float sums of the path
         float lmean = 0, amean = 0, bmean = 0;
         for (int j = 0; j < d; ++j) {
-            const float t = static_cast<float>(j + 1) * dt, Rj = R[j + 1];
+            const float t = small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, Rj = R[j + 1];
             lmean += omega * t + sig * Rj;
             amean += lead_loading<float>(c, j);
             bmean += Rj - sig * t;
@@ -566,7 +566,7 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
         float s1 = 0;
         for (int j = 0; j < d; ++j) {
             const float b = sig * lead_loading<float>(c, j);
-            const float e = Arith<float>::ex(fmaf(omega, static_cast<float>(j + 1) * dt, fmaf(sig, R[j + 1], b * x)));
+            const float e = Arith<float>::ex(fmaf(omega, small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, fmaf(sig, R[j + 1], b * x)));
             if (polish) s0 = ff_add(s0, ff{e, 0.0f});
             else s0.hi += e;
             s1 = fmaf(b, e, s1);
@@ -605,7 +605,7 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
     float X1 = 0, X2 = 0, SP = 0, SA = 0, V1 = 0, B = 0;
     ff Xs{0.0f, 0.0f}, W0{0.0f, 0.0f};
     for (int j = 0; j < d; ++j) {
-        const float t = static_cast<float>(j + 1) * dt, a = lead_loading<float>(c, j), b = sig * a, Rj = R[j + 1];
+        const float t = small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, a = lead_loading<float>(c, j), b = sig * a, Rj = R[j + 1];
         const float e = S0d * Arith<float>::ex(fmaf(omega, t, fmaf(sig, Rj, b * x)));  // c_j e^{b_j x*}
         float P = mk[kMillsTerms - 1];
 #pragma unroll
@@ -836,17 +836,32 @@ __device__ __forceinline__ void merge_partials(const void *base, int P, int slot
 }
 
 // X^ = X/S0 and D^ = D/S0 of a point from its merged accumulator.
+// omega, sigma and the date spacing in the kernel's type (float: the
+// contract's float copies)
+template <typename T>
+__device__ __forceinline__ void market_of(const ContractDev &c, T &omega, T &sigma, T &dt) {
+    if constexpr (sizeof(T) == 4) {
+        omega = c.f_omega;
+        sigma = c.f_sigma;
+        dt = c.f_dt;
+    } else {
+        omega = c.omega;
+        sigma = c.sigma;
+        dt = c.dt;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void finish_functional(const ContractDev &c, const PathAcc<T> &acc, T &xhat, T &dhat) {
     if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
         xhat = acc.x;
         dhat = acc.dsum;
     } else if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-        const T inv_d = static_cast<T>(c.inv_d);
+        const T inv_d = sizeof(T) == 4 ? T(c.f_inv_d) : T(c.inv_d);
         xhat = Arith<T>::ex(acc.x * inv_d);
         dhat = xhat * acc.dsum * inv_d;
     } else {
-        const T inv_d = static_cast<T>(c.inv_d);
+        const T inv_d = sizeof(T) == 4 ? T(c.f_inv_d) : T(c.inv_d);
         xhat = acc.x * inv_d;
         dhat = acc.dsum * inv_d;
     }

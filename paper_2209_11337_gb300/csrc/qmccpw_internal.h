@@ -99,6 +99,8 @@ struct ContractDev {
     float ff_disc[2], ff_k_bin_delta[2], ff_k_bin_gamma[2];
     float ff_sqrt_t1[2];                 // sqrt(dt) as hi + lo: the scale of every path increment
     float ff_psi0[2], ff_inv_a[2], ff_inv_sigma[2];
+    // float copies of market constants (the float kernels read these: no conversion on the device)
+    float f_omega, f_sigma, f_dt, f_a, f_inv_d;
 };
 
 // hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)

@@ -202,6 +202,11 @@ void contract_constants(ContractDev &c) {
     split_ff(c.k_bin_delta, c.ff_k_bin_delta);
     split_ff(c.k_bin_gamma, c.ff_k_bin_gamma);
     split_ff(c.sqrt_t1, c.ff_sqrt_t1);
+    c.f_omega = static_cast<float>(c.omega);
+    c.f_sigma = static_cast<float>(c.sigma);
+    c.f_dt = static_cast<float>(c.dt);
+    c.f_a = static_cast<float>(c.a);
+    c.f_inv_d = static_cast<float>(c.inv_d);
     split_ff(c.psi0, c.ff_psi0);
     split_ff(c.inv_a, c.ff_inv_a);
     split_ff(c.inv_sigma, c.ff_inv_sigma);
