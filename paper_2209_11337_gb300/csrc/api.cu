@@ -315,13 +315,26 @@ int choose_tile_log2(int precision, int n, int construction = QMCCPW_BB) {
     return lg;
 }
 
-// Gray-code run length of the Sobol' phase: with n >= 32 a warp takes whole
-// runs, so aim for one run per warp (8 per tile); with small n, (run, dim)
-// items, at least two per thread.
-int chunk_log2_for(int n, int tile_log2) {
+// Gray-code run length of the Sobol' phase.  n >= 32: a warp takes items of
+// one run x 32 dimensions (CUDA cores) or x 64 (tensor cores).  CUDA cores:
+// the longest run of at most 32 points whose item count splits evenly over
+// the 8 warps (or is at least 32), since each run starts with a walk over
+// the bits of its first index (64-point runs were slower at d = 64: the
+// unrolled run no longer fits the instruction cache as well).
+// Tensor cores: 8 runs per tile.  Small n: (run, dim) items, at least two
+// per thread.
+int chunk_log2_for(int n, int tile_log2, bool tc) {
     const int P = 1 << tile_log2;
     int lg = tile_log2;
-    if (n >= 32) {
+    if (n >= 32 && !tc) {
+        const long per = (n + 31) >> 5;
+        lg = std::min(tile_log2, 5);
+        while (lg > 2) {
+            const long items = static_cast<long>(P >> lg) * per;
+            if (items % (kThreads / 32) == 0 || items >= 4L * (kThreads / 32)) break;
+            --lg;
+        }
+    } else if (n >= 32) {
         while (lg > 2 && (P >> lg) < kThreads / 32) --lg;
     } else {
         while (lg > 0 && static_cast<long>(n) * (P >> lg) < 2L * kThreads) --lg;
@@ -348,7 +361,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
         c.tile_log2 = tt != p->tuned_tile.end() ? tt->second : choose_tile_log2(precision, c.n, c.construction);
     }
     const int P = 1 << c.tile_log2;
-    c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2);
+    c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2, is_tc(precision));
     c.R = in.R;
     c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
     c.groups = kThreads / P;
@@ -1121,7 +1134,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.construction = construction;
     c.tile_log2 = choose_tile_log2(precision, n, construction);
     const int P = 1 << c.tile_log2;
-    c.chunk_log2 = chunk_log2_for(n, c.tile_log2);
+    c.chunk_log2 = chunk_log2_for(n, c.tile_log2, false);
     c.R = R;
     c.tiles = static_cast<int32_t>((N + P - 1) / P);
     c.groups = kThreads / P;
