@@ -27,7 +27,7 @@ def qlib():
     return qmccpw
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_plan_greeks_free_entry_points():
     names = declared_functions()
     for must in ("qmccpw_plan", "qmccpw_greeks", "qmccpw_free"):
         assert must in names
