@@ -2,7 +2,8 @@
 //
 // W~ = A z with A A^T = Sigma (eq. WboldTilde); for equal spacing
 // A = sqrt(dt) * Ahat where Ahat (the factor for dt = 1) depends on n only.
-// One CTA (256 threads) per work item of 128 points:
+// One CTA (256 threads; 512 in the streamed variant) per work item of 128
+// points:
 //   1. Sobol' + inverse normal as in the CUDA-core kernel; z is split into
 //      hi + lo parts (bf16 or tf32) written straight into the operand layout
 //      (K-major, 128-byte swizzle, so a warp's stores hit distinct banks).
@@ -262,19 +263,21 @@ __device__ __forceinline__ void split_store_pair(unsigned char *hi_base, unsigne
     }
 }
 
-// Path sums of this thread's point over its warpgroup's half of the dates:
-// W~ = sqrt(dt) (D1 + D2), D2 at column offset NPAD.
-template <int TYPE, int NPAD>
+// Path sums of this thread's point over its warpgroup's share of the dates
+// (NWG warpgroups, each NPAD / NWG consecutive columns): W~ = sqrt(dt)
+// (D1 + D2), D2 at column offset NPAD.
+template <int TYPE, int NPAD, int NWG>
 __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float> &acc) {
+    static_assert((NPAD / NWG) % 16 == 0, "whole 16-column loads per warpgroup");
     const int warp = threadIdx.x >> 5;
-    const int half = warp >> 2;                 // warpgroup: which half of the dates
+    const int half = warp >> 2;                 // warpgroup: which share of the dates
     const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
     const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
     const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
     acc.init(TYPE, half == 0);
-    const int last = min(c.n, (half + 1) * (NPAD / 2));  // dates beyond n are padding
+    const int last = min(c.n, (half + 1) * (NPAD / NWG));  // dates beyond n are padding
 #pragma unroll 1
-    for (int col = half * (NPAD / 2); col < last; col += 16) {
+    for (int col = half * (NPAD / NWG); col < last; col += 16) {
         float d1[16], d2[16];
         tmem_ld16x2(tmem + lane_base + static_cast<uint32_t>(col), tmem + lane_base + static_cast<uint32_t>(col + NPAD),
                     d1, d2);
@@ -293,18 +296,19 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
     }
 }
 
-template <int NPAD>
+template <int NPAD, int NWG>
 __device__ __forceinline__ void epilogue_dispatch(const ContractDev &c, uint32_t tmem, PathAcc<float> &acc) {
     switch (c.type) {
-        case QMCCPW_ARITH_ASIAN_CALL: epilogue_sums<QMCCPW_ARITH_ASIAN_CALL, NPAD>(c, tmem, acc); break;
-        case QMCCPW_BINARY_ASIAN: epilogue_sums<QMCCPW_BINARY_ASIAN, NPAD>(c, tmem, acc); break;
-        case QMCCPW_LOOKBACK_FIXED_CALL: epilogue_sums<QMCCPW_LOOKBACK_FIXED_CALL, NPAD>(c, tmem, acc); break;
-        default: epilogue_sums<QMCCPW_GEOMETRIC_ASIAN_CALL, NPAD>(c, tmem, acc); break;
+        case QMCCPW_ARITH_ASIAN_CALL: epilogue_sums<QMCCPW_ARITH_ASIAN_CALL, NPAD, NWG>(c, tmem, acc); break;
+        case QMCCPW_BINARY_ASIAN: epilogue_sums<QMCCPW_BINARY_ASIAN, NPAD, NWG>(c, tmem, acc); break;
+        case QMCCPW_LOOKBACK_FIXED_CALL: epilogue_sums<QMCCPW_LOOKBACK_FIXED_CALL, NPAD, NWG>(c, tmem, acc); break;
+        default: epilogue_sums<QMCCPW_GEOMETRIC_ASIAN_CALL, NPAD, NWG>(c, tmem, acc); break;
     }
 }
 
-// Merge the two warpgroups' partial sums of each point, the conditional step
-// and the tile sum (shared by both variants).
+// Merge the NWG warpgroups' partial sums of each point (in date order), the
+// conditional step and the tile sum (shared by both variants).
+template <int NWG>
 __device__ __forceinline__ void finish_tile(const LaunchParams &p, const ContractDev &c, uint64_t item, uint64_t tile,
                                            PathAcc<float> &acc, unsigned char *scratch) {
     const int warp = threadIdx.x >> 5;
@@ -314,7 +318,7 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
     ff v[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     const uint64_t local_point = tile * kM + point;
     if (warp < 4) {
-        merge_partials<float>(scratch, kM, 2, point, c.type, acc);
+        merge_partials<float>(scratch, kM, NWG, point, c.type, acc);
         if (local_point < c.N) {
             float xhat, dhat;
             finish_functional(c, acc, xhat, dhat);
@@ -382,7 +386,7 @@ __device__ __forceinline__ void sobol_chain_pair(const uint32_t *__restrict__ ta
 // (128-byte swizzled rows: conflict-free).  Points past N are 0.  Columns of Z
 // at or beyond n meet only zero Ahat columns: an odd last dimension is
 // paired with a copy of itself in the next (padding) column.
-template <int KIND>
+template <int KIND, int NW>
 __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const ContractDev &c, uint32_t rep, uint64_t tile,
                                            unsigned char *z_hi, unsigned char *z_lo, int j0, int j1) {
     constexpr int ES = KIND == 0 ? 2 : 4;
@@ -392,7 +396,7 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
     const int nchunks = kM >> c.chunk_log2;
     const int per = (j1 - j0 + 63) >> 6;
     const int work = nchunks * per;
-    for (int it = threadIdx.x >> 5; it < work; it += kThreads / 32) {
+    for (int it = threadIdx.x >> 5; it < work; it += NW) {
         const int ch = it / per;
         const int col = (it - ch * per) * 64 + 2 * (threadIdx.x & 31);
         const int ja = j0 + col;
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
         if (sh.abort) break;
 
         // ---- phase 1: Sobol' + inverse normal -> split operand
-        sobol_to_z<KIND>(p, c, rep, tile, z_hi, z_lo, 0, n);
+        sobol_to_z<KIND, kThreads / 32>(p, c, rep, tile, z_hi, z_lo, 0, n);
         fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
         tc_fence_before();
         __syncthreads();
@@ -519,9 +523,9 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
 
         // ---- phase 3: path sums from D, merged across the two warpgroups
         PathAcc<float> acc;
-        epilogue_dispatch<kNpad>(c, tmem, acc);
+        epilogue_dispatch<kNpad, 2>(c, tmem, acc);
         tc_fence_before();
-        finish_tile(p, c, item, tile, acc, scratch);
+        finish_tile<2>(p, c, item, tile, acc, scratch);
     }
 
     // release tensor memory (also after an abort)
@@ -547,6 +551,10 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
 // second after the products of the first are done.  D1 and D2 take all 512
 // TMEM columns: one CTA per SM.
 constexpr int kNbig = 256;
+// The streamed kernel runs alone on its SM (all 512 TMEM columns), so it
+// takes 16 warps: four warpgroups share each point's dates in the epilogue
+// and twice as many warps hide the latency of the Sobol' phase.
+constexpr int kThreadsS = 512;
 
 template <int KIND> struct Streamed {
     static constexpr int ES = KIND == 0 ? 2 : 4;
@@ -565,7 +573,7 @@ struct TcSharedS {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_constant__ LaunchParams p) {
+__global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_constant__ LaunchParams p) {
     using S = Streamed<KIND>;
     constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 1u : 2u, kNbig);
     constexpr uint32_t kLbo = 128;
@@ -596,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sh.tmem_addr;
-    for (uint32_t i = threadIdx.x; i < 2 * S::ZPart / 4; i += kThreads) reinterpret_cast<uint32_t *>(z_hi)[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < 2 * S::ZPart / 4; i += kThreadsS) reinterpret_cast<uint32_t *>(z_hi)[i] = 0u;
 
     // barrier phases and the chunk pipeline are thread 0's alone; chunk q of
     // the CTA's running sequence uses buffer q & 1
@@ -653,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_const
                 __syncthreads();
             }
             // ---- phase 1: Sobol' + inverse normal -> split Z, columns j0..
-            sobol_to_z<KIND>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
+            sobol_to_z<KIND, kThreadsS / 32>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();
@@ -705,9 +713,9 @@ __global__ void __launch_bounds__(kThreads, 1) pca_tcs_kernel(const __grid_const
 
         // ---- phase 3: path sums from D1 + D2, then values and the tile sum
         PathAcc<float> acc;
-        epilogue_dispatch<kNbig>(c, tmem, acc);
+        epilogue_dispatch<kNbig, kThreadsS / 128>(c, tmem, acc);
         tc_fence_before();
-        finish_tile(p, c, item, tile, acc, scratch);
+        finish_tile<kThreadsS / 128>(p, c, item, tile, acc, scratch);
     }
 
     // the prefetched chunks must land before the CTA exits
@@ -791,9 +799,10 @@ int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks) {
         return static_cast<int>(e);
     const size_t per_block = smem_bytes + fa.sharedSizeBytes + static_cast<size_t>(reserved);
     const int by_smem = static_cast<int>(static_cast<size_t>(smem_sm) / per_block);
+    const int threads = kind >= 2 ? kThreadsS : kThreads;
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-    const int by_regs = regs_warp > 0 ? (regs_sm / regs_warp) / (kThreads / 32) : 0;
-    const int by_threads = threads_sm / kThreads;
+    const int by_regs = regs_warp > 0 ? (regs_sm / regs_warp) / (threads / 32) : 0;
+    const int by_threads = threads_sm / threads;
     const int by_tmem = 512 / (kind >= 2 ? 2 * kNbig : 2 * kNpad);
     *blocks = std::max(0, std::min(std::min(by_smem, by_regs), std::min(by_threads, by_tmem)));
     return 0;
@@ -803,8 +812,8 @@ int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (kind == 0) pca_tc_kernel<0><<<grid, kThreads, smem_bytes, s>>>(p);
     else if (kind == 1) pca_tc_kernel<1><<<grid, kThreads, smem_bytes, s>>>(p);
-    else if (kind == 2) pca_tcs_kernel<0><<<grid, kThreads, smem_bytes, s>>>(p);
-    else pca_tcs_kernel<1><<<grid, kThreads, smem_bytes, s>>>(p);
+    else if (kind == 2) pca_tcs_kernel<0><<<grid, kThreadsS, smem_bytes, s>>>(p);
+    else pca_tcs_kernel<1><<<grid, kThreadsS, smem_bytes, s>>>(p);
     return static_cast<int>(cudaGetLastError());
 }
 

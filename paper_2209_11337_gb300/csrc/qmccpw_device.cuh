@@ -896,10 +896,12 @@ __device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, c
 __device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, const ff (&v)[4], unsigned char *smem) {
     __syncthreads();
     float *vals = reinterpret_cast<float *>(smem);
+    if (threadIdx.x < kThreads) {  // larger blocks: the values live in the first kThreads threads
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        vals[(2 * g) * kThreads + threadIdx.x] = v[g].hi;
-        vals[(2 * g + 1) * kThreads + threadIdx.x] = v[g].lo;
+        for (int g = 0; g < 4; ++g) {
+            vals[(2 * g) * kThreads + threadIdx.x] = v[g].hi;
+            vals[(2 * g + 1) * kThreads + threadIdx.x] = v[g].lo;
+        }
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
