@@ -42,23 +42,37 @@ template <typename T> __device__ __forceinline__ T small_int_to(int i);
 template <> __device__ __forceinline__ float small_int_to<float>(int i) { return small_uint_to_float(static_cast<uint32_t>(i)); }
 template <> __device__ __forceinline__ double small_int_to<double>(int i) { return static_cast<double>(i); }
 
+// The contract fields a bridge node reads, copied to registers once per
+// phase (a store to the row could otherwise make the compiler read them again
+// from the contract in global memory at every node).
+struct BridgeTables {
+    const int4 *steps;
+    const double *w64;
+    const float4 *w32;
+    double sqrt_t1;
+    float sdt_hi, sdt_lo;
+    __device__ explicit BridgeTables(const ContractDev &c)
+        : steps(reinterpret_cast<const int4 *>(c.steps)), w64(c.w64), w32(reinterpret_cast<const float4 *>(c.w32)),
+          sqrt_t1(c.sqrt_t1), sdt_hi(c.ff_sqrt_t1[0]), sdt_lo(c.ff_sqrt_t1[1]) {}
+};
+
 // Node b of a bridge schedule in a point's row: W~ at its date from its
 // endpoints and z (unit-spacing weights, z scaled by sqrt(dt)), written in
 // place of z.
 template <typename T>
-__device__ __forceinline__ T bridge_node(const ContractDev &c, T *row, int b, int4 &st) {
-    st = __ldg(reinterpret_cast<const int4 *>(c.steps) + b);
+__device__ __forceinline__ T bridge_node(const BridgeTables &t, T *row, int b, int4 &st) {
+    st = __ldg(t.steps + b);
     const T Wl = row[st.y], Wr = row[st.z];
     T z = row[st.x];
     T Wm;
     if constexpr (sizeof(T) == 8) {
-        const double *w = c.w64 + 3 * b;
-        Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (c.sqrt_t1 * z);
+        const double *w = t.w64 + 3 * b;
+        Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (t.sqrt_t1 * z);
     } else {
-        z = fmaf(z, c.ff_sqrt_t1[0], z * c.ff_sqrt_t1[1]);  // z sqrt(dt): the tables hold unit-spacing weights
+        z = fmaf(z, t.sdt_hi, z * t.sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
         // hi + lo coefficients: the low parts first, then the high parts
-        const float4 h = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b);
-        const float4 g = __ldg(reinterpret_cast<const float4 *>(c.w32) + 2 * b + 1);
+        const float4 h = __ldg(t.w32 + 2 * b);
+        const float4 g = __ldg(t.w32 + 2 * b + 1);
         float lo = h.y * Wl;
         lo = fmaf(h.w, Wr, lo);
         lo = fmaf(g.y, z, lo);
@@ -76,13 +90,16 @@ __device__ void bridge_store(const ContractDev &c, T *zw, int stride) {
     const int P = 1 << c.tile_log2;
     T *row = zw + (threadIdx.x & (P - 1)) * stride;
     const int grp = threadIdx.x >> c.tile_log2;
-    for (int lvl = 0; lvl < c.n_levels; ++lvl) {
-        const int b_end = __ldg(c.level_start + lvl + 1);
-        for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += c.groups) {
+    const BridgeTables t(c);
+    const int32_t *level_start = c.level_start;
+    const int n_levels = c.n_levels, G = c.groups;
+    for (int lvl = 0; lvl < n_levels; ++lvl) {
+        const int b_end = __ldg(level_start + lvl + 1);
+        for (int b = __ldg(level_start + lvl) + grp; b < b_end; b += G) {
             int4 st;
-            bridge_node<T>(c, row, b, st);
+            bridge_node<T>(t, row, b, st);
         }
-        if (c.groups > 1) __syncthreads();
+        if (G > 1) __syncthreads();
     }
 }
 
@@ -120,12 +137,15 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     T *row = zw + pt * stride;
     T omega, sigma, dt;
     market_of(c, omega, sigma, dt);
-    auto node = [&](int b, int4 &st) -> T { return bridge_node<T>(c, row, b, st); };
-    for (int lvl = 0; lvl < c.n_levels; ++lvl) {
-        const int b_end = __ldg(c.level_start + lvl + 1);
+    const BridgeTables t(c);
+    const int32_t *level_start = c.level_start;
+    const int n_levels = c.n_levels;
+    auto node = [&](int b, int4 &st) -> T { return bridge_node<T>(t, row, b, st); };
+    for (int lvl = 0; lvl < n_levels; ++lvl) {
+        const int b_end = __ldg(level_start + lvl + 1);
         // the nodes of a level are independent: a thread takes two at a time
         // (float: their exponentials in packed form)
-        for (int b = __ldg(c.level_start + lvl) + grp; b < b_end; b += 2 * G) {
+        for (int b = __ldg(level_start + lvl) + grp; b < b_end; b += 2 * G) {
             int4 s0, s1;
             const T W0 = node(b, s0);
             if constexpr (sizeof(T) == 4) {
