@@ -197,14 +197,6 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)
 }
 
 // ---- operand element addressing ----------------------------------------------
-// Element (row, k) of a K-major operand without swizzle, NPAD columns of
-// ESIZE bytes: core matrix (row/8, k/T) of 128 bytes, T = 16/ESIZE.
-template <int ESIZE, int NPAD = kNpad>
-__device__ __forceinline__ uint32_t operand_offset(int row, int k) {
-    constexpr int T = 16 / ESIZE;
-    return static_cast<uint32_t>(((row >> 3) * (NPAD / T) + k / T) * 128 + (row & 7) * 16 + (k % T) * ESIZE);
-}
-
 // Element (row, k) of Z (kM rows), K-major with the 128-byte swizzle: K
 // columns of 128 bytes each hold kM rows of 128 bytes; the 16-byte unit u of
 // row r sits at u ^ (r % 8).  With lanes over k a warp's stores cover whole
@@ -218,31 +210,15 @@ __device__ __forceinline__ uint32_t z_offset(int row, int k) {
 // Start of the K slice [kb, kb + 32 bytes) of Z for one instruction.
 __device__ __forceinline__ uint32_t z_slice(uint32_t base, uint32_t kb) { return base + (kb >> 7) * (kM * 128u) + (kb & 127u); }
 
-// hi + lo split of z: hi on the fixed grid (2^-5 bf16, 2^-8 tf32; rounding
-// by the add-and-subtract of 1.5 2^23, exact for |z| 2^8 < 2^22), so it is
-// exact in the operand type; lo = z - hi is exact in float, then rounded.
-template <int KIND>
-__device__ __forceinline__ void split_store(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, float z) {
-    constexpr float kScale = KIND == 0 ? 32.0f : 256.0f;
-    const float h = __fadd_rn(__fadd_rn(z * kScale, 12582912.0f), -12582912.0f) * (1.0f / kScale);
-    const float l = z - h;
-    if constexpr (KIND == 0) {
-        *reinterpret_cast<__nv_bfloat16 *>(hi_base + off) = __float2bfloat16_rn(h);
-        *reinterpret_cast<__nv_bfloat16 *>(lo_base + off) = __float2bfloat16_rn(l);
-    } else {
-        // tf32 keeps 10 explicit mantissa bits: round to nearest at bit 13
-        *reinterpret_cast<uint32_t *>(hi_base + off) = __float_as_uint(h);
-        *reinterpret_cast<uint32_t *>(lo_base + off) = (__float_as_uint(l) + 0x1000u) & 0xFFFFE000u;
-    }
-}
-
-// The same split for two adjacent dimensions (k even, k + 1) of one point:
-// one 32-bit word per part for bf16 (hi is exact, so its bf16 is the top
-// half of its bits, gathered by one byte permutation; lo is rounded to
-// nearest even by the packed conversion), one 64-bit word per part for tf32.
-// hs = z kScale rounded to an integer; lo = z - hs / kScale is exact, so one
-// FMA forms it.  `off` is element k's offset (4- or 8-byte aligned: the
-// swizzle permutes whole 16-byte units).
+// hi + lo split of z for two adjacent dimensions (k even, k + 1) of one
+// point: hi on the fixed grid (2^-5 bf16, 2^-8 tf32; rounding by the
+// add-and-subtract of 1.5 2^23, exact for |z| 2^8 < 2^22), so it is exact in
+// the operand type.  Stored as one 32-bit word per part for bf16 (hi is
+// exact, so its bf16 is the top half of its bits, gathered by one byte
+// permutation; lo is rounded to nearest even by the packed conversion), one
+// 64-bit word per part for tf32.  hs = z kScale rounded to an integer;
+// lo = z - hs / kScale is exact, so one FMA forms it.  `off` is element k's
+// offset (4- or 8-byte aligned: the swizzle permutes whole 16-byte units).
 template <int KIND>
 __device__ __forceinline__ void split_store_pair(unsigned char *hi_base, unsigned char *lo_base, uint32_t off,
                                                  float2 z) {

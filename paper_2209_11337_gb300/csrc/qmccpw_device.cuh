@@ -300,10 +300,6 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_of(const float (&c)[2]) { return {c[0], c[1]}; }
-__device__ __forceinline__ ff ff_of_double(double x) {
-    const float h = static_cast<float>(x);
-    return {h, static_cast<float>(x - static_cast<double>(h))};
-}
 __device__ __forceinline__ double ff_to_double(ff a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
 
 // 1/x to ~1 ulp for positive normal x: the SFU approximation and one Newton
