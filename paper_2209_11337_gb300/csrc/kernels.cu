@@ -105,24 +105,52 @@ __device__ void bridge_store(const ContractDev &c, T *zw, int stride) {
 
 // The rest of the PCA path of the leading-coordinate construction: R_i =
 // sqrt(dt) sum_k Ahat[i][k] z_k over the d components (z_1 = 0 in slot 1),
-// into the second row; the G threads of a point take every G-th date.
+// into the second row.  FP64: the G threads of a point take every G-th date.
+// Float: they take blocks of 8 consecutive dates, each k step reading the
+// block's 8 entries of row k of A^T as two float4 (one load per four FMAs;
+// each date's sum still runs over k in order).
 template <typename T>
 __device__ void lead_pca_store(const ContractDev &c, const T *zw, T *rbuf, int stride) {
     const int P = 1 << c.tile_log2;
     const int pt = threadIdx.x & (P - 1);
+    const int grp = threadIdx.x >> c.tile_log2;
+    const int G = c.groups;
     const int nd = c.d;  // whole-path dimension
     const T *row = zw + pt * stride;
     T *out = rbuf + pt * stride;
-    for (int i = 1 + (threadIdx.x >> c.tile_log2); i <= nd; i += c.groups) {
-        T w = T(0);
-        if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
+        for (int i = 1 + grp; i <= nd; i += G) {
+            T w = T(0);
             const double *Ai = c.pca64 + static_cast<size_t>(i - 1) * nd;
             for (int k = 2; k <= nd; ++k) w = fma(__ldg(Ai + k - 1), row[k], w);
             out[i] = w * c.sqrt_t1;
-        } else {
-            const int n_pad = (nd + 15) & ~15;
-            for (int k = 2; k <= nd; ++k) w = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k - 1) * n_pad + (i - 1)), row[k], w);
-            out[i] = fmaf(w, c.ff_sqrt_t1[0], w * c.ff_sqrt_t1[1]);
+        }
+    } else {
+        const int n_pad = (nd + 15) & ~15;  // A^T rows padded with zeros to a multiple of 16
+        const float4 *AT = reinterpret_cast<const float4 *>(c.pcaT32);
+        const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
+        for (int blk = grp; 8 * blk < nd; blk += G) {
+            float w[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) w[r] = 0.0f;
+            const float4 *a = AT + static_cast<size_t>(n_pad / 4) + 2 * blk;  // row k = 2 (index 1)
+            for (int k = 2; k <= nd; ++k, a += n_pad / 4) {
+                const float z = row[k];
+                const float4 a0 = __ldg(a), a1 = __ldg(a + 1);
+                w[0] = fmaf(a0.x, z, w[0]);
+                w[1] = fmaf(a0.y, z, w[1]);
+                w[2] = fmaf(a0.z, z, w[2]);
+                w[3] = fmaf(a0.w, z, w[3]);
+                w[4] = fmaf(a1.x, z, w[4]);
+                w[5] = fmaf(a1.y, z, w[5]);
+                w[6] = fmaf(a1.z, z, w[6]);
+                w[7] = fmaf(a1.w, z, w[7]);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int i = 8 * blk + r + 1;
+                if (i <= nd) out[i] = fmaf(w[r], sh, w[r] * sl);
+            }
         }
     }
 }
