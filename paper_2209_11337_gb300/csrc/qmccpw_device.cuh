@@ -582,20 +582,23 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
         last = mag;
     }
     // (2) the Mills ratio at x* and its series coefficients, in double
+    // (the loop is unrolled: k and 1/k! are constants, so the FP64 pipe,
+    // 1/64 of the FP32 rate, sees no division or conversion here)
     const double xd = x;
-    const double Mx = 0.5 * erfc(xd * 0.70710678118654752440) / (0.39894228040143267794 * exp(-0.5 * xd * xd));
     const double pdf = 0.39894228040143267794 * exp(-0.5 * xd * xd);
+    const double Mx = 0.5 * erfc(xd * 0.70710678118654752440) / pdf;
     float mk[kMillsTerms];
     {
         double m_prev = Mx, m_cur = xd * Mx - 1.0;  // M, M'
-        double fact = 1.0, sign = -1.0;
+        double inv_fact = 1.0;
+#pragma unroll
         for (int k = 1; k <= kMillsTerms; ++k) {
-            fact *= k;
-            mk[k - 1] = static_cast<float>(sign * m_cur / fact);
-            const double m_next = xd * m_cur + k * m_prev;
+            inv_fact *= 1.0 / static_cast<double>(k);
+            const double m = m_cur * inv_fact;  // (-1)^k m_k
+            mk[k - 1] = static_cast<float>((k & 1) ? -m : m);
+            const double m_next = xd * m_cur + static_cast<double>(k) * m_prev;
             m_prev = m_cur;
             m_cur = m_next;
-            sign = -sign;
         }
     }
     float X1 = 0, X2 = 0, SP = 0, SA = 0, V1 = 0, B = 0;
