@@ -351,7 +351,7 @@ def latency_small(q, plan, stream, calls: int) -> dict:
         ts.append(time.perf_counter() - t0)
     out = {"workload": "arith Asian call, d=16, bridge, N=2^14, R=8, FP64 (one contract)",
            "sync_call": quantiles(ts[warm:])}
-    for mode in ("launch", "graph"):
+    def prepared(mode, dst):
         b = q.Batch(plan, [c], q.QMCCPW_FP64)
         if mode == "graph":
             b.use_graph(True)
@@ -361,14 +361,27 @@ def latency_small(q, plan, stream, calls: int) -> dict:
             b.launch(stream.cuda_stream)
             stream.synchronize()
             ts.append(time.perf_counter() - t0)
-        out[mode + "_and_wait"] = quantiles(ts[warm:])
+        dst[mode + "_and_wait"] = quantiles(ts[warm:])
         b.set_timing(calls)
         for _ in range(calls):
             b.launch(stream.cuda_stream)
         ms, n = b.timing()
-        out[mode + "_device_us"] = 1e3 * ms / max(1, n)
-        out[mode + "_kernels"] = b.launch_count()
+        dst[mode + "_device_us"] = 1e3 * ms / max(1, n)
+        dst[mode + "_kernels"] = b.launch_count()
         b.free()
+
+    for mode in ("launch", "graph"):
+        prepared(mode, out)
+    # the same after the plan's tuner has chosen the tile for this contract
+    # (a 2^14 x 8-point job is about one wave of 256-point tiles), then the
+    # default restored for the rest of the run
+    out["default_points_per_tile"] = q.qmccpw_tuning_get(plan, q.QMCCPW_FP64, c.construction, c.d)
+    q.qmccpw_autotune(plan, [c], q.QMCCPW_FP64)
+    tuned = {"points_per_tile": q.qmccpw_tuning_get(plan, q.QMCCPW_FP64, c.construction, c.d)}
+    for mode in ("launch", "graph"):
+        prepared(mode, tuned)
+    out["tuned"] = tuned
+    q.qmccpw_tuning_set(plan, q.QMCCPW_FP64, c.construction, c.d, 0)
     return out
 
 
