@@ -137,14 +137,8 @@ FLOPS_STD = FLOPS_BRIDGE - 2      # standard construction: a running sum and the
 GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 2148096 + 99276288, "fused_kernel<float, bridge>": 689664 + 25074688}
 
 
-def roofline(grid_precision: str, contracts, segment_ms) -> dict:
-    """Roofline of the launch segment that takes the most time (its kernel
-    is the dominant one of the step): algorithmic FP32 flops of its
-    contracts / its event-timed duration against the FP32 pipe peak; for a
-    tensor-core segment also the useful PCA product (2 n flops per
-    point-date) against the measured dense bf16 peak."""
-    seg = max(range(len(segment_ms)), key=lambda k: segment_ms[k])
-    ms = segment_ms[seg]
+def segment_flops(grid_precision: str, contracts, seg: int):
+    """The contracts of a launch segment and their algorithmic FP32 flops."""
     if seg == 0:
         mine = [c for c in contracts if c.construction == W.BB]
     elif seg == 1:
@@ -157,14 +151,35 @@ def roofline(grid_precision: str, contracts, segment_ms) -> dict:
         per = FLOPS_BRIDGE if seg == 0 else FLOPS_STD if seg == 1 else (
             FLOPS_TC_FP32 if tc else FLOPS_BRIDGE - 5 + 2 * (c.d - 1))
         flops += float(c.N) * c.R * c.d * per
-    achieved = flops / (ms / 1e3) / 1e12
+    return mine, tc, flops
+
+
+def roofline(grid_precision: str, contracts, segment_ms) -> dict:
+    """Roofline of the launch segment that takes the most time (its kernel
+    is the dominant one of the step): algorithmic FP32 flops of its
+    contracts / its event-timed duration against the FP32 pipe peak; for a
+    tensor-core segment also the useful PCA product (2 n flops per
+    point-date) against the measured dense bf16 peak.  `segments` gives the
+    same FP32 figures for every segment of the step that did work."""
     peak = fp32_peak_tflops()
+    segments = []
+    for k, ms_k in enumerate(segment_ms):
+        mine_k, _, flops_k = segment_flops(grid_precision, contracts, k)
+        if mine_k and ms_k > 0:
+            ach = flops_k / (ms_k / 1e3) / 1e12
+            segments.append({"kernel": SEGMENT_KERNELS[grid_precision][k], "ms_per_launch": ms_k,
+                             "achieved": ach, "frac": ach / peak})
+    seg = max(range(len(segment_ms)), key=lambda k: segment_ms[k])
+    ms = segment_ms[seg]
+    mine, tc, flops = segment_flops(grid_precision, contracts, seg)
+    achieved = flops / (ms / 1e3) / 1e12
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
            "traffic": GRID_TRAFFIC.get(SEGMENT_KERNELS[grid_precision][seg]),
            "kernel": SEGMENT_KERNELS[grid_precision][seg], "ms_per_launch": ms,
            "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flops x 2070 MHz (unit counts, max clock)",
            "flops_note": "FP32 flops per point-date: bridge 32; standard 30; PCA on CUDA cores 27 + 2(d-1); "
-                         "tensor-core PCA 27 (the product is on the tensor pipe)"}
+                         "tensor-core PCA 27 (the product is on the tensor pipe)",
+           "segments": segments}
     if tc:
         gemm = sum(float(c.N) * c.R * c.d * 2 * (c.d - 1) for c in mine)
         bf16 = measured_peaks().get("bf16_tflops_sustained")
