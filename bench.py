@@ -137,8 +137,15 @@ FLOPS_STD = FLOPS_BRIDGE - 2      # standard construction: a running sum and the
 GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 2148096 + 99276288, "fused_kernel<float, bridge>": 689664 + 25074688}
 
 
+# launch segments with an algorithmic flop model: bridge, standard, streamed
+# and resident PCA (the leading-coordinate segments that follow have none)
+ROOFLINE_SEGMENTS = 4
+
+
 def segment_flops(grid_precision: str, contracts, seg: int):
     """The contracts of a launch segment and their algorithmic FP32 flops."""
+    if seg >= ROOFLINE_SEGMENTS:
+        return [], False, 0.0
     if seg == 0:
         mine = [c for c in contracts if c.construction == W.BB]
     elif seg == 1:
@@ -162,6 +169,7 @@ def roofline(grid_precision: str, contracts, segment_ms) -> dict:
     point-date) against the measured dense bf16 peak.  `segments` gives the
     same FP32 figures for every segment of the step that did work."""
     peak = fp32_peak_tflops()
+    segment_ms = list(segment_ms)[:ROOFLINE_SEGMENTS]
     segments = []
     for k, ms_k in enumerate(segment_ms):
         mine_k, _, flops_k = segment_flops(grid_precision, contracts, k)

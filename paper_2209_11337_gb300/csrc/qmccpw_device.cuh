@@ -34,15 +34,19 @@ template <> struct Arith<double> {
 // Float inverse normal in the two-branch form of Giles ("Approximating the
 // erfinv function", GPU Computing Gems Jade, 2011): with x = 1 - 2q and
 // w = -ln(4q(1-q)), Phi^{-1}(q) = -x p(w) for w < W0 and -x p_t(sqrt w)
-// beyond.  The polynomials are this project's own fits (gen_invnorm.py);
-// max relative error 1.8e-7 in float.  The central branch serves 99.9% of
-// draws, so a warp rarely takes the tail.
+// beyond.  The polynomials are this project's own fits (gen_invnorm.py):
+// max relative error 1.1e-7 in float, the coefficients rounded so that their
+// roundings leave no smooth error (a smooth error of Phi^{-1} is the same for
+// every point and biases the estimates).  The central branch serves 99.9% of
+// draws, so a warp rarely takes the tail.  Central branch: c1.. by Horner,
+// then t times that plus the constant term, a float pair (lo first, then hi).
 __device__ __forceinline__ float horner_c(float t) {
     constexpr float c[] = QMC_INVN_CENTRAL;
-    float acc = c[9];
+    constexpr int n = sizeof(c) / sizeof(c[0]);
+    float acc = c[n - 1];
 #pragma unroll
-    for (int i = 8; i >= 0; --i) acc = fmaf(acc, t, c[i]);
-    return acc;
+    for (int i = n - 2; i >= 0; --i) acc = fmaf(acc, t, c[i]);
+    return fmaf(acc, t, QMC_INVN_C0_LO) + QMC_INVN_C0_HI;
 }
 
 __device__ __forceinline__ float horner_t(float t) {
@@ -121,10 +125,12 @@ template <> struct Arith<float> {
         float2 p;
         if (w.x < QMC_INVN_W0 && w.y < QMC_INVN_W0) {
             constexpr float c[] = QMC_INVN_CENTRAL;
+            constexpr int n = sizeof(c) / sizeof(c[0]);
             const float2 t = add2(w, f2(-QMC_INVN_SHIFT_C));
-            p = f2(c[9]);
+            p = f2(c[n - 1]);
 #pragma unroll
-            for (int i = 8; i >= 0; --i) p = fma2(p, t, f2(c[i]));
+            for (int i = n - 2; i >= 0; --i) p = fma2(p, t, f2(c[i]));
+            p = add2(fma2(p, t, f2(QMC_INVN_C0_LO)), f2(QMC_INVN_C0_HI));
         } else {
             p.x = w.x < QMC_INVN_W0 ? horner_c(w.x - QMC_INVN_SHIFT_C) : tail(w.x);
             p.y = w.y < QMC_INVN_W0 ? horner_c(w.y - QMC_INVN_SHIFT_C) : tail(w.y);
@@ -135,7 +141,7 @@ template <> struct Arith<float> {
     // e^x for the path sums (|x| well below 80): 2^k 2^f with k the nearest
     // integer to x log2 e, read from the low bits of x log2 e + 1.5 2^23
     // (no conversion instruction), f = x log2 e - k in [-1/2, 1/2] with the
-    // residual of log2 e, 2^f from the fitted polynomial (8.7e-8), and 2^k
+    // residual of log2 e, 2^f from the fitted polynomial (6.1e-8), and 2^k
     // added to the exponent field (the bias term of r cancels modulo 2^32).
     __device__ static float ex(float x) {
         constexpr float c[] = QMC_EXP2_POLY;
