@@ -134,7 +134,7 @@ FLOPS_STD = FLOPS_BRIDGE - 2      # standard construction: a running sum and the
 # DRAM read + write bytes of one full-size launch of the grid's kernels, from
 # one ncu capture (profiles/dram_bytes_grid_d64_tcbf16.md); None for a kernel
 # that changed since
-GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 2148096 + 99276288, "fused_kernel<float, bridge>": 689664 + 25074688}
+GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 2924288 + 98998784, "fused_kernel<float, bridge>": 886528 + 25334784}
 
 
 # launch segments with an algorithmic flop model: bridge, standard, streamed
