@@ -76,14 +76,16 @@ def greek_scale(c):
 def test_tc_estimator_unbiased_against_fp64(q, plan, prec):
     """The PCA contracts of the d=64, N=2^20, R=32 grid against FP64: every
     Greek within 0.1 SE + 2^-21 mean |per-point value| (the MIXED bar) and
-    within 1 SE, and the share within 0.1 SE no more than 0.1 below the
+    within 0.6 SE, and the share within 0.1 SE no more than 0.1 below the
     CUDA-core MIXED path's on the same contracts.  Here the RQMC standard
     error sits at the float floor (PCA at sigma = 0.1: 1-4e-8 relative), so
-    MIXED itself has only about half the pairs within 0.1 SE, and that share
-    moves by a few pairs with any change of float rounding.  A tensor-core
-    accumulation bias of ~1 ulp of |W~| per instruction showed here as 6-13
-    SE before the leading product was made exact, and a two-part bf16 Ahat
-    (off by up to 2^-15) as up to 11 SE."""
+    MIXED itself has about four fifths of the pairs within 0.1 SE (measured:
+    worst 0.44 SE; tensor cores 0.46), and that share moves by a few pairs
+    with any change of float rounding.  A tensor-core accumulation bias of
+    ~1 ulp of |W~| per instruction showed here as 6-13 SE before the leading
+    product was made exact, a two-part bf16 Ahat (off by up to 2^-15) as up
+    to 11 SE, and inverse-normal coefficients whose roundings added up to a
+    smooth error as 0.8 SE."""
     cs = [c for c in W.grid_d64() if c.construction == W.PCA]
     tc = q.qmccpw_greeks_batch(plan, cs, prec)
     mixed = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_MIXED)
@@ -94,7 +96,7 @@ def test_tc_estimator_unbiased_against_fp64(q, plan, prec):
         met += int(np.sum(err <= 0.1 * s64))
         met_mixed += int(np.sum(np.abs(mm - m64) <= 0.1 * s64))
         total += 4
-        if np.any(err > 0.1 * s64 + 2.0 ** -21 * greek_scale(c)) or np.any(err > s64):
+        if np.any(err > 0.1 * s64 + 2.0 ** -21 * greek_scale(c)) or np.any(err > 0.6 * s64):
             bad.append((c.label(), (err / s64).tolist()))
     assert not bad, bad[:5]
     assert met / total >= met_mixed / total - 0.1, (met / total, met_mixed / total)
