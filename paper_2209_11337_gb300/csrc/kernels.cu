@@ -479,6 +479,10 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
 // Register budget: the float PCA product's register block needs up to 128
 // registers and the double forms more than 80 (two CTAs per SM); the other
 // float forms fit three CTAs per SM.
+// the first Sobol' point of the current tile, per dimension (phase 1)
+constexpr int kTileStartDims = 1024;
+__shared__ uint32_t tile_start[kTileStartDims];
+
 template <typename T, int CONS>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CONS != QMCCPW_PCA) ? 3 : 2)
     fused_kernel(const __grid_constant__ LaunchParams p) {
@@ -503,6 +507,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CONS != QMCCPW_PC
             const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
             const int chunk = 1 << c.chunk_log2;
             const int nchunks = P >> c.chunk_log2;
+            // the tile's first point, one walk per dimension, when the tile starts
+            // on a multiple of P (every run then starts from it by the bits of
+            // its own offset); otherwise each run walks from its own index
+            const uint64_t k_tile = p.point_k0 + tile * static_cast<uint64_t>(P);
+            const bool from_tile = nchunks > 1 && (k_tile & static_cast<uint64_t>(P - 1)) == 0 && n <= kTileStartDims;
+            if (from_tile) {
+                for (int j = threadIdx.x; j < n; j += kThreads)
+                    tile_start[j] = sobol_first(tab, p.jstride, j, __ldg(shf + j), static_cast<uint32_t>(k_tile));
+                __syncthreads();
+            }
             // n >= 32: a warp takes whole chunks, its lanes consecutive dimensions
             // (stores to one row: no bank conflicts); smaller n: (chunk, dim) items
             const bool by_warp = n >= 32;
@@ -528,9 +542,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CONS != QMCCPW_PC
                 const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
                 if (len > 0) {
                     const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
+                    const uint32_t off = static_cast<uint32_t>(ch * chunk);
+                    const uint32_t y0 = from_tile ? sobol_from_gray(tab, p.jstride, j, tile_start[j], off ^ (off >> 1))
+                                                  : sobol_first(tab, p.jstride, j, __ldg(shf + j), k0);
                     if constexpr (sizeof(T) == 4) {
                         sobol_point_pairs(
-                            tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2,
+                            tab, p.jstride, j, y0, k0, len, c.chunk_log2,
                             [&](int s, uint32_t y) { dst[s * stride] = Arith<float>::inv_normal(y); },
                             [&](int s, uint32_t y0, uint32_t y1) {
                                 const float2 z = Arith<float>::inv_normal2(y0, y1);
@@ -538,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CONS != QMCCPW_PC
                                 dst[(s + 1) * stride] = z.y;
                             });
                     } else {
-                        sobol_points(tab, p.jstride, j, __ldg(shf + j), k0, len, c.chunk_log2,
+                        sobol_points(tab, p.jstride, j, y0, k0, len, c.chunk_log2,
                                      [&](int s, uint32_t y) { dst[s * stride] = Arith<T>::inv_normal(y); });
                     }
                 }

@@ -362,7 +362,12 @@ __device__ __forceinline__ void sobol_chain_pair(const uint32_t *__restrict__ ta
 // (128-byte swizzled rows: conflict-free).  Points past N are 0.  Columns of Z
 // at or beyond n meet only zero Ahat columns: an odd last dimension is
 // paired with a copy of itself in the next (padding) column.
-template <int KIND, int NW>
+// the first Sobol' point of the current tile, per dimension of the Z columns
+// being built (phase 1 of both variants)
+constexpr int kTcTileDims = 256;
+__shared__ uint32_t tc_tile_start[kTcTileDims];
+
+template <int KIND, int NW, bool TILE_START>
 __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const ContractDev &c, uint32_t rep, uint64_t tile,
                                            unsigned char *z_hi, unsigned char *z_lo, int j0, int j1) {
     constexpr int ES = KIND == 0 ? 2 : 4;
@@ -372,6 +377,19 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
     const int nchunks = kM >> c.chunk_log2;
     const int per = (j1 - j0 + 63) >> 6;
     const int work = nchunks * per;
+    // TILE_START (the streamed variant): the tile's first point for dimensions
+    // j0..j1, one walk each, when the tile starts on a multiple of kM; every
+    // run then starts from it by the bits of its own offset (sobol_from_gray).
+    // The resident variant (at most 64 dimensions) measured 0.7% slower with
+    // it (one more barrier per tile), so its runs walk from their own index.
+    const uint64_t k_tile = p.point_k0 + tile * static_cast<uint64_t>(kM);
+    const bool from_tile = TILE_START && nchunks > 1 && (k_tile & static_cast<uint64_t>(kM - 1)) == 0 &&
+                           j1 - j0 <= kTcTileDims;
+    if (from_tile) {
+        for (int j = j0 + static_cast<int>(threadIdx.x); j < j1; j += static_cast<int>(blockDim.x))
+            tc_tile_start[j - j0] = sobol_first(tab, p.jstride, j, __ldg(shf + j), static_cast<uint32_t>(k_tile));
+        __syncthreads();
+    }
     for (int it = threadIdx.x >> 5; it < work; it += NW) {
         const int ch = it / per;
         const int col = (it - ch * per) * 64 + 2 * (threadIdx.x & 31);
@@ -384,7 +402,13 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
         if (len > 0) {
             const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
             uint32_t ya, yb;
-            sobol_first_pair(tab, p.jstride, ja, jb, __ldg(shf + ja), __ldg(shf + jb), k0, ya, yb);
+            if (from_tile) {
+                const uint32_t off = static_cast<uint32_t>(row0);
+                sobol_from_gray_pair(tab, p.jstride, ja, jb, tc_tile_start[ja - j0], tc_tile_start[jb - j0],
+                                     off ^ (off >> 1), ya, yb);
+            } else {
+                sobol_first_pair(tab, p.jstride, ja, jb, __ldg(shf + ja), __ldg(shf + jb), k0, ya, yb);
+            }
             auto emit = [&](int s, uint32_t a, uint32_t b) {
                 split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), Arith<float>::inv_normal2(a, b));
             };
@@ -467,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
         if (sh.abort) break;
 
         // ---- phase 1: Sobol' + inverse normal -> split operand
-        sobol_to_z<KIND, kThreads / 32>(p, c, rep, tile, z_hi, z_lo, 0, n);
+        sobol_to_z<KIND, kThreads / 32, false>(p, c, rep, tile, z_hi, z_lo, 0, n);
         fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
         tc_fence_before();
         __syncthreads();
@@ -637,7 +661,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
                 __syncthreads();
             }
             // ---- phase 1: Sobol' + inverse normal -> split Z, columns j0..
-            sobol_to_z<KIND, kThreadsS / 32>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
+            sobol_to_z<KIND, kThreadsS / 32, true>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();

@@ -659,6 +659,34 @@ __device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab
     return y;
 }
 
+// y XORed with the direction integers of the set bits of g: the point whose
+// Gray code differs from y's by g.  For a tile starting at k_t, a multiple
+// of a power of two above every in-tile offset b, g(k_t + b) = g(k_t) ^ g(b)
+// (the bits of k_t and b, and of their halves, do not overlap), so a run at
+// offset b starts from the tile's first point by the few bits of g(b).
+__device__ __forceinline__ uint32_t sobol_from_gray(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
+                                                    uint32_t g) {
+    while (g) {
+        y ^= __ldg(tab + (__ffs(g) - 1) * jstride + j);
+        g &= g - 1u;
+    }
+    return y;
+}
+
+// the same for two dimensions (one walk over the set bits of g)
+__device__ __forceinline__ void sobol_from_gray_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
+                                                     uint32_t ya0, uint32_t yb0, uint32_t g, uint32_t &ya,
+                                                     uint32_t &yb) {
+    ya = ya0;
+    yb = yb0;
+    while (g) {
+        const uint32_t *row = tab + (__ffs(g) - 1) * jstride;
+        ya ^= __ldg(row + ja);
+        yb ^= __ldg(row + jb);
+        g &= g - 1u;
+    }
+}
+
 // The first point of two dimensions at once (one walk over the set bits of
 // g(k0), two loads per bit).
 __device__ __forceinline__ void sobol_first_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
@@ -706,9 +734,9 @@ __device__ __forceinline__ void sobol_run(const uint32_t *__restrict__ tab, int 
 // order (x(g(k+1)) = x(g(k)) xor v_ctz(k+1)), handed to emit(s, y).  A full
 // aligned run of 4..64 points takes the unrolled form above.
 template <typename Emit>
-__device__ __forceinline__ void sobol_points(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t shift,
+__device__ __forceinline__ void sobol_points(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
                                              uint32_t k0, int len, int chunk_log2, Emit &&emit) {
-    uint32_t y = sobol_first(tab, jstride, j, shift, k0);
+    // y: the point k0 (sobol_first, or the tile's first point and sobol_from_gray)
     if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
         switch (chunk_log2) {
             case 2: sobol_run<2>(tab, jstride, j, y, emit); return;
@@ -746,9 +774,9 @@ __device__ __forceinline__ void sobol_run_pairs(const uint32_t *__restrict__ tab
 
 template <typename Emit1, typename Emit2>
 __device__ __forceinline__ void sobol_point_pairs(const uint32_t *__restrict__ tab, int jstride, int j,
-                                                  uint32_t shift, uint32_t k0, int len, int chunk_log2,
+                                                  uint32_t y, uint32_t k0, int len, int chunk_log2,
                                                   Emit1 &&emit1, Emit2 &&emit2) {
-    uint32_t y = sobol_first(tab, jstride, j, shift, k0);
+    // y: the point k0 (sobol_first, or the tile's first point and sobol_from_gray)
     if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
         switch (chunk_log2) {
             case 2: sobol_run_pairs<2>(tab, jstride, j, y, emit2); return;
