@@ -645,25 +645,12 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
 // ---------------------------------------------------------------------------
 // Sobol' integers of one dimension over a run of consecutive points
 // ---------------------------------------------------------------------------
-// First point k0: XOR of the direction integers of the set bits of g(k0),
-// starting from the digital shift.
-__device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab, int jstride, int j,
-                                                uint32_t shift, uint32_t k0) {
-    uint32_t g = k0 ^ (k0 >> 1);
-    uint32_t y = shift;
-    while (g) {
-        const int b = __ffs(g) - 1;
-        y ^= __ldg(tab + b * jstride + j);
-        g &= g - 1u;
-    }
-    return y;
-}
-
 // y XORed with the direction integers of the set bits of g: the point whose
-// Gray code differs from y's by g.  For a tile starting at k_t, a multiple
-// of a power of two above every in-tile offset b, g(k_t + b) = g(k_t) ^ g(b)
-// (the bits of k_t and b, and of their halves, do not overlap), so a run at
-// offset b starts from the tile's first point by the few bits of g(b).
+// Gray code differs from y's by g.  From the digital shift and g(k0) it is
+// point k0.  For a tile starting at k_t, a multiple of a power of two above
+// every in-tile offset b, g(k_t + b) = g(k_t) ^ g(b) (the bits of k_t and b,
+// and of their halves, do not overlap), so a run at offset b starts from the
+// tile's first point by the few bits of g(b).
 __device__ __forceinline__ uint32_t sobol_from_gray(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
                                                     uint32_t g) {
     while (g) {
@@ -673,7 +660,7 @@ __device__ __forceinline__ uint32_t sobol_from_gray(const uint32_t *__restrict__
     return y;
 }
 
-// the same for two dimensions (one walk over the set bits of g)
+// the same for two dimensions (one walk over the set bits of g, two loads per bit)
 __device__ __forceinline__ void sobol_from_gray_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
                                                      uint32_t ya0, uint32_t yb0, uint32_t g, uint32_t &ya,
                                                      uint32_t &yb) {
@@ -687,20 +674,17 @@ __device__ __forceinline__ void sobol_from_gray_pair(const uint32_t *__restrict_
     }
 }
 
-// The first point of two dimensions at once (one walk over the set bits of
-// g(k0), two loads per bit).
+// First point k0 of a dimension (or two): from the digital shift by the set
+// bits of g(k0).
+__device__ __forceinline__ uint32_t sobol_first(const uint32_t *__restrict__ tab, int jstride, int j,
+                                                uint32_t shift, uint32_t k0) {
+    return sobol_from_gray(tab, jstride, j, shift, k0 ^ (k0 >> 1));
+}
+
 __device__ __forceinline__ void sobol_first_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
                                                  uint32_t shift_a, uint32_t shift_b, uint32_t k0, uint32_t &ya,
                                                  uint32_t &yb) {
-    uint32_t g = k0 ^ (k0 >> 1);
-    ya = shift_a;
-    yb = shift_b;
-    while (g) {
-        const uint32_t *row = tab + (__ffs(g) - 1) * jstride;
-        ya ^= __ldg(row + ja);
-        yb ^= __ldg(row + jb);
-        g &= g - 1u;
-    }
+    sobol_from_gray_pair(tab, jstride, ja, jb, shift_a, shift_b, k0 ^ (k0 >> 1), ya, yb);
 }
 
 __host__ __device__ constexpr int ctz_const(int s) {
