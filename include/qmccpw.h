@@ -125,6 +125,14 @@ typedef struct {
     uint64_t N;                /* points per replicate, 1..2^32 (powers of two recommended) */
     int32_t R;                 /* replicates, 2..plan r_max */
     int32_t construction;      /* qmccpw_construction */
+    int32_t first_replicate;   /* the contract uses replicates first_replicate .. first_replicate+R-1
+                                  of the plan's randomisation (first_replicate + R <= r_max); 0 for
+                                  the usual estimate.  Replicate r is the same set of points whichever
+                                  call, batch or GPU computes it, so a contract split into replicate
+                                  ranges (plans with the same seed) gives per-replicate estimates
+                                  bit-identical to one call over the whole range; mean and SE are
+                                  those of the call's own R replicates */
+    int32_t reserved;          /* must be 0 */
 } qmccpw_contract;
 
 /*
@@ -244,10 +252,11 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
 /*
  * Allocation-free form of qmccpw_greeks (the paper has no counterpart: this
  * is a deployment aid).  Some callers must not allocate device memory per
- * request: code that runs while a CUDA stream is being captured, latency-
- * critical services (cudaMalloc can block and cudaFree synchronises the whole
- * device), and hosts whose device memory is owned by another allocator such
- * as a framework's caching pool.  This entry point performs no cudaMalloc,
+ * request: latency-critical services (cudaMalloc can block and cudaFree
+ * synchronises the whole device), and hosts whose device memory is owned by
+ * another allocator such as a framework's caching pool, where a stray
+ * cudaMalloc competes with that pool for the same memory.  This entry point
+ * performs no cudaMalloc,
  * cudaFree or other device-memory allocation: every per-call device array
  * (tile partial sums, the contract descriptor, the bridge or PCA tables) is
  * placed in one fixed 16 MiB array compiled into the library, which every
@@ -337,6 +346,66 @@ int qmccpw_free(qmccpw_plan_t plan);
 /* Thread-local description of the last failure of this thread ("" if none).
  * The string stays valid until the thread's next qmccpw call. */
 const char *qmccpw_last_error(void);
+
+/*
+ * Splitting a job over several GPUs (a deployment aid; the paper runs one GPU).
+ * Replicates are independent (Sec. 5: the estimate is the mean of R
+ * independently randomised replicate estimates), so a contract's replicates
+ * can be split into ranges (qmccpw_contract.first_replicate) computed on
+ * different GPUs with plans of the same seed, and a book's contracts split
+ * among GPUs.  The only exchange is the R x 4 replicate estimates of each
+ * contract.
+ *
+ * qmccpw_batch_scatter_replicates: after every later launch of `batch`, copy
+ * the R x 4 replicate estimates of its contract i (caller's order) to rows
+ * first_row[i] .. first_row[i] + R_i - 1 of the device array `dst` (4 doubles
+ * a row), on the launch's stream, by a kernel.  first_row is a host array of
+ * the batch's count entries, read during the call; dst is caller-owned device
+ * memory of the batch's device and must stay valid while launches use it.
+ * dst = NULL turns the copy off.  The call waits for the device to be idle.
+ * Errors: INVALID_ARG (NULL batch, NULL first_row with dst, negative row),
+ * OOM, CUDA.
+ *
+ * qmccpw_replicate_stats: mean and standard error over replicates (as
+ * qmccpw_result: mean of the R replicate estimates and sd / sqrt(R) with the
+ * (R - 1) sample variance, both sums compensated, in replicate order) of
+ * `count` contracts whose replicate estimates sit in the device array
+ * per_replicate: contract i's R[i] rows of 4 doubles from row first_row[i].
+ * first_row (int64), R (int32, each >= 2) and stats (count x 8 doubles:
+ * mean[4] then se[4] per contract) are device arrays; the kernel is enqueued
+ * on `stream` (a cudaStream_t of the current device, NULL: the default
+ * stream) and the call returns without waiting.  It allocates nothing.
+ * With the rows of every range of a split contract in place, the result is
+ * bit-identical to one call over all of its replicates.
+ * Errors: INVALID_ARG (NULL array, count < 1), CUDA.
+ */
+int qmccpw_batch_scatter_replicates(qmccpw_batch_t batch, double *dst, const int64_t *first_row);
+int qmccpw_replicate_stats(const double *per_replicate, const int64_t *first_row, const int32_t *R,
+                           int32_t count, double *stats, void *stream);
+
+/*
+ * Pipe micro-benchmarks (a measurement aid; the paper reports no pipe rates):
+ * the issue rates that bound the kernels, measured on `device` with CUDA
+ * events (best of five launches after a warm-up), each from long chains of
+ * independent operations of one kind over every SM.  The roofline of the
+ * float path divides by the FP32 and SFU rates, that of the FP64 path by the
+ * FP64 rate, and that of the tensor-core PCA product by the tcgen05 rates.
+ *   fp32_fma_tflops:  FFMA, 2 flops per lane and instruction
+ *   fp32_fma2_tflops: packed two-lane FFMA2, 4 flops per lane and instruction
+ *   fp64_fma_tflops:  DFMA, 2 flops
+ *   sfu_*_gops:       ex2.approx, lg2.approx, rcp.approx results per second / 1e9
+ *   tc_*_tflops:      dense tcgen05.mma kind::f16 (bf16) and kind::tf32,
+ *                     M = 128, N = 256, FP32 accumulation in tensor memory
+ * The call allocates a few bytes of device memory, runs about 0.1 s of
+ * kernels and changes no device setting.  Errors: CUDA; TIMEOUT if the
+ * bounded wait for the tensor-core products expired.
+ */
+typedef struct {
+    double fp32_fma_tflops, fp32_fma2_tflops, fp64_fma_tflops;
+    double sfu_ex2_gops, sfu_lg2_gops, sfu_rcp_gops;
+    double tc_bf16_tflops, tc_tf32_tflops;
+} qmccpw_pipe_peaks;
+int qmccpw_measure_pipe_peaks(int32_t device, qmccpw_pipe_peaks *out);
 
 /* Library version string, e.g. "qmccpw 0.1 sm_103a". */
 const char *qmccpw_version(void);

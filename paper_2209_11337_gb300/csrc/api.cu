@@ -164,6 +164,9 @@ struct qmccpw_batch_s {
     int grid[kSegments] = {};
     BatchBuffers own;          // used by prepared batches
     BatchBuffers *buf = &own;  // one-shot calls point this at the plan's workspace
+    // replicate estimates copied after every launch to caller rows (qmccpw_batch_scatter_replicates)
+    double *scatter_dst = nullptr;
+    DevBuf scatter_rows;  // int64 destination row of each replicate slot
     // diagnostics
     double *point_out = nullptr;
     uint64_t point_k0 = 0;
@@ -237,6 +240,16 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
                         "tensor-core PCA supports d <= " + std::to_string(pca_tc_max_n(kind) + 1));
     }
     return QMCCPW_OK;
+}
+
+// A public contract descriptor: its replicate range within the plan's
+// randomisation, then the option, market and sizes.
+int validate_qc(const qmccpw_plan_s *p, const qmccpw_contract &c, int32_t precision, bool diagnostic) {
+    if (c.reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "qmccpw_contract.reserved must be 0");
+    if (c.first_replicate < 0 || (!diagnostic && static_cast<int64_t>(c.first_replicate) + c.R > p->r_max))
+        return fail(QMCCPW_ERR_INVALID_ARG, "replicates first_replicate .. first_replicate + R - 1 must lie in "
+                                            "0..r_max-1 (r_max=" + std::to_string(p->r_max) + ")");
+    return validate_contract(p, c.option, c.market, c.N, c.R, c.construction, precision, diagnostic);
 }
 
 // Bridge / PCA tables of d dates for unit spacing (dt = 1), built on first use
@@ -363,6 +376,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     const int P = 1 << c.tile_log2;
     c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2, is_tc(precision));
     c.R = in.R;
+    c.rep_first = in.first_replicate;
     c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
     c.groups = kThreads / P;
     c.n_levels = t->n_levels;
@@ -414,8 +428,7 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
     cudaStream_t st = stream ? stream : p->stream;
     if (count < 1) return fail(QMCCPW_ERR_INVALID_ARG, "count must be >= 1");
     for (int i = 0; i < count; ++i)
-        QMC_TRY(validate_contract(p, cs[i].option, cs[i].market, cs[i].N, cs[i].R, cs[i].construction, precision,
-                                  diagnostic));
+        QMC_TRY(validate_qc(p, cs[i], precision, diagnostic));
     QMC_CUDA(cudaSetDevice(p->device));
     b->plan = p;
     b->count = count;
@@ -533,6 +546,9 @@ int batch_enqueue(qmccpw_batch_s *b, cudaStream_t s, bool record_events = true) 
                                                         B.tile_sums.as<double>(), B.per_rep.as<double>(),
                                                         B.stats.as<double>(), b->total_reps,
                                                         B.rep_owner.as<uint64_t>(), s)));
+    if (!b->point_out && b->scatter_dst)
+        QMC_CUDA(static_cast<cudaError_t>(launch_scatter_replicates(
+            B.per_rep.as<double>(), b->scatter_rows.as<int64_t>(), b->total_reps, b->scatter_dst, s)));
     return QMCCPW_OK;
 }
 
@@ -782,6 +798,19 @@ const char *qmccpw_last_error(void) { return g_last_error.c_str(); }
 
 const char *qmccpw_version(void) { return "qmccpw 0.1 sm_103a"; }
 
+int qmccpw_measure_pipe_peaks(int32_t device, qmccpw_pipe_peaks *out) {
+    g_last_error.clear();
+    if (!out || device < 0) return fail(QMCCPW_ERR_INVALID_ARG, "qmccpw_measure_pipe_peaks: NULL output or bad device");
+    qmccpw_pipe_peaks r{};
+    const int rc = measure_pipe_peaks(device, &r);
+    if (rc < 0) return fail(QMCCPW_ERR_TIMEOUT, "qmccpw_measure_pipe_peaks: the wait for the tensor-core products expired");
+    if (rc > 0)
+        return fail(QMCCPW_ERR_CUDA, std::string("qmccpw_measure_pipe_peaks: ") +
+                                         cudaGetErrorString(static_cast<cudaError_t>(rc)));
+    *out = r;
+    return QMCCPW_OK;
+}
+
 int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
     g_last_error.clear();
     if (!out || !desc) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
@@ -898,6 +927,39 @@ int qmccpw_batch_use_graph(qmccpw_batch_t batch, int32_t enable) {
         batch->drop_graph();
     }
     batch->use_graph = enable != 0;
+    return QMCCPW_OK;
+}
+
+int qmccpw_batch_scatter_replicates(qmccpw_batch_t batch, double *dst, const int64_t *first_row) {
+    g_last_error.clear();
+    if (!batch) return fail(QMCCPW_ERR_INVALID_ARG, "NULL batch");
+    if (!dst) {
+        batch->scatter_dst = nullptr;
+        return QMCCPW_OK;
+    }
+    if (!first_row) return fail(QMCCPW_ERR_INVALID_ARG, "NULL first_row");
+    std::vector<int64_t> rows(batch->total_reps);
+    uint64_t slot = 0;
+    for (int k = 0; k < batch->count; ++k) {
+        const int64_t f = first_row[batch->order[k]];
+        if (f < 0) return fail(QMCCPW_ERR_INVALID_ARG, "negative first_row");
+        for (int r = 0; r < batch->R[k]; ++r) rows[slot++] = f + r;
+    }
+    QMC_CUDA(cudaSetDevice(batch->plan->device));
+    QMC_CUDA(cudaDeviceSynchronize());  // no launch in flight reads the rows being replaced
+    QMC_TRY(batch->scatter_rows.ensure(sizeof(int64_t) * rows.size()));
+    QMC_CUDA(cudaMemcpy(batch->scatter_rows.ptr, rows.data(), sizeof(int64_t) * rows.size(), cudaMemcpyHostToDevice));
+    batch->scatter_dst = dst;
+    batch->drop_graph();  // a captured sequence would lack (or keep) the copy
+    return QMCCPW_OK;
+}
+
+int qmccpw_replicate_stats(const double *per_replicate, const int64_t *first_row, const int32_t *R, int32_t count,
+                           double *stats, void *stream) {
+    g_last_error.clear();
+    if (!per_replicate || !first_row || !R || !stats || count < 1)
+        return fail(QMCCPW_ERR_INVALID_ARG, "qmccpw_replicate_stats: NULL array or count < 1");
+    QMC_CUDA(static_cast<cudaError_t>(launch_gathered_stats(per_replicate, first_row, R, count, stats, stream)));
     return QMCCPW_OK;
 }
 
@@ -1264,8 +1326,7 @@ int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t 
     if (!plan || !contract || !ticket) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
     QmcServer *sv = plan->server;
     if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
-    QMC_TRY(validate_contract(plan, contract->option, contract->market, contract->N, contract->R,
-                              contract->construction, sv->desc.precision, false));
+    QMC_TRY(validate_qc(plan, *contract, sv->desc.precision, false));
     if (sv->bytes_of(*contract) > plan->workspace_bytes)
         return fail(QMCCPW_ERR_OOM, "the request needs more device scratch than the plan's workspace budget");
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -1390,7 +1451,7 @@ int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t c
     std::map<std::pair<int, int>, bool> seen;
     for (int i = 0; i < count && rc == QMCCPW_OK; ++i) {
         const qmccpw_contract &src = sample[i];
-        rc = validate_contract(plan, src.option, src.market, src.N, src.R, src.construction, precision, false);
+        rc = validate_qc(plan, src, precision, false);
         if (rc != QMCCPW_OK) break;
         if (seen[std::make_pair(src.construction, src.option.d)]) continue;
         seen[std::make_pair(src.construction, src.option.d)] = true;
@@ -1400,6 +1461,7 @@ int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t c
         // a workload of its own size: about 2^24 point-dates (2^21 in FP64)
         qmccpw_contract c = src;
         c.R = 4;
+        c.first_replicate = 0;
         const uint64_t target = precision == QMCCPW_FP64 ? (1ull << 21) : (1ull << 24);
         c.N = std::max<uint64_t>(1024, target / (4ull * static_cast<uint64_t>(c.option.d)));
         int best = base;

@@ -39,7 +39,6 @@ namespace {
 // ---------------------------------------------------------------------------
 // small non-negative int as T (float: without a conversion instruction)
 template <typename T> __device__ __forceinline__ T small_int_to(int i);
-template <> __device__ __forceinline__ float small_int_to<float>(int i) { return small_uint_to_float(static_cast<uint32_t>(i)); }
 template <> __device__ __forceinline__ double small_int_to<double>(int i) { return static_cast<double>(i); }
 
 // The contract fields a bridge node reads, copied to registers once per
@@ -59,7 +58,9 @@ struct BridgeTables {
 // Node b of a bridge schedule in a point's row: W~ at its date from its
 // endpoints and z (unit-spacing weights, z scaled by sqrt(dt)), written in
 // place of z.
-template <typename T>
+// Float: SCALED gives W~ (z scaled by sqrt(dt)); otherwise the path of unit
+// spacing w = W~ / sqrt(dt) that the float accumulator takes.
+template <typename T, bool SCALED = true>
 __device__ __forceinline__ T bridge_node(const BridgeTables &t, T *row, int b, int4 &st) {
     st = __ldg(t.steps + b);
     const T Wl = row[st.y], Wr = row[st.z];
@@ -69,7 +70,7 @@ __device__ __forceinline__ T bridge_node(const BridgeTables &t, T *row, int b, i
         const double *w = t.w64 + 3 * b;
         Wm = __ldg(w) * Wl + __ldg(w + 1) * Wr + __ldg(w + 2) * (t.sqrt_t1 * z);
     } else {
-        z = fmaf(z, t.sdt_hi, z * t.sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
+        if constexpr (SCALED) z = fmaf(z, t.sdt_hi, z * t.sdt_lo);  // z sqrt(dt): the tables hold unit-spacing weights
         // hi + lo coefficients: the low parts first, then the high parts
         const float4 h = __ldg(t.w32 + 2 * b);
         const float4 g = __ldg(t.w32 + 2 * b + 1);
@@ -163,31 +164,31 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     const int grp = threadIdx.x >> c.tile_log2;
     const int G = c.groups;
     T *row = zw + pt * stride;
-    T omega, sigma, dt;
-    market_of(c, omega, sigma, dt);
     const BridgeTables t(c);
     const int32_t *level_start = c.level_start;
     const int n_levels = c.n_levels;
-    auto node = [&](int b, int4 &st) -> T { return bridge_node<T>(t, row, b, st); };
     for (int lvl = 0; lvl < n_levels; ++lvl) {
         const int b_end = __ldg(level_start + lvl + 1);
         // the nodes of a level are independent: a thread takes two at a time
         // (float: their exponentials in packed form)
         for (int b = __ldg(level_start + lvl) + grp; b < b_end; b += 2 * G) {
             int4 s0, s1;
-            const T W0 = node(b, s0);
             if constexpr (sizeof(T) == 4) {
+                const PathConst k(c);
+                const float w0 = bridge_node<float, false>(t, row, b, s0);
                 if (b + G < b_end) {
-                    const T W1 = node(b + G, s1);
-                    acc.template add2<TYPE>(s0.x, s1.x, W0, W1, omega, sigma, __int_as_float(s0.w) * dt,
-                                            __int_as_float(s1.w) * dt);
+                    const float w1 = bridge_node<float, false>(t, row, b + G, s1);
+                    acc.template add2<TYPE>(s0.x, s1.x, w0, w1, k);
                     continue;
                 }
-                acc.template add<TYPE>(s0.x, W0, omega, sigma, __int_as_float(s0.w) * dt);
+                acc.template add<TYPE>(s0.x, w0, k);
             } else {
+                double omega, sigma, dt;
+                market_of(c, omega, sigma, dt);
+                const T W0 = bridge_node<T>(t, row, b, s0);
                 acc.template add<TYPE>(s0.x, W0, omega, sigma, static_cast<T>(__int_as_float(s0.w)) * dt);
                 if (b + G < b_end) {
-                    const T W1 = node(b + G, s1);
+                    const T W1 = bridge_node<T>(t, row, b + G, s1);
                     acc.template add<TYPE>(s1.x, W1, omega, sigma, static_cast<T>(__int_as_float(s1.w)) * dt);
                 }
             }
@@ -240,13 +241,11 @@ template <int N, int TYPE>
 __device__ __forceinline__ void bridge_registers(const ContractDev &c, const float *row, PathAcc<float> &acc) {
     constexpr BridgeSchedule S = make_schedule(N);
     static_assert(S.count == N, "bridge schedule size");
-    const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
-    const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
-    float W[N + 1];
+    const PathConst k(c);
+    float W[N + 1];  // the path of unit spacing
     W[0] = 0.0f;
     auto node = [&](int b) {
-        const float z0 = row[b + 1];  // z of dimension b (stored by dimension)
-        const float z = fmaf(z0, sdt_hi, z0 * sdt_lo);  // z sqrt(dt), sqrt(dt) carried as hi + lo
+        const float z = row[b + 1];  // z of dimension b (stored by dimension)
         const float Wl = W[S.l[b]], Wr = W[S.r[b]];
         const float Wm = fmaf(static_cast<float>(S.c[b]), z, fmaf(static_cast<float>(S.wr[b]), Wr - Wl, Wl));
         W[S.m[b]] = Wm;
@@ -256,12 +255,11 @@ __device__ __forceinline__ void bridge_registers(const ContractDev &c, const flo
 #pragma unroll
     for (int b = 0; b + 1 < N; b += 2) {
         const float W0 = node(b), W1 = node(b + 1);
-        acc.template add2<TYPE>(S.m[b], S.m[b + 1], W0, W1, omega, sigma, static_cast<float>(S.m[b]) * dt,
-                                static_cast<float>(S.m[b + 1]) * dt);
+        acc.template add2<TYPE>(S.m[b], S.m[b + 1], W0, W1, k);
     }
     if constexpr (N % 2 == 1) {
         const float W0 = node(N - 1);
-        acc.template add<TYPE>(S.m[N - 1], W0, omega, sigma, static_cast<float>(S.m[N - 1]) * dt);
+        acc.template add<TYPE>(S.m[N - 1], W0, k);
     }
 }
 
@@ -273,23 +271,27 @@ __device__ void pca_rows_phase(const ContractDev &c, const T *zw, int stride, Pa
     const int pt = threadIdx.x & (P - 1);
     const int grp = threadIdx.x >> c.tile_log2;
     const T *row = zw + pt * stride;
-    T omega, sigma, dt;
-    market_of(c, omega, sigma, dt);
     const int n = c.n;
-    T s_i = small_int_to<T>(1 + grp) * dt;
-    const T ds = small_int_to<T>(c.groups) * dt;
-    for (int i = 1 + grp; i <= n; i += c.groups, s_i += ds) {
-        T Wi = T(0);
-        if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
+        double omega, sigma, dt;
+        market_of(c, omega, sigma, dt);
+        double s_i = static_cast<double>(1 + grp) * dt;
+        const double ds = static_cast<double>(c.groups) * dt;
+        for (int i = 1 + grp; i <= n; i += c.groups, s_i += ds) {
+            T Wi = T(0);
             const double *Ai = c.pca64 + static_cast<size_t>(i - 1) * n;
             for (int k = 0; k < n; ++k) Wi += __ldg(Ai + k) * row[k + 1];
             Wi *= c.sqrt_t1;
-        } else {
-            const int n_pad = (n + 15) & ~15;
-            for (int k = 0; k < n; ++k) Wi = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k) * n_pad + (i - 1)), row[k + 1], Wi);
-            Wi = fmaf(Wi, c.ff_sqrt_t1[0], Wi * c.ff_sqrt_t1[1]);
+            acc.template add<TYPE>(i, Wi, omega, sigma, s_i);
         }
-        acc.template add<TYPE>(i, Wi, omega, sigma, s_i);
+    } else {
+        const PathConst kc(c);
+        const int n_pad = (n + 15) & ~15;
+        for (int i = 1 + grp; i <= n; i += c.groups) {
+            float w = 0.0f;  // unit spacing
+            for (int k = 0; k < n; ++k) w = fmaf(__ldg(c.pcaT32 + static_cast<size_t>(k) * n_pad + (i - 1)), row[k + 1], w);
+            acc.template add<TYPE>(i, w, kc);
+        }
     }
 }
 
@@ -307,7 +309,7 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
     const int g = warp % groups;
     slot = warp / groups;
     const int n = c.n, n4 = ((n + 15) & ~15) >> 2;
-    const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
+    const PathConst kc(c);
     const float *zr[PB];
 #pragma unroll
     for (int j = 0; j < PB; ++j) {
@@ -334,21 +336,15 @@ __device__ void pca_gemm_phase(const ContractDev &c, const float *zw, int stride
                 for (int r = 0; r < 16; ++r) w[j][r] = fmaf(av[r], z, w[j][r]);
             }
         }
-        const float s0 = small_uint_to_float(static_cast<uint32_t>(rb * 16 + 1)) * dt;
-        const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
 #pragma unroll
-        for (int r = 0; r < 16; r += 2) {  // dates i, i + 1: exponentials in packed form
+        for (int r = 0; r < 16; r += 2) {  // dates i, i + 1 (unit-spacing path): exponentials in packed form
             const int i = rb * 16 + r + 1;
-            const float s_i = fmaf(static_cast<float>(r), dt, s0), s_i1 = fmaf(static_cast<float>(r + 1), dt, s0);
             if (i + 1 <= n) {
 #pragma unroll
-                for (int j = 0; j < PB; ++j)
-                    acc[j].template add2<TYPE>(i, i + 1, fmaf(w[j][r], sh, w[j][r] * sl),
-                                               fmaf(w[j][r + 1], sh, w[j][r + 1] * sl), omega, sigma, s_i, s_i1);
+                for (int j = 0; j < PB; ++j) acc[j].template add2<TYPE>(i, i + 1, w[j][r], w[j][r + 1], kc);
             } else if (i <= n) {
 #pragma unroll
-                for (int j = 0; j < PB; ++j)
-                    acc[j].template add<TYPE>(i, fmaf(w[j][r], sh, w[j][r] * sl), omega, sigma, s_i);
+                for (int j = 0; j < PB; ++j) acc[j].template add<TYPE>(i, w[j][r], kc);
             }
         }
     }
@@ -380,25 +376,24 @@ __device__ void forward_phase(const ContractDev &c, const T *zw, int stride, Pat
         w = T(0);
         for (int h = 0; h < g; ++h) w += block_sum[h * P + pt];
     }
-    T omega, sigma, dt;
-    market_of(c, omega, sigma, dt);
     if constexpr (sizeof(T) == 8) {
+        double omega, sigma, dt;
+        market_of(c, omega, sigma, dt);
         for (int i = i0; i <= i1; ++i) {
             w += row[i];
             acc.template add<TYPE>(i, w * c.sqrt_t1, omega, sigma, small_int_to<T>(i) * dt);
         }
     } else {
-        const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
+        const PathConst kc(c);
         int i = i0;
-        for (; i + 1 <= i1; i += 2) {  // two dates at a time: exponentials in packed form
+        for (; i + 1 <= i1; i += 2) {  // two dates at a time (unit spacing): exponentials in packed form
             const float w0 = w + row[i];
             w = w0 + row[i + 1];
-            acc.template add2<TYPE>(i, i + 1, fmaf(w0, sh, w0 * sl), fmaf(w, sh, w * sl), omega, sigma,
-                                    small_int_to<float>(i) * dt, small_int_to<float>(i + 1) * dt);
+            acc.template add2<TYPE>(i, i + 1, w0, w, kc);
         }
         if (i <= i1) {
             w += row[i];
-            acc.template add<TYPE>(i, fmaf(w, sh, w * sl), omega, sigma, small_int_to<float>(i) * dt);
+            acc.template add<TYPE>(i, w, kc);
         }
     }
 }
@@ -421,18 +416,18 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
         bridge_phase<T, TYPE>(c, zw, stride, acc);
         if (c.groups == 1) return;
         __syncthreads();
-        stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
+        stage_partial(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
         __syncthreads();
-        if (threadIdx.x < P) merge_partials<T>(zw, P, c.groups, threadIdx.x, TYPE, acc);
+        if (threadIdx.x < P) merge_partials(zw, P, c.groups, threadIdx.x, TYPE, acc);
         return;
     } else if constexpr (CONS == QMCCPW_STD) {
         acc.init(TYPE, threadIdx.x < P);
         forward_phase<T, TYPE>(c, zw, stride, acc);
         if (c.groups == 1) return;
         __syncthreads();
-        stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
+        stage_partial(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
         __syncthreads();
-        if (threadIdx.x < P) merge_partials<T>(zw, P, c.groups, threadIdx.x, TYPE, acc);
+        if (threadIdx.x < P) merge_partials(zw, P, c.groups, threadIdx.x, TYPE, acc);
         return;
     } else {
     if constexpr (sizeof(T) == 4) {
@@ -444,23 +439,23 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
                 pca_gemm_phase<4, TYPE>(c, zw, stride, a4, slot, slots, pts);
                 __syncthreads();
 #pragma unroll
-                for (int j = 0; j < 4; ++j) stage_partial<float>(zw, P, slot, pts[j], a4[j]);
+                for (int j = 0; j < 4; ++j) stage_partial(zw, P, slot, pts[j], a4[j]);
             } else if (P == 64) {
                 PathAcc<float> a2[2];
                 int pts[2];
                 pca_gemm_phase<2, TYPE>(c, zw, stride, a2, slot, slots, pts);
                 __syncthreads();
 #pragma unroll
-                for (int j = 0; j < 2; ++j) stage_partial<float>(zw, P, slot, pts[j], a2[j]);
+                for (int j = 0; j < 2; ++j) stage_partial(zw, P, slot, pts[j], a2[j]);
             } else {
                 PathAcc<float> a1[1];
                 int pts[1];
                 pca_gemm_phase<1, TYPE>(c, zw, stride, a1, slot, slots, pts);
                 __syncthreads();
-                stage_partial<float>(zw, P, slot, pts[0], a1[0]);
+                stage_partial(zw, P, slot, pts[0], a1[0]);
             }
             __syncthreads();
-            if (threadIdx.x < P) merge_partials<float>(zw, P, slots, threadIdx.x, TYPE, acc);
+            if (threadIdx.x < P) merge_partials(zw, P, slots, threadIdx.x, TYPE, acc);
             return;
         }
     }
@@ -468,9 +463,9 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
     pca_rows_phase<T, TYPE>(c, zw, stride, acc);
     if (c.groups == 1) return;
     __syncthreads();
-    stage_partial<T>(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
+    stage_partial(zw, P, threadIdx.x >> c.tile_log2, threadIdx.x & (P - 1), acc);
     __syncthreads();
-    if (threadIdx.x < P) merge_partials<T>(zw, P, c.groups, threadIdx.x, TYPE, acc);
+    if (threadIdx.x < P) merge_partials(zw, P, c.groups, threadIdx.x, TYPE, acc);
     }
 }
 
@@ -663,22 +658,46 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ContractDev *__restri
     if (threadIdx.x < 4) per_rep[slot * 4 + threadIdx.x] = part[0][threadIdx.x].value() / static_cast<double>(c.N);
 }
 
+// Mean over the R replicate estimates of Greek g (rows of 4 doubles from
+// `rows`) and the standard error of that mean, sd / sqrt(R) with the (R - 1)
+// sample variance (Sec. 5); both sums compensated, in replicate order.
+__device__ void replicate_stats(const double *__restrict__ rows, int R, int g, double &mean, double &se) {
+    Neumaier s = {0, 0};
+    for (int r = 0; r < R; ++r) s.add(rows[r * 4 + g]);
+    mean = s.value() / R;
+    Neumaier dev = {0, 0};
+    for (int r = 0; r < R; ++r) {
+        const double e = rows[r * 4 + g] - mean;
+        dev.add(e * e);
+    }
+    se = sqrt(dev.value() / (static_cast<double>(R) * (R - 1)));
+}
+
 __global__ void stats_kernel(const ContractDev *__restrict__ contracts, int count,
                              const double *__restrict__ per_rep, double *__restrict__ stats) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count * 4) return;
     const int ci = t >> 2, g = t & 3;
     const ContractDev &c = contracts[ci];
-    Neumaier s = {0, 0};
-    for (int r = 0; r < c.R; ++r) s.add(per_rep[(c.rep_base + r) * 4 + g]);
-    const double mean = s.value() / c.R;
-    Neumaier dev = {0, 0};
-    for (int r = 0; r < c.R; ++r) {
-        const double e = per_rep[(c.rep_base + r) * 4 + g] - mean;
-        dev.add(e * e);
-    }
-    stats[ci * 8 + g] = mean;
-    stats[ci * 8 + 4 + g] = sqrt(dev.value() / (static_cast<double>(c.R) * (c.R - 1)));
+    replicate_stats(per_rep + c.rep_base * 4, c.R, g, stats[ci * 8 + g], stats[ci * 8 + 4 + g]);
+}
+
+// The same statistics for replicate estimates assembled elsewhere (contract
+// i's R[i] rows start at row first_row[i] of per_rep).
+__global__ void gathered_stats_kernel(const double *__restrict__ per_rep, const int64_t *__restrict__ first_row,
+                                      const int32_t *__restrict__ R, int count, double *__restrict__ stats) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count * 4) return;
+    const int ci = t >> 2, g = t & 3;
+    replicate_stats(per_rep + first_row[ci] * 4, R[ci], g, stats[ci * 8 + g], stats[ci * 8 + 4 + g]);
+}
+
+// Copy replicate slot s of a batch (4 doubles) to row dst_row[s] of dst.
+__global__ void scatter_replicates_kernel(const double *__restrict__ per_rep, const int64_t *__restrict__ dst_row,
+                                          uint64_t slots, double *__restrict__ dst) {
+    const uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+    if (t >= slots * 4) return;
+    dst[dst_row[t >> 2] * 4 + (t & 3)] = per_rep[t];
 }
 
 // ---------------------------------------------------------------------------
@@ -745,8 +764,9 @@ __global__ void sobol_dump_kernel(const uint32_t *__restrict__ tab, const uint32
 size_t fused_smem_bytes(int precision, int construction, int n, int tile_log2) {
     const size_t elem = (precision == QMCCPW_FP64) ? 8 : 4;
     const size_t zw = static_cast<size_t>(1u << tile_log2) * tile_row_elems(construction, n) * elem;
-    // staging of partial accumulators: up to 4 * kThreads (slot, point) entries of (x, dsum, m)
-    const size_t red = 4 * kThreads * (2 * elem + sizeof(int32_t));  // >= 4 * kThreads doubles for the tile sum
+    // staging of partial accumulators: up to 4 * kThreads (slot, point) entries of kStageBytes
+    // (double: x, dsum, m; float: x, yw, yn, m), >= 4 * kThreads doubles for the tile sum
+    const size_t red = 4 * kThreads * static_cast<size_t>(kStageBytes);
     return ((zw > red ? zw : red) + 15) & ~size_t(15);
 }
 
@@ -807,6 +827,20 @@ int launch_reduce(const ContractDev *contracts, int32_t count, const double *til
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return static_cast<int>(e);
     stats_kernel<<<(count * 4 + 127) / 128, 128, 0, s>>>(contracts, count, per_rep, stats);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_gathered_stats(const double *per_rep, const int64_t *first_row, const int32_t *R, int count,
+                          double *stats, void *stream) {
+    gathered_stats_kernel<<<(count * 4 + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        per_rep, first_row, R, count, stats);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_scatter_replicates(const double *per_rep, const int64_t *dst_row, uint64_t slots, double *dst,
+                              void *stream) {
+    scatter_replicates_kernel<<<static_cast<unsigned>((slots * 4 + 255) / 256), 256, 0,
+                                static_cast<cudaStream_t>(stream)>>>(per_rep, dst_row, slots, dst);
     return static_cast<int>(cudaGetLastError());
 }
 

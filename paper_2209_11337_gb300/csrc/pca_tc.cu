@@ -52,150 +52,13 @@
 
 #include "qmccpw_internal.h"
 #include "qmccpw_device.cuh"
+#include "tc_ptx.cuh"
 
 namespace qmccpw {
 namespace {
 
 constexpr int kM = 128;        // points per tile (UMMA M)
 constexpr int kNpad = 64;      // dates and dimensions, padded (UMMA N and K)
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up on an mbarrier after 2 s
-
-// ---- PTX wrappers ---------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Poll the barrier for the given phase parity; false if limit_ns passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
-    const uint32_t addr = smem_u32(bar);
-    const uint64_t start = global_ns();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (global_ns() - start > limit_ns) return false;
-    }
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
-// 8 rows x 16 bytes; LBO = distance of K-adjacent core matrices, SBO = of
-// row-adjacent (8-row) groups; bits 46-48 = 0b001.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
-    d |= static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16;
-    d |= static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32;
-    d |= static_cast<uint64_t>(1) << 46;
-    return d;  // base offset 0, relative LBO mode, no swizzle
-}
-
-// The same for a K-major operand with the 128-byte swizzle: rows of 128
-// bytes, 8-row atoms of 1024 bytes (1024-byte aligned), atoms of one K
-// column SBO = 1024 apart; layout type 2 in bits 61-63; LBO unused.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
-    d |= static_cast<uint64_t>(1) << 16;
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;
-    d |= static_cast<uint64_t>(1) << 46;
-    d |= static_cast<uint64_t>(2) << 61;
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulate, A and B of format `fmt`
-// (kind::f16: 1 = bf16; kind::tf32: 2 = tf32), both K-major, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int n = kNpad) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
-           (static_cast<uint32_t>(kM >> 4) << 24);
-}
-
-template <int KIND>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
-    if constexpr (KIND == 0) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 16 columns of D1 and of D2 for this warp's 32 lanes, one wait for both.
-__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
-        "[%33];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(ta), "r"(tb)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        a[i] = __uint_as_float(r[i]);
-        b[i] = __uint_as_float(r[16 + i]);
-    }
-}
-
 // ---- operand element addressing ----------------------------------------------
 // Element (row, k) of Z (kM rows), K-major with the 128-byte swizzle: K
 // columns of 128 bytes each hold kM rows of 128 bytes; the 16-byte unit u of
@@ -248,8 +111,7 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
     const int warp = threadIdx.x >> 5;
     const int half = warp >> 2;                 // warpgroup: which share of the dates
     const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
-    const float sdt_hi = c.ff_sqrt_t1[0], sdt_lo = c.ff_sqrt_t1[1];
-    const float omega = c.f_omega, sigma = c.f_sigma, dt = c.f_dt;
+    const PathConst k(c);
     acc.init(TYPE, half == 0);
     const int last = min(c.n, (half + 1) * (NPAD / NWG));  // dates beyond n are padding
 #pragma unroll 1
@@ -257,17 +119,14 @@ __device__ void epilogue_sums(const ContractDev &c, uint32_t tmem, PathAcc<float
         float d1[16], d2[16];
         tmem_ld16x2(tmem + lane_base + static_cast<uint32_t>(col), tmem + lane_base + static_cast<uint32_t>(col + NPAD),
                     d1, d2);
-        const float s0 = small_uint_to_float(static_cast<uint32_t>(col + 1)) * dt;
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {  // dates (W~ at s_date) two at a time, in packed form
+        for (int i = 0; i < 16; i += 2) {  // dates two at a time, in packed form (unit-spacing path D1 + D2)
             const int date = col + i + 1;
             const float2 w = add2(make_float2(d1[i], d1[i + 1]), make_float2(d2[i], d2[i + 1]));
-            const float2 W = fma2(w, f2(sdt_hi), mul2(w, f2(sdt_lo)));
-            const float2 sd = fma2(make_float2(static_cast<float>(i), static_cast<float>(i + 1)), f2(dt), f2(s0));
             if (date + 1 <= c.n)
-                acc.template add2<TYPE>(date, date + 1, W.x, W.y, omega, sigma, sd.x, sd.y);
+                acc.template add2<TYPE>(date, date + 1, w.x, w.y, k);
             else if (date <= c.n)
-                acc.template add<TYPE>(date, W.x, omega, sigma, sd.x);
+                acc.template add<TYPE>(date, w.x, k);
         }
     }
 }
@@ -289,12 +148,12 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
                                            PathAcc<float> &acc, unsigned char *scratch) {
     const int warp = threadIdx.x >> 5;
     const int point = 32 * (warp & 3) + (threadIdx.x & 31);
-    stage_partial<float>(scratch, kM, warp >> 2, point, acc);
+    stage_partial(scratch, kM, warp >> 2, point, acc, kM * NWG);
     __syncthreads();
     ff v[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     const uint64_t local_point = tile * kM + point;
     if (warp < 4) {
-        merge_partials<float>(scratch, kM, NWG, point, c.type, acc);
+        merge_partials(scratch, kM, NWG, point, c.type, acc, kM * NWG);
         if (local_point < c.N) {
             float xhat, dhat;
             finish_functional(c, acc, xhat, dhat);
@@ -438,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
     constexpr uint32_t kOpBytesZ = kM * kNpad * ES;        // one split part of Z
     constexpr uint32_t kOpBytesB = kNpad * kNpad * ES;     // one split part of Ahat
     constexpr int kPartsB = KIND == 0 ? 3 : 2;             // Ahat parts: bf16 hi/mid/lo, tf32 hi/lo
-    constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 1u : 2u);
+    constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 1u : 2u, kNpad);
     constexpr uint32_t kLbo = 128, kSbo = (kNpad / (16 / ES)) * 128;
     constexpr uint32_t kCols = 2 * kNpad;                  // D1 and D2
 
@@ -483,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
                 mbar_expect_tx(&sh.bar_b, kPartsB * kOpBytesB);
                 bulk_copy_g2s(b_hi, c.tc_operand, kPartsB * kOpBytesB, &sh.bar_b);
             }
-            if (!mbar_wait(&sh.bar_b, b_phase & 1u)) atomicExch(&sh.abort, 1);
+            if (!mbar_wait(&sh.bar_b, b_phase & 1u)) atomicExch(&sh.abort, 1);  // 1: the copy may still land
             ++b_phase;
             __syncthreads();
             if (threadIdx.x == 0) sh.loaded_n = n;
@@ -517,7 +376,9 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
             }
             mma_commit(&sh.bar_mma);
         }
-        if (!mbar_wait(&sh.bar_mma, mma_phase & 1u)) atomicExch(&sh.abort, 1);
+        if (!mbar_wait(&sh.bar_mma, mma_phase & 1u)) atomicExch(&sh.abort, 2);  // 2: products may still run
+        __syncthreads();
+        if (sh.abort) break;  // an unfinished accumulator is never read or summed
         ++mma_phase;
         tc_fence_after();
 
@@ -528,10 +389,16 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
         finish_tile<2>(p, c, item, tile, acc, scratch);
     }
 
-    // release tensor memory (also after an abort)
+    // release tensor memory (also after an abort: first, with the same bounded
+    // wait, let the copy or the products the expired wait left in flight land)
     tc_fence_before();
     __syncthreads();
-    if (sh.abort && threadIdx.x == 0 && p.error_flag) atomicExch(p.error_flag, QMCCPW_ERR_TIMEOUT);
+    if (sh.abort && threadIdx.x == 0) {
+        if (sh.abort == 1) mbar_wait(&sh.bar_b, (b_phase - 1u) & 1u);
+        else mbar_wait(&sh.bar_mma, mma_phase & 1u);
+        if (p.error_flag) atomicExch(p.error_flag, QMCCPW_ERR_TIMEOUT);
+    }
+    __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kCols);
@@ -652,13 +519,18 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
             }
         }
 
+        bool late = false;  // a wait for the products expired: leave the item unfinished
         for (int j0 = 0; j0 < c.n; j0 += S::Kz) {
             if (j0 > 0) {
                 // Z is rewritten: the products of the previous half must be done
-                if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 1);
+                if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 2);  // 2: products may still run
+                __syncthreads();
+                if (sh.abort == 2) {
+                    late = true;
+                    break;
+                }
                 ++mma_ph;
                 tc_fence_after();
-                __syncthreads();
             }
             // ---- phase 1: Sobol' + inverse normal -> split Z, columns j0..
             sobol_to_z<KIND, kThreadsS / 32, true>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
@@ -707,7 +579,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
                 if (!ok) sh.abort = 1;
             }
         }
-        if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 1);
+        if (late) break;
+        if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 2);
+        __syncthreads();
+        if (sh.abort == 2) break;  // an unfinished accumulator is never read or summed
         ++mma_ph;
         tc_fence_after();
 
@@ -718,7 +593,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
         finish_tile<kThreadsS / 128>(p, c, item, tile, acc, scratch);
     }
 
-    // the prefetched chunks must land before the CTA exits
+    // the prefetched chunks, and products an expired wait left running, must
+    // land before the CTA exits (bounded waits again)
+    if (threadIdx.x == 0 && sh.abort == 2) mbar_wait(&sh.bar_mma, mma_ph & 1u);
     if (threadIdx.x == 0 && ok && loaded != nullptr) {
         wait_b(q & 1);
         wait_b((q + 1) & 1);
@@ -756,8 +633,9 @@ int launch_bounded_wait_probe(uint64_t limit_ns, int *status, void *stream) {
 }
 
 size_t pca_tc_smem_bytes(int kind) {
-    const size_t scratch = 4 * kThreads * sizeof(double) > 4 * kThreads * 12 ? 4 * kThreads * sizeof(double)
-                                                                            : 4 * kThreads * 12;
+    // staging of the warpgroups' partial sums (4 arrays of kM x 4 entries at most) and the
+    // float-float tile sum (8 x kThreads floats)
+    const size_t scratch = std::max<size_t>(16 * kM * 4, 8 * kThreads * sizeof(float));
     if (kind == 2) return 1024 + 2 * static_cast<size_t>(Streamed<0>::ZPart) + 2 * Streamed<0>::ChunkBytes + scratch;
     if (kind == 3) return 1024 + 2 * static_cast<size_t>(Streamed<1>::ZPart) + 2 * Streamed<1>::ChunkBytes + scratch;
     const size_t es = kind == 0 ? 2 : 4, parts = kind == 0 ? 3 : 2;

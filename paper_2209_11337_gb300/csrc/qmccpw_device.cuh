@@ -7,7 +7,7 @@
 
 #include <cstdint>
 
-#include "invnorm_coeffs.h"
+#include "float_coeffs.h"
 #include "qmccpw_internal.h"
 
 namespace qmccpw {
@@ -31,39 +31,16 @@ template <> struct Arith<double> {
     __device__ static double ex(double x) { return exp(x); }
 };
 
-// Float inverse normal in the two-branch form of Giles ("Approximating the
-// erfinv function", GPU Computing Gems Jade, 2011): with x = 1 - 2q and
-// w = -ln(4q(1-q)), Phi^{-1}(q) = -x p(w) for w < W0 and -x p_t(sqrt w)
-// beyond.  The polynomials are this project's own fits (gen_invnorm.py):
-// max relative error 1.1e-7 in float, the coefficients rounded so that their
-// roundings leave no smooth error (a smooth error of Phi^{-1} is the same for
-// every point and biases the estimates).  The central branch serves 99.9% of
-// draws, so a warp rarely takes the tail.  Central branch: c1.. by Horner,
-// then t times that plus the constant term, a float pair (lo first, then hi).
-__device__ __forceinline__ float horner_c(float t) {
-    constexpr float c[] = QMC_INVN_CENTRAL;
-    constexpr int n = sizeof(c) / sizeof(c[0]);
-    float acc = c[n - 1];
-#pragma unroll
-    for (int i = n - 2; i >= 0; --i) acc = fmaf(acc, t, c[i]);
-    return fmaf(acc, t, QMC_INVN_C0_LO) + QMC_INVN_C0_HI;
-}
-
-__device__ __forceinline__ float horner_t(float t) {
-    constexpr float c[] = QMC_INVN_TAIL;
-    float acc = c[9];
-#pragma unroll
-    for (int i = 8; i >= 0; --i) acc = fmaf(acc, t, c[i]);
-    return acc;
-}
-
-// Exact float of an integer below 2^23 without a conversion instruction
-// (conversions share the slow FP64 pipe on this GPU): place it in the
-// mantissa of 2^23 and subtract 2^23.
-__device__ __forceinline__ float small_uint_to_float(uint32_t x) {
-    return __uint_as_float(0x4B000000u | x) - 8388608.0f;
-}
-
+// ---------------------------------------------------------------------------
+// float functions of the MIXED path: this project's own polynomials
+// (float_coeffs.h, fitted by gen_float_coeffs.py), evaluated with IEEE float
+// adds and fused multiply-adds, plus reciprocals from rcp.approx refined by
+// one Newton step.  The hardware approximations (lg2/ex2.approx, and the
+// library's expf/erfcf built on them) carry error patterns of a few 1e-8
+// with a nonzero mean over any range of arguments; such an error is the same
+// for every point and does not average out, while a rounding error of an
+// IEEE operation on a continuously varying value has mean zero.
+// ---------------------------------------------------------------------------
 // Packed two-lane FP32 arithmetic (one instruction for two elements): the
 // polynomial chains below run on pairs of independent elements, with the
 // same operations in the same order as the one-element forms, so a pair
@@ -73,21 +50,142 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// Exact float of an integer below 2^23 without a conversion instruction
+// (conversions share the slow FP64 pipe on this GPU): place it in the
+// mantissa of 2^23 and subtract 2^23.
+__device__ __forceinline__ float small_uint_to_float(uint32_t x) {
+    return __uint_as_float(0x4B000000u | x) - 8388608.0f;
+}
+
+namespace fx {
+constexpr float kMagic = 12582912.0f;              // 1.5 2^23: x + kMagic holds rint(x) in its low mantissa bits
+constexpr float kLog2e = 1.44269502f;              // only picks k: any nearby value is exact enough
+constexpr float kLn2Hi = 0.693147182464599609375f; // ln 2 = kLn2Hi + kLn2Lo to ~2^-48
+constexpr float kLn2Lo = -1.904654290e-09f;
+
+// 1/x to ~0.5 ulp for positive normal x: rcp.approx and one Newton step
+__device__ __forceinline__ float rcp_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ float2 rcp_nr2(float2 x) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(x.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(x.y));
+    return fma2(r, fma2(make_float2(-x.x, -x.y), r, f2(1.0f)), r);
+}
+
+// e^x for |x| <= 86: 2^k e^r, k the nearest integer to x log2 e, r = x - k ln2
+// by two FMAs (ln2 as a float pair), e^r by the degree-8 polynomial (c0 = c1
+// = 1 exact), 2^k added to the exponent field (k in the low bits of the
+// magic sum, shifted out of its high bits).
+__device__ __forceinline__ float exp_f(float x) {
+    constexpr float c[] = QMC_EXP_POLY;
+    const float m = fmaf(x, kLog2e, kMagic);
+    const float nk = kMagic - m;  // -k, exact
+    float r = fmaf(nk, kLn2Hi, x);
+    r = fmaf(nk, kLn2Lo, r);
+    float p = c[8];
+#pragma unroll
+    for (int i = 7; i >= 0; --i) p = fmaf(p, r, c[i]);
+    return __uint_as_float(__float_as_uint(p) + (__float_as_uint(m) << 23));
+}
+__device__ __forceinline__ float2 exp_f2(float2 x) {
+    constexpr float c[] = QMC_EXP_POLY;
+    const float2 m = fma2(x, f2(kLog2e), f2(kMagic));
+    const float2 nk = fma2(m, f2(-1.0f), f2(kMagic));  // -k, exact
+    float2 r = fma2(nk, f2(kLn2Hi), x);
+    r = fma2(nk, f2(kLn2Lo), r);
+    float2 p = f2(c[8]);
+#pragma unroll
+    for (int i = 7; i >= 0; --i) p = fma2(p, r, f2(c[i]));
+    return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(m.x) << 23)),
+                       __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(m.y) << 23)));
+}
+
+// e^{xh + xl} for a float-float argument (|xl| <= ulp(xh)/2, -86 <= xh <=
+// 0).  For large |xh| the float xh lies on a grid coarser than the reduced
+// argument's, so a reduction rounded on its own would err by the same amount
+// for every xh with the same k; here k ln2 is split exactly (its product
+// error by an FMA), xh - P is exact (Sterbenz), and all the small parts,
+// with xl among them, meet the exact difference in one final rounding.
+__device__ __forceinline__ float exp_ff(float xh, float xl) {
+    constexpr float c[] = QMC_EXP_POLY;
+    const float m = fmaf(xh, kLog2e, kMagic);
+    const float nk = kMagic - m;
+    const float P = nk * kLn2Hi;                       // -k ln2 (hi part), rounded
+    const float Perr = fmaf(nk, kLn2Hi, -P);           // its rounding error, exact
+    const float r0 = xh + P;                           // exact: xh and -P within a factor 2 (or k = 0)
+    const float small = fmaf(nk, kLn2Lo, xl) + Perr;   // -k ln2 (lo part) + xl + Perr
+    const float r = r0 + small;
+    float p = c[8];
+#pragma unroll
+    for (int i = 7; i >= 0; --i) p = fmaf(p, r, c[i]);
+    return __uint_as_float(__float_as_uint(p) + (__float_as_uint(m) << 23));
+}
+
+// -ln a for positive normal floats a (two at a time): a = 2^e m, m in
+// [sqrt(1/2), sqrt 2) by integer operations on the bits, ln m = f P(f^2)
+// with f = (m - 1)/(m + 1) (the atanh series; m - 1 is exact), e ln2 with
+// ln2 as a float pair.  P's coefficients enter negated, so the packed chain
+// forms -ln m without a negated operand.
+__device__ __forceinline__ float2 neg_ln2(float2 a) {
+    constexpr float c[] = QMC_LN_POLY;
+    constexpr int n = sizeof(c) / sizeof(c[0]);
+    const uint32_t bx = __float_as_uint(a.x), by = __float_as_uint(a.y);
+    const int32_t ex = static_cast<int32_t>(bx - 0x3F3504F3u) >> 23;  // floor(log2(a / sqrt(1/2)))
+    const int32_t ey = static_cast<int32_t>(by - 0x3F3504F3u) >> 23;
+    const float2 m = make_float2(__uint_as_float(bx - (static_cast<uint32_t>(ex) << 23)),
+                                 __uint_as_float(by - (static_cast<uint32_t>(ey) << 23)));
+    // e as a float (|e| < 2^22) through the magic constant: no conversion instruction
+    const float2 ef = add2(make_float2(__uint_as_float(0x4B400000u + static_cast<uint32_t>(ex)),
+                                       __uint_as_float(0x4B400000u + static_cast<uint32_t>(ey))), f2(-kMagic));
+    const float2 num = add2(m, f2(-1.0f));
+    const float2 den = add2(m, f2(1.0f));
+    const float2 f = mul2(num, rcp_nr2(den));
+    const float2 t = mul2(f, f);
+    float2 p = f2(-c[n - 1]);
+#pragma unroll
+    for (int i = n - 2; i >= 0; --i) p = fma2(p, t, f2(-c[i]));
+    // -ln m - e ln2_lo in one rounding (the unrounded product f P meets the
+    // small term: added to a rounded -ln m, a term below half its ulp would be
+    // lost the same way for every a with that e), then - e ln2_hi
+    const float2 nlnm = fma2(f, p, mul2(ef, f2(-kLn2Lo)));
+    return fma2(ef, f2(-kLn2Hi), nlnm);  // -(e ln2 + ln m)
+}
+
+// Upper normal tail T(y) = Phi(-y) for 0 <= y <= YMAX (float-float y:
+// y^2 / 2 enters the exponential to float-float accuracy):
+// T = e^{-y^2/2} t g(t), t = 1/(1 + KAPPA y), g fitted (the Mills ratio times
+// (1 + KAPPA y)/sqrt(2 pi)), its constant and linear terms as float pairs.
+// Beyond YMAX the tail is 0 (below 1e-38).  Also returns e^{-y^2/2}.
+__device__ __forceinline__ float ntail(float yh, float yl, float &gauss) {
+    constexpr float c[] = QMC_NTAIL_POLY;
+    constexpr int n = sizeof(c) / sizeof(c[0]);
+    const float y = fminf(yh, QMC_NTAIL_YMAX);
+    // y^2 as a float-float (Dekker product), halved exactly
+    const float sh = yh * yh;
+    const float sl = fmaf(yh, yh, -sh) + 2.0f * yh * yl;
+    gauss = yh <= QMC_NTAIL_YMAX ? exp_ff(-0.5f * sh, -0.5f * sl) : 0.0f;
+    const float t = rcp_nr(fmaf(QMC_NTAIL_KAPPA, y, 1.0f));
+    const float u = t - QMC_NTAIL_SHIFT;
+    float p = c[n - 1];
+#pragma unroll
+    for (int i = n - 2; i >= 0; --i) p = fmaf(p, u, c[i]);
+    p = fmaf(p, u, QMC_NTAIL_C1_LO) + QMC_NTAIL_C1_HI;
+    p = fmaf(p, u, QMC_NTAIL_C0_LO) + QMC_NTAIL_C0_HI;
+    return gauss * (t * p);
+}
+}  // namespace fx
+
 template <> struct Arith<float> {
     // q = (lo + 1/2) 2^-32 <= 1/2 from lo = a 2^23 + b (one rounding), the
-    // reflection sign of the upper half, and w = -ln(4q(1-q)); shared by the
-    // one- and two-element forms.  With B = 2^23 + b (b placed in the
-    // mantissa of 2^23), B 2^-32 - (2^-9 - 2^-33) = (2b + 1) 2^-33 exactly
-    // (2b + 1 < 2^24), so one FMA gives the low part and one more q.
+    // reflection sign of the upper half; shared by the one- and two-element
+    // forms.  With B = 2^23 + b (b placed in the mantissa of 2^23),
+    // B 2^-32 - (2^-9 - 2^-33) = (2b + 1) 2^-33 exactly (2b + 1 < 2^24), so one
+    // FMA gives the low part and one more q.
     static constexpr float kQLow = -(0x1p-9f - 0x1p-33f);  // exact: 24 significant bits
-    __device__ static __forceinline__ float q_of(uint32_t y, uint32_t &sign) {
-        const uint32_t m = static_cast<uint32_t>(static_cast<int32_t>(y) >> 31);  // all ones on the upper half
-        const uint32_t lo = y ^ m;
-        sign = y & 0x80000000u;
-        const float fa = small_uint_to_float(lo >> 23);
-        const float t = fmaf(__uint_as_float(0x4B000000u | (lo & 0x007FFFFFu)), 0x1p-32f, kQLow);
-        return fmaf(fa, 0x1p-9f, t);
-    }
     // -q for two draws, the floating-point steps in packed form (the
     // negated constants give exactly -q; the packed form then needs no
     // negated operands below)
@@ -102,26 +200,35 @@ template <> struct Arith<float> {
                                       __uint_as_float(0x4B000000u | (lo1 & 0x007FFFFFu)));
         return fma2(fa, f2(-0x1p-9f), fma2(fb, f2(-0x1p-32f), f2(-kQLow)));
     }
-    __device__ static __forceinline__ float tail(float w) { return horner_t(sqrtf(w) - QMC_INVN_SHIFT_T); }
-    __device__ static float inv_normal(uint32_t y) {
-        uint32_t sign;
-        const float q = q_of(y, sign);
-        const float x = fmaf(-2.0f, q, 1.0f);
-        const float q4 = 4.0f * q;
-        const float w = -0.693147181f * __log2f(fmaf(-q4, q, q4));  // -ln(4q(1-q))
-        const float p = w < QMC_INVN_W0 ? horner_c(w - QMC_INVN_SHIFT_C) : tail(w);
-        const float z = -x * p;  // <= 0 on the lower half
-        return __uint_as_float(__float_as_uint(z) ^ sign);
+    // the tail polynomial of one draw in s = sqrt(w) (0.1% of draws)
+    __device__ static __forceinline__ float tail(float w) {
+        constexpr float c[] = QMC_INVN_TAIL;
+        constexpr int n = sizeof(c) / sizeof(c[0]);
+        const float t = sqrtf(w) - QMC_INVN_SHIFT_T;
+        float p = c[n - 1];
+#pragma unroll
+        for (int i = n - 2; i >= 0; --i) p = fmaf(p, t, c[i]);
+        return fmaf(p, t, QMC_INVN_T0_LO) + QMC_INVN_T0_HI;
     }
-    // two draws at once: the central branch (99.9% of draws) in packed form;
-    // a pair with a tail draw takes the one-element branches
+    __device__ static __forceinline__ float central(float w) {
+        constexpr float c[] = QMC_INVN_CENTRAL;
+        constexpr int n = sizeof(c) / sizeof(c[0]);
+        const float t = w - QMC_INVN_SHIFT_C;
+        float p = c[n - 1];
+#pragma unroll
+        for (int i = n - 2; i >= 0; --i) p = fmaf(p, t, c[i]);
+        return fmaf(p, t, QMC_INVN_C0_LO) + QMC_INVN_C0_HI;
+    }
+    // z = Phi^{-1}(u), u = (y + 1/2) 2^-32, for two draws: w = -ln(4q(1-q))
+    // by the own logarithm, the central branch (99.9% of draws) in packed
+    // form; a pair with a tail draw takes the one-element branches
     __device__ static float2 inv_normal2(uint32_t y0, uint32_t y1) {
         uint32_t s0, s1;
         const float2 nq = neg_q_of2(y0, y1, s0, s1);
         const float2 xm = fma2(f2(-2.0f), nq, f2(-1.0f));  // 2q - 1 = -x
         const float2 q4 = mul2(f2(-4.0f), nq);
         const float2 a = fma2(q4, nq, q4);                 // 4q(1 - q), one rounding
-        const float2 w = mul2(f2(-0.693147181f), make_float2(__log2f(a.x), __log2f(a.y)));
+        const float2 w = fx::neg_ln2(a);
         float2 p;
         if (w.x < QMC_INVN_W0 && w.y < QMC_INVN_W0) {
             constexpr float c[] = QMC_INVN_CENTRAL;
@@ -132,38 +239,16 @@ template <> struct Arith<float> {
             for (int i = n - 2; i >= 0; --i) p = fma2(p, t, f2(c[i]));
             p = add2(fma2(p, t, f2(QMC_INVN_C0_LO)), f2(QMC_INVN_C0_HI));
         } else {
-            p.x = w.x < QMC_INVN_W0 ? horner_c(w.x - QMC_INVN_SHIFT_C) : tail(w.x);
-            p.y = w.y < QMC_INVN_W0 ? horner_c(w.y - QMC_INVN_SHIFT_C) : tail(w.y);
+            p.x = w.x < QMC_INVN_W0 ? central(w.x) : tail(w.x);
+            p.y = w.y < QMC_INVN_W0 ? central(w.y) : tail(w.y);
         }
         const float2 z = mul2(xm, p);
         return make_float2(__uint_as_float(__float_as_uint(z.x) ^ s0), __uint_as_float(__float_as_uint(z.y) ^ s1));
     }
-    // e^x for the path sums (|x| well below 80): 2^k 2^f with k the nearest
-    // integer to x log2 e, read from the low bits of x log2 e + 1.5 2^23
-    // (no conversion instruction), f = x log2 e - k in [-1/2, 1/2] with the
-    // residual of log2 e, 2^f from the fitted polynomial (6.1e-8), and 2^k
-    // added to the exponent field (the bias term of r cancels modulo 2^32).
-    __device__ static float ex(float x) {
-        constexpr float c[] = QMC_EXP2_POLY;
-        const float r = fmaf(x, 1.44269502f, 12582912.0f);
-        const float kf = r - 12582912.0f;
-        const float f = fmaf(x, 1.92596299e-8f, fmaf(x, 1.44269502f, -kf));
-        float p = c[6];
-#pragma unroll
-        for (int i = 5; i >= 0; --i) p = fmaf(p, f, c[i]);
-        return __uint_as_float(__float_as_uint(p) + (__float_as_uint(r) << 23));
-    }
-    __device__ static float2 ex2(float2 x) {
-        constexpr float c[] = QMC_EXP2_POLY;
-        const float2 r = fma2(x, f2(1.44269502f), f2(12582912.0f));
-        const float2 nkf = fma2(r, f2(-1.0f), f2(12582912.0f));  // -k, exact
-        const float2 f = fma2(x, f2(1.92596299e-8f), fma2(x, f2(1.44269502f), nkf));
-        float2 p = f2(c[6]);
-#pragma unroll
-        for (int i = 5; i >= 0; --i) p = fma2(p, f, f2(c[i]));
-        return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(r.x) << 23)),
-                           __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(r.y) << 23)));
-    }
+    // one draw: the pair form's second lane duplicated (the same operations)
+    __device__ static float inv_normal(uint32_t y) { return inv_normal2(y, y).x; }
+    __device__ static float ex(float x) { return fx::exp_f(x); }
+    __device__ static float2 ex2(float2 x) { return fx::exp_f2(x); }
 };
 
 // ---------------------------------------------------------------------------
@@ -201,27 +286,6 @@ template <typename T> struct PathAcc {
         }
     }
 
-    // two dates at once (node0 before node1), float: the exponent arguments
-    // and the exponentials in packed form, the sums in date order, so the
-    // result equals two calls of add
-    template <int TYPE>
-    __device__ __forceinline__ void add2(int32_t node0, int32_t node1, float W0, float W1, float omega, float sigma,
-                                         float s0, float s1) {
-        const float2 s = make_float2(s0, s1), W = make_float2(W0, W1);
-        const float2 lx = fma2(f2(sigma), W, mul2(f2(omega), s));
-        const float2 wv = fma2(f2(-sigma), s, W);
-        if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-            x += lx.x;
-            dsum += wv.x;
-            x += lx.y;
-            dsum += wv.y;
-        } else {
-            const float2 e = Arith<float>::ex2(lx);
-            take<TYPE>(node0, e.x, wv.x);
-            take<TYPE>(node1, e.y, wv.y);
-        }
-    }
-
     template <int TYPE>
     __device__ __forceinline__ void take(int32_t node, T e, T wv) {
         if constexpr (TYPE == QMCCPW_LOOKBACK_FIXED_CALL) {
@@ -246,6 +310,107 @@ template <typename T> struct PathAcc {
         } else {
             x += o.x;
             dsum += o.dsum;
+        }
+    }
+};
+
+
+// The float path works on the path of unit spacing w = W~ / sqrt(dt) (the
+// bridge, PCA and standard factors for dt = 1, no rescaling per element) and
+// takes every constant that scales it as a float pair: the exponent
+// omega s + sigma W~ = (sigma sqrt(dt)) w + (omega dt) node.  A float sigma
+// alone (0.1 is 0.1 + 1.5e-9) would act as a shifted volatility on every
+// path, and a float omega as a shifted drift.
+struct PathConst {
+    float a_hi, a_lo;  // sigma sqrt(dt)
+    float b_hi, b_lo;  // omega dt
+    __device__ explicit PathConst(const ContractDev &c)
+        : a_hi(c.ff_sig_sdt[0]), a_lo(c.ff_sig_sdt[1]), b_hi(c.ff_om_dt[0]), b_lo(c.ff_om_dt[1]) {}
+    // the exponent at a date: the small terms first, each FMA one rounding
+    __device__ __forceinline__ float lx(float node, float w) const {
+        return fmaf(w, a_hi, fmaf(node, b_hi, fmaf(w, a_lo, node * b_lo)));
+    }
+    __device__ __forceinline__ float2 lx2(float2 node, float2 w) const {
+        return fma2(w, f2(a_hi), fma2(node, f2(b_hi), fma2(w, f2(a_lo), mul2(node, f2(b_lo)))));
+    }
+};
+
+// Float accumulator of a point's path sums.  Arithmetic and binary: x =
+// sum_j e_j (e_j = S~_j / S0), yw = sum_j e_j w_j, yn = sum_j e_j node_j, so
+// that D = dX/dsigma = sqrt(dt) yw - sigma dt yn is formed once per point
+// with its constants in float-float.  Lookback: x = max_j e_j, yw and m the
+// w and the date index there (lowest on ties).  Geometric: x = sum_j w_j
+// (the date indices sum to a constant).
+template <> struct PathAcc<float> {
+    float x, yw, yn;
+    int32_t m;
+
+    __device__ void init(int type, bool has_first_date) {
+        // date t_1 (node 0, w = 0): e = 1, no vega term
+        yw = 0.0f;
+        yn = 0.0f;
+        if (type == QMCCPW_LOOKBACK_FIXED_CALL) {
+            x = has_first_date ? 1.0f : -1.0f;
+            m = has_first_date ? 0 : 0x7fffffff;
+        } else {
+            x = (type == QMCCPW_GEOMETRIC_ASIAN_CALL || !has_first_date) ? 0.0f : 1.0f;
+            m = 0;
+        }
+    }
+
+    template <int TYPE>
+    __device__ __forceinline__ void take(int32_t node, float nf, float e, float w) {
+        if constexpr (TYPE == QMCCPW_LOOKBACK_FIXED_CALL) {
+            if (e > x || (e == x && node < m)) {
+                x = e;
+                yw = w;
+                m = node;
+            }
+        } else {
+            x += e;
+            yw = fmaf(e, w, yw);
+            yn = fmaf(e, nf, yn);
+        }
+    }
+
+    // one date: node = its index after t_1, w the unit-spacing path there
+    template <int TYPE>
+    __device__ __forceinline__ void add(int32_t node, float w, const PathConst &k) {
+        if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+            x += w;
+        } else {
+            const float nf = small_uint_to_float(static_cast<uint32_t>(node));
+            take<TYPE>(node, nf, fx::exp_f(k.lx(nf, w)), w);
+        }
+    }
+
+    // two dates (node0 before node1): exponents and exponentials in packed
+    // form, the sums in date order (equal to two calls of add)
+    template <int TYPE>
+    __device__ __forceinline__ void add2(int32_t node0, int32_t node1, float w0, float w1, const PathConst &k) {
+        if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+            x += w0;
+            x += w1;
+        } else {
+            const float2 nf = make_float2(small_uint_to_float(static_cast<uint32_t>(node0)),
+                                          small_uint_to_float(static_cast<uint32_t>(node1)));
+            const float2 e = fx::exp_f2(k.lx2(nf, make_float2(w0, w1)));
+            take<TYPE>(node0, nf.x, e.x, w0);
+            take<TYPE>(node1, nf.y, e.y, w1);
+        }
+    }
+
+    __device__ void merge(int type, const PathAcc &o) {
+        if (type == QMCCPW_LOOKBACK_FIXED_CALL) {
+            if (o.x > x || (o.x == x && o.m < m)) {
+                x = o.x;
+                yw = o.yw;
+                m = o.m;
+            }
+        } else {
+            x += o.x;
+            yw += o.yw;
+            yn += o.yn;
         }
     }
 };
@@ -358,40 +523,40 @@ __device__ __forceinline__ ff ln_ff(float x) {
 // Mixed precision: the switch point psi and every combination with the
 // contract constants in float-float (about 44 significant bits, on the FP32
 // pipe: on this GPU a warp's FP64 instruction holds its sub-partition's FP64
-// unit ~64x longer than an FP32 one, and ~25 of them per point halved the
-// throughput of the whole kernel); the normal tail and density in float.
-// The price of a call is the difference of two terms of size ~K: a float
-// product there would bias every point by ~2^-24 K, which no averaging
-// removes.  Far out (|psi| beyond ~13) the float density and the small tail
-// underflow to zero while the exact terms they scale are below 1e-35; the
-// large tail is 1 there, so every value keeps its limit and no point leaves the FP32
-// pipe (with a = sigma sqrt(t_1) small, such points are common, and one of
-// them in a warp would send the whole warp down a double-precision branch).
+// unit ~64x longer than an FP32 one).  The normal tails come from the own
+// T(y) (fx::ntail): relative accuracy for every y, so Phi-bar near 1 is kept
+// as the float-float 1 - T (a float Phi-bar there rounds to 1 and drops a
+// one-signed tail), and e^{-psi^2/2} from the float-float psi^2.  The price of
+// a call is a difference of two terms of size ~K; both are formed in
+// float-float, and 1/sqrt(2 pi) sits in the float-float constants.
 __device__ void values_mixed(const ContractDev &c, float xhat, float dhat, ff v[4]) {
     const ff psi = ff_mul_ff(ff_add(ff_of(c.ff_psi0), ff_neg(ln_ff(xhat))), ff_of(c.ff_inv_a));
-    const float p = psi.hi;
-    const float pdf = 0.398942280f * expf(-0.5f * p * p);
+    float g2;  // e^{-psi^2/2}
+    const bool up2 = psi.hi >= 0.0f;
+    const float T2 = fx::ntail(up2 ? psi.hi : -psi.hi, up2 ? psi.lo : -psi.lo, g2);
+    const ff sf2 = up2 ? ff{T2, 0.0f} : ff_two_sum(1.0f, -T2);  // Phi-bar(psi)
     if (c.type == QMCCPW_BINARY_ASIAN) {
-        const float sf = 0.5f * erfcf(p * 0.707106781f);
-        v[0] = ff_mul(ff_of(c.ff_disc), sf);
-        v[1] = ff_mul(ff_of(c.ff_k_bin_delta), pdf);
+        v[0] = ff_mul_ff(ff_of(c.ff_disc), sf2);
+        v[1] = ff_mul(ff_of(c.ff_kd_bin), g2);
         // D/(a X) + psi/sigma - sqrt(t1), then times e^{-rT} phi(psi)
-        ff br = ff_mul(ff_of(c.ff_inv_a), dhat * rcp_f32(xhat));
+        ff br = ff_mul(ff_of(c.ff_inv_a), dhat * fx::rcp_nr(xhat));
         br = ff_add(br, ff_mul_ff(psi, ff_of(c.ff_inv_sigma)));
         br = ff_add(br, ff_neg(ff_of(c.ff_sqrt_t1)));
-        v[2] = ff_mul_ff(ff_mul(ff_of(c.ff_disc), pdf), br);
+        v[2] = ff_mul_ff(ff_mul(ff_of(c.ff_kphi), g2), br);
         // e^{-rT} phi(psi) / (S0^2 a) (psi/a - 1)
         const ff g = ff_add(ff_mul_ff(psi, ff_of(c.ff_inv_a)), ff{-1.0f, 0.0f});
-        v[3] = ff_mul_ff(ff_mul(ff_of(c.ff_k_bin_gamma), pdf), g);
+        v[3] = ff_mul_ff(ff_mul(ff_of(c.ff_kg_bin), g2), g);
     } else {
-        const float a = c.f_a;
-        const float sfs = 0.5f * erfcf((p - a) * 0.707106781f);
-        const float sf = 0.5f * erfcf(p * 0.707106781f);
+        const ff psi1 = ff_add(psi, ff_neg(ff_of(c.ff_a)));  // psi - a
+        const bool up1 = psi1.hi >= 0.0f;
+        float g1;
+        const float T1 = fx::ntail(up1 ? psi1.hi : -psi1.hi, up1 ? psi1.lo : -psi1.lo, g1);
+        const ff sf1 = up1 ? ff{T1, 0.0f} : ff_two_sum(1.0f, -T1);  // Phi-bar(psi - a)
         const ff cx = ff_mul(ff_of(c.ff_disc1_S0), xhat);
-        v[0] = ff_add(ff_mul(cx, sfs), ff_neg(ff_mul(ff_of(c.ff_disc_K), sf)));
-        v[1] = ff_mul(ff_mul(ff_of(c.ff_disc1), xhat), sfs);
-        v[2] = ff_add(ff_mul(ff_mul(ff_of(c.ff_disc1_S0), sfs), dhat), ff_mul(ff_of(c.ff_disc_K_sqrt_t1), pdf));
-        v[3] = ff_mul(ff_of(c.ff_k_call_gamma), pdf);
+        v[0] = ff_add(ff_mul_ff(cx, sf1), ff_neg(ff_mul_ff(ff_of(c.ff_disc_K), sf2)));
+        v[1] = ff_mul_ff(ff_mul(ff_of(c.ff_disc1), xhat), sf1);
+        v[2] = ff_add(ff_mul(ff_mul_ff(ff_of(c.ff_disc1_S0), sf1), dhat), ff_mul(ff_of(c.ff_kv_call), g2));
+        v[3] = ff_mul(ff_of(c.ff_kg_call), g2);
     }
 }
 
@@ -815,7 +980,7 @@ __device__ __forceinline__ void next_work(const LaunchParams &p, WorkItem &w, bo
             const uint64_t tiles = static_cast<uint64_t>(p.contracts[ci].tiles);
             const uint64_t r = local / tiles;
             w.ci = ci;
-            w.rep = static_cast<uint32_t>(r) + p.rep_offset;
+            w.rep = static_cast<uint32_t>(r) + static_cast<uint32_t>(p.contracts[ci].rep_first) + p.rep_offset;
             w.tile = local - r * tiles;
         }
     }
@@ -825,26 +990,28 @@ __device__ __forceinline__ void next_work(const LaunchParams &p, WorkItem &w, bo
 // Partial accumulators of a point live in several threads; they are staged
 // in shared memory as slot-major arrays and merged by one thread per point in
 // slot order (a fixed order, so the result does not depend on scheduling).
-template <typename T>
-__device__ __forceinline__ void stage_partial(void *base, int P, int slot, int point, const PathAcc<T> &a) {
-    T *rx = reinterpret_cast<T *>(base);
-    T *rd = rx + kThreads * 4;
+// Staging needs kStageBytes per (slot, point) entry, at most 4 * kThreads
+// entries.
+constexpr int kStageBytes = 20;
+
+__device__ __forceinline__ void stage_partial(void *base, int P, int slot, int point, const PathAcc<double> &a) {
+    double *rx = reinterpret_cast<double *>(base);
+    double *rd = rx + kThreads * 4;
     int32_t *rm = reinterpret_cast<int32_t *>(rd + kThreads * 4);
     rx[slot * P + point] = a.x;
     rd[slot * P + point] = a.dsum;
     rm[slot * P + point] = a.m;
 }
 
-template <typename T>
-__device__ __forceinline__ void merge_partials(const void *base, int P, int slots, int point, int type, PathAcc<T> &a) {
-    const T *rx = reinterpret_cast<const T *>(base);
-    const T *rd = rx + kThreads * 4;
+__device__ __forceinline__ void merge_partials(const void *base, int P, int slots, int point, int type, PathAcc<double> &a) {
+    const double *rx = reinterpret_cast<const double *>(base);
+    const double *rd = rx + kThreads * 4;
     const int32_t *rm = reinterpret_cast<const int32_t *>(rd + kThreads * 4);
     a.x = rx[point];
     a.dsum = rd[point];
     a.m = rm[point];
     for (int s = 1; s < slots; ++s) {
-        PathAcc<T> o;
+        PathAcc<double> o;
         o.x = rx[s * P + point];
         o.dsum = rd[s * P + point];
         o.m = rm[s * P + point];
@@ -852,35 +1019,81 @@ __device__ __forceinline__ void merge_partials(const void *base, int P, int slot
     }
 }
 
-// X^ = X/S0 and D^ = D/S0 of a point from its merged accumulator.
-// omega, sigma and the date spacing in the kernel's type (float: the
-// contract's float copies)
-template <typename T>
-__device__ __forceinline__ void market_of(const ContractDev &c, T &omega, T &sigma, T &dt) {
-    if constexpr (sizeof(T) == 4) {
-        omega = c.f_omega;
-        sigma = c.f_sigma;
-        dt = c.f_dt;
-    } else {
-        omega = c.omega;
-        sigma = c.sigma;
-        dt = c.dt;
+// (float: `cap` entries per array, at least slots x P)
+__device__ __forceinline__ void stage_partial(void *base, int P, int slot, int point, const PathAcc<float> &a,
+                                              int cap = kThreads * 4) {
+    float *rx = reinterpret_cast<float *>(base);
+    float *rw = rx + cap;
+    float *rn = rw + cap;
+    int32_t *rm = reinterpret_cast<int32_t *>(rn + cap);
+    rx[slot * P + point] = a.x;
+    rw[slot * P + point] = a.yw;
+    rn[slot * P + point] = a.yn;
+    rm[slot * P + point] = a.m;
+}
+
+__device__ __forceinline__ void merge_partials(const void *base, int P, int slots, int point, int type, PathAcc<float> &a,
+                                               int cap = kThreads * 4) {
+    const float *rx = reinterpret_cast<const float *>(base);
+    const float *rw = rx + cap;
+    const float *rn = rw + cap;
+    const int32_t *rm = reinterpret_cast<const int32_t *>(rn + cap);
+    a.x = rx[point];
+    a.yw = rw[point];
+    a.yn = rn[point];
+    a.m = rm[point];
+    for (int s = 1; s < slots; ++s) {
+        PathAcc<float> o;
+        o.x = rx[s * P + point];
+        o.yw = rw[s * P + point];
+        o.yn = rn[s * P + point];
+        o.m = rm[s * P + point];
+        a.merge(type, o);
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void finish_functional(const ContractDev &c, const PathAcc<T> &acc, T &xhat, T &dhat) {
+// X^ = X/S0 and D^ = D/S0 of a point from its merged accumulator (double:
+// the accumulator holds D itself; float: see PathAcc<float>, with the
+// constants 1/d, sqrt(dt)/d, -sigma dt/d as float pairs)
+__device__ __forceinline__ void finish_functional(const ContractDev &c, const PathAcc<double> &acc, double &xhat,
+                                                  double &dhat) {
     if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
         xhat = acc.x;
         dhat = acc.dsum;
     } else if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-        const T inv_d = sizeof(T) == 4 ? T(c.f_inv_d) : T(c.inv_d);
-        xhat = Arith<T>::ex(acc.x * inv_d);
-        dhat = xhat * acc.dsum * inv_d;
+        xhat = exp(acc.x * c.inv_d);
+        dhat = xhat * acc.dsum * c.inv_d;
     } else {
-        const T inv_d = sizeof(T) == 4 ? T(c.f_inv_d) : T(c.inv_d);
-        xhat = acc.x * inv_d;
-        dhat = acc.dsum * inv_d;
+        xhat = acc.x * c.inv_d;
+        dhat = acc.dsum * c.inv_d;
+    }
+}
+
+// omega, sigma and the date spacing of the double path
+__device__ __forceinline__ void market_of(const ContractDev &c, double &omega, double &sigma, double &dt) {
+    omega = c.omega;
+    sigma = c.sigma;
+    dt = c.dt;
+}
+
+// a w + b n with a, b float pairs: the small terms first
+__device__ __forceinline__ float lin2(const float (&a)[2], float w, const float (&b)[2], float n) {
+    return fmaf(w, a[0], fmaf(n, b[0], fmaf(w, a[1], n * b[1])));
+}
+
+__device__ __forceinline__ void finish_functional(const ContractDev &c, const PathAcc<float> &acc, float &xhat,
+                                                  float &dhat) {
+    if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
+        // D^ = e* (sqrt(dt) w* - sigma dt node*)
+        xhat = acc.x;
+        dhat = acc.x * lin2(c.ff_sqrt_t1, acc.yw, c.ff_nsig_dt, small_uint_to_float(static_cast<uint32_t>(acc.m)));
+    } else if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
+        // mean log = (sigma sqrt(dt) sum w + omega dt sum node)/d, the second a constant
+        xhat = fx::exp_f(fmaf(acc.x, c.ff_sig_sdt_d[0], fmaf(acc.x, c.ff_sig_sdt_d[1], c.ff_geo_l0[1])) + c.ff_geo_l0[0]);
+        dhat = xhat * (fmaf(acc.x, c.ff_sdt_d[0], fmaf(acc.x, c.ff_sdt_d[1], c.ff_geo_d0[1])) + c.ff_geo_d0[0]);
+    } else {
+        xhat = fmaf(acc.x, c.ff_inv_d[0], acc.x * c.ff_inv_d[1]);
+        dhat = lin2(c.ff_sdt_d, acc.yw, c.ff_nsigdt_d, acc.yn);
     }
 }
 

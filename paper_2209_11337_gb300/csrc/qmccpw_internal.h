@@ -62,6 +62,7 @@ struct ContractDev {
     int32_t row_stride;                  // shared-memory row (point) stride in elements, odd
     int32_t z_by_dim;                    // 1: z of dimension j at column j+1+slot_shift; 0: at the date node j+slot_shift drives
     int32_t slot_shift;                  // 1 for the leading-coordinate constructions (dimension j drives node j+1), else 0
+    int32_t rep_first;                   // randomisation index of the contract's replicate 0
     uint64_t N;
     uint64_t item_base;                  // first work item of this contract
     uint64_t rep_base;                   // first replicate slot of this contract (in per-replicate arrays)
@@ -94,13 +95,25 @@ struct ContractDev {
     double inv_d;                        // 1/d
     double ln_lead_c0;                   // ln(S0/d): leading-coordinate constructions
     double ln_K;
-    // the same constants as float hi + lo pairs (float-float arithmetic of the mixed path)
-    float ff_disc1_S0[2], ff_disc_K[2], ff_disc1[2], ff_disc_K_sqrt_t1[2], ff_k_call_gamma[2];
-    float ff_disc[2], ff_k_bin_delta[2], ff_k_bin_gamma[2];
-    float ff_sqrt_t1[2];                 // sqrt(dt) as hi + lo: the scale of every path increment
-    float ff_psi0[2], ff_inv_a[2], ff_inv_sigma[2];
-    // float copies of market constants (the float kernels read these: no conversion on the device)
-    float f_omega, f_sigma, f_dt, f_a, f_inv_d;
+    // constants of the float path as float hi + lo pairs (split_ff)
+    // path: the exponent (sigma sqrt(dt)) w + (omega dt) node of the unit-spacing path w
+    float ff_sig_sdt[2], ff_om_dt[2];
+    float ff_sqrt_t1[2];                 // sqrt(dt)
+    float ff_nsig_dt[2];                 // -sigma dt
+    float ff_inv_d[2], ff_sdt_d[2];      // 1/d, sqrt(dt)/d
+    float ff_nsigdt_d[2];                // -sigma dt / d
+    float ff_sig_sdt_d[2];               // sigma sqrt(dt) / d (geometric mean)
+    float ff_geo_l0[2], ff_geo_d0[2];    // omega dt S1 / d and -sigma dt S1 / d, S1 = n(n+1)/2
+    // conditional step (1/sqrt(2 pi) folded into the density's constants)
+    float ff_psi0[2], ff_inv_a[2], ff_inv_sigma[2], ff_a[2];
+    float ff_disc1_S0[2], ff_disc_K[2], ff_disc1[2], ff_disc[2];
+    float ff_kv_call[2];                 // disc K sqrt(t_1) / sqrt(2 pi)
+    float ff_kg_call[2];                 // disc K / (S0^2 a sqrt(2 pi))
+    float ff_kd_bin[2];                  // disc / (S0 a sqrt(2 pi))
+    float ff_kg_bin[2];                  // disc / (S0^2 a sqrt(2 pi))
+    float ff_kphi[2];                    // disc / sqrt(2 pi)
+    // float copies of market constants (the leading-coordinate float path)
+    float f_omega, f_sigma, f_dt;
 };
 
 // hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)
@@ -135,6 +148,10 @@ int launch_fused(const LaunchParams &p, int precision, int construction, size_t 
 int launch_reduce(const ContractDev *contracts, int32_t count, const double *tile_sums,
                   double *per_rep, double *stats, uint64_t total_reps, const uint64_t *rep_owner,
                   void *stream);
+int launch_gathered_stats(const double *per_rep, const int64_t *first_row, const int32_t *R, int count,
+                          double *stats, void *stream);
+int launch_scatter_replicates(const double *per_rep, const int64_t *dst_row, uint64_t slots, double *dst,
+                              void *stream);
 int launch_scramble(uint64_t seed, const uint32_t *v, int ndims, int jstride, int reps,
                     uint32_t *table, uint32_t *shift, void *stream);
 int launch_sobol_dump(const uint32_t *table, const uint32_t *shift, int jstride, int ndims,
@@ -162,5 +179,8 @@ int pca_tc_prepare(int kind, size_t smem_bytes);     // raise the dynamic shared
 int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks);
 int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, void *stream);
 void pca_tc_operand(int kind, int n, const std::vector<double> &A_unit, std::vector<unsigned char> &out);
+
+// Pipe micro-benchmarks (peaks.cu): 0, a cudaError_t, or -QMCCPW_ERR_TIMEOUT.
+int measure_pipe_peaks(int device, qmccpw_pipe_peaks *out);
 
 }  // namespace qmccpw

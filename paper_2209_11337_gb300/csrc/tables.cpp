@@ -193,23 +193,35 @@ void contract_constants(ContractDev &c) {
     c.k_call_gamma = c.disc * c.K / (c.S0 * c.S0 * c.a);
     c.inv_sigma = 1.0 / c.sigma;
     c.inv_d = 1.0 / c.d;
-    split_ff(c.disc1_S0, c.ff_disc1_S0);
-    split_ff(c.disc_K, c.ff_disc_K);
-    split_ff(c.disc1, c.ff_disc1);
-    split_ff(c.disc_K * c.sqrt_t1, c.ff_disc_K_sqrt_t1);
-    split_ff(c.k_call_gamma, c.ff_k_call_gamma);
-    split_ff(c.disc, c.ff_disc);
-    split_ff(c.k_bin_delta, c.ff_k_bin_delta);
-    split_ff(c.k_bin_gamma, c.ff_k_bin_gamma);
+    const double inv_sqrt_2pi = 0.398942280401432677939946059934;  // 1/sqrt(2 pi)
+    const double n = c.d - 1;
+    const double s1 = 0.5 * n * (n + 1.0);  // sum of the date indices after t_1
+    split_ff(c.sigma * c.sqrt_t1, c.ff_sig_sdt);
+    split_ff(c.omega * c.dt, c.ff_om_dt);
     split_ff(c.sqrt_t1, c.ff_sqrt_t1);
-    c.f_omega = static_cast<float>(c.omega);
-    c.f_sigma = static_cast<float>(c.sigma);
-    c.f_dt = static_cast<float>(c.dt);
-    c.f_a = static_cast<float>(c.a);
-    c.f_inv_d = static_cast<float>(c.inv_d);
+    split_ff(-c.sigma * c.dt, c.ff_nsig_dt);
+    split_ff(c.inv_d, c.ff_inv_d);
+    split_ff(c.sqrt_t1 * c.inv_d, c.ff_sdt_d);
+    split_ff(-c.sigma * c.dt * c.inv_d, c.ff_nsigdt_d);
+    split_ff(c.sigma * c.sqrt_t1 * c.inv_d, c.ff_sig_sdt_d);
+    split_ff(c.omega * c.dt * s1 * c.inv_d, c.ff_geo_l0);
+    split_ff(-c.sigma * c.dt * s1 * c.inv_d, c.ff_geo_d0);
     split_ff(c.psi0, c.ff_psi0);
     split_ff(c.inv_a, c.ff_inv_a);
     split_ff(c.inv_sigma, c.ff_inv_sigma);
+    split_ff(c.a, c.ff_a);
+    split_ff(c.disc1_S0, c.ff_disc1_S0);
+    split_ff(c.disc_K, c.ff_disc_K);
+    split_ff(c.disc1, c.ff_disc1);
+    split_ff(c.disc, c.ff_disc);
+    split_ff(c.disc_K * c.sqrt_t1 * inv_sqrt_2pi, c.ff_kv_call);
+    split_ff(c.k_call_gamma * inv_sqrt_2pi, c.ff_kg_call);
+    split_ff(c.k_bin_delta * inv_sqrt_2pi, c.ff_kd_bin);
+    split_ff(c.k_bin_gamma * inv_sqrt_2pi, c.ff_kg_bin);
+    split_ff(c.disc * inv_sqrt_2pi, c.ff_kphi);
+    c.f_omega = static_cast<float>(c.omega);
+    c.f_sigma = static_cast<float>(c.sigma);
+    c.f_dt = static_cast<float>(c.dt);
 }
 
 }  // namespace qmccpw

@@ -60,7 +60,7 @@ EXPORTS = (
     "qmccpw_point_values", "qmccpw_greeks_noalloc", "qmccpw_server_start", "qmccpw_submit", "qmccpw_poll",
     "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_autotune", "qmccpw_tuning_get",
     "qmccpw_tuning_set", "qmccpw_free", "qmccpw_last_error",
-    "qmccpw_version",
+    "qmccpw_version", "qmccpw_measure_pipe_peaks", "qmccpw_batch_scatter_replicates", "qmccpw_replicate_stats",
 )
 
 
@@ -92,7 +92,8 @@ class qmccpw_result(ctypes.Structure):
 
 class qmccpw_contract(ctypes.Structure):
     _fields_ = [("option", qmccpw_option), ("market", qmccpw_market), ("N", ctypes.c_uint64),
-                ("R", ctypes.c_int32), ("construction", ctypes.c_int32)]
+                ("R", ctypes.c_int32), ("construction", ctypes.c_int32), ("first_replicate", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class qmccpw_server_desc(ctypes.Structure):
@@ -104,6 +105,12 @@ class qmccpw_server_desc(ctypes.Structure):
 class qmccpw_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("point_dates", ctypes.c_uint64), ("pending", ctypes.c_uint64)]
+
+
+class qmccpw_pipe_peaks(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_double) for name in (
+        "fp32_fma_tflops", "fp32_fma2_tflops", "fp64_fma_tflops", "sfu_ex2_gops", "sfu_lg2_gops",
+        "sfu_rcp_gops", "tc_bf16_tflops", "tc_tf32_tflops")]
 
 
 _lib = None
@@ -135,6 +142,9 @@ def library() -> ctypes.CDLL:
             L.qmccpw_selftest_bounded_wait.argtypes = [i32, i32, P(i32)]
             L.qmccpw_batch_segment_timing.argtypes = [vp, P(ctypes.c_float), P(i32)]
             L.qmccpw_batch_free.argtypes = [vp]
+            L.qmccpw_measure_pipe_peaks.argtypes = [i32, P(qmccpw_pipe_peaks)]
+            L.qmccpw_batch_scatter_replicates.argtypes = [vp, vp, P(ctypes.c_int64)]
+            L.qmccpw_replicate_stats.argtypes = [vp, vp, vp, i32, vp, vp]
             L.qmccpw_sobol_points.argtypes = [vp, u32, i32, u64, u64, P(u32)]
             L.qmccpw_point_values.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), i32, i32, u32, u64, u64,
                                               P(ctypes.c_double)]
@@ -201,7 +211,7 @@ def contract_array(contracts: Sequence) -> ctypes.Array:
     arr = (qmccpw_contract * len(contracts))()
     for i, c in enumerate(contracts):
         arr[i] = qmccpw_contract(qmccpw_option(c.type, c.d, c.K, c.T), qmccpw_market(c.S0, c.r, c.sigma),
-                                 c.N, c.R, c.construction)
+                                 c.N, c.R, c.construction, getattr(c, "first_replicate", 0), 0)
     return arr
 
 
@@ -245,6 +255,10 @@ class Batch:
         ms, n = (ctypes.c_float * 6)(), ctypes.c_int32()
         _check(library().qmccpw_batch_segment_timing(self.handle, ms, ctypes.byref(n)))
         return list(ms), n.value
+
+    def scatter_replicates(self, dst_ptr: Optional[int], first_row: Sequence[int]) -> None:
+        """qmccpw_batch_scatter_replicates: rows of a device array receive the replicate estimates."""
+        qmccpw_batch_scatter_replicates(self.handle, dst_ptr, first_row)
 
     def use_graph(self, enable: bool = True) -> None:
         """Replay the launch sequence as one CUDA graph (qmccpw_batch_use_graph)."""
@@ -384,3 +398,23 @@ def qmccpw_last_error() -> str:
 
 def qmccpw_version() -> str:
     return library().qmccpw_version().decode()
+
+
+def qmccpw_batch_scatter_replicates(batch, dst_ptr: Optional[int], first_row: Sequence[int]) -> None:
+    """After each later launch, copy the batch's replicate estimates to rows of the device array at
+    ``dst_ptr`` (e.g. ``tensor.data_ptr()``); ``None`` turns the copy off."""
+    rows = (ctypes.c_int64 * max(1, len(first_row)))(*first_row)
+    _check(library().qmccpw_batch_scatter_replicates(batch, dst_ptr, rows if dst_ptr else None))
+
+
+def qmccpw_replicate_stats(per_replicate_ptr: int, first_row_ptr: int, R_ptr: int, count: int, stats_ptr: int,
+                           stream=None) -> None:
+    """Mean and SE over replicates of device-resident replicate estimates (all arguments device pointers)."""
+    _check(library().qmccpw_replicate_stats(per_replicate_ptr, first_row_ptr, R_ptr, count, stats_ptr, stream))
+
+
+def qmccpw_measure_pipe_peaks(device: int = 0) -> dict:
+    """The pipe micro-benchmarks of ``device`` as a dict of the struct's fields."""
+    out = qmccpw_pipe_peaks()
+    _check(library().qmccpw_measure_pipe_peaks(device, ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in qmccpw_pipe_peaks._fields_}

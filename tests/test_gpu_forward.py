@@ -2,7 +2,7 @@
 
 Bars as in test_gpu_parity: FP64 points and estimates within 1e-12 x
 max(|oracle|, mean |per-point value|) (points times max(1, n/64)); MIXED
-against FP64 within 0.1 SE + 2^-21 mean |per-point value|.  Tile sizes are
+against FP64 within 0.1 SE per Greek.  Tile sizes are
 chosen so that one thread walks a whole path (d = 16) and so that several
 threads split a path's dates into blocks (d = 200, 365).
 """
@@ -63,7 +63,7 @@ def test_forward_mixed_against_fp64(q, plan):
     m32 = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_MIXED)
     m64 = q.qmccpw_greeks_batch(plan, cs, q.QMCCPW_FP64)
     for c, (a, _, _), (b, s, _) in zip(cs, m32, m64):
-        assert np.all(np.abs(a - b) <= 0.1 * s + 2.0 ** -21 * scale_of(c)), (c.label(), (np.abs(a - b) / s).tolist())
+        assert np.all(np.abs(a - b) <= 0.1 * s), (c.label(), (np.abs(a - b) / s).tolist())
 
 
 def test_forward_in_a_mixed_batch_equals_alone(q, plan):

@@ -198,32 +198,21 @@ def test_full_size_sampled_replicates_and_points(q, plan, c):
 
 
 def test_mixed_error_against_fp64_in_standard_errors(q, plan):
-    """MIXED vs FP64 on the d=64, N=2^20, R=32 grid, per contract and Greek.
-
-    Target: |mixed - fp64| <= 0.1 SE(fp64).  A float path also carries a
-    systematic error of about one float ulp of each point's value, so Greeks
-    whose RQMC standard error is itself near 1e-8 relative (PCA at
-    sigma = 0.1) cannot always reach 0.1 SE in float arithmetic.  The bar
-    checked is 0.1 SE + 2^-21 * mean |per-point value| (four float ulps of the
-    terms that are averaged) for every pair, every pair within 0.6 SE, and at
-    least 80% of the pairs within the plain 0.1 SE target (measured: worst
-    0.44 SE, 89%; every bridge pair meets it).  With the earlier
-    inverse-normal coefficients, whose roundings added up to a smooth error
-    the same for every point, the worst pair was 0.78 SE and 78% met it.
-    """
+    """MIXED vs FP64 on the d=64, N=2^20, R=32 grid, per contract and Greek:
+    |mixed - fp64| <= 0.1 SE(fp64) for every pair.  The PCA contracts at
+    sigma = 0.1 have standard errors near 1e-8 relative, and a path-level
+    bias b moves an at-the-money call price by about S0 delta b / price ~
+    25 b, so every systematic error of the float path must stay near 1e-10:
+    own polynomials for e^x, ln, Phi^{-1} and the normal tail (no hardware
+    approximation with a nonzero mean error), float-pair constants wherever a
+    float rounding of sigma, omega dt, 1/d or 1/sqrt(2 pi) would act on every
+    point the same way."""
     grid = W.grid_d64()
     r64 = q.qmccpw_greeks_batch(plan, grid, q.QMCCPW_FP64)
     r32 = q.qmccpw_greeks_batch(plan, grid, q.QMCCPW_MIXED)
-    bad, met, total, worst = [], 0, 0, 0.0
+    bad = []
     for c, (m64, se64, _), (m32, _, _) in zip(grid, r64, r32):
-        scale = greek_scale(c, c.construction, count=1024)
         err = np.abs(m32 - m64)
-        worst = max(worst, float(np.max(err / se64)))
-        met += int(np.sum(err <= 0.1 * se64))
-        total += 4
-        over = err > 0.1 * se64 + 2.0 ** -21 * scale
-        if over.any():
-            bad.append((c.label(), (err / se64).tolist()))
-    assert not bad, bad[:5]
-    assert worst <= 0.6, worst
-    assert met / total >= 0.8, met / total
+        if np.any(err > 0.1 * se64):
+            bad.append((c.label(), np.round(err / se64, 3).tolist()))
+    assert not bad, bad

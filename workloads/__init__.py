@@ -36,10 +36,11 @@ class Contract:
     N: int
     R: int
     construction: int = BB
+    first_replicate: int = 0  # replicates first_replicate .. first_replicate + R - 1 of the randomisation
 
     def label(self) -> str:
         return (f"{TYPE_NAMES[self.type]}-{CONS_NAMES[self.construction]}-d{self.d}-K{self.K:g}"
-                f"-s{self.sigma:g}-N{self.N}-R{self.R}")
+                f"-s{self.sigma:g}-N{self.N}-R{self.R}" + (f"@{self.first_replicate}" if self.first_replicate else ""))
 
 
 def splitmix64(state: int):
