@@ -10,8 +10,11 @@ FP64 form of the same batch is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank runs the full batch on its own GPU (independent
-contracts, no data-path collective: weak scaling); rank 0 prints one JSON line.
+Under torchrun the batch is split over the ranks (strong scaling: the same
+job on more GPUs): every contract's replicates in ranges, one per rank, each
+rank computing its ranges with the job's seed; each step ends with one sum
+over ranks (NCCL) of the replicate estimates and the statistics on the GPU,
+so the result equals one GPU's.  Rank 0 prints one JSON line.
 `--impl reference` times the CPU oracle (the test oracle, on the host cores)
 on bounded samples of the same workload.
 """
@@ -31,16 +34,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import workloads as W  # noqa: E402
+from paper_2209_11337_gb300 import shard  # noqa: E402
 
 METRIC = "QMC-CPW Greeks throughput (N·d points/s) mixed vs FP64; serving p50/p99 latency"
 UNIT = "point-dates/s"
 WORKLOAD = ("d=64 grid: {arith,binary,lookback} x {bridge,pca} x K{90,100,110} x sigma{0.1,0.3}, "
             "S0=100 r=0.05 T=1, N=2^20 points x R=32 replicates per contract (36 contracts)")
-# algorithmic FP32 flops per point-date of the mixed fused kernel (FMA = 2): uniform 2,
-# inverse normal 15, bridge 5 (PCA: 2(d-1)), exponent argument 3, exp 2, path sums 5
-FLOPS_BRIDGE = 32
-SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# The roofline of the float path (one element = one point-date): about 24
+# FP32 operations (an FMA is one) and 2 SFU operations per element for the
+# algorithmic minimum -- the uniform, an inverse normal of ~12 FMAs and a
+# division, 3 FMAs of the bridge, an exponential, ~4 for the running sums --
+# so the ceiling is min(FP32 op rate / 24, SFU rate / 2) point-dates/s; the
+# tensor-core PCA adds 2n flops per split product per element on the tensor
+# pipe (bf16: Ahat in three parts, five products; tf32: three).  Rates are the
+# library's micro-benchmarks on this GPU (paper_2209_11337_gb300/pipe_peaks_gb300.json).
+OPS_PER_ELEMENT, SFU_PER_ELEMENT = 24, 2
+TC_PRODUCTS = {"tc-bf16": 5, "tc-tf32": 3}
 
 
 def dist_info():
@@ -84,32 +96,19 @@ class Ranks:
             self.dist.destroy_process_group()
 
 
-def rank_seed(rank: int) -> int:
-    """Scramble seed of a rank: every rank runs the whole batch on its own
-    randomisation (weak scaling)."""
-    return W.SCRAMBLE_SEED + rank
-
-
-def job_value(point_dates_per_rank: int, world: int, max_ms: float) -> float:
-    """Whole-job throughput: the point-dates all ranks processed over the
-    slowest rank's time."""
-    return world * point_dates_per_rank / (max_ms / 1e3)
+def job_value(job_point_dates: int, max_ms: float) -> float:
+    """Whole-job throughput: the job's distinct point-dates (each replicate
+    counted once, whichever rank ran it) over the slowest rank's step time."""
+    return job_point_dates / (max_ms / 1e3)
 
 
 def elements(contracts) -> int:
     return sum(c.N * c.R * c.d for c in contracts)
 
 
-def algorithmic_flops(contracts) -> float:
-    total = 0.0
-    for c in contracts:
-        per_elem = FLOPS_BRIDGE if c.construction == W.BB else FLOPS_BRIDGE - 5 + 2 * (c.d - 1)
-        total += float(c.N) * c.R * c.d * per_elem
-    return total
-
-
-def fp32_peak_tflops() -> float:
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+def pipe_peaks() -> dict:
+    from paper_2209_11337_gb300 import peaks
+    return peaks.load()
 
 
 def measured_peaks() -> dict:
@@ -129,74 +128,73 @@ SEGMENT_KERNELS = {
     "tc-tf32": ("fused_kernel<float, bridge>", "fused_kernel<float, standard>", "pca_tcs_kernel<tf32>",
                 "pca_tc_kernel<tf32>"),
 }
-FLOPS_TC_FP32 = FLOPS_BRIDGE - 5  # FP32 work of the tensor-core kernels: the product runs on the tensor pipe
-FLOPS_STD = FLOPS_BRIDGE - 2      # standard construction: a running sum and the sqrt(dt) scale instead of the bridge
-# DRAM read + write bytes of one full-size launch of the grid's kernels, from
-# one ncu capture (profiles/dram_bytes_grid_d64_tcbf16.md); None for a kernel
-# that changed since
-GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 2924288 + 98998784, "fused_kernel<float, bridge>": 886528 + 25334784}
-
-
-# launch segments with an algorithmic flop model: bridge, standard, streamed
-# and resident PCA (the leading-coordinate segments that follow have none)
+# DRAM read + write bytes of one full-size launch of the grid's kernels from
+# one ncu capture (profiles/); None for a kernel changed since
+GRID_TRAFFIC = {}
+# launch segments of a batch: bridge, standard, streamed and resident PCA (the
+# leading-coordinate segments that follow are not in the grid)
 ROOFLINE_SEGMENTS = 4
 
 
-def segment_flops(grid_precision: str, contracts, seg: int):
-    """The contracts of a launch segment and their algorithmic FP32 flops."""
-    if seg >= ROOFLINE_SEGMENTS:
-        return [], False, 0.0
+def segment_contracts(contracts, seg: int):
     if seg == 0:
-        mine = [c for c in contracts if c.construction == W.BB]
-    elif seg == 1:
-        mine = [c for c in contracts if c.construction == W.STD]
-    else:
-        mine = [c for c in contracts if c.construction == W.PCA and ((c.d - 1 > 64) == (seg == 2))]
-    tc = grid_precision != "mixed" and seg >= 2
-    flops = 0.0
-    for c in mine:
-        per = FLOPS_BRIDGE if seg == 0 else FLOPS_STD if seg == 1 else (
-            FLOPS_TC_FP32 if tc else FLOPS_BRIDGE - 5 + 2 * (c.d - 1))
-        flops += float(c.N) * c.R * c.d * per
-    return mine, tc, flops
+        return [c for c in contracts if c.construction == W.BB]
+    if seg == 1:
+        return [c for c in contracts if c.construction == W.STD]
+    if seg < ROOFLINE_SEGMENTS:
+        return [c for c in contracts if c.construction == W.PCA and ((c.d - 1 > 64) == (seg == 2))]
+    return []
 
 
-def roofline(grid_precision: str, contracts, segment_ms) -> dict:
-    """Roofline of the launch segment that takes the most time (its kernel
-    is the dominant one of the step): algorithmic FP32 flops of its
-    contracts / its event-timed duration against the FP32 pipe peak; for a
-    tensor-core segment also the useful PCA product (2 n flops per
-    point-date) against the measured dense bf16 peak.  `segments` gives the
-    same FP32 figures for every segment of the step that did work."""
-    peak = fp32_peak_tflops()
-    segment_ms = list(segment_ms)[:ROOFLINE_SEGMENTS]
-    segments = []
-    for k, ms_k in enumerate(segment_ms):
-        mine_k, _, flops_k = segment_flops(grid_precision, contracts, k)
-        if mine_k and ms_k > 0:
-            ach = flops_k / (ms_k / 1e3) / 1e12
-            segments.append({"kernel": SEGMENT_KERNELS[grid_precision][k], "ms_per_launch": ms_k,
-                             "achieved": ach, "frac": ach / peak})
-    seg = max(range(len(segment_ms)), key=lambda k: segment_ms[k])
-    ms = segment_ms[seg]
-    mine, tc, flops = segment_flops(grid_precision, contracts, seg)
-    achieved = flops / (ms / 1e3) / 1e12
-    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-           "traffic": GRID_TRAFFIC.get(SEGMENT_KERNELS[grid_precision][seg]),
-           "kernel": SEGMENT_KERNELS[grid_precision][seg], "ms_per_launch": ms,
-           "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flops x 2070 MHz (unit counts, max clock)",
-           "flops_note": "FP32 flops per point-date: bridge 32; standard 30; PCA on CUDA cores 27 + 2(d-1); "
-                         "tensor-core PCA 27 (the product is on the tensor pipe)",
-           "segments": segments}
-    if tc:
-        gemm = sum(float(c.N) * c.R * c.d * 2 * (c.d - 1) for c in mine)
-        bf16 = measured_peaks().get("bf16_tflops_sustained")
-        t_ach = gemm / (ms / 1e3) / 1e12
-        out["tensor"] = {"achieved": t_ach, "peak": bf16, "unit": "TFLOP/s",
-                         "frac": (t_ach / bf16) if bf16 else None,
-                         "note": "useful product W = A z, 2 n flops per point-date, against the measured "
-                                 "sustained dense bf16 peak (of measured)"}
+def ceilings(grid_precision: str, contracts, peaks: dict) -> dict:
+    """Point-dates/s ceilings of a launch segment's contracts: FP32 op rate /
+    24, SFU rate / 2, and for tensor-core PCA the bf16/tf32 rate over the
+    split products' flops per element (averaged over the contracts' work)."""
+    out = {}
+    if peaks.get("fp32_fma_tflops"):
+        out["fp32"] = peaks["fp32_fma_tflops"] * 1e12 / 2 / OPS_PER_ELEMENT
+    sfu = peaks.get("sfu_ex2_gops")
+    if sfu:
+        out["sfu"] = sfu * 1e9 / SFU_PER_ELEMENT
+    if grid_precision in TC_PRODUCTS and contracts and all(c.construction == W.PCA for c in contracts):
+        rate = peaks.get("tc_bf16_tflops" if grid_precision == "tc-bf16" else "tc_tf32_tflops")
+        work = sum(c.N * c.R * c.d for c in contracts)
+        flops = sum(c.N * c.R * c.d * 2.0 * (c.d - 1) * TC_PRODUCTS[grid_precision] for c in contracts)
+        if rate and flops > 0:
+            out["tensor"] = rate * 1e12 / (flops / work)
     return out
+
+
+def roofline(grid_precision: str, contracts, segment_ms, peaks: dict) -> dict:
+    """Roofline of the launch segment that takes the most time (its kernel is
+    the dominant one of the step): its point-dates over its event-timed
+    duration against the lowest ceiling, reported as FP32 operations (24 per
+    point-date) against the measured FP32 operation rate when that ceiling is
+    the FP32 one.  `segments` gives the same for every segment with work."""
+    segment_ms = list(segment_ms)[:ROOFLINE_SEGMENTS]
+    segs = []
+    for k, ms_k in enumerate(segment_ms):
+        mine = segment_contracts(contracts, k)
+        if not mine or ms_k <= 0:
+            continue
+        pd = sum(c.N * c.R * c.d for c in mine) / (ms_k / 1e3)
+        ceil = ceilings(grid_precision if k >= 2 else "mixed", mine, peaks)
+        bound = min(ceil, key=ceil.get) if ceil else None
+        segs.append({"kernel": SEGMENT_KERNELS[grid_precision][k], "ms_per_launch": ms_k, "point_dates_per_s": pd,
+                     "ceilings_point_dates_per_s": ceil, "limit": bound,
+                     "frac": pd / ceil[bound] if bound else None})
+    top = max(segs, key=lambda x: x["ms_per_launch"])
+    op_peak = peaks.get("fp32_fma_tflops", 0.0) / 2  # tera-operations/s (an FMA is one)
+    achieved_ops = top["point_dates_per_s"] * OPS_PER_ELEMENT / 1e12
+    return {"bound": "alu", "achieved": achieved_ops, "peak": op_peak, "unit": "Top/s (FP32 operations)",
+            "frac": achieved_ops / op_peak if op_peak else None,
+            "traffic": GRID_TRAFFIC.get(top["kernel"]), "kernel": top["kernel"], "ms_per_launch": top["ms_per_launch"],
+            "point_dates_per_s": top["point_dates_per_s"], "ceilings_point_dates_per_s": top["ceilings_point_dates_per_s"],
+            "limit": top["limit"], "frac_of_lowest_ceiling": top["frac"],
+            "peak_note": "of measured: FP32 operation rate = FFMA lane rate of the library's micro-benchmark "
+                         "(pipe_peaks_gb300.json, burst); ceilings per SURVEY-style count: FP32/24, SFU(ex2)/2, "
+                         "tensor/(2n x split products)",
+            "segments": segs}
 
 
 # ---------------------------------------------------------------------------
@@ -275,9 +273,21 @@ def cpu_baseline(contracts, budget_s: float = 12.0) -> dict:
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    # one core, comparable to the paper's sequential CPU: the first contracts at N = 2^9
+    t1, e1, done1 = time.perf_counter(), 0, 0
+    for c in contracts:
+        n = 2 ** 9
+        oracle.greeks(W.SCRAMBLE_SEED, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.construction, n, c.R, threads=1)
+        done1 += 1
+        e1 += n * c.R * c.d
+        if time.perf_counter() - t1 > budget_s / 3:
+            break
+    dt1 = time.perf_counter() - t1
     return {"value": elems / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} of {len(contracts)} contracts at N=2^11, R=32, d=64 ({elems} point-dates, "
-                      f"{dt:.1f} s wall)"}
+                      f"{dt:.1f} s wall)",
+            "single_core": {"value": e1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"{done1} contracts at N=2^9, R=32, d=64 ({e1} point-dates, {dt1:.1f} s)"}}
 
 
 def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5, max_inflight=3):
@@ -413,7 +423,7 @@ def pca_stress(q, local, rank, stream, steps: int) -> dict:
     tensor-core precisions, device time per step; error against FP64 at
     N = 2^16 (the same estimator on fewer points) in units of its SE."""
     import torch
-    plan = q.qmccpw_plan(device=local, d_max=257, r_max=16, seed=rank_seed(rank), stream=stream.cuda_stream)
+    plan = q.qmccpw_plan(device=local, d_max=257, r_max=16, seed=W.SCRAMBLE_SEED, stream=stream.cuda_stream)
     full = W.pca_stress()
     small = W.pca_stress(N=2 ** 16)
     el = elements(full)
@@ -491,17 +501,36 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()  # one non-default stream for the library, the events and the L2 flush
     torch.cuda.set_stream(stream)
-    plan = q.qmccpw_plan(device=local, d_max=max(65, args.case_d + 1), r_max=32, seed=rank_seed(rank),
+    # every rank: the job's seed (a replicate is the same point set whichever rank runs it)
+    plan = q.qmccpw_plan(device=local, d_max=max(65, args.case_d + 1), r_max=32, seed=W.SCRAMBLE_SEED,
                          stream=stream.cuda_stream)
     contracts = W.grid_d64()
-    elems = elements(contracts)
+    elems = elements(contracts)  # the job's distinct point-dates
+    pieces = shard.replicate_shards(contracts, world)[rank]
+    mine = shard.piece_contracts(contracts, pieces)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    peaks = pipe_peaks()
 
     def timed(precision, steps, warmup, with_clocks=False):
-        batch = q.Batch(plan, contracts, precision)
+        """Per step: L2 flush, this rank's batch; with several ranks also the
+        sum over ranks of the replicate estimates and the statistics."""
+        batch = q.Batch(plan, mine, precision)
+        rows = None
+        if world > 1:
+            rows = torch.zeros((shard.total_rows(contracts), 4), dtype=torch.float64, device="cuda")
+            batch.scatter_replicates(rows.data_ptr(), shard.piece_rows(contracts, pieces))
+        stats = [None]
+
+        def step():
+            if rows is not None:
+                rows.zero_()
+            batch.launch(stream.cuda_stream)
+            if rows is not None:
+                stats[0] = shard.gather_stats(rows, contracts, stream=stream.cuda_stream)
+
         for _ in range(warmup):
             flush.zero_()
-            batch.launch(stream.cuda_stream)
+            step()
         torch.cuda.synchronize()
         batch.set_timing(max(1, steps))
         sampler = ClockSampler(local) if with_clocks else None
@@ -517,7 +546,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            batch.launch(stream.cuda_stream)
+            step()
             e1.record(stream)
             events.append((e0, e1))
         torch.cuda.synchronize()
@@ -528,7 +557,12 @@ def run_ours(args):
         seg_ms, _ = batch.segment_timing()
         fused_ms, nl = batch.timing()
         launches = batch.launch_count() * steps
-        res = batch.results()
+        if rows is None:
+            res = [(m, s_, None) for m, s_, _ in batch.results()]
+        else:
+            st = stats[0].cpu().numpy()
+            res = [(st[i, :4], st[i, 4:], None) for i in range(len(contracts))]
+            launches += steps  # the statistics kernel
         batch.free()
         return {"ms_per_step": sum(step_ms) / steps, "wall_s": wall, "fused_ms": fused_ms / max(1, nl),
                 "segment_ms": [x / max(1, nl) for x in seg_ms], "clocks": clocks, "launches": launches,
@@ -568,7 +602,9 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: contracts in, results out
     def e2e_once():
-        return q.qmccpw_greeks_batch(plan, contracts, grid_prec)
+        if world == 1:
+            return q.qmccpw_greeks_batch(plan, contracts, grid_prec)
+        return shard.sharded_greeks(plan, contracts, grid_prec, rank, world)
 
     e2e_once()
     torch.cuda.synchronize()
@@ -581,71 +617,76 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
 
     ms = max_over_ranks(mixed["ms_per_step"])
-    value = job_value(elems, world, ms)
+    value = job_value(elems, ms)
     seg_ms = [max_over_ranks(x) for x in mixed["segment_ms"]]
 
-    # MIXED against FP64 on the same points, in units of the FP64 standard error
-    err_se = None
-    err_frac = None
+    # the float path against FP64 on the same points, in units of the FP64 standard error
+    err_se = err_frac = per_greek = None
     if fp64 is not None:
-        worst = 0.0
+        worst = np.zeros(4)
         table = []
         met = 0
         for c, (m32, _, _), (m64, se64, _) in zip(contracts, mixed["results"], fp64["results"]):
-            row = {"contract": c.label(), "fp64": list(m64), "se": list(se64), "mixed": list(m32),
-                   "err_in_se": [abs(m32[g] - m64[g]) / se64[g] if se64[g] > 0 else None for g in range(4)]}
-            table.append(row)
-            for g in range(4):
-                if se64[g] > 0:
-                    worst = max(worst, abs(m32[g] - m64[g]) / se64[g])
-                    met += int(abs(m32[g] - m64[g]) <= 0.1 * se64[g])
-        err_se = worst
+            e = np.abs(np.asarray(m32) - np.asarray(m64)) / np.asarray(se64)
+            table.append({"contract": c.label(), "fp64": list(m64), "se": list(se64), "mixed": list(m32),
+                          "err_in_se": e.tolist()})
+            worst = np.maximum(worst, e)
+            met += int(np.sum(e <= 0.1))
+        err_se = float(worst.max())
         err_frac = met / (4.0 * len(contracts))
+        per_greek = dict(zip(("price", "delta", "vega", "gamma"), worst.tolist()))
         if args.errors_out and rank == 0:
             with open(args.errors_out, "w") as f:
                 json.dump(table, f, indent=1)
 
-    sizeof_contract = 200  # bytes per qmccpw_contract descriptor uploaded, rounded up
-    h2d = len(contracts) * (sizeof_contract + 8) + sum(c.R for c in contracts) * 8
-    d2h = len(contracts) * 8 * 8 + sum(c.R for c in contracts) * 4 * 8
+    sizeof_contract = 72  # bytes of one qmccpw_contract descriptor uploaded
+    h2d = len(mine) * (sizeof_contract + 8) + sum(c.R for c in mine) * 8
+    d2h = len(mine) * 8 * 8 + sum(c.R for c in mine) * 4 * 8
+    if world > 1:
+        h2d += shard.total_rows(contracts) * 4 * 8  # the assembled estimates, up for the sum over ranks
+        d2h += shard.total_rows(contracts) * 4 * 8 + len(contracts) * 8 * 8
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "contracts": len(contracts), "d": 64, "N": 2 ** 20, "R": 32,
                    "precision": {"mixed": "MIXED", "tc-bf16": "MIXED_TC_BF16X3",
                                  "tc-tf32": "MIXED_TC_TF32X3"}[args.grid_precision] +
-                                ": inverse normal and path in f32; switch point and per-point values in "
+                                ": inverse normal, path and exponentials in f32 from the library's own "
+                                "polynomials with float-pair constants; switch point and per-point values in "
                                 "float-float; tile and replicate sums in f64",
                    "point_dates_per_step": elems, "l2": "flushed between timed steps (512 MiB write)",
-                   "parallelism": f"dp{world} (independent contracts per GPU)"},
+                   "parallelism": (f"{world} GPUs: each contract's 32 replicates in {world} ranges, one per GPU; "
+                                   "one sum over GPUs of the replicate estimates per step" if world > 1 else
+                                   "1 GPU")},
         "fp64": None if fp64 is None else {
-            "value": job_value(elems, world, max_over_ranks(fp64["ms_per_step"])), "unit": UNIT,
+            "value": job_value(elems, max_over_ranks(fp64["ms_per_step"])), "unit": UNIT,
             "ms_per_step": max_over_ranks(fp64["ms_per_step"]), "steps": args.fp64_steps},
         "mixed_vs_fp64_max_err_in_se": err_se,
+        "mixed_vs_fp64_worst_in_se_per_greek": per_greek,
         "mixed_vs_fp64_share_within_0p1_se": err_frac,
-        "roofline": roofline(args.grid_precision, contracts, seg_ms),
+        "roofline": roofline(args.grid_precision, mine, seg_ms, peaks),
         "segment_ms": {"bridge": seg_ms[0], "standard": seg_ms[1], "pca_streamed": seg_ms[2], "pca": seg_ms[3]},
         "mixed_cuda_core": None if cuda_core is None else {
-            "value": job_value(elems, world, max_over_ranks(cuda_core["ms_per_step"])), "unit": UNIT,
+            "value": job_value(elems, max_over_ranks(cuda_core["ms_per_step"])), "unit": UNIT,
             "ms_per_step": max_over_ranks(cuda_core["ms_per_step"]),
             "note": "the same grid in MIXED precision with the PCA product on the CUDA cores"},
-        "e2e": {"value": world * elems / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": {"value": elems / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
     }
     if args.book_steps > 0:
-        # the 4096-contract book: one batched launch sequence per step, MIXED, plus an FP64 sample
-        bplan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=rank_seed(rank),
+        # the 4096-contract book: whole contracts spread over the ranks by point-dates, MIXED, plus an FP64 sample
+        bplan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED,
                               stream=stream.cuda_stream, workspace_bytes=8 << 30)
         bk = W.book(4096, seed=4, R=16)
         bel = elements(bk)
-        bb = q.Batch(bplan, bk, q.QMCCPW_MIXED)
+        bmine = shard.piece_contracts(bk, shard.contract_shards(bk, world)[rank])
+        bb = q.Batch(bplan, bmine, q.QMCCPW_MIXED)
         bb.launch(stream.cuda_stream)
         torch.cuda.synchronize()
         bb.set_timing(args.book_steps)
-        t0 = time.perf_counter()
+        barrier()
         ev = []
         for _ in range(args.book_steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -670,24 +711,26 @@ def run_ours(args):
         q.qmccpw_free(bplan)
         line["book"] = {"workload": "4096 contracts (seed 4): type U{3}, d U{12..365}, K U(80,120), sigma U(0.1,0.5), "
                                     "T U(0.25,2), r U(0,0.08), N=2^U{12..18}, R=16, bridge",
-                        "point_dates": bel, "mixed": {"value": job_value(bel, world, max_over_ranks(bms)), "unit": UNIT,
+                        "point_dates": bel, "mixed": {"value": job_value(bel, max_over_ranks(bms)), "unit": UNIT,
                                                       "ms_per_step": max_over_ranks(bms), "steps": args.book_steps},
                         "fp64_sample": {"contracts": 64, "value": elements(sample) / (f64ms / 1e3), "unit": UNIT,
                                         "ms": f64ms}}
-    if args.latency_calls > 0:
+    # the latency, stress and serving sections run on rank 0's GPU only
+    if rank == 0 and args.latency_calls > 0:
         line["latency_small"] = latency_small(q, plan, stream, args.latency_calls)
-    if args.stress_steps > 0:
+    if rank == 0 and args.stress_steps > 0:
         line["pca_stress"] = pca_stress(q, local, rank, stream, args.stress_steps)
-    if args.serving_s > 0:
-        # at the configured rate (2000/s: its offered load is above what the GPU serves, so the queue grows
-        # over the window), at a rate the GPU sustains, and FP64 at a rate its path sustains
-        splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=rank_seed(rank))
+    if rank == 0 and args.serving_s > 0:
+        # at the configured rate (2000/s), at a rate well within what the GPU serves, and FP64 at a rate
+        # its path sustains
+        splan = q.qmccpw_plan(device=local, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED)
         line["serving"] = {
             "mixed": serve(q, splan, q.QMCCPW_MIXED, args.serving_rate, args.serving_s),
             "mixed_sustained": serve(q, splan, q.QMCCPW_MIXED, args.serving_rate_sustained, args.serving_s),
             "fp64": serve(q, splan, q.QMCCPW_FP64, args.serving_rate_fp64, args.serving_s),
         }
         q.qmccpw_free(splan)
+    barrier()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(contracts)
     elif rank == 0 and world == 1:

@@ -71,8 +71,9 @@ __global__ void __launch_bounds__(256) dfma_kernel(double b, double c, int iters
     if (s == 1234.5) sink[threadIdx.x] = static_cast<float>(s);
 }
 
-// SFU chains: x <- 2^-x (fixed point ~0.64), x <- log2(x) + 2 (fixed point 4;
-// the add runs on the FMA pipe, 8x the SFU rate), x <- 1/x (alternates).
+// SFU chains: x <- 2^-x (fixed point ~0.64), x <- log2(x) + 2 (fixed point 4),
+// x <- 1/x + 1/2 (fixed point ~1.28); the adds run on the FMA pipe, at
+// several times the SFU rate.
 template <int OP>
 __device__ __forceinline__ float sfu_step(float x) {
     float y;
@@ -83,6 +84,7 @@ __device__ __forceinline__ float sfu_step(float x) {
         y += 2.0f;
     } else {
         asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        y += 0.5f;
     }
     return y;
 }

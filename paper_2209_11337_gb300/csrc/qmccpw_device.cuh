@@ -70,9 +70,11 @@ __device__ __forceinline__ float rcp_nr(float x) {
     return fmaf(r, fmaf(-x, r, 1.0f), r);
 }
 __device__ __forceinline__ float2 rcp_nr2(float2 x) {
-    float2 r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(x.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(x.y));
+    // scalar asm operands (an output bound to a float2 member lost one lane)
+    float rx, ry;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(x.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(x.y));
+    const float2 r = make_float2(rx, ry);
     return fma2(r, fma2(make_float2(-x.x, -x.y), r, f2(1.0f)), r);
 }
 
@@ -133,14 +135,18 @@ __device__ __forceinline__ float exp_ff(float xh, float xl) {
 __device__ __forceinline__ float2 neg_ln2(float2 a) {
     constexpr float c[] = QMC_LN_POLY;
     constexpr int n = sizeof(c) / sizeof(c[0]);
+    // e + 127 = floor(log2(a / sqrt(1/2))) + 127 from the bits of a (a normal,
+    // 0 < a < 2^127): unsigned adds and logical shifts only (an arithmetic
+    // shift of the signed difference gave one lane of the pair unshifted)
     const uint32_t bx = __float_as_uint(a.x), by = __float_as_uint(a.y);
-    const int32_t ex = static_cast<int32_t>(bx - 0x3F3504F3u) >> 23;  // floor(log2(a / sqrt(1/2)))
-    const int32_t ey = static_cast<int32_t>(by - 0x3F3504F3u) >> 23;
-    const float2 m = make_float2(__uint_as_float(bx - (static_cast<uint32_t>(ex) << 23)),
-                                 __uint_as_float(by - (static_cast<uint32_t>(ey) << 23)));
-    // e as a float (|e| < 2^22) through the magic constant: no conversion instruction
-    const float2 ef = add2(make_float2(__uint_as_float(0x4B400000u + static_cast<uint32_t>(ex)),
-                                       __uint_as_float(0x4B400000u + static_cast<uint32_t>(ey))), f2(-kMagic));
+    const uint32_t ebx = (bx + (0x3F800000u - 0x3F3504F3u)) >> 23;
+    const uint32_t eby = (by + (0x3F800000u - 0x3F3504F3u)) >> 23;
+    // m = a 2^-e in [sqrt(1/2), sqrt 2): the exponent field less e
+    const float2 m = make_float2(__uint_as_float(bx - (ebx << 23) + (127u << 23)),
+                                 __uint_as_float(by - (eby << 23) + (127u << 23)));
+    // e as a float through the magic constant (1.5 2^23 + e - kMagic): no conversion instruction
+    const float2 ef = add2(make_float2(__uint_as_float(0x4B400000u - 127u + ebx),
+                                       __uint_as_float(0x4B400000u - 127u + eby)), f2(-kMagic));
     const float2 num = add2(m, f2(-1.0f));
     const float2 den = add2(m, f2(1.0f));
     const float2 f = mul2(num, rcp_nr2(den));

@@ -105,3 +105,51 @@ def point_dates(contracts: Sequence, pieces: Sequence[Piece] = None) -> int:
     if pieces is None:
         return sum(c.N * c.R * c.d for c in contracts)
     return sum(contracts[i].N * n * contracts[i].d for i, _, n in pieces)
+
+
+def gather_stats(per_rep_rows, contracts, group=None, stream=None):
+    """The job's statistics from a device array of replicate estimates.
+
+    ``per_rep_rows``: float64 CUDA tensor of total_rows(contracts) x 4, this
+    rank's rows filled and zeros elsewhere.  One sum over the ranks of
+    ``group`` (torch.distributed, NCCL on the GPUs) assembles every rank's
+    rows; the library's statistics kernel then forms mean and SE per contract
+    on this GPU.  Returns a CUDA tensor of len(contracts) x 8 (mean[4], se[4])."""
+    import torch
+    import torch.distributed as dist
+    from . import qmccpw as q
+    if group is not None or (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        dist.all_reduce(per_rep_rows, group=group)
+    dev = per_rep_rows.device
+    first = torch.tensor(rows(contracts), dtype=torch.int64, device=dev)
+    R = torch.tensor([c.R for c in contracts], dtype=torch.int32, device=dev)
+    stats = torch.empty((len(contracts), 8), dtype=torch.float64, device=dev)
+    cur = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+    q.qmccpw_replicate_stats(per_rep_rows.data_ptr(), first.data_ptr(), R.data_ptr(), len(contracts),
+                             stats.data_ptr(), cur)
+    return stats
+
+
+def sharded_greeks(plan, contracts, precision, rank: int, world: int, mode: str = "replicates"):
+    """One job over `world` GPUs, called on every rank (torch.distributed
+    initialised, one GPU per rank, `plan` on this rank's GPU with the job's
+    seed): this rank computes its pieces through qmccpw_greeks_batch (host
+    buffers), the replicate estimates are assembled on the GPUs by one sum over
+    ranks, and every rank gets (mean[C,4], se[C,4], per_replicate list of [R,4])
+    for all contracts, identical to one GPU running the whole job."""
+    import numpy as np
+    import torch
+    from . import qmccpw as q
+    shards = replicate_shards(contracts, world) if mode == "replicates" else contract_shards(contracts, world)
+    pieces = shards[rank]
+    buf = torch.zeros((total_rows(contracts), 4), dtype=torch.float64)
+    if pieces:
+        res = q.qmccpw_greeks_batch(plan, piece_contracts(contracts, pieces), precision)
+        for row, (_, _, per) in zip(piece_rows(contracts, pieces), res):
+            buf[row:row + per.shape[0]] = torch.from_numpy(per)
+    dev_buf = buf.cuda()
+    stats = gather_stats(dev_buf, contracts).cpu().numpy()
+    per_all = dev_buf.cpu().numpy()
+    base = rows(contracts)
+    per = [per_all[b:b + c.R] for b, c in zip(base, contracts)]
+    return stats[:, :4].copy(), stats[:, 4:].copy(), per

@@ -1,8 +1,8 @@
 """Host side of the multi-GPU path, on CPU: two gloo ranks (127.0.0.1).
 
-Each rank runs the whole batch on its own randomisation (weak scaling, no
-data-path collective); the job's value is all ranks' point-dates over the
-slowest rank's time; the reference arm runs on rank 0 only."""
+The job is split over the ranks (each contract's replicates in ranges, one
+per rank, with the job's seed); the job's value counts each replicate once,
+over the slowest rank's time; the reference arm runs on rank 0 only."""
 import json
 import os
 import socket
@@ -25,16 +25,22 @@ def _rank_main(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     sys.path.insert(0, ROOT)
     import bench
+    import workloads as W
+    from paper_2209_11337_gb300 import shard
     r = bench.Ranks(world, "gloo")
     r.barrier()
     step_ms = 100.0 + 50.0 * rank  # rank 1 is the slower one
     worst = r.max_over_ranks(step_ms)
     r.barrier()
-    out.put((rank, worst, bench.rank_seed(rank), bench.job_value(1000, world, worst)))
+    grid = W.grid_d64()
+    mine = shard.replicate_shards(grid, world)[rank]
+    out.put((rank, worst, mine, bench.job_value(bench.elements(grid), worst)))
     r.close()
 
 
-def test_two_gloo_ranks_take_the_max_time_and_distinct_seeds():
+def test_two_gloo_ranks_take_the_max_time_and_split_the_replicates():
+    import workloads as W
+    from paper_2209_11337_gb300 import shard
     world, port = 2, free_port()
     ctx = mp.get_context("spawn")
     out = ctx.Queue()
@@ -46,8 +52,12 @@ def test_two_gloo_ranks_take_the_max_time_and_distinct_seeds():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert [g[1] for g in got] == [150.0, 150.0]           # both ranks see the slowest step
-    assert got[0][2] != got[1][2]                           # independent randomisations
-    assert got[0][3] == pytest.approx(2 * 1000 / 0.150)     # whole-job point-dates / slowest time
+    grid = W.grid_d64()
+    reps = sorted((i, f + k) for g in got for i, f, n in g[2] for k in range(n))
+    assert reps == sorted((i, r) for i, c in enumerate(grid) for r in range(c.R))  # each replicate once
+    assert shard.point_dates(grid, got[0][2]) == shard.point_dates(grid, got[1][2])  # the same work per rank
+    total = sum(c.N * c.R * c.d for c in grid)
+    assert got[0][3] == pytest.approx(total / 0.150)         # the job's distinct point-dates / slowest time
 
 
 def test_reference_arm_under_torchrun_prints_on_rank_zero_only():
