@@ -90,6 +90,7 @@ struct DTables {
     int n_levels = 0;
     DevBuf steps, w64, w32, level_start, pca64, pca32;
     DevBuf lead64, lead32;  // loadings of the leading coordinate, dates 1..n: bridge (j/sqrt(n)) then PCA (first column)
+    double lead_sum[2] = {0.0, 0.0};  // the sum of each form's loadings
     DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32; resident or streamed form by n), built on first use
 };
 
@@ -297,7 +298,12 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
         lead[i - 1] = static_cast<double>(i) / std::sqrt(static_cast<double>(n));
         lead[nl + i - 1] = A[static_cast<size_t>(i - 1) * n];
     }
-    std::vector<float> lead32(lead.begin(), lead.end());
+    for (int i = 0; i < n; ++i) {
+        t->lead_sum[0] += lead[i];
+        t->lead_sum[1] += lead[nl + i];
+    }
+    std::vector<float> lead32(2 * lead.size());  // float pairs (hi, lo)
+    for (size_t i = 0; i < lead.size(); ++i) split_ff(lead[i], &lead32[2 * i]);
     QMC_TRY(t->lead64.alloc(sizeof(double) * lead.size()));
     QMC_TRY(t->lead32.alloc(sizeof(float) * lead32.size()));
     QMC_CUDA(cudaMemcpy(t->lead64.ptr, lead.data(), sizeof(double) * lead.size(), cudaMemcpyHostToDevice));
@@ -391,7 +397,8 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     if (lead) {
         const size_t off = c.construction == QMCCPW_PCA_LEAD ? static_cast<size_t>(std::max(1, c.d)) : 0;
         c.lead_a64 = t->lead64.as<double>() + off;
-        c.lead_a32 = t->lead32.as<float>() + off;
+        c.lead_a32 = t->lead32.as<float>() + 2 * off;
+        c.lead_amean = t->lead_sum[c.construction == QMCCPW_PCA_LEAD ? 1 : 0] / c.d;  // times sqrt(dt) below
     }
     c.N = in.N;
     c.item_base = item_base;
@@ -419,6 +426,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.r = in.market.r;
     c.sigma = in.market.sigma;
     contract_constants(c);
+    if (lead) c.lead_amean *= c.sqrt_t1;
     *out = c;
     return QMCCPW_OK;
 }

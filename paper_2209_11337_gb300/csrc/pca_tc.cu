@@ -164,7 +164,7 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
             }
         }
     }
-    tile_sum(p, item, v, scratch);
+    tile_sum(p.tile_sums + item * 4, v, scratch);
 }
 
 // Two Gray-code chains (dimensions ja and jb) over the same run of points,

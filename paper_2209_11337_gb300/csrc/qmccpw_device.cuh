@@ -599,9 +599,8 @@ template <> struct LeadMath<float> {
 };
 
 template <typename T>
-__device__ __forceinline__ T lead_loading(const ContractDev &c, int j) {  // a_{j+1}, 0-based j
-    if constexpr (sizeof(T) == 8) return __ldg(c.lead_a64 + j) * c.sqrt_t1;
-    else return __ldg(c.lead_a32 + j) * (c.ff_sqrt_t1[0] + c.ff_sqrt_t1[1]);
+__device__ __forceinline__ T lead_loading(const ContractDev &c, int j) {  // a_{j+1}, 0-based j (double)
+    return __ldg(c.lead_a64 + j) * c.sqrt_t1;
 }
 
 // values of one point: out = price, delta, vega, gamma (before the tile sum)
@@ -695,24 +694,28 @@ __device__ void lead_values<double>(const ContractDev &c, const double *R, doubl
 //     added back at first order.
 constexpr int kMillsTerms = 20;
 
+// The loading of date j+1 times sqrt(dt) as a float pair (the table holds
+// the unit-spacing loading as float pairs: the PCA's first column is no float).
+__device__ __forceinline__ ff lead_loading_ff(const ContractDev &c, int j) {
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(c.lead_a32) + j);
+    return ff_mul_ff(ff{a.x, a.y}, ff_of(c.ff_sqrt_t1));
+}
+
 template <>
 __device__ void lead_values<float>(const ContractDev &c, const float *R, float out[4]) {
     const int d = c.d;
-    const float dt = c.f_dt, sig = c.f_sigma;
-    const float omega = c.f_omega;
     const double K = c.K, S0 = c.S0, disc = c.disc;
-    const float S0d = static_cast<float>(c.S0 * c.inv_d);
+    const float sh = c.ff_sig[0], sl = c.ff_sig[1];
     if (c.type == QMCCPW_GEOMETRIC_ASIAN_CALL) {
-        // log-linear in x: the double formulas from float sums of the path
-        float lmean = 0, amean = 0, bmean = 0;
-        for (int j = 0; j < d; ++j) {
-            const float t = small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, Rj = R[j + 1];
-            lmean += omega * t + sig * Rj;
-            amean += lead_loading<float>(c, j);
-            bmean += Rj - sig * t;
-        }
+        // log-linear in x: a float sum of the path, the rest per point in double
+        // (the sums of t_j and of the loadings are the contract's constants)
+        float sumR = 0.0f;
+        for (int j = 0; j < d; ++j) sumR += R[j + 1];
+        const double st = c.dt * 0.5 * d * (d + 1.0);  // sum of t_j
+        const double lm = (c.sigma * sumR + c.omega * st) * c.inv_d;
+        const double am = c.lead_amean;
+        const double bm = (sumR - c.sigma * st) * c.inv_d;
         double o[4];
-        const double lm = lmean * c.inv_d, am = amean * c.inv_d, bm = bmean * c.inv_d;
         const double b = c.sigma * am;
         const double xs = (c.psi0 + c.omega * c.dt - lm) / b;
         const double eb = S0 * exp(lm + 0.5 * b * b);
@@ -726,32 +729,44 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
         for (int g = 0; g < 4; ++g) out[g] = static_cast<float>(o[g]);
         return;
     }
-    // (1) switch point
-    float cst[2];
-    cst[0] = static_cast<float>(c.ln_lead_c0 - c.ln_K);
-    cst[1] = static_cast<float>((c.ln_lead_c0 - c.ln_K) - static_cast<double>(cst[0]));
-    // float Newton steps to the rounding floor, then one step with the sum in
-    // float-float and g in float-float
+    // the exponent of c_j e^{b_j x}: ln(S0/d) + omega t_j + sigma R_j + b_j x
+    // with b_j x = a_j (sigma sqrt(dt) x), every constant a float pair, the
+    // small terms first (a float sigma, omega or loading would bias every point)
+    auto expo = [&](int j, const ff &ys) {
+        const float2 a = __ldg(reinterpret_cast<const float2 *>(c.lead_a32) + j);
+        const float nf = small_uint_to_float(static_cast<uint32_t>(j + 1)), Rj = R[j + 1];
+        float t = fmaf(a.y, ys.hi, c.ff_lnS0d[1]);
+        t = fmaf(a.x, ys.lo, t);
+        t = fmaf(Rj, sl, t);
+        t = fmaf(nf, c.ff_om_dt[1], t);
+        t = fmaf(nf, c.ff_om_dt[0], t);
+        t = fmaf(Rj, sh, t);
+        t = fmaf(a.x, ys.hi, t);
+        return t + c.ff_lnS0d[0];
+    };
+    // (1) switch point: Newton on ln X(x) - ln K in float to its rounding
+    // floor, then one step with the sum and g in float-float
     float x = 0, last = 1e30f;
     for (int it = 0; it <= LeadMath<float>::iters; ++it) {
         const bool polish = it == LeadMath<float>::iters;
+        const ff ys = ff_mul(ff_of(c.ff_sig_sdt), x);
         ff s0{0.0f, 0.0f};
         float s1 = 0;
         for (int j = 0; j < d; ++j) {
-            const float b = sig * lead_loading<float>(c, j);
-            const float e = Arith<float>::ex(fmaf(omega, small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, fmaf(sig, R[j + 1], b * x)));
+            const float e = fx::exp_f(expo(j, ys));
+            const float2 a = __ldg(reinterpret_cast<const float2 *>(c.lead_a32) + j);
             if (polish) s0 = ff_add(s0, ff{e, 0.0f});
             else s0.hi += e;
-            s1 = fmaf(b, e, s1);
+            s1 = fmaf(a.x, e, s1);  // sum a_j e_j: the derivative's scale, times sigma sqrt(dt) below
         }
         float gv;
         if (polish) {
-            const ff g = ff_add(ln_ff(s0.hi), ff{cst[0], cst[1] + s0.lo / s0.hi});  // {hi, lo}
+            const ff g = ff_add(ff_add(ln_ff(s0.hi), ff{s0.lo / s0.hi, 0.0f}), ff_neg(ff_of(c.ff_lnK)));
             gv = g.hi + g.lo;
         } else {
-            gv = logf(s0.hi) + (cst[0] + cst[1]);
+            gv = logf(s0.hi) - (c.ff_lnK[0] + c.ff_lnK[1]);
         }
-        const float step = gv * (s0.hi / s1);
+        const float step = gv * (s0.hi / (s1 * (c.ff_sig_sdt[0] + c.ff_sig_sdt[1])));
         x -= step;
         if (polish) break;
         const float mag = fabsf(step);
@@ -778,24 +793,29 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
             m_cur = m_next;
         }
     }
+    const ff ys = ff_mul(ff_of(c.ff_sig_sdt), x);
+    const float dt = c.ff_dt[0];
     float X1 = 0, X2 = 0, SP = 0, SA = 0, V1 = 0, B = 0;
     ff Xs{0.0f, 0.0f}, W0{0.0f, 0.0f};
     for (int j = 0; j < d; ++j) {
-        const float t = small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, a = lead_loading<float>(c, j), b = sig * a, Rj = R[j + 1];
-        const float e = S0d * Arith<float>::ex(fmaf(omega, t, fmaf(sig, Rj, b * x)));  // c_j e^{b_j x*}
-        float P = mk[kMillsTerms - 1];
+        const ff as = lead_loading_ff(c, j);                  // a_j sqrt(dt)
+        const ff b = ff_mul_ff(as, ff{sh, sl});               // b_j = sigma a_j sqrt(dt)
+        const float t = small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, Rj = R[j + 1];
+        const float e = fx::exp_f(expo(j, ys));               // c_j e^{b_j x*}
+        float Q = mk[kMillsTerms - 1];
 #pragma unroll
-        for (int k = kMillsTerms - 2; k >= 0; --k) P = fmaf(P, b, mk[k]);
-        P *= b;                                    // M(x* - b) - M(x*)
-        const float w = fmaf(sig, a * a, Rj - sig * t);
+        for (int k = kMillsTerms - 2; k >= 0; --k) Q = fmaf(Q, b.hi, mk[k]);
+        const float P = fmaf(Q, b.hi, Q * b.lo);              // M(x* - b) - M(x*) = b Q(b)
+        const float a = as.hi;
+        const float w = fmaf(sh, a * a, fmaf(-sh, t, Rj));
         Xs = ff_add(Xs, ff{e, 0.0f});
-        X1 = fmaf(b, e, X1);
-        X2 = fmaf(b * b, e, X2);
+        X1 = fmaf(b.hi, e, X1);
+        X2 = fmaf(b.hi * b.hi, e, X2);
         SP = fmaf(e, P, SP);                       // sum e_j [M(x*-b_j) - M(x*)]
         SA = fmaf(a, e, SA);
         V1 = fmaf(e * w, P, V1);
         W0 = ff_add(W0, ff{e * w, 0.0f});          // sum e_j w_j: signs mixed, kept in float-float
-        B = fmaf(e, fmaf(a, x, Rj - sig * t), B);
+        B = fmaf(e, fmaf(a, x, fmaf(-sh, t, Rj)), B);
     }
     // X(x*) - K of the float switch point
     const double resid = (static_cast<double>(Xs.hi) + Xs.lo) - K;
@@ -1106,9 +1126,9 @@ __device__ __forceinline__ void finish_functional(const ContractDev &c, const Pa
 // Tile sum of the 4 values of every thread (zero for threads without a
 // point): the kThreads x 4 values go through shared memory; warp g < 4 sums
 // Greek g (each lane kThreads/32 consecutive threads, then a shuffle tree),
-// a fixed order.  `smem` needs 4 * kThreads doubles; the caller's shared
+// a fixed order, and writes it to out[g].  `smem` needs 4 * kThreads doubles; the caller's shared
 // memory must be free on entry.  Ends with a barrier.
-__device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, const double (&v)[4], unsigned char *smem) {
+__device__ __forceinline__ void tile_sum(double *out, const double (&v)[4], unsigned char *smem) {
     __syncthreads();
     double *vals = reinterpret_cast<double *>(smem);
 #pragma unroll
@@ -1122,14 +1142,14 @@ __device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, c
         for (int i = 0; i < kThreads / 32; ++i) s += col[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) p.tile_sums[item * 4 + warp] = s;
+        if (lane == 0) out[warp] = s;
     }
     __syncthreads();
 }
 
 // The same tile sum for float-float values: TwoSum-based adds on the FP32
 // pipe, one conversion to double per Greek.  `smem` needs 8 * kThreads floats.
-__device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, const ff (&v)[4], unsigned char *smem) {
+__device__ __forceinline__ void tile_sum(double *out, const ff (&v)[4], unsigned char *smem) {
     __syncthreads();
     float *vals = reinterpret_cast<float *>(smem);
     if (threadIdx.x < kThreads) {  // larger blocks: the values live in the first kThreads threads
@@ -1152,7 +1172,7 @@ __device__ __forceinline__ void tile_sum(const LaunchParams &p, uint64_t item, c
             const ff o = {__shfl_down_sync(0xffffffffu, s.hi, off), __shfl_down_sync(0xffffffffu, s.lo, off)};
             s = ff_add(s, o);
         }
-        if (lane == 0) p.tile_sums[item * 4 + warp] = ff_to_double(s);
+        if (lane == 0) out[warp] = ff_to_double(s);
     }
     __syncthreads();
 }

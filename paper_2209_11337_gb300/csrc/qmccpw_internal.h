@@ -75,7 +75,7 @@ struct ContractDev {
     const float *pcaT32;                 // A^T as float, [k][i], i padded to a multiple of 16 with zeros
     const void *tc_operand;              // tensor-core PCA: Ahat hi then lo, K-major core-matrix layout
     const double *lead_a64;              // leading-coordinate constructions: its loading on dates 1..d, unit spacing
-    const float *lead_a32;
+    const float *lead_a32;               // the same as float pairs (hi, lo)
     // market-derived constants
     double S0, K, T, r, sigma;
     double dt;                           // t_1 = T/d: spacing of the separated dates
@@ -95,6 +95,7 @@ struct ContractDev {
     double inv_d;                        // 1/d
     double ln_lead_c0;                   // ln(S0/d): leading-coordinate constructions
     double ln_K;
+    double lead_amean;                   // leading-coordinate constructions: mean over the dates of the loading times sqrt(dt)
     // constants of the float path as float hi + lo pairs (split_ff)
     // path: the exponent (sigma sqrt(dt)) w + (omega dt) node of the unit-spacing path w
     float ff_sig_sdt[2], ff_om_dt[2];
@@ -112,8 +113,8 @@ struct ContractDev {
     float ff_kd_bin[2];                  // disc / (S0 a sqrt(2 pi))
     float ff_kg_bin[2];                  // disc / (S0^2 a sqrt(2 pi))
     float ff_kphi[2];                    // disc / sqrt(2 pi)
-    // float copies of market constants (the leading-coordinate float path)
-    float f_omega, f_sigma, f_dt;
+    // the leading-coordinate float path
+    float ff_sig[2], ff_lnS0d[2], ff_lnK[2], ff_dt[2];
 };
 
 // hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)

@@ -219,9 +219,10 @@ void contract_constants(ContractDev &c) {
     split_ff(c.k_bin_delta * inv_sqrt_2pi, c.ff_kd_bin);
     split_ff(c.k_bin_gamma * inv_sqrt_2pi, c.ff_kg_bin);
     split_ff(c.disc * inv_sqrt_2pi, c.ff_kphi);
-    c.f_omega = static_cast<float>(c.omega);
-    c.f_sigma = static_cast<float>(c.sigma);
-    c.f_dt = static_cast<float>(c.dt);
+    split_ff(c.sigma, c.ff_sig);
+    split_ff(c.ln_lead_c0, c.ff_lnS0d);
+    split_ff(c.ln_K, c.ff_lnK);
+    split_ff(c.dt, c.ff_dt);
 }
 
 }  // namespace qmccpw
