@@ -290,8 +290,8 @@ def cpu_baseline(contracts, budget_s: float = 12.0) -> dict:
                             "sample": f"{done1} contracts at N=2^9, R=32, d=64 ({e1} point-dates, {dt1:.1f} s)"}}
 
 
-def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5, max_inflight=3):
-    """Poisson arrivals through the continuous-batching service.
+def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
+    """Poisson arrivals through the device-resident serving loop.
 
     Each request is a book-like contract with a target delta standard error in
     {1e-3, 1e-4, 1e-5}: a pilot run (N = 2^12, R = 16) gives the delta SE at
@@ -302,8 +302,7 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5, max_inf
     import queue
 
     reqs = W.arrivals(rate_hz=rate_hz, duration_s=warmup_s + duration_s, seed=seed, R=16)
-    q.qmccpw_server_start(plan, precision=precision, max_inflight=max_inflight, max_batch_contracts=4096,
-                          max_batch_bytes=256 << 20)
+    q.qmccpw_server_start(plan, precision=precision, max_inflight=1024, max_inflight_bytes=256 << 20)
     pilots = queue.Queue()
     mains = queue.Queue()
     lat, main_elems, Ns = [], [0], []
@@ -360,7 +359,8 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5, max_inf
     return {"rate_hz": rate_hz, "window_s": duration_s, "requests": len(lat_ms), "p50_ms": pct(0.50),
             "p99_ms": pct(0.99), "max_ms": lat_ms[-1] if lat_ms else None,
             "throughput_point_dates_per_s": stats["point_dates"] / wall, "wall_s": wall,
-            "offered_point_dates_per_s": offered, "batches": stats["batches"],
+            "offered_point_dates_per_s": offered, "kernel_launches": stats["launches"],
+            "idle_exits": stats["idle_exits"],
             "mean_N": statistics.mean(Ns) if Ns else None,
             "precision": {0: "fp64", 1: "mixed", 2: "tc-bf16", 3: "tc-tf32"}[precision]}
 

@@ -301,34 +301,54 @@ int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t c
 int qmccpw_tuning_get(qmccpw_plan_t plan, int32_t precision, int32_t construction, int32_t d, int32_t *points_per_tile);
 int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t construction, int32_t d, int32_t points_per_tile);
 
-/* ---- serving: continuous batching ------------------------------------------
+/* ---- serving: a device-resident request loop ------------------------------
  * Sec. 7 proposes wrapping the estimator in a microservice; this is its GPU
- * side.  Requests (contracts) queue on the host; a worker thread forms
- * batches from whatever is pending each time one of its `max_inflight`
- * slots is free, admitting requests in arrival order while the batch's
- * device scratch (about 32 * R * N / P bytes of tile sums per contract) stays
- * within `max_batch_bytes`, and runs up to `max_inflight` batches on the GPU
- * at once, one stream each.  A request's result does not depend on the batch
- * it ran in (bit-identical to qmccpw_greeks).  While a server runs, the plan
- * must not be used by the other entry points. */
+ * side.  A persistent kernel runs on the plan's device while work arrives.
+ * Requests (contracts) are written into a ring of pinned, host-mapped
+ * entries and published through two host-written counters; the kernel's
+ * CTAs take the published requests' work items (replicate, tile) in
+ * publication order from one device counter, so a request that arrives while
+ * others run fills the SMs as they free up, and the CTA that finishes a
+ * request's last item reduces it on the device and raises the request's
+ * completion flag in host-mapped memory.  Admission is in arrival order,
+ * while the admitted requests' device scratch (32 bytes per tile slot and
+ * per replicate: about 32 * R * N / P bytes, P the points per tile) fits
+ * `max_inflight_bytes` and at most `max_inflight` requests are on the
+ * device; the rest wait on the host.  Every wait of the kernel is bounded by
+ * %globaltimer: after `idle_limit_us` without a published work item its CTAs
+ * leave (the launch ends with an idle status, counted in idle_exits) and the
+ * host launches it again when a request arrives; the work items a leaving
+ * CTA held are handed out first by that launch.  A host thread watches the
+ * flags and relaunches; qmccpw_submit, qmccpw_poll and qmccpw_wait do the
+ * same steps themselves.  A request's result does not depend on what else
+ * runs: its tiles and their reduction order are those of qmccpw_greeks
+ * (bit-identical).  Precisions FP64 and MIXED; the tensor-core precisions
+ * return UNSUPPORTED (their PCA kernel is a batch kernel).  While a server
+ * runs, the plan must not be used by the other entry points. */
 typedef struct {
-    int32_t precision;             /* qmccpw_precision of every request */
-    int32_t max_inflight;          /* batches on the GPU at once, 1..8 (0: 2) */
-    int32_t max_batch_contracts;   /* requests per batch (<= 0: 1024) */
+    int32_t precision;             /* QMCCPW_FP64 or QMCCPW_MIXED for every request */
+    int32_t max_inflight;          /* requests on the device at once, 1..4096 (0: 1024); fewer when
+                                      r_max * 32 + 64 bytes of host-mapped results per request
+                                      would pass 256 MiB */
+    int32_t idle_limit_us;         /* the kernel leaves after this long without work, 1..10^7 (0: 20000) */
     int32_t reserved;              /* must be 0 */
-    uint64_t max_batch_bytes;      /* device scratch admitted per batch (0: 256 MiB) */
+    uint64_t max_inflight_bytes;   /* device scratch of the requests on the device (0: 256 MiB) */
 } qmccpw_server_desc;
 
 typedef struct {
-    uint64_t submitted, completed, failed, batches;
+    uint64_t submitted, completed, failed;
+    uint64_t launches;             /* serving-kernel launches: the first and one per return from idle */
+    uint64_t idle_exits;           /* launches that ended on the idle limit */
     uint64_t point_dates;          /* sum of N * R * d over completed requests */
-    uint64_t pending;              /* requests waiting for a batch */
+    uint64_t pending;              /* requests waiting for admission */
+    uint64_t inflight;             /* requests on the device, not yet collected by the host */
+    uint64_t running;              /* 1 while a serving kernel runs */
 } qmccpw_server_stats;
 
 /* Start the service on a plan (INVALID_ARG if one already runs). */
 int qmccpw_server_start(qmccpw_plan_t plan, const qmccpw_server_desc *desc);
 /* Queue one contract; *ticket identifies it.  Validation as qmccpw_greeks;
- * OOM if the contract alone exceeds the plan's workspace budget. */
+ * OOM if the contract alone needs more than max_inflight_bytes. */
 int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t *ticket);
 /* Non-blocking: OK and the result (per_replicate filled if non-NULL, R*4
  * doubles) once finished, QMCCPW_NOT_READY before; a collected ticket is
@@ -337,7 +357,8 @@ int qmccpw_poll(qmccpw_plan_t plan, uint64_t ticket, qmccpw_result *out);
 /* Blocking form of qmccpw_poll, at most timeout_ms milliseconds (TIMEOUT). */
 int qmccpw_wait(qmccpw_plan_t plan, uint64_t ticket, int32_t timeout_ms, qmccpw_result *out);
 int qmccpw_server_get_stats(qmccpw_plan_t plan, qmccpw_server_stats *out);
-/* Finish every queued request, then stop the worker (no-op without a server). */
+/* Finish every queued request, then stop the kernel and the host thread
+ * (no-op without a server). */
 int qmccpw_server_stop(qmccpw_plan_t plan);
 
 /* Release a plan after waiting for its work; NULL is accepted (no-op). */

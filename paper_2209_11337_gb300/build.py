@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libqmccpw.so")
-SOURCES = ["api.cu", "kernels.cu", "pca_tc.cu", "peaks.cu", "tables.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "serve.cu", "pca_tc.cu", "peaks.cu", "tables.cpp"]
 HEADERS = [os.path.join(CSRC, h) for h in ("qmccpw_internal.h", "qmccpw_device.cuh", "fused_body.cuh", "float_coeffs.h", "tc_ptx.cuh")] + \
     [os.path.join(ROOT, "include", "qmccpw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -89,6 +89,7 @@ struct DTables {
     int n = 0;
     int n_levels = 0;
     DevBuf steps, w64, w32, level_start, pca64, pca32;
+    DevBuf pca32lo;  // A^T - float(A^T): the leading-coordinate PCA carries the factor as hi + lo
     DevBuf lead64, lead32;  // loadings of the leading coordinate, dates 1..n: bridge (j/sqrt(n)) then PCA (first column)
     double lead_sum[2] = {0.0, 0.0};  // the sum of each form's loadings
     DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32; resident or streamed form by n), built on first use
@@ -281,15 +282,20 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
     std::vector<double> A = n > 0 ? pca_factor(n, dt) : std::vector<double>();
     // float A^T, rows k, columns i padded to a multiple of 16 (the register block of the product)
     const int n_pad = (n + 15) & ~15;
-    std::vector<float> A32(static_cast<size_t>(n) * n_pad, 0.0f);
+    std::vector<float> A32(static_cast<size_t>(n) * n_pad, 0.0f), A32lo(A32.size(), 0.0f);
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < n; ++k) A32[static_cast<size_t>(k) * n_pad + i] = static_cast<float>(A[static_cast<size_t>(i) * n + k]);
+        for (int k = 0; k < n; ++k) {
+            const double a = A[static_cast<size_t>(i) * n + k];
+            A32[static_cast<size_t>(k) * n_pad + i] = static_cast<float>(a);
+            A32lo[static_cast<size_t>(k) * n_pad + i] = static_cast<float>(a - static_cast<double>(static_cast<float>(a)));
+        }
     QMC_TRY(t->steps.alloc(sizeof(BridgeStep) * std::max<size_t>(1, bp.steps.size())));
     QMC_TRY(t->w64.alloc(sizeof(double) * std::max<size_t>(1, bp.w.size())));
     QMC_TRY(t->w32.alloc(sizeof(float) * std::max<size_t>(1, w32.size())));
     QMC_TRY(t->level_start.alloc(sizeof(int32_t) * bp.level_start.size()));
     QMC_TRY(t->pca64.alloc(sizeof(double) * std::max<size_t>(1, A.size())));
     QMC_TRY(t->pca32.alloc(sizeof(float) * std::max<size_t>(1, A32.size())));
+    QMC_TRY(t->pca32lo.alloc(sizeof(float) * std::max<size_t>(1, A32lo.size())));
     // the leading coordinate's loading when these n dates are a whole path: the bridge's
     // terminal value (W~(s_i) = (i/n) sqrt(n) z), then the first principal component
     const int nl = std::max(1, n);
@@ -314,6 +320,7 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
         QMC_CUDA(cudaMemcpy(t->w32.ptr, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
         QMC_CUDA(cudaMemcpy(t->pca64.ptr, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice));
         QMC_CUDA(cudaMemcpy(t->pca32.ptr, A32.data(), sizeof(float) * A32.size(), cudaMemcpyHostToDevice));
+        QMC_CUDA(cudaMemcpy(t->pca32lo.ptr, A32lo.data(), sizeof(float) * A32lo.size(), cudaMemcpyHostToDevice));
     }
     QMC_CUDA(cudaMemcpy(t->level_start.ptr, bp.level_start.data(), sizeof(int32_t) * bp.level_start.size(),
                         cudaMemcpyHostToDevice));
@@ -361,6 +368,14 @@ int chunk_log2_for(int n, int tile_log2, bool tc) {
     return lg;
 }
 
+// log2 of the points per tile of a contract: 128 on tensor cores, else the
+// plan's tuned tile for (precision, construction, d) or the default
+int contract_tile_log2(const qmccpw_plan_s *p, int precision, int construction, int d) {
+    if (is_tc(precision)) return 7;
+    auto tt = p->tuned_tile.find(std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, construction, d));
+    return tt != p->tuned_tile.end() ? tt->second : choose_tile_log2(precision, d - 1, construction);
+}
+
 int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precision, uint64_t item_base,
                    uint64_t rep_base, ContractDev *out) {
     const int precision = contract_precision(batch_precision, in.construction);
@@ -373,12 +388,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.d = in.option.d;
     c.n = in.option.d - 1;
     c.construction = in.construction;
-    if (is_tc(precision)) {
-        c.tile_log2 = 7;
-    } else {
-        auto tt = p->tuned_tile.find(std::make_tuple(precision == QMCCPW_FP64 ? 0 : 1, in.construction, c.d));
-        c.tile_log2 = tt != p->tuned_tile.end() ? tt->second : choose_tile_log2(precision, c.n, c.construction);
-    }
+    c.tile_log2 = contract_tile_log2(p, precision, in.construction, c.d);
     const int P = 1 << c.tile_log2;
     c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2, is_tc(precision));
     c.R = in.R;
@@ -409,6 +419,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.level_start = t->level_start.as<int32_t>();
     c.pca64 = t->pca64.as<double>();
     c.pcaT32 = t->pca32.as<float>();
+    c.pcaT32lo = t->pca32lo.as<float>();
     if (is_tc(precision)) {
         DTables *mt = const_cast<DTables *>(t);
         DevBuf &op = mt->tc[tc_slot(precision)];
@@ -590,15 +601,14 @@ int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Continuous batching service (qmccpw_server_*): requests queue on the host;
-// a worker forms batches from whatever is pending whenever one of its
-// in-flight slots is free, admitting requests while the batch's device
-// scratch stays within the budget, and keeps up to max_inflight batches on
-// the GPU at once (one stream each), so work that arrives while others run
-// overlaps on the device.  A host callback on each slot's stream wakes the
-// worker when the batch's results have landed in pinned host memory.
-// Each contract's result depends only on the contract (its tiles and their
-// reduction order are fixed), so it is the same alone and in any mix.
+// Serving (qmccpw_server_*): the host side of the device-resident loop of
+// serve.cu.  Requests are admitted in arrival order while their device
+// scratch fits the arena and the ring has a free entry, written into the
+// ring and published; a monitor thread collects finished requests (their
+// completion flags in host-mapped memory), admits waiting ones, and launches
+// the serving kernel again after it has left on its idle limit while work is
+// published.  submit/poll/wait do the same steps themselves, so a request
+// does not wait for the monitor's next turn.
 // ---------------------------------------------------------------------------
 struct ServerResult {
     int status = QMCCPW_OK;
@@ -606,169 +616,337 @@ struct ServerResult {
     std::vector<double> per_rep;
 };
 
-struct ServerSlot {
-    cudaStream_t stream = nullptr;
-    qmccpw_batch_s batch;
-    std::vector<qmccpw_contract> contracts;
-    std::vector<uint64_t> tickets;
-    double *h_stats = nullptr, *h_per = nullptr;  // pinned
-    size_t h_stats_cap = 0, h_per_cap = 0;
-    bool busy = false;
-    std::atomic<bool> done{false};
-    void *owner = nullptr;  // the QmcServer
+// First-fit allocator over [0, size) (offsets in bytes, 256-byte granules).
+struct ArenaAllocator {
+    std::map<uint64_t, uint64_t> free_;  // offset -> length
+    void init(uint64_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(uint64_t bytes, uint64_t *off) {
+        bytes = (bytes + 255) & ~uint64_t(255);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            const uint64_t rest = it->second - bytes, at = it->first + bytes;
+            free_.erase(it);
+            if (rest) free_[at] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t bytes) {
+        bytes = (bytes + 255) & ~uint64_t(255);
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
 };
+
+struct PendingRequest {
+    uint64_t ticket;
+    qmccpw_contract in;
+    ContractDev c;
+    uint64_t items, bytes;
+};
+
+struct LiveRequest {
+    uint64_t ticket, seq, slot, arena_off, bytes;
+    int R;
+    uint64_t point_dates;
+};
+
+template <typename T> bool host_alloc_mapped(T **host, T **dev, size_t count) {
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, sizeof(T) * count, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) return false;
+    std::memset(h, 0, sizeof(T) * count);
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+        cudaFreeHost(h);
+        return false;
+    }
+    *host = static_cast<T *>(h);
+    *dev = static_cast<T *>(d);
+    return true;
+}
 
 struct QmcServer {
     qmccpw_plan_s *plan = nullptr;
     qmccpw_server_desc desc{};
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<std::pair<uint64_t, qmccpw_contract>> pending;
+    std::deque<PendingRequest> pending;
+    std::deque<LiveRequest> live;  // in request (seq) order
     std::unordered_map<uint64_t, ServerResult> results;
     std::unordered_map<uint64_t, bool> known;  // ticket -> submitted and not yet collected
-    uint64_t next_ticket = 1;
+    uint64_t next_ticket_id = 1;
+    uint64_t next_seq = 0, next_first_ticket = 0;
     bool stopping = false;
-    std::vector<std::unique_ptr<ServerSlot>> slots;
-    std::thread worker;
+    bool broken = false;  // a launch failed or ended inconsistently
     qmccpw_server_stats stats{};
+    // ring and control words, host-mapped (h_ host view, d_ device view)
+    uint64_t cap = 0, out_stride = 0;
+    ServeRequest *h_ring = nullptr, *d_ring = nullptr;
+    ServeControl *h_ctl = nullptr, *d_ctl = nullptr;
+    uint64_t *h_done = nullptr, *d_done = nullptr;
+    ServeExit *h_exit = nullptr, *d_exit = nullptr;
+    double *h_out = nullptr, *d_out = nullptr;  // cap x out_stride doubles
+    // device state and the tile-slot arena
+    DevBuf state, arena_buf;
+    ArenaAllocator arena;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t exit_ev = nullptr;
+    bool running = false;
+    uint32_t launch_no = 0;
+    size_t smem = 0;
+    int grid = 0;
+    std::thread monitor;
 
-    static void CUDART_CB on_done(void *arg) {
-        ServerSlot *sl = static_cast<ServerSlot *>(arg);
-        sl->done.store(true);
-        QmcServer *sv = static_cast<QmcServer *>(sl->owner);
-        std::lock_guard<std::mutex> lk(sv->mu);
-        sv->cv_work.notify_all();
-    }
+    uint64_t oldest_live() const { return live.empty() ? next_seq : live.front().seq; }
 
-    // device scratch one contract needs in a batch (tile sums + replicate sums)
-    uint64_t bytes_of(const qmccpw_contract &c) const {
-        const int n = c.option.d - 1;
-        const int kp = contract_precision(desc.precision, c.construction);
-        const int P = 1 << (is_tc(kp) ? 7 : choose_tile_log2(kp, n, c.construction));
-        const uint64_t tiles = (c.N + P - 1) / P;
-        return tiles * static_cast<uint64_t>(c.R) * 32u + static_cast<uint64_t>(c.R) * 40u + sizeof(ContractDev) + 16u;
-    }
-
-    void retire(ServerSlot &sl) {
-        qmccpw_batch_s &b = sl.batch;
-        uint64_t rep = 0;
-        for (int k = 0; k < b.count; ++k) {
-            const int caller = b.order[k];
-            ServerResult r;
-            std::memcpy(r.mean, sl.h_stats + 8 * k, sizeof(r.mean));
-            std::memcpy(r.se, sl.h_stats + 8 * k + 4, sizeof(r.se));
-            r.per_rep.assign(sl.h_per + 4 * rep, sl.h_per + 4 * (rep + b.R[k]));
-            rep += b.R[k];
-            const qmccpw_contract &c = sl.contracts[caller];
-            stats.point_dates += c.N * static_cast<uint64_t>(c.R) * static_cast<uint64_t>(c.option.d);
-            results[sl.tickets[caller]] = std::move(r);
-            ++stats.completed;
+    // the kernel has left (stream work done): record why
+    void check_exit() {
+        if (!running) return;
+        const cudaError_t q = cudaEventQuery(exit_ev);
+        if (q == cudaErrorNotReady) return;
+        running = false;
+        if (q != cudaSuccess) {
+            fail_live(QMCCPW_ERR_CUDA);
+            return;
         }
-        sl.busy = false;
-        sl.done.store(false);
-        cv_done.notify_all();
+        const uint32_t reason = __atomic_load_n(&h_exit->reason, __ATOMIC_ACQUIRE);
+        if (reason == 1u) ++stats.idle_exits;
+        // 3: carried tickets above capacity, 4: a ticket without its request (neither expected)
+        if (reason == 3u || reason == 4u) fail_live(QMCCPW_ERR_CUDA);
     }
 
-    void fail_all(ServerSlot &sl, int status) {
-        for (uint64_t t : sl.tickets) {
-            ServerResult r;
-            r.status = status;
-            results[t] = std::move(r);
+    void finish(const LiveRequest &lr, int status) {
+        ServerResult r;
+        r.status = status;
+        if (status == QMCCPW_OK) {
+            const double *o = h_out + lr.slot * out_stride;
+            r.per_rep.assign(o, o + 4 * static_cast<size_t>(lr.R));
+            std::memcpy(r.mean, o + 4 * lr.R, sizeof(r.mean));
+            std::memcpy(r.se, o + 4 * lr.R + 4, sizeof(r.se));
+            ++stats.completed;
+            stats.point_dates += lr.point_dates;
+        } else {
             ++stats.failed;
         }
-        sl.busy = false;
+        arena.release(lr.arena_off, lr.bytes);
+        results[lr.ticket] = std::move(r);
+    }
+
+    // the device side failed: every request fails, and the server takes no more
+    void fail_live(int status) {
+        broken = true;
+        for (const LiveRequest &lr : live) finish(lr, status);
+        live.clear();
+        for (const PendingRequest &pr : pending) {
+            ServerResult r;
+            r.status = status;
+            results[pr.ticket] = std::move(r);
+            ++stats.failed;
+        }
+        pending.clear();
         cv_done.notify_all();
     }
 
-    // Build and enqueue one batch on a free slot (called without the lock).
-    int launch(ServerSlot &sl) {
-        const int count = static_cast<int>(sl.contracts.size());
-        sl.batch.reset_meta();
-        QMC_TRY(batch_build(plan, sl.contracts.data(), count, desc.precision, false, &sl.batch, sl.stream));
-        if (sl.h_stats_cap < 8u * count) {
-            if (sl.h_stats) cudaFreeHost(sl.h_stats);
-            sl.h_stats = nullptr;
-            QMC_CUDA(cudaMallocHost(&sl.h_stats, sizeof(double) * 8 * count));
-            sl.h_stats_cap = 8u * count;
+    // finished requests: flag == seq + 1
+    void harvest() {
+        bool any = false;
+        for (auto it = live.begin(); it != live.end();) {
+            if (__atomic_load_n(h_done + it->slot, __ATOMIC_ACQUIRE) == it->seq + 1) {
+                finish(*it, QMCCPW_OK);
+                it = live.erase(it);
+                any = true;
+            } else {
+                ++it;
+            }
         }
-        if (sl.h_per_cap < 4u * sl.batch.total_reps) {
-            if (sl.h_per) cudaFreeHost(sl.h_per);
-            sl.h_per = nullptr;
-            QMC_CUDA(cudaMallocHost(&sl.h_per, sizeof(double) * 4 * sl.batch.total_reps));
-            sl.h_per_cap = 4u * sl.batch.total_reps;
+        if (any) {
+            __atomic_store_n(&h_ctl->oldest_live, oldest_live(), __ATOMIC_RELEASE);
+            cv_done.notify_all();
         }
-        QMC_TRY(batch_enqueue(&sl.batch, sl.stream));
-        const BatchBuffers &B = *sl.batch.buf;
-        QMC_CUDA(cudaMemcpyAsync(sl.h_stats, B.stats.ptr, sizeof(double) * 8 * count, cudaMemcpyDeviceToHost, sl.stream));
-        QMC_CUDA(cudaMemcpyAsync(sl.h_per, B.per_rep.ptr, sizeof(double) * 4 * sl.batch.total_reps,
-                                 cudaMemcpyDeviceToHost, sl.stream));
-        QMC_CUDA(cudaLaunchHostFunc(sl.stream, &QmcServer::on_done, &sl));
+    }
+
+    void publish(PendingRequest &pr, uint64_t arena_off) {
+        const uint64_t seq = next_seq++;
+        const uint64_t slot = seq & (cap - 1);
+        ServeRequest *e = h_ring + slot;
+        __atomic_store_n(&e->seq, ~0ull, __ATOMIC_RELAXED);
+        std::atomic_thread_fence(std::memory_order_release);
+        e->first_ticket = next_first_ticket;
+        e->items = pr.items;
+        e->tile_sums = reinterpret_cast<double *>(arena_buf.as<unsigned char>() + arena_off);
+        e->out = d_out + slot * out_stride;
+        e->c = pr.c;
+        __atomic_store_n(&e->seq, seq, __ATOMIC_RELEASE);
+        next_first_ticket += pr.items;
+        __atomic_store_n(&h_ctl->published_seq, seq + 1, __ATOMIC_RELEASE);
+        __atomic_store_n(&h_ctl->published_tickets, next_first_ticket, __ATOMIC_RELEASE);
+        LiveRequest lr;
+        lr.ticket = pr.ticket;
+        lr.seq = seq;
+        lr.slot = slot;
+        lr.arena_off = arena_off;
+        lr.bytes = pr.bytes;
+        lr.R = pr.in.R;
+        lr.point_dates = pr.in.N * static_cast<uint64_t>(pr.in.R) * static_cast<uint64_t>(pr.in.option.d);
+        live.push_back(lr);
+    }
+
+    // admission in arrival order: a free ring entry (the one of request
+    // seq - cap finished, with every request before it) and arena space
+    void admit() {
+        while (!pending.empty() && next_seq - oldest_live() < cap &&
+               static_cast<int64_t>(live.size()) < desc.max_inflight) {
+            uint64_t off = 0;
+            if (!arena.alloc(pending.front().bytes, &off)) break;
+            publish(pending.front(), off);
+            pending.pop_front();
+        }
+    }
+
+    int launch() {
+        ServeParams sp{};
+        sp.ring = d_ring;
+        sp.cap = cap;
+        sp.ctl = d_ctl;
+        sp.done = d_done;
+        sp.exit_rec = d_exit;
+        sp.st = state.as<ServeState>();
+        sp.done_items = reinterpret_cast<unsigned long long *>(state.as<unsigned char>() + sizeof(ServeState));
+        sp.sobol_table = plan->table.as<uint32_t>();
+        sp.sobol_shift = plan->shift.as<uint32_t>();
+        sp.jstride = plan->jstride;
+        sp.launch = ++launch_no;
+        sp.idle_ns = static_cast<uint64_t>(desc.idle_limit_us) * 1000u;
+        QMC_CUDA(static_cast<cudaError_t>(launch_serve(sp, desc.precision, smem, grid, stream)));
+        QMC_CUDA(cudaEventRecord(exit_ev, stream));
+        running = true;
+        ++stats.launches;
         return QMCCPW_OK;
+    }
+
+    // one turn of the host side (under mu): exit, finished requests,
+    // admission, and a launch when published work has no kernel
+    void step() {
+        check_exit();
+        if (broken) return;
+        harvest();
+        admit();
+        if (!running && !live.empty()) {
+            const int rc = launch();
+            if (rc != QMCCPW_OK) fail_live(rc);
+        }
     }
 
     void run() {
         cudaSetDevice(plan->device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
-            for (auto &sl : slots)
-                if (sl->busy && sl->done.load()) retire(*sl);
-            for (auto &slp : slots) {
-                ServerSlot &sl = *slp;
-                if (sl.busy || pending.empty()) continue;
-                // admission: requests in arrival order while the batch fits the budget
-                sl.contracts.clear();
-                sl.tickets.clear();
-                uint64_t bytes = 0;
-                while (!pending.empty() && static_cast<int>(sl.contracts.size()) < desc.max_batch_contracts) {
-                    const uint64_t need = bytes_of(pending.front().second);
-                    if (!sl.contracts.empty() && bytes + need > desc.max_batch_bytes) break;
-                    bytes += need;
-                    sl.tickets.push_back(pending.front().first);
-                    sl.contracts.push_back(pending.front().second);
-                    pending.pop_front();
-                }
-                sl.busy = true;
-                ++stats.batches;
-                lk.unlock();
-                const int rc = launch(sl);
-                lk.lock();
-                if (rc != QMCCPW_OK) fail_all(sl, rc);
-            }
-            bool any_busy = false;
-            for (auto &sl : slots) any_busy |= sl->busy;
-            if (stopping && pending.empty() && !any_busy) break;
-            cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] {
-                if (stopping && pending.empty()) return true;
-                for (auto &sl : slots) {
-                    if (sl->busy && sl->done.load()) return true;
-                    if (!sl->busy && !pending.empty()) return true;
-                }
-                return false;
-            });
+            step();
+            if (stopping && pending.empty() && live.empty()) break;
+            const bool busy = !live.empty() || !pending.empty();
+            cv_work.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::microseconds(2000));
         }
+        // every request is finished: ask the kernel to leave and wait for it
+        __atomic_store_n(&h_ctl->stop, 1u, __ATOMIC_RELEASE);
+        lk.unlock();
+        cudaStreamSynchronize(stream);
+        lk.lock();
+        check_exit();
     }
 
+    int init(qmccpw_plan_s *p, const qmccpw_server_desc &d);
+
     ~QmcServer() {
-        for (auto &sl : slots) {
-            if (sl->stream) {
-                cudaStreamSynchronize(sl->stream);
-                cudaStreamDestroy(sl->stream);
-            }
-            if (sl->h_stats) cudaFreeHost(sl->h_stats);
-            if (sl->h_per) cudaFreeHost(sl->h_per);
+        if (stream) {
+            cudaStreamSynchronize(stream);
+            cudaStreamDestroy(stream);
         }
+        if (exit_ev) cudaEventDestroy(exit_ev);
+        for (void *h : {static_cast<void *>(h_ring), static_cast<void *>(h_ctl), static_cast<void *>(h_done),
+                        static_cast<void *>(h_exit), static_cast<void *>(h_out)})
+            if (h) cudaFreeHost(h);
     }
 };
 
 namespace {
 
 int fill_result(const ServerResult &r, qmccpw_result *out) {
-    if (r.status != QMCCPW_OK) return fail(r.status, "the request's batch failed");
+    if (r.status != QMCCPW_OK) return fail(r.status, "the request failed on the device");
     std::memcpy(out->mean, r.mean, sizeof(r.mean));
     std::memcpy(out->se, r.se, sizeof(r.se));
     if (out->per_replicate) std::memcpy(out->per_replicate, r.per_rep.data(), sizeof(double) * r.per_rep.size());
     return QMCCPW_OK;
 }
+
+// Device scratch of one request: its tile slots and its replicate estimates.
+uint64_t serve_bytes(uint64_t items, int R) { return (items + static_cast<uint64_t>(R)) * 32u; }
+
+// Largest dynamic shared memory of any contract the plan accepts in this precision.
+size_t serve_smem(const qmccpw_plan_s *p, int precision) {
+    size_t m = 0;
+    for (int cons : {QMCCPW_BB, QMCCPW_STD, QMCCPW_PCA, QMCCPW_BB_LEAD, QMCCPW_PCA_LEAD})
+        for (int d = 1; d <= p->d_max; ++d) {
+            if (is_lead(cons) && d + 1 > QMCCPW_D_LIMIT) continue;
+            m = std::max(m, fused_smem_bytes(precision, cons, d - 1, contract_tile_log2(p, precision, cons, d)));
+        }
+    return m;
+}
+
+}  // namespace
+
+int QmcServer::init(qmccpw_plan_s *p, const qmccpw_server_desc &d) {
+    plan = p;
+    desc = d;
+    if (desc.max_inflight == 0) desc.max_inflight = 1024;
+    if (desc.idle_limit_us == 0) desc.idle_limit_us = 20000;
+    if (desc.max_inflight_bytes == 0) desc.max_inflight_bytes = uint64_t(256) << 20;
+    // ring entries: a power of two >= max_inflight, fewer when the host-mapped
+    // results (R_max x 4 + 8 doubles per entry) would pass 256 MiB
+    out_stride = 4u * static_cast<uint64_t>(plan->r_max) + 8u;
+    cap = 1;
+    while (cap < static_cast<uint64_t>(desc.max_inflight)) cap <<= 1;
+    while (cap > 1 && cap * out_stride * sizeof(double) > (uint64_t(256) << 20)) cap >>= 1;
+    if (static_cast<uint64_t>(desc.max_inflight) > cap) desc.max_inflight = static_cast<int32_t>(cap);
+    QMC_CUDA(cudaSetDevice(plan->device));
+    if (!host_alloc_mapped(&h_ring, &d_ring, cap) || !host_alloc_mapped(&h_ctl, &d_ctl, 1) ||
+        !host_alloc_mapped(&h_done, &d_done, cap) || !host_alloc_mapped(&h_exit, &d_exit, 1) ||
+        !host_alloc_mapped(&h_out, &d_out, cap * out_stride))
+        return fail(QMCCPW_ERR_OOM, "cudaHostAlloc of the serving ring failed");
+    for (uint64_t i = 0; i < cap; ++i) h_ring[i].seq = ~0ull;
+    QMC_TRY(state.alloc(sizeof(ServeState) + sizeof(unsigned long long) * cap));
+    QMC_TRY(arena_buf.alloc(desc.max_inflight_bytes));
+    arena.init(desc.max_inflight_bytes);
+    QMC_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    QMC_CUDA(cudaEventCreateWithFlags(&exit_ev, cudaEventDisableTiming));
+    QMC_CUDA(cudaMemsetAsync(state.ptr, 0, state.bytes, stream));
+    QMC_CUDA(cudaStreamSynchronize(stream));
+    smem = serve_smem(plan, desc.precision);
+    cudaDeviceProp prop{};
+    QMC_CUDA(cudaGetDeviceProperties(&prop, plan->device));
+    QMC_CUDA(static_cast<cudaError_t>(serve_prepare(desc.precision, prop.sharedMemPerBlockOptin)));
+    int per_sm = 0;
+    QMC_CUDA(static_cast<cudaError_t>(serve_occupancy(desc.precision, smem, &per_sm)));
+    if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "the serving kernel does not fit on an SM");
+    grid = std::min(kServeMaxGrid, per_sm * plan->sm_count);
+    return QMCCPW_OK;
+}
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // Allocation-free form (qmccpw_greeks_noalloc): every per-call device array
@@ -1309,22 +1487,16 @@ int qmccpw_server_start(qmccpw_plan_t plan, const qmccpw_server_desc *desc) {
     if (desc->reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "reserved must be 0");
     if (desc->precision < QMCCPW_FP64 || desc->precision > QMCCPW_MIXED_TC_TF32X3)
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
-    if (desc->max_inflight < 0 || desc->max_inflight > 8) return fail(QMCCPW_ERR_INVALID_ARG, "max_inflight out of 0..8");
+    if (is_tc(desc->precision))
+        return fail(QMCCPW_ERR_UNSUPPORTED, "the serving loop runs the CUDA-core kernels: precision FP64 or MIXED");
+    if (desc->max_inflight < 0 || desc->max_inflight > 4096)
+        return fail(QMCCPW_ERR_INVALID_ARG, "max_inflight out of 0..4096");
+    if (desc->idle_limit_us < 0 || desc->idle_limit_us > 10000000)
+        return fail(QMCCPW_ERR_INVALID_ARG, "idle_limit_us out of 0..10^7");
     auto sv = std::make_unique<QmcServer>();
-    sv->plan = plan;
-    sv->desc = *desc;
-    if (sv->desc.max_inflight == 0) sv->desc.max_inflight = 2;
-    if (sv->desc.max_batch_contracts <= 0) sv->desc.max_batch_contracts = 1024;
-    if (sv->desc.max_batch_bytes == 0) sv->desc.max_batch_bytes = uint64_t(256) << 20;
-    QMC_CUDA(cudaSetDevice(plan->device));
-    for (int i = 0; i < sv->desc.max_inflight; ++i) {
-        auto sl = std::make_unique<ServerSlot>();
-        sl->owner = sv.get();
-        QMC_CUDA(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
-        sv->slots.push_back(std::move(sl));
-    }
+    QMC_TRY(sv->init(plan, *desc));
     QmcServer *raw = sv.get();
-    sv->worker = std::thread([raw] { raw->run(); });
+    sv->monitor = std::thread([raw] { raw->run(); });
     plan->server = sv.release();
     return QMCCPW_OK;
 }
@@ -1335,14 +1507,24 @@ int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t 
     QmcServer *sv = plan->server;
     if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
     QMC_TRY(validate_qc(plan, *contract, sv->desc.precision, false));
-    if (sv->bytes_of(*contract) > plan->workspace_bytes)
-        return fail(QMCCPW_ERR_OOM, "the request needs more device scratch than the plan's workspace budget");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stopping) return fail(QMCCPW_ERR_INVALID_ARG, "the server is stopping");
-    *ticket = sv->next_ticket++;
-    sv->pending.emplace_back(*ticket, *contract);
-    sv->known[*ticket] = true;
+    if (sv->broken) return fail(QMCCPW_ERR_CUDA, "the serving kernel failed; stop the server");
+    PendingRequest pr;
+    pr.in = *contract;
+    QMC_TRY(build_contract(plan, *contract, sv->desc.precision, 0, 0, &pr.c));
+    if (fused_smem_bytes(sv->desc.precision, contract->construction, pr.c.n, pr.c.tile_log2) > sv->smem)
+        return fail(QMCCPW_ERR_UNSUPPORTED, "the request's tile needs more shared memory than the serving kernel has");
+    pr.items = static_cast<uint64_t>(pr.c.R) * static_cast<uint64_t>(pr.c.tiles);
+    pr.bytes = serve_bytes(pr.items, pr.c.R);
+    if (((pr.bytes + 255) & ~uint64_t(255)) > sv->desc.max_inflight_bytes)
+        return fail(QMCCPW_ERR_OOM, "the request needs more device scratch than max_inflight_bytes");
+    pr.ticket = sv->next_ticket_id++;
+    *ticket = pr.ticket;
+    sv->known[pr.ticket] = true;
+    sv->pending.push_back(pr);
     ++sv->stats.submitted;
+    sv->step();  // publish now if it fits, launching the kernel if none runs
     sv->cv_work.notify_all();
     return QMCCPW_OK;
 }
@@ -1354,6 +1536,7 @@ int qmccpw_poll(qmccpw_plan_t plan, uint64_t ticket, qmccpw_result *out) {
     if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (!sv->known.count(ticket)) return fail(QMCCPW_ERR_INVALID_ARG, "unknown or already collected ticket");
+    sv->step();
     auto it = sv->results.find(ticket);
     if (it == sv->results.end()) return QMCCPW_NOT_READY;
     const int rc = fill_result(it->second, out);
@@ -1369,9 +1552,13 @@ int qmccpw_wait(qmccpw_plan_t plan, uint64_t ticket, int32_t timeout_ms, qmccpw_
     if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
     std::unique_lock<std::mutex> lk(sv->mu);
     if (!sv->known.count(ticket)) return fail(QMCCPW_ERR_INVALID_ARG, "unknown or already collected ticket");
-    const bool ready = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
-                                            [&] { return sv->results.count(ticket) > 0; });
-    if (!ready) return fail(QMCCPW_ERR_TIMEOUT, "the request is not finished");
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (true) {
+        sv->step();
+        if (sv->results.count(ticket)) break;
+        if (std::chrono::steady_clock::now() >= deadline) return fail(QMCCPW_ERR_TIMEOUT, "the request is not finished");
+        sv->cv_done.wait_for(lk, std::chrono::microseconds(20));
+    }
     auto it = sv->results.find(ticket);
     const int rc = fill_result(it->second, out);
     sv->results.erase(it);
@@ -1385,8 +1572,11 @@ int qmccpw_server_get_stats(qmccpw_plan_t plan, qmccpw_server_stats *out) {
     QmcServer *sv = plan->server;
     if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
     std::lock_guard<std::mutex> lk(sv->mu);
+    sv->check_exit();
     *out = sv->stats;
     out->pending = sv->pending.size();
+    out->inflight = sv->live.size();
+    out->running = sv->running ? 1u : 0u;
     return QMCCPW_OK;
 }
 
@@ -1400,7 +1590,7 @@ int qmccpw_server_stop(qmccpw_plan_t plan) {
         sv->stopping = true;
         sv->cv_work.notify_all();
     }
-    sv->worker.join();
+    sv->monitor.join();
     plan->server = nullptr;
     delete sv;
     return QMCCPW_OK;

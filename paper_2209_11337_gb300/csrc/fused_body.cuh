@@ -111,8 +111,11 @@ __device__ void bridge_store(const ContractDev &c, T *zw, int stride) {
 // sqrt(dt) sum_k Ahat[i][k] z_k over the d components (z_1 = 0 in slot 1),
 // into the second row.  FP64: the G threads of a point take every G-th date.
 // Float: they take blocks of 8 consecutive dates, each k step reading the
-// block's 8 entries of row k of A^T as two float4 (one load per four FMAs;
-// each date's sum still runs over k in order).
+// block's 8 entries of row k of A^T (hi and lo parts) as float4 pairs; the
+// factor is carried as hi + lo because its float rounding would be one fixed
+// perturbation of the covariance of the rest, which the conditioning on the
+// leading component makes the dominant error.  Each date's sum runs over k
+// in order.
 template <typename T>
 __device__ void lead_pca_store(const ContractDev &c, const T *zw, T *rbuf, int stride) {
     const int P = 1 << c.tile_log2;
@@ -132,15 +135,18 @@ __device__ void lead_pca_store(const ContractDev &c, const T *zw, T *rbuf, int s
     } else {
         const int n_pad = (nd + 15) & ~15;  // A^T rows padded with zeros to a multiple of 16
         const float4 *AT = reinterpret_cast<const float4 *>(c.pcaT32);
+        const float4 *ATlo = reinterpret_cast<const float4 *>(c.pcaT32lo);
         const float sh = c.ff_sqrt_t1[0], sl = c.ff_sqrt_t1[1];
         for (int blk = grp; 8 * blk < nd; blk += G) {
-            float w[8];
+            float w[8], wl[8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) w[r] = 0.0f;
-            const float4 *a = AT + static_cast<size_t>(n_pad / 4) + 2 * blk;  // row k = 2 (index 1)
-            for (int k = 2; k <= nd; ++k, a += n_pad / 4) {
+            for (int r = 0; r < 8; ++r) w[r] = wl[r] = 0.0f;
+            const size_t first = static_cast<size_t>(n_pad / 4) + 2 * blk;  // row k = 2 (index 1)
+            const float4 *a = AT + first, *al = ATlo + first;
+            for (int k = 2; k <= nd; ++k, a += n_pad / 4, al += n_pad / 4) {
                 const float z = row[k];
                 const float4 a0 = __ldg(a), a1 = __ldg(a + 1);
+                const float4 l0 = __ldg(al), l1 = __ldg(al + 1);
                 w[0] = fmaf(a0.x, z, w[0]);
                 w[1] = fmaf(a0.y, z, w[1]);
                 w[2] = fmaf(a0.z, z, w[2]);
@@ -149,11 +155,20 @@ __device__ void lead_pca_store(const ContractDev &c, const T *zw, T *rbuf, int s
                 w[5] = fmaf(a1.y, z, w[5]);
                 w[6] = fmaf(a1.z, z, w[6]);
                 w[7] = fmaf(a1.w, z, w[7]);
+                wl[0] = fmaf(l0.x, z, wl[0]);
+                wl[1] = fmaf(l0.y, z, wl[1]);
+                wl[2] = fmaf(l0.z, z, wl[2]);
+                wl[3] = fmaf(l0.w, z, wl[3]);
+                wl[4] = fmaf(l1.x, z, wl[4]);
+                wl[5] = fmaf(l1.y, z, wl[5]);
+                wl[6] = fmaf(l1.z, z, wl[6]);
+                wl[7] = fmaf(l1.w, z, wl[7]);
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const int i = 8 * blk + r + 1;
-                if (i <= nd) out[i] = fmaf(w[r], sh, w[r] * sl);
+                // (w + wl) (sh + sl), the small products first
+                if (i <= nd) out[i] = fmaf(w[r], sh, fmaf(wl[r], sh, w[r] * sl));
             }
         }
     }
@@ -639,7 +654,7 @@ __device__ __forceinline__ double reduce_replicate(const double *__restrict__ fi
                                                    Neumaier (*part)[4]) {
     Neumaier acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (uint64_t t = threadIdx.x; t < tiles; t += 256)
-        for (int g = 0; g < 4; ++g) acc[g].add(first[t * 4 + g]);
+        for (int g = 0; g < 4; ++g) acc[g].add(__ldcg(first + t * 4 + g));  // L2: written by other CTAs
     for (int g = 0; g < 4; ++g) part[threadIdx.x][g] = acc[g];
     __syncthreads();
     for (int half = 128; half > 0; half >>= 1) {

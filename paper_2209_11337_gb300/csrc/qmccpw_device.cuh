@@ -79,29 +79,37 @@ __device__ __forceinline__ float2 rcp_nr2(float2 x) {
 }
 
 // e^x for |x| <= 86: 2^k e^r, k the nearest integer to x log2 e, r = x - k ln2
-// by two FMAs (ln2 as a float pair), e^r by the degree-8 polynomial (c0 = c1
-// = 1 exact), 2^k added to the exponent field (k in the low bits of the
-// magic sum, shifted out of its high bits).
+// with ln2 = hi + lo: r1 = x - k hi is exact (a multiple of 2^-24 below 1/2
+// in magnitude), e^r = (1 + r1 q(r1))(1 + delta) with the degree-8
+// polynomial 1 + r q(r) (c0 = c1 = 1 exact) and delta = -k lo, i.e.
+// 1 + [r1 q + delta (1 + r1 q)]: the small bracket term meets the unrounded
+// product r1 q in the last FMA.  Added to r1 instead, delta sits below half
+// an ulp of the float r1 for most arguments and is dropped the same way for
+// every x of that k (e^x near x = 1.8, k = 3, came out 5.6e-9 low on
+// average); added to the rounded result, the same.  2^k goes to the exponent
+// field (k in the low bits of the magic sum, shifted out of its high bits).
 __device__ __forceinline__ float exp_f(float x) {
     constexpr float c[] = QMC_EXP_POLY;
     const float m = fmaf(x, kLog2e, kMagic);
     const float nk = kMagic - m;  // -k, exact
-    float r = fmaf(nk, kLn2Hi, x);
-    r = fmaf(nk, kLn2Lo, r);
-    float p = c[8];
+    const float r = fmaf(nk, kLn2Hi, x);
+    float q = c[8];
 #pragma unroll
-    for (int i = 7; i >= 0; --i) p = fmaf(p, r, c[i]);
+    for (int i = 7; i >= 1; --i) q = fmaf(q, r, c[i]);
+    const float delta = nk * kLn2Lo;
+    const float p = 1.0f + fmaf(q, r, fmaf(delta, q * r, delta));
     return __uint_as_float(__float_as_uint(p) + (__float_as_uint(m) << 23));
 }
 __device__ __forceinline__ float2 exp_f2(float2 x) {
     constexpr float c[] = QMC_EXP_POLY;
     const float2 m = fma2(x, f2(kLog2e), f2(kMagic));
     const float2 nk = fma2(m, f2(-1.0f), f2(kMagic));  // -k, exact
-    float2 r = fma2(nk, f2(kLn2Hi), x);
-    r = fma2(nk, f2(kLn2Lo), r);
-    float2 p = f2(c[8]);
+    const float2 r = fma2(nk, f2(kLn2Hi), x);
+    float2 q = f2(c[8]);
 #pragma unroll
-    for (int i = 7; i >= 0; --i) p = fma2(p, r, f2(c[i]));
+    for (int i = 7; i >= 1; --i) q = fma2(q, r, f2(c[i]));
+    const float2 delta = mul2(nk, f2(kLn2Lo));
+    const float2 p = add2(f2(1.0f), fma2(q, r, fma2(delta, mul2(q, r), delta)));
     return make_float2(__uint_as_float(__float_as_uint(p.x) + (__float_as_uint(m.x) << 23)),
                        __uint_as_float(__float_as_uint(p.y) + (__float_as_uint(m.y) << 23)));
 }
@@ -794,28 +802,32 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
         }
     }
     const ff ys = ff_mul(ff_of(c.ff_sig_sdt), x);
-    const float dt = c.ff_dt[0];
     float X1 = 0, X2 = 0, SP = 0, SA = 0, V1 = 0, B = 0;
     ff Xs{0.0f, 0.0f}, W0{0.0f, 0.0f};
     for (int j = 0; j < d; ++j) {
         const ff as = lead_loading_ff(c, j);                  // a_j sqrt(dt)
         const ff b = ff_mul_ff(as, ff{sh, sl});               // b_j = sigma a_j sqrt(dt)
-        const float t = small_uint_to_float(static_cast<uint32_t>(j + 1)) * dt, Rj = R[j + 1];
+        const ff bb = ff_mul_ff(b, b);
+        const ff sa2 = ff_mul_ff(b, as);                      // sigma a_j^2 dt
+        const float nf = small_uint_to_float(static_cast<uint32_t>(j + 1)), Rj = R[j + 1];
         const float e = fx::exp_f(expo(j, ys));               // c_j e^{b_j x*}
         float Q = mk[kMillsTerms - 1];
 #pragma unroll
         for (int k = kMillsTerms - 2; k >= 0; --k) Q = fmaf(Q, b.hi, mk[k]);
         const float P = fmaf(Q, b.hi, Q * b.lo);              // M(x* - b) - M(x*) = b Q(b)
-        const float a = as.hi;
-        const float w = fmaf(sh, a * a, fmaf(-sh, t, Rj));
+        // w_j = R_j + sigma a_j^2 - sigma t_j and B_j = R_j + a_j x* - sigma t_j with
+        // sigma t_j = (j + 1)(sigma dt) and the loadings as float pairs, the small
+        // parts first: a float constant here would shift every point's vega alike
+        const float w = Rj + fmaf(nf, c.ff_nsig_dt[0], sa2.hi) + fmaf(nf, c.ff_nsig_dt[1], sa2.lo);
+        const float Bj = Rj + fmaf(as.hi, x, fmaf(nf, c.ff_nsig_dt[0], fmaf(as.lo, x, nf * c.ff_nsig_dt[1])));
         Xs = ff_add(Xs, ff{e, 0.0f});
-        X1 = fmaf(b.hi, e, X1);
-        X2 = fmaf(b.hi * b.hi, e, X2);
+        X1 = fmaf(b.hi, e, fmaf(b.lo, e, X1));
+        X2 = fmaf(bb.hi, e, fmaf(bb.lo, e, X2));
         SP = fmaf(e, P, SP);                       // sum e_j [M(x*-b_j) - M(x*)]
-        SA = fmaf(a, e, SA);
+        SA = fmaf(as.hi, e, fmaf(as.lo, e, SA));
         V1 = fmaf(e * w, P, V1);
         W0 = ff_add(W0, ff{e * w, 0.0f});          // sum e_j w_j: signs mixed, kept in float-float
-        B = fmaf(e, fmaf(a, x, fmaf(-sh, t, Rj)), B);
+        B = fmaf(e, Bj, B);
     }
     // X(x*) - K of the float switch point
     const double resid = (static_cast<double>(Xs.hi) + Xs.lo) - K;

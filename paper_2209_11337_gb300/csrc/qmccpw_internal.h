@@ -73,6 +73,7 @@ struct ContractDev {
     const int32_t *level_start;
     const double *pca64;                 // n x n row-major
     const float *pcaT32;                 // A^T as float, [k][i], i padded to a multiple of 16 with zeros
+    const float *pcaT32lo;               // A^T - float(A^T) in the same layout (leading-coordinate PCA)
     const void *tc_operand;              // tensor-core PCA: Ahat hi then lo, K-major core-matrix layout
     const double *lead_a64;              // leading-coordinate constructions: its loading on dates 1..d, unit spacing
     const float *lead_a32;               // the same as float pairs (hi, lo)
@@ -114,7 +115,7 @@ struct ContractDev {
     float ff_kg_bin[2];                  // disc / (S0^2 a sqrt(2 pi))
     float ff_kphi[2];                    // disc / sqrt(2 pi)
     // the leading-coordinate float path
-    float ff_sig[2], ff_lnS0d[2], ff_lnK[2], ff_dt[2];
+    float ff_sig[2], ff_lnS0d[2], ff_lnK[2];
 };
 
 // hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)
@@ -169,6 +170,84 @@ inline int tile_row_elems(int construction, int n) {
 size_t fused_smem_bytes(int precision, int construction, int n, int tile_log2);
 int fused_set_smem_limit(int precision, size_t optin_bytes);  // optin_bytes: the device's per-block opt-in maximum
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
+
+// ----------------------------------------------------------------------------
+// Device-resident serving loop (serve.cu; host side in api.cu)
+// ----------------------------------------------------------------------------
+// The work items of every request, in publication order, are numbered by
+// one global ticket sequence: request s owns tickets [first_ticket,
+// first_ticket + items), item = replicate-major (replicate, tile) as in a
+// batch.  The host writes a request into a ring of host-mapped entries, then
+// publishes it by raising published_seq and published_tickets.  A
+// persistent kernel's CTAs take tickets from a device counter, wait (bounded
+// by %globaltimer) until their ticket is published, run the item and count
+// it; the CTA that finishes a request's last item reduces it and raises the
+// request's completion flag.  A CTA that waits longer than the idle limit
+// (or sees the stop word) records the ticket it holds and leaves; the last
+// one to leave carries every held ticket over to the next launch, which
+// hands them out first, so no published item is lost when the kernel exits
+// and the host launches it again.
+constexpr int kServeMaxGrid = 1024;          // CTAs of one serving launch at most
+constexpr int kServeRetryCap = 2 * kServeMaxGrid;
+
+// One ring entry (host-mapped; the host writes it before publication and
+// while seq holds ~0, so a reader that sees the same seq before and after
+// reading knows the entry was not being rewritten).
+struct ServeRequest {
+    uint64_t seq;                            // request number
+    uint64_t first_ticket, items;            // its tickets
+    double *tile_sums;                       // device: items x 4 tile slots, then R x 4 replicate estimates
+    double *out;                             // host-mapped: R x 4 replicate estimates, mean[4], se[4]
+    ContractDev c;                           // rep_first set; item_base and rep_base unused
+};
+
+// Words the host writes (host-mapped).
+struct ServeControl {
+    uint64_t published_tickets;              // tickets below it belong to published requests
+    uint64_t published_seq;                  // requests below it are in the ring
+    uint64_t oldest_live;                    // requests below it are finished (their entries may be reused)
+    uint32_t stop;                           // nonzero: every CTA leaves at its next wait
+    uint32_t pad;
+};
+
+// Written by the last CTA of a launch (host-mapped).
+struct ServeExit {
+    uint32_t launch;                         // the launch's number
+    uint32_t reason;                         // 1 idle limit, 2 stop word, 3 carried tickets above capacity,
+                                             // 4 a ticket without a request in the ring
+    uint64_t next_ticket;                    // first ticket never handed out
+    uint32_t carried;                        // tickets carried to the next launch
+    uint32_t pad;
+};
+
+// Device-memory state carried from one launch to the next (zeroed once).
+struct ServeState {
+    unsigned long long next_ticket;          // fresh tickets
+    unsigned int retry_count;                // carried tickets of this launch, handed out first
+    unsigned int retry_next;
+    unsigned int exited;                     // CTAs of this launch that have left
+    unsigned int bad_ticket;                 // nonzero: a CTA found no request for its ticket (exit reason 4)
+    unsigned long long retry[kServeRetryCap];
+    unsigned long long abandoned[kServeMaxGrid];  // the ticket each CTA held when it left
+};
+
+struct ServeParams {
+    const ServeRequest *ring;                // host-mapped, cap entries
+    uint64_t cap;                            // ring entries, a power of two
+    const ServeControl *ctl;                 // host-mapped
+    uint64_t *done;                          // host-mapped, per entry: seq + 1 once that request finished
+    ServeExit *exit_rec;                     // host-mapped
+    ServeState *st;                          // device
+    unsigned long long *done_items;          // device, per entry: finished items of the request there
+    const uint32_t *sobol_table;
+    const uint32_t *sobol_shift;
+    int32_t jstride;
+    uint32_t launch;
+    uint64_t idle_ns;                        // a CTA leaves after waiting this long for a published ticket
+};
+int launch_serve(const ServeParams &p, int precision, size_t smem_bytes, int grid, void *stream);
+int serve_prepare(int precision, size_t optin_bytes);  // raise the dynamic shared-memory limit
+int serve_occupancy(int precision, size_t smem_bytes, int *blocks_per_sm);
 
 // Tensor-core PCA (pca_tc.cu).  kind 0: bf16 split (4 products), 1: tf32
 // split (3 products), both n <= 64 with Ahat resident; kinds 2 (bf16) and 3

@@ -222,7 +222,6 @@ void contract_constants(ContractDev &c) {
     split_ff(c.sigma, c.ff_sig);
     split_ff(c.ln_lead_c0, c.ff_lnS0d);
     split_ff(c.ln_K, c.ff_lnK);
-    split_ff(c.dt, c.ff_dt);
 }
 
 }  // namespace qmccpw

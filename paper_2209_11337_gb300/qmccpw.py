@@ -98,13 +98,14 @@ class qmccpw_contract(ctypes.Structure):
 
 class qmccpw_server_desc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
-                ("max_batch_contracts", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("max_batch_bytes", ctypes.c_uint64)]
+                ("idle_limit_us", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_inflight_bytes", ctypes.c_uint64)]
 
 
 class qmccpw_server_stats(ctypes.Structure):
-    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
-                ("batches", ctypes.c_uint64), ("point_dates", ctypes.c_uint64), ("pending", ctypes.c_uint64)]
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "submitted", "completed", "failed", "launches", "idle_exits", "point_dates", "pending", "inflight",
+        "running")]
 
 
 class qmccpw_pipe_peaks(ctypes.Structure):
@@ -331,9 +332,10 @@ def qmccpw_greeks_noalloc(plan, type: int, d: int, K: float, T: float, S0: float
                                            precision, ctypes.c_void_p(out_device_ptr), stream))
 
 
-def qmccpw_server_start(plan, precision: int = QMCCPW_MIXED, max_inflight: int = 2,
-                        max_batch_contracts: int = 1024, max_batch_bytes: int = 0) -> None:
-    desc = qmccpw_server_desc(precision, max_inflight, max_batch_contracts, 0, max_batch_bytes)
+def qmccpw_server_start(plan, precision: int = QMCCPW_MIXED, max_inflight: int = 0, idle_limit_us: int = 0,
+                        max_inflight_bytes: int = 0) -> None:
+    """Start the device-resident serving loop (0: the library's default for each limit)."""
+    desc = qmccpw_server_desc(precision, max_inflight, idle_limit_us, 0, max_inflight_bytes)
     _check(library().qmccpw_server_start(plan, ctypes.byref(desc)))
 
 

@@ -68,8 +68,8 @@ def test_lead_mixed_against_fp64(q, plan):
     bad = []
     for c, (a, _, _), (b, s, _) in zip(cs, m32, m64):
         if not np.all(np.abs(a - b) <= 0.1 * s):  # a NaN fails too
-            bad.append((c.label(), (np.abs(a - b) / s).tolist()))
-    assert not bad, bad
+            bad.append((c.label(), np.round(np.abs(a - b) / s, 3).tolist()))
+    assert not bad, "\n".join(f"{lab}: {err}" for lab, err in bad)
 
 
 def test_lead_batch_equals_alone_and_rejects_lookback(q, plan):

@@ -1,8 +1,11 @@
-"""Continuous-batching service: every request's result equals the result of
+"""Device-resident serving loop: every request's result equals the result of
 the same contract computed alone (bit-identical: a contract's tiles and
-their reduction order do not depend on the batch), with requests arriving
-from several threads while earlier batches are on the GPU."""
+their reduction order do not depend on what else runs), with requests
+arriving from several threads while earlier ones are on the GPU, admitted
+by device memory; the kernel leaves on its idle limit and is launched again
+when work arrives, losing no work item."""
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -36,8 +39,9 @@ def test_results_same_alone_and_in_the_mix(q, precision):
         cs = mix(48, 11 + precision)
         alone = [q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, c.construction, precision)
                  for c in cs]
-        q.qmccpw_server_start(plan, precision=precision, max_inflight=3, max_batch_contracts=7,
-                              max_batch_bytes=1 << 22)
+        # 256 KiB of device scratch holds a few requests at a time (the largest,
+        # d = 365 in FP64, about 66 KB): the rest wait for admission
+        q.qmccpw_server_start(plan, precision=precision, max_inflight=8, max_inflight_bytes=1 << 18)
         tickets = [None] * len(cs)
 
         def submit(idx):
@@ -56,7 +60,7 @@ def test_results_same_alone_and_in_the_mix(q, precision):
             assert np.array_equal(p, p1), c.label()
             assert np.array_equal(m, m1) and np.array_equal(s, s1)
         assert stats["completed"] == len(cs) and stats["failed"] == 0
-        assert stats["batches"] >= len(cs) // 7
+        assert stats["launches"] >= 1 and stats["inflight"] == 0 and stats["pending"] == 0
         assert stats["point_dates"] == sum(c.N * c.R * c.d for c in cs)
     finally:
         q.qmccpw_free(plan)
@@ -88,5 +92,69 @@ def test_poll_semantics_and_errors(q):
         q.qmccpw_server_stop(plan)                        # idempotent
         ref = q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, c.construction, 1)
         assert np.array_equal(res[2], ref[2])
+    finally:
+        q.qmccpw_free(plan)
+
+
+def test_tensor_core_precisions_are_not_served(q):
+    plan = q.qmccpw_plan(device=0, d_max=65, r_max=8, seed=W.SCRAMBLE_SEED)
+    try:
+        for prec in (2, 3):
+            with pytest.raises(q.QmcCpwError) as e:
+                q.qmccpw_server_start(plan, precision=prec)
+            assert e.value.code == q.QMCCPW_ERR_UNSUPPORTED
+    finally:
+        q.qmccpw_free(plan)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_idle_limit_runs_out_and_the_kernel_is_launched_again(q, precision):
+    """A 2 ms idle limit: after each burst the kernel's CTAs wait for a
+    published work item, the limit runs out and the launch ends (idle_exits);
+    the next burst launches it again, and the work items the leaving CTAs
+    held are handed out first.  Every result is the one computed alone."""
+    plan = q.qmccpw_plan(device=0, d_max=366, r_max=8, seed=W.SCRAMBLE_SEED)
+    try:
+        cs = mix(12, 31 + precision)
+        alone = [q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, c.construction, precision)
+                 for c in cs]
+        q.qmccpw_server_start(plan, precision=precision, idle_limit_us=2000)
+        got = []
+        for burst in range(3):
+            part = cs[4 * burst:4 * burst + 4]
+            tickets = [q.qmccpw_submit(plan, c) for c in part]
+            got += [q.qmccpw_wait(plan, t, c.R, 60000) for t, c in zip(tickets, part)]
+            deadline = time.time() + 5.0
+            while q.qmccpw_server_get_stats(plan)["running"] and time.time() < deadline:
+                time.sleep(0.005)
+            st = q.qmccpw_server_get_stats(plan)
+            assert st["running"] == 0, st
+            # every launch so far ended on the idle limit (more than one per burst
+            # only if a gap between two submissions passed the limit)
+            assert st["idle_exits"] >= burst + 1 and st["launches"] == st["idle_exits"], st
+        t0 = time.time()
+        q.qmccpw_server_stop(plan)
+        assert time.time() - t0 < 5.0
+        for c, (m, s, p), (m1, s1, p1) in zip(cs, got, alone):
+            assert np.array_equal(p, p1), c.label()
+            assert np.array_equal(m, m1) and np.array_equal(s, s1)
+    finally:
+        q.qmccpw_free(plan)
+
+
+def test_stop_ends_a_waiting_kernel(q):
+    """With a long idle limit the kernel stays up between requests; stop ends it
+    at its next wait (every wait also checks the stop word)."""
+    plan = q.qmccpw_plan(device=0, d_max=65, r_max=8, seed=W.SCRAMBLE_SEED)
+    try:
+        c = W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 12, 4, W.BB)
+        q.qmccpw_server_start(plan, precision=1, idle_limit_us=5000000)
+        q.qmccpw_wait(plan, q.qmccpw_submit(plan, c), c.R, 60000)
+        time.sleep(0.05)
+        st = q.qmccpw_server_get_stats(plan)
+        assert st["running"] == 1 and st["idle_exits"] == 0
+        t0 = time.time()
+        q.qmccpw_server_stop(plan)
+        assert time.time() - t0 < 2.0
     finally:
         q.qmccpw_free(plan)
