@@ -302,7 +302,9 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
     import queue
 
     reqs = W.arrivals(rate_hz=rate_hz, duration_s=warmup_s + duration_s, seed=seed, R=16)
-    q.qmccpw_server_start(plan, precision=precision, max_inflight=1024, max_inflight_bytes=256 << 20)
+    # the requests are bridge contracts: the MIXED kernel without the PCA product fits three CTAs per SM
+    q.qmccpw_server_start(plan, precision=precision, max_inflight=1024, max_inflight_bytes=256 << 20,
+                          constructions=[q.QMCCPW_BB])
     pilots = queue.Queue()
     mains = queue.Queue()
     lat, main_elems, Ns = [], [0], []

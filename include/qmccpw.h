@@ -305,12 +305,13 @@ int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t constructio
  * Sec. 7 proposes wrapping the estimator in a microservice; this is its GPU
  * side.  A persistent kernel runs on the plan's device while work arrives.
  * Requests (contracts) are written into a ring of pinned, host-mapped
- * entries and published through two host-written counters; the kernel's
- * CTAs take the published requests' work items (replicate, tile) in
- * publication order from one device counter, so a request that arrives while
- * others run fills the SMs as they free up, and the CTA that finishes a
- * request's last item reduces it on the device and raises the request's
- * completion flag in host-mapped memory.  Admission is in arrival order,
+ * entries and published through two host-written counters; one CTA of the
+ * kernel copies each new entry into device memory and republishes it there,
+ * and the other CTAs take the published requests' work items (replicate,
+ * tile) in publication order from one device counter, so a request that
+ * arrives while others run fills the SMs as they free up; the CTA that
+ * finishes a request's last item reduces it on the device and raises the
+ * request's completion flag in host-mapped memory.  Admission is in arrival order,
  * while the admitted requests' device scratch (32 bytes per tile slot and
  * per replicate: about 32 * R * N / P bytes, P the points per tile) fits
  * `max_inflight_bytes` and at most `max_inflight` requests are on the
@@ -331,7 +332,9 @@ typedef struct {
                                       r_max * 32 + 64 bytes of host-mapped results per request
                                       would pass 256 MiB */
     int32_t idle_limit_us;         /* the kernel leaves after this long without work, 1..10^7 (0: 20000) */
-    int32_t reserved;              /* must be 0 */
+    int32_t constructions;         /* accepted constructions, bit c for qmccpw_construction c (0: all);
+                                      MIXED without QMCCPW_PCA runs a kernel that fits three CTAs per SM
+                                      instead of two; other requests return UNSUPPORTED */
     uint64_t max_inflight_bytes;   /* device scratch of the requests on the device (0: 256 MiB) */
 } qmccpw_server_desc;
 

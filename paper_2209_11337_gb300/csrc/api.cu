@@ -610,6 +610,20 @@ int batch_collect(qmccpw_batch_s *b, qmccpw_result *out, cudaStream_t s) {
 // published.  submit/poll/wait do the same steps themselves, so a request
 // does not wait for the monitor's next turn.
 // ---------------------------------------------------------------------------
+// The serving kernel of a precision (serve_f32.cu, serve_f64.cu).
+int qmccpw::launch_serve(const ServeParams &p, int precision, bool with_pca, size_t smem_bytes, int grid,
+                         void *stream) {
+    return precision == QMCCPW_FP64 ? serve_f64_launch(p, smem_bytes, grid, stream)
+                                    : serve_f32_launch(p, with_pca, smem_bytes, grid, stream);
+}
+int qmccpw::serve_prepare(int precision, bool with_pca, size_t optin_bytes) {
+    return precision == QMCCPW_FP64 ? serve_f64_prepare(optin_bytes) : serve_f32_prepare(with_pca, optin_bytes);
+}
+int qmccpw::serve_occupancy(int precision, bool with_pca, size_t smem_bytes, int *blocks_per_sm) {
+    return precision == QMCCPW_FP64 ? serve_f64_occupancy(smem_bytes, blocks_per_sm)
+                                    : serve_f32_occupancy(with_pca, smem_bytes, blocks_per_sm);
+}
+
 struct ServerResult {
     int status = QMCCPW_OK;
     double mean[4] = {0, 0, 0, 0}, se[4] = {0, 0, 0, 0};
@@ -701,8 +715,9 @@ struct QmcServer {
     uint64_t *h_done = nullptr, *d_done = nullptr;
     ServeExit *h_exit = nullptr, *d_exit = nullptr;
     double *h_out = nullptr, *d_out = nullptr;  // cap x out_stride doubles
-    // device state and the tile-slot arena
-    DevBuf state, arena_buf;
+    // device state, the device copy of the ring, and the tile-slot arena
+    DevBuf state, dev_ring, arena_buf;
+    bool with_pca = true;  // the serving kernel carries the PCA product
     ArenaAllocator arena;
     cudaStream_t stream = nullptr;
     cudaEvent_t exit_ev = nullptr;
@@ -821,6 +836,7 @@ struct QmcServer {
     int launch() {
         ServeParams sp{};
         sp.ring = d_ring;
+        sp.dev_ring = dev_ring.as<ServeRequest>();
         sp.cap = cap;
         sp.ctl = d_ctl;
         sp.done = d_done;
@@ -832,7 +848,7 @@ struct QmcServer {
         sp.jstride = plan->jstride;
         sp.launch = ++launch_no;
         sp.idle_ns = static_cast<uint64_t>(desc.idle_limit_us) * 1000u;
-        QMC_CUDA(static_cast<cudaError_t>(launch_serve(sp, desc.precision, smem, grid, stream)));
+        QMC_CUDA(static_cast<cudaError_t>(launch_serve(sp, desc.precision, with_pca, smem, grid, stream)));
         QMC_CUDA(cudaEventRecord(exit_ev, stream));
         running = true;
         ++stats.launches;
@@ -896,11 +912,12 @@ int fill_result(const ServerResult &r, qmccpw_result *out) {
 // Device scratch of one request: its tile slots and its replicate estimates.
 uint64_t serve_bytes(uint64_t items, int R) { return (items + static_cast<uint64_t>(R)) * 32u; }
 
-// Largest dynamic shared memory of any contract the plan accepts in this precision.
-size_t serve_smem(const qmccpw_plan_s *p, int precision) {
+// Largest dynamic shared memory of any contract the plan accepts in this
+// precision among the constructions of `mask`.
+size_t serve_smem(const qmccpw_plan_s *p, int precision, int32_t mask) {
     size_t m = 0;
     for (int cons : {QMCCPW_BB, QMCCPW_STD, QMCCPW_PCA, QMCCPW_BB_LEAD, QMCCPW_PCA_LEAD})
-        for (int d = 1; d <= p->d_max; ++d) {
+        for (int d = 1; d <= p->d_max && (mask >> cons) & 1; ++d) {
             if (is_lead(cons) && d + 1 > QMCCPW_D_LIMIT) continue;
             m = std::max(m, fused_smem_bytes(precision, cons, d - 1, contract_tile_log2(p, precision, cons, d)));
         }
@@ -915,6 +932,7 @@ int QmcServer::init(qmccpw_plan_s *p, const qmccpw_server_desc &d) {
     if (desc.max_inflight == 0) desc.max_inflight = 1024;
     if (desc.idle_limit_us == 0) desc.idle_limit_us = 20000;
     if (desc.max_inflight_bytes == 0) desc.max_inflight_bytes = uint64_t(256) << 20;
+    if (desc.constructions == 0) desc.constructions = 0x1F;  // every construction
     // ring entries: a power of two >= max_inflight, fewer when the host-mapped
     // results (R_max x 4 + 8 doubles per entry) would pass 256 MiB
     out_stride = 4u * static_cast<uint64_t>(plan->r_max) + 8u;
@@ -929,20 +947,23 @@ int QmcServer::init(qmccpw_plan_s *p, const qmccpw_server_desc &d) {
         return fail(QMCCPW_ERR_OOM, "cudaHostAlloc of the serving ring failed");
     for (uint64_t i = 0; i < cap; ++i) h_ring[i].seq = ~0ull;
     QMC_TRY(state.alloc(sizeof(ServeState) + sizeof(unsigned long long) * cap));
+    QMC_TRY(dev_ring.alloc(sizeof(ServeRequest) * cap));
     QMC_TRY(arena_buf.alloc(desc.max_inflight_bytes));
     arena.init(desc.max_inflight_bytes);
     QMC_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
     QMC_CUDA(cudaEventCreateWithFlags(&exit_ev, cudaEventDisableTiming));
     QMC_CUDA(cudaMemsetAsync(state.ptr, 0, state.bytes, stream));
+    QMC_CUDA(cudaMemsetAsync(dev_ring.ptr, 0xFF, dev_ring.bytes, stream));  // every sequence word ~0
     QMC_CUDA(cudaStreamSynchronize(stream));
-    smem = serve_smem(plan, desc.precision);
+    with_pca = desc.precision == QMCCPW_FP64 || ((desc.constructions >> QMCCPW_PCA) & 1);
+    smem = serve_smem(plan, desc.precision, desc.constructions);
     cudaDeviceProp prop{};
     QMC_CUDA(cudaGetDeviceProperties(&prop, plan->device));
-    QMC_CUDA(static_cast<cudaError_t>(serve_prepare(desc.precision, prop.sharedMemPerBlockOptin)));
+    QMC_CUDA(static_cast<cudaError_t>(serve_prepare(desc.precision, with_pca, prop.sharedMemPerBlockOptin)));
     int per_sm = 0;
-    QMC_CUDA(static_cast<cudaError_t>(serve_occupancy(desc.precision, smem, &per_sm)));
+    QMC_CUDA(static_cast<cudaError_t>(serve_occupancy(desc.precision, with_pca, smem, &per_sm)));
     if (per_sm < 1) return fail(QMCCPW_ERR_CUDA, "the serving kernel does not fit on an SM");
-    grid = std::min(kServeMaxGrid, per_sm * plan->sm_count);
+    grid = std::min(kServeMaxGrid, per_sm * plan->sm_count);  // the workers and the dispatcher
     return QMCCPW_OK;
 }
 
@@ -1484,7 +1505,8 @@ int qmccpw_server_start(qmccpw_plan_t plan, const qmccpw_server_desc *desc) {
     g_last_error.clear();
     if (!plan || !desc) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
     if (plan->server) return fail(QMCCPW_ERR_INVALID_ARG, "the plan already runs a server");
-    if (desc->reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "reserved must be 0");
+    if (desc->constructions < 0 || desc->constructions > 0x1F)
+        return fail(QMCCPW_ERR_INVALID_ARG, "constructions: a mask of bits 0..4");
     if (desc->precision < QMCCPW_FP64 || desc->precision > QMCCPW_MIXED_TC_TF32X3)
         return fail(QMCCPW_ERR_INVALID_ARG, "precision out of range");
     if (is_tc(desc->precision))
@@ -1507,6 +1529,8 @@ int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t 
     QmcServer *sv = plan->server;
     if (!sv) return fail(QMCCPW_ERR_INVALID_ARG, "no server runs on this plan");
     QMC_TRY(validate_qc(plan, *contract, sv->desc.precision, false));
+    if (!((sv->desc.constructions >> contract->construction) & 1))
+        return fail(QMCCPW_ERR_UNSUPPORTED, "the server was started without this construction");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stopping) return fail(QMCCPW_ERR_INVALID_ARG, "the server is stopping");
     if (sv->broken) return fail(QMCCPW_ERR_CUDA, "the serving kernel failed; stop the server");

@@ -592,14 +592,13 @@ __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *_
         __syncthreads();
         // ---- phase 3: the switch point and the values of the point, tile sum
         if (pt < P && local_point < c.N) {
-            T o[4];
-            lead_values<T>(c, rbuf + pt * stride, o);
-            for (int g = 0; g < 4; ++g) {
-                if constexpr (sizeof(T) == 8) v[g] = o[g];
-                else v[g] = ff{o[g], 0.0f};
+            lead_values<T>(c, rbuf + pt * stride, v);
+            if (point_out) {
+                for (int g = 0; g < 4; ++g) {
+                    if constexpr (sizeof(T) == 8) point_out[local_point * 4 + g] = v[g];
+                    else point_out[local_point * 4 + g] = ff_to_double(v[g]);
+                }
             }
-            if (point_out)
-                for (int g = 0; g < 4; ++g) point_out[local_point * 4 + g] = static_cast<double>(o[g]);
         }
     } else {
         // ---- phase 2: path construction and running sums, merged per point

@@ -611,9 +611,19 @@ __device__ __forceinline__ T lead_loading(const ContractDev &c, int j) {  // a_{
     return __ldg(c.lead_a64 + j) * c.sqrt_t1;
 }
 
-// values of one point: out = price, delta, vega, gamma (before the tile sum)
+// values of one point: out = price, delta, vega, gamma (before the tile sum);
+// the float path returns them as float pairs: the conditioning on the leading
+// coordinate leaves the per-point values so close together that rounding each
+// to one float would round them all the same way (a bias of up to half an
+// ulp, above the standard error)
+template <typename T> struct LeadOut { using type = double; };
+template <> struct LeadOut<float> { using type = ff; };
+__device__ __forceinline__ ff split_to_ff(double x) {
+    const float hi = static_cast<float>(x);
+    return ff{hi, static_cast<float>(x - static_cast<double>(hi))};
+}
 template <typename T>
-__device__ void lead_values(const ContractDev &c, const T *R, T out[4]);
+__device__ void lead_values(const ContractDev &c, const T *R, typename LeadOut<T>::type out[4]);
 
 // FP64: the formulas as they stand
 template <>
@@ -710,7 +720,7 @@ __device__ __forceinline__ ff lead_loading_ff(const ContractDev &c, int j) {
 }
 
 template <>
-__device__ void lead_values<float>(const ContractDev &c, const float *R, float out[4]) {
+__device__ void lead_values<float>(const ContractDev &c, const float *R, ff out[4]) {
     const int d = c.d;
     const double K = c.K, S0 = c.S0, disc = c.disc;
     const float sh = c.ff_sig[0], sl = c.ff_sig[1];
@@ -734,7 +744,7 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
         o[1] = disc * eb * sfb / S0;
         o[2] = disc * eb * ((am * b + bm) * sfb + am * pb);
         o[3] = disc * px * K / (S0 * S0 * b);
-        for (int g = 0; g < 4; ++g) out[g] = static_cast<float>(o[g]);
+        for (int g = 0; g < 4; ++g) out[g] = split_to_ff(o[g]);
         return;
     }
     // the exponent of c_j e^{b_j x}: ln(S0/d) + omega t_j + sigma R_j + b_j x
@@ -833,15 +843,15 @@ __device__ void lead_values<float>(const ContractDev &c, const float *R, float o
     const double resid = (static_cast<double>(Xs.hi) + Xs.lo) - K;
     const double sfx = Mx * pdf;  // Phi(-x*)
     if (c.type == QMCCPW_ARITH_ASIAN_CALL) {
-        out[0] = static_cast<float>(disc * (pdf * SP + resid * sfx));
-        out[1] = static_cast<float>(disc * (pdf * SP + (K + resid) * sfx) / S0);
-        out[2] = static_cast<float>(disc * pdf * (Mx * (static_cast<double>(W0.hi) + W0.lo) + V1 + SA));
-        out[3] = static_cast<float>(disc * pdf * K * K / (S0 * S0 * X1));
+        out[0] = split_to_ff(disc * (pdf * SP + resid * sfx));
+        out[1] = split_to_ff(disc * (pdf * SP + (K + resid) * sfx) / S0);
+        out[2] = split_to_ff(disc * pdf * (Mx * (static_cast<double>(W0.hi) + W0.lo) + V1 + SA));
+        out[3] = split_to_ff(disc * pdf * K * K / (S0 * S0 * X1));
     } else {
-        out[0] = static_cast<float>(disc * sfx);
-        out[1] = static_cast<float>(disc * pdf * K / (S0 * X1));
-        out[2] = static_cast<float>(disc * pdf * B / X1);
-        out[3] = static_cast<float>(disc * K * pdf * (xd * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1)));
+        out[0] = split_to_ff(disc * sfx);
+        out[1] = split_to_ff(disc * pdf * K / (S0 * X1));
+        out[2] = split_to_ff(disc * pdf * B / X1);
+        out[3] = split_to_ff(disc * K * pdf * (xd * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1)));
     }
 }
 

@@ -172,27 +172,33 @@ int fused_set_smem_limit(int precision, size_t optin_bytes);  // optin_bytes: th
 int fused_occupancy(int precision, int construction, size_t smem_bytes, int *blocks_per_sm);
 
 // ----------------------------------------------------------------------------
-// Device-resident serving loop (serve.cu; host side in api.cu)
+// Device-resident serving loop (serve_impl.cuh, serve_f32.cu, serve_f64.cu;
+// host side in api.cu)
 // ----------------------------------------------------------------------------
 // The work items of every request, in publication order, are numbered by
 // one global ticket sequence: request s owns tickets [first_ticket,
 // first_ticket + items), item = replicate-major (replicate, tile) as in a
 // batch.  The host writes a request into a ring of host-mapped entries, then
-// publishes it by raising published_seq and published_tickets.  A
-// persistent kernel's CTAs take tickets from a device counter, wait (bounded
-// by %globaltimer) until their ticket is published, run the item and count
-// it; the CTA that finishes a request's last item reduces it and raises the
-// request's completion flag.  A CTA that waits longer than the idle limit
-// (or sees the stop word) records the ticket it holds and leaves; the last
-// one to leave carries every held ticket over to the next launch, which
-// hands them out first, so no published item is lost when the kernel exits
-// and the host launches it again.
-constexpr int kServeMaxGrid = 1024;          // CTAs of one serving launch at most
+// publishes it by raising published_seq and published_tickets.  One CTA of
+// the persistent kernel, the dispatcher, watches those host words, copies
+// each new entry into a device-memory ring and republishes it in device
+// memory; the other CTAs, the workers, touch host memory only to write
+// results: they take tickets from a device counter, wait (bounded by
+// %globaltimer) until their ticket is published on the device, run the item
+// and count it; the worker that finishes a request's last item reduces it
+// and raises the request's completion flag in host-mapped memory.  A worker
+// that waits longer than the idle limit (or sees the stop word) records the
+// ticket it holds and leaves, the dispatcher leaves after the last worker
+// (or on the stop word), and the last CTA to leave carries every held ticket
+// over to the next launch, which hands them out first, so no published item
+// is lost when the kernel exits and the host launches it again.
+constexpr int kServeMaxGrid = 1024;          // CTAs of one serving launch at most (workers + dispatcher)
 constexpr int kServeRetryCap = 2 * kServeMaxGrid;
 
-// One ring entry (host-mapped; the host writes it before publication and
-// while seq holds ~0, so a reader that sees the same seq before and after
-// reading knows the entry was not being rewritten).
+// One ring entry (host-mapped, and its copy in the device ring).  The host
+// writes an entry before publication and while seq holds ~0, the
+// dispatcher its copy likewise, so a reader that sees the same seq before
+// and after reading knows the entry was not being rewritten.
 struct ServeRequest {
     uint64_t seq;                            // request number
     uint64_t first_ticket, items;            // its tickets
@@ -227,12 +233,19 @@ struct ServeState {
     unsigned int retry_next;
     unsigned int exited;                     // CTAs of this launch that have left
     unsigned int bad_ticket;                 // nonzero: a CTA found no request for its ticket (exit reason 4)
+    // the dispatcher's device copies of the host words
+    uint64_t pub_tickets;                    // tickets below it are published in the device ring
+    uint64_t pub_seq;                        // requests below it are in the device ring
+    uint64_t oldest_live;
+    uint32_t stop;
+    uint32_t pad;
     unsigned long long retry[kServeRetryCap];
-    unsigned long long abandoned[kServeMaxGrid];  // the ticket each CTA held when it left
+    unsigned long long abandoned[kServeMaxGrid];  // the ticket each worker held when it left
 };
 
 struct ServeParams {
     const ServeRequest *ring;                // host-mapped, cap entries
+    ServeRequest *dev_ring;                  // device copies, cap entries
     uint64_t cap;                            // ring entries, a power of two
     const ServeControl *ctl;                 // host-mapped
     uint64_t *done;                          // host-mapped, per entry: seq + 1 once that request finished
@@ -243,11 +256,20 @@ struct ServeParams {
     const uint32_t *sobol_shift;
     int32_t jstride;
     uint32_t launch;
-    uint64_t idle_ns;                        // a CTA leaves after waiting this long for a published ticket
+    uint64_t idle_ns;                        // a worker leaves after waiting this long for a published ticket
 };
-int launch_serve(const ServeParams &p, int precision, size_t smem_bytes, int grid, void *stream);
-int serve_prepare(int precision, size_t optin_bytes);  // raise the dynamic shared-memory limit
-int serve_occupancy(int precision, size_t smem_bytes, int *blocks_per_sm);
+// The serving kernels: precision FP64 or MIXED; with_pca false builds the
+// MIXED kernel without the PCA product (three CTAs per SM instead of two).
+// grid = workers + 1 (the last CTA is the dispatcher).
+int launch_serve(const ServeParams &p, int precision, bool with_pca, size_t smem_bytes, int grid, void *stream);
+int serve_prepare(int precision, bool with_pca, size_t optin_bytes);  // raise the dynamic shared-memory limit
+int serve_occupancy(int precision, bool with_pca, size_t smem_bytes, int *blocks_per_sm);
+int serve_f32_launch(const ServeParams &p, bool with_pca, size_t smem_bytes, int grid, void *stream);
+int serve_f32_prepare(bool with_pca, size_t optin_bytes);
+int serve_f32_occupancy(bool with_pca, size_t smem_bytes, int *blocks_per_sm);
+int serve_f64_launch(const ServeParams &p, size_t smem_bytes, int grid, void *stream);
+int serve_f64_prepare(size_t optin_bytes);
+int serve_f64_occupancy(size_t smem_bytes, int *blocks_per_sm);
 
 // Tensor-core PCA (pca_tc.cu).  kind 0: bf16 split (4 products), 1: tf32
 // split (3 products), both n <= 64 with Ahat resident; kinds 2 (bf16) and 3

@@ -98,7 +98,7 @@ class qmccpw_contract(ctypes.Structure):
 
 class qmccpw_server_desc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
-                ("idle_limit_us", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("idle_limit_us", ctypes.c_int32), ("constructions", ctypes.c_int32),
                 ("max_inflight_bytes", ctypes.c_uint64)]
 
 
@@ -333,9 +333,13 @@ def qmccpw_greeks_noalloc(plan, type: int, d: int, K: float, T: float, S0: float
 
 
 def qmccpw_server_start(plan, precision: int = QMCCPW_MIXED, max_inflight: int = 0, idle_limit_us: int = 0,
-                        max_inflight_bytes: int = 0) -> None:
-    """Start the device-resident serving loop (0: the library's default for each limit)."""
-    desc = qmccpw_server_desc(precision, max_inflight, idle_limit_us, 0, max_inflight_bytes)
+                        max_inflight_bytes: int = 0, constructions: Sequence[int] = ()) -> None:
+    """Start the device-resident serving loop (0: the library's default for each limit; constructions:
+    the accepted qmccpw_construction values, empty for all)."""
+    mask = 0
+    for cons in constructions:
+        mask |= 1 << cons
+    desc = qmccpw_server_desc(precision, max_inflight, idle_limit_us, mask, max_inflight_bytes)
     _check(library().qmccpw_server_start(plan, ctypes.byref(desc)))
 
 

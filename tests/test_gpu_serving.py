@@ -158,3 +158,24 @@ def test_stop_ends_a_waiting_kernel(q):
         assert time.time() - t0 < 2.0
     finally:
         q.qmccpw_free(plan)
+
+
+def test_construction_mask(q):
+    """A MIXED server started for bridge contracts only runs the kernel
+    without the PCA product and refuses the other constructions; results as
+    alone."""
+    plan = q.qmccpw_plan(device=0, d_max=130, r_max=8, seed=W.SCRAMBLE_SEED)
+    try:
+        cs = [W.Contract(W.ARITH, d, 100.0, 1.0, 100.0, 0.05, 0.2, 3000 + 7 * d, 4, W.BB) for d in (16, 64, 100, 129)]
+        alone = [q.qmccpw_greeks(plan, c.type, c.d, c.K, c.T, c.S0, c.r, c.sigma, c.N, c.R, c.construction, 1)
+                 for c in cs]
+        q.qmccpw_server_start(plan, precision=1, constructions=[W.BB])
+        with pytest.raises(q.QmcCpwError) as e:
+            q.qmccpw_submit(plan, W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 1024, 4, W.PCA))
+        assert e.value.code == q.QMCCPW_ERR_UNSUPPORTED
+        got = [q.qmccpw_wait(plan, q.qmccpw_submit(plan, c), c.R, 60000) for c in cs]
+        q.qmccpw_server_stop(plan)
+        for c, (m, s, p), (m1, s1, p1) in zip(cs, got, alone):
+            assert np.array_equal(p, p1), c.label()
+    finally:
+        q.qmccpw_free(plan)
