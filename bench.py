@@ -192,7 +192,7 @@ def roofline(grid_precision: str, contracts, segment_ms, peaks: dict) -> dict:
             "point_dates_per_s": top["point_dates_per_s"], "ceilings_point_dates_per_s": top["ceilings_point_dates_per_s"],
             "limit": top["limit"], "frac_of_lowest_ceiling": top["frac"],
             "peak_note": "of measured: FP32 operation rate = FFMA lane rate of the library's micro-benchmark "
-                         "(pipe_peaks_gb300.json, burst); ceilings per SURVEY-style count: FP32/24, SFU(ex2)/2, "
+                         "(pipe_peaks_gb300.json, burst); ceilings per point-date: FP32 ops/24, SFU(ex2)/2, "
                          "tensor/(2n x split products)",
             "segments": segs}
 
