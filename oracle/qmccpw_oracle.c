@@ -335,7 +335,6 @@ static int check_contract(const contract_t *c, int construction)
     if (!(c->K > 0.0) || !(c->T > 0.0) || !(c->S0 > 0.0) || !(c->sigma > 0.0)) return -1;
     if (!isfinite(c->K) || !isfinite(c->T) || !isfinite(c->S0) || !isfinite(c->sigma) || !isfinite(c->r)) return -1;
     if (construction < 0 || construction > 4) return -1;
-    if (construction >= 3 && c->type == 2) return -1;  /* leading-coordinate conditioning: no lookback */
     return 0;
 }
 
@@ -423,7 +422,16 @@ static void greeks_from_path(const contract_t *c, const double *W, double out[4]
 /* and the pathwise Greeks by differentiating these at fixed R (the terms  */
 /* from moving x* cancel in the call price, since X(x*) = K).  The          */
 /* geometric mean is log-linear in x: X(x) = G e^{b x}, b = sigma mean(a),  */
-/* and x* is explicit.  The lookback maximum is not offered here.           */
+/* and x* is explicit.  The lookback maximum M(x) = max_j c_j e^{b_j x}     */
+/* (c_j = S0 exp(omega t_j + sigma R_j), no 1/d) is the upper envelope of    */
+/* the lines ln c_j + b_j x: increasing (every b_j > 0), so x* = min_j of    */
+/* the lines' own roots (ln K - ln c_j)/b_j, and right of x* the envelope   */
+/* is a run of pieces [u, v], each one line j, the next line the first of   */
+/* steeper slope to overtake it; each piece contributes                      */
+/*   c_j e^{b_j^2/2} [Phi(b_j - u) - Phi(b_j - v)]                            */
+/* (e^{bx} phi(x) = e^{b^2/2} phi(x - b)), the price less K Phi(-x*); delta   */
+/* is that sum over S0, vega the same pieces with the derivative of each     */
+/* line, gamma = e^{-rT} K phi(x*) / (S0^2 b_j*) from moving x*.              */
 /* ------------------------------------------------------------------------ */
 static double phi_bar(double y) { return norm_sf(y); }  /* P(x > y) */
 
@@ -455,6 +463,68 @@ static int lead_path(const contract_t *c, int construction, const double *A, con
     return 0;
 }
 
+/* The lookback under leading-coordinate conditioning: the envelope pieces
+ * right of the switch point, walked from its active line. */
+static void lead_lookback_values(const contract_t *c, const double *R, const double *a, double out[4])
+{
+    const int d = c->d;
+    const double dt = c->T / d, sig = c->sigma, K = c->K, S0 = c->S0;
+    const double omega = c->r - 0.5 * sig * sig;
+    const double disc = exp(-c->r * c->T);
+    double xs = INFINITY;
+    int cur = -1;
+    for (int j = 0; j < d; ++j) {                   /* x* and its line: the smallest root, steeper on ties */
+        const double lc = log(S0) + omega * (j + 1) * dt + sig * R[j];
+        const double root = (log(K) - lc) / (sig * a[j]);
+        if (cur < 0 || root < xs || (root == xs && a[j] > a[cur])) {
+            xs = root;
+            cur = j;
+        }
+    }
+    double price = 0.0, vega = 0.0;
+    double u = xs;
+    while (1) {
+        const double lc_cur = log(S0) + omega * (cur + 1) * dt + sig * R[cur];
+        const double b = sig * a[cur];
+        /* the first steeper line to overtake the current one */
+        double v = INFINITY;
+        int next = -1;
+        for (int j = 0; j < d; ++j) {
+            if (!(a[j] > a[cur])) continue;
+            const double lc = log(S0) + omega * (j + 1) * dt + sig * R[j];
+            double xj = (lc_cur - lc) / (sig * a[j] - b);
+            if (xj < u) xj = u;                     /* already level with it at u */
+            if (xj < v || (xj == v && next >= 0 && a[j] > a[next])) {
+                v = xj;
+                next = j;
+            }
+        }
+        const double ch = exp(lc_cur + 0.5 * b * b);  /* c_j e^{b^2/2} */
+        const double mass = phi_bar(u - b) - (isinf(v) ? 0.0 : phi_bar(v - b));
+        const double dens = norm_pdf(u - b) - (isinf(v) ? 0.0 : norm_pdf(v - b));
+        const double t = (cur + 1) * dt;
+        price += ch * mass;
+        vega += ch * ((R[cur] - sig * t + a[cur] * b) * mass + a[cur] * dens);
+        if (next < 0) break;
+        u = v;
+        cur = next;
+    }
+    /* the line active at x* again, for gamma */
+    double b_star = INFINITY, xs2 = INFINITY;
+    for (int j = 0; j < d; ++j) {
+        const double lc = log(S0) + omega * (j + 1) * dt + sig * R[j];
+        const double root = (log(K) - lc) / (sig * a[j]);
+        if (root < xs2 || (root == xs2 && sig * a[j] > b_star)) {
+            xs2 = root;
+            b_star = sig * a[j];
+        }
+    }
+    out[0] = disc * (price - K * phi_bar(xs));
+    out[1] = disc * price / S0;
+    out[2] = disc * vega;
+    out[3] = disc * K * norm_pdf(xs) / (S0 * S0 * b_star);
+}
+
 static void lead_values(const contract_t *c, const double *R, const double *a, double out[4])
 {
     const int d = c->d;
@@ -477,6 +547,10 @@ static void lead_values(const contract_t *c, const double *R, const double *a, d
         out[1] = disc * eb * phi_bar(xs - b) / S0;
         out[2] = disc * eb * ((amean * b + bmean) * phi_bar(xs - b) + amean * norm_pdf(xs - b));
         out[3] = disc * norm_pdf(xs) * K / (S0 * S0 * b);
+        return;
+    }
+    if (c->type == 2) {
+        lead_lookback_values(c, R, a, out);
         return;
     }
     /* log c_j and b_j; Newton on g(x) = ln X(x) - ln K from x = 0 */

@@ -11,6 +11,10 @@ method (the next reduction the paper names in Sec. 6-7).
 - d = 1: the Black-Scholes call / cash-or-nothing.
 - Full estimator: the geometric-Asian closed form, and the same mean as the
   first-increment conditioning (both are unbiased).
+- The lookback: its maximum is the upper envelope of the dates' exponentials
+  in the leading coordinate; the quadrature integrates the raw maximum
+  between every pairwise crossing (found by brute force), and a path built to
+  change its leading date several times checks the pieces.
 """
 import math
 
@@ -45,18 +49,35 @@ def value_by_quadrature(opt, K, T, S0, r, sig, R, a):
 
     def X(x):
         S = S0 * np.exp(omega * t + sig * (a * x + R))
+        if opt == 2:
+            return float(np.max(S))
         return float(np.mean(S)) if opt in (0, 1) else float(np.exp(np.mean(np.log(S))))
 
     xs = optimize.brentq(lambda x: X(x) - K, -80.0, 80.0, xtol=1e-15, rtol=1e-15, maxiter=500)
     disc = math.exp(-r * T)
     if opt == 1:
         return disc * 0.5 * math.erfc(xs / math.sqrt(2.0))
-    val, _ = integrate.quad(lambda x: (X(x) - K) * cpw.pdf(x), xs, max(xs, 0.0) + 40.0,
-                            epsabs=1e-14, epsrel=1e-13, limit=200)
+    # the maximum has kinks where the leading date changes: integrate between
+    # them (every pairwise crossing right of x*, found here by brute force)
+    pts = [xs]
+    if opt == 2:
+        ln = np.log(S0) + omega * t + sig * R
+        b = sig * a
+        for i in range(d):
+            for j in range(i + 1, d):
+                if b[i] != b[j]:
+                    x = (ln[i] - ln[j]) / (b[j] - b[i])
+                    if xs < x < max(xs, 0.0) + 40.0:
+                        pts.append(x)
+    pts = sorted(pts) + [max(xs, 0.0) + 40.0]
+    val = 0.0
+    for lo, hi in zip(pts[:-1], pts[1:]):
+        part, _ = integrate.quad(lambda x: (X(x) - K) * cpw.pdf(x), lo, hi, epsabs=1e-15, epsrel=1e-13, limit=200)
+        val += part
     return disc * val
 
 
-CASES = [(opt, d, cons) for opt in (0, 1, 3) for d, cons in ((2, 3), (5, 3), (16, 3), (2, 4), (7, 4), (16, 4))]
+CASES = [(opt, d, cons) for opt in (0, 1, 2, 3) for d, cons in ((2, 3), (5, 3), (16, 3), (2, 4), (7, 4), (16, 4))]
 
 
 @pytest.mark.parametrize("opt,d,cons", CASES)
@@ -92,7 +113,7 @@ def test_lead_greeks_equal_finite_differences(oracle_lib, opt, d, cons):
 
 
 @pytest.mark.parametrize("cons", [3, 4])
-@pytest.mark.parametrize("opt", [0, 1, 3])
+@pytest.mark.parametrize("opt", [0, 1, 2, 3])
 def test_lead_single_date_reduces_to_black_scholes(oracle_lib, cons, opt):
     for S0, K, r, sig, T in ((100, 100, 0.05, 0.2, 1.0), (100, 80, 0.0, 0.45, 0.25), (90, 120, 0.08, 0.1, 2.0)):
         ref = cpw.bs_digital(S0, K, r, sig, T) if opt == 1 else cpw.bs_call(S0, K, r, sig, T)
@@ -101,9 +122,27 @@ def test_lead_single_date_reduces_to_black_scholes(oracle_lib, cons, opt):
             assert abs(vals[g] - ref[g]) <= 1e-12 * max(1.0, abs(ref[g])), (g, vals[g], ref[g])
 
 
-def test_lead_rejects_the_lookback(oracle_lib):
-    with pytest.raises(ValueError):
-        oracle_lib.point(2, 4, 100.0, 1.0, 100.0, 0.05, 0.2, 3, np.zeros(3))
+@pytest.mark.parametrize("cons", [3, 4])
+def test_lead_lookback_envelope_pieces(oracle_lib, cons):
+    """Paths built so the maximum changes its leading date several times
+    right of x* (a falling rest of the path, then rising): the value still
+    equals the piecewise quadrature, and gamma the slope formula
+    K phi(x*) / (S0^2 sigma a_j*) at the date that leads at x*."""
+    d, T, r, sig, S0, K = 8, 1.0, 0.03, 0.3, 100.0, 101.0
+    rng = np.random.default_rng(23 + cons)
+    for _ in range(6):
+        z = rng.standard_normal(d - 1) * 2.0
+        vals, _ = oracle_lib.point(2, d, K, T, S0, r, sig, cons, z)
+        R, a = rest_and_loading(cons, d, T / d, z)
+        ref = value_by_quadrature(2, K, T, S0, r, sig, R, a)
+        assert abs(vals[0] - ref) <= 1e-10 * max(1.0, abs(ref)), (vals[0], ref)
+        t = T / d * np.arange(1, d + 1)
+        ln = np.log(S0) + (r - 0.5 * sig * sig) * t + sig * R
+        roots = (np.log(K) - ln) / (sig * a)
+        j = int(np.argmin(roots))
+        xs = roots[j]
+        g = math.exp(-r * T) * K * cpw.pdf(xs) / (S0 * S0 * sig * a[j])
+        assert abs(vals[3] - g) <= 1e-12 * abs(g), (vals[3], g)
 
 
 @pytest.mark.parametrize("cons", [3, 4])
@@ -117,7 +156,7 @@ def test_lead_estimator_matches_geometric_asian_closed_form(oracle_lib, cons, K)
         assert abs(mean[g] - ref) <= 4.0 * se[g] + 1e-9 * abs(ref), (g, mean[g], ref, se[g])
 
 
-@pytest.mark.parametrize("opt", [0, 1])
+@pytest.mark.parametrize("opt", [0, 1, 2])
 def test_lead_and_first_increment_conditioning_agree(oracle_lib, opt):
     """Both conditionings are unbiased estimators of the same Greeks."""
     S0, K, r, sig, T, d = 100.0, 105.0, 0.05, 0.25, 1.0, 16
