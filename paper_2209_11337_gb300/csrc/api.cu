@@ -229,8 +229,6 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
         return fail(QMCCPW_ERR_INVALID_ARG, "R " + std::to_string(R) + " outside 2..r_max=" + std::to_string(p->r_max));
     if (construction < QMCCPW_BB || construction > QMCCPW_PCA_LEAD)
         return fail(QMCCPW_ERR_INVALID_ARG, "construction out of range");
-    if (is_lead(construction) && o.type == QMCCPW_LOOKBACK_FIXED_CALL)
-        return fail(QMCCPW_ERR_UNSUPPORTED, "the leading-coordinate constructions do not offer the lookback");
     if (is_lead(construction) && o.d + 1 > QMCCPW_D_LIMIT)
         return fail(QMCCPW_ERR_INVALID_ARG, "d too large for the full-path construction");
     if (precision < QMCCPW_FP64 || precision > QMCCPW_MIXED_TC_TF32X3)

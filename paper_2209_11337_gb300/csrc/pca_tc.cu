@@ -410,267 +410,6 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
     }
 }
 
-// ---------------------------------------------------------------------------
-// Warp-specialised resident kernel (d <= 65): the tile's phases overlap
-// across tiles instead of running in turn.  384 threads in two roles:
-//   producers (warps 0-7): Sobol' + inverse normal into one of two Z buffers;
-//     their thread 0 also issues the split product of a finished buffer into
-//     one of two TMEM accumulator sets (D1 + D2, 128 columns each);
-//   consumers (warps 8-11, one warpgroup: TMEM lanes 0-127, one point per
-//     thread): path sums over all the dates of a finished accumulator set,
-//     the conditional step and the tile sum.
-// Hand-offs by mbarriers, per buffer b (tile i uses b = i % 2, phase i / 2):
-//   full[b]      producer warps -> issuer: Z(b) written (8 arrivals);
-//   mma_done[b]  the products of the tile in set b have completed (commit)
-//                and its work item is in cslot[b] (issuer's arrival): 2;
-//                consumers wait for it before reading the set, producers
-//                before overwriting Z(b);
-//   tmem_free[b] consumer warps -> issuer: set b read (4 arrivals).
-// Roles synchronise internally by named barriers (1: producers, 2:
-// consumers), never by __syncthreads inside the loop.  Every mbarrier wait is
-// bounded and gives up once another role has aborted; the waits that decide
-// whether a role goes on are taken by one thread and shared through a named
-// barrier, so a role leaves its loop together.
-constexpr int kProducerWarps = 8, kConsumerWarps = 4;
-constexpr int kThreadsW = 32 * (kProducerWarps + kConsumerWarps);
-constexpr int kProducers = 32 * kProducerWarps;
-constexpr int kColsW = 2 * 2 * kNpad;  // two accumulator sets of D1 and D2
-
-struct TileSlot {
-    uint64_t item, tile;
-    int32_t ci;
-    uint32_t rep;
-    int32_t end;
-    int32_t pad;
-};
-
-struct TcwShared {
-    uint64_t full[2], mma_done[2], tmem_free[2], bar_b;
-    TileSlot pslot[2], cslot[2];
-    uint32_t tmem_addr;
-    int32_t abort;       // 1 the Ahat copy, 2 the products, 3 a hand-off wait expired
-    int32_t loaded_n;
-    int32_t issued;      // tiles whose products were issued
-    uint32_t b_phase;    // Ahat copies so far (the copy barrier's phase)
-};
-
-// Consumers: float-float tile sum of the warpgroup's 128 points (warp g sums
-// Greek g: each lane four consecutive points, then a shuffle tree), written
-// to out[g]; `vals` holds 8 x 128 floats.
-__device__ __forceinline__ void consumer_tile_sum(double *out, const ff (&v)[4], float *vals, int ct) {
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        vals[(2 * g) * kM + ct] = v[g].hi;
-        vals[(2 * g + 1) * kM + ct] = v[g].lo;
-    }
-    named_sync(2, 32 * kConsumerWarps);
-    const int warp = ct >> 5, lane = ct & 31;
-    const float *hi = vals + (2 * warp) * kM + lane * (kM / 32);
-    const float *lo = vals + (2 * warp + 1) * kM + lane * (kM / 32);
-    ff s = {0.0f, 0.0f};
-#pragma unroll
-    for (int i = 0; i < kM / 32; ++i) s = ff_add(s, ff{hi[i], lo[i]});
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const ff o = {__shfl_down_sync(0xffffffffu, s.hi, off), __shfl_down_sync(0xffffffffu, s.lo, off)};
-        s = ff_add(s, o);
-    }
-    if (lane == 0) out[warp] = ff_to_double(s);
-    named_sync(2, 32 * kConsumerWarps);  // vals free again
-}
-
-// Producer thread 0: hand tile i (buffer b) to the tensor core, or the end of
-// the work to the consumers.  False once a wait expired (sh.abort set).
-template <int KIND>
-__device__ bool tcw_issue(const LaunchParams &p, TcwShared &sh, int i, uint32_t tmem, unsigned char *z_base,
-                          unsigned char *b_hi) {
-    constexpr int ES = KIND == 0 ? 2 : 4;
-    constexpr uint32_t kOpBytesZ = kM * kNpad * ES;
-    constexpr uint32_t kOpBytesB = kNpad * kNpad * ES;
-    constexpr int kPartsB = KIND == 0 ? 3 : 2;
-    constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 1u : 2u, kNpad);
-    constexpr uint32_t kLbo = 128, kSbo = (kNpad / (16 / ES)) * 128;
-    const int b = i & 1;
-    const uint32_t ph = static_cast<uint32_t>(i >> 1) & 1u;
-    const uint32_t ph_prev = static_cast<uint32_t>((i - 2) >> 1) & 1u;
-    volatile int32_t *abort = &sh.abort;
-    if (!mbar_wait_or_abort(&sh.full[b], ph, abort)) return false;
-    // the consumers are done with this accumulator set (tile i - 2)
-    if (i >= 2 && !mbar_wait_or_abort(&sh.tmem_free[b], ph_prev, abort)) return false;
-    const TileSlot ps = sh.pslot[b];
-    if (ps.end) {
-        sh.cslot[b] = ps;
-        mbar_arrive(&sh.mma_done[b], 2);  // no products: both arrivals from here
-        return true;
-    }
-    const ContractDev &c = p.contracts[ps.ci];
-    if (sh.loaded_n != c.n) {
-        // Ahat for this n, once no product of the previous tile reads it
-        if (i >= 1 && !mbar_wait_or_abort(&sh.mma_done[(i - 1) & 1], static_cast<uint32_t>((i - 1) >> 1) & 1u, abort))
-            return false;
-        mbar_expect_tx(&sh.bar_b, kPartsB * kOpBytesB);
-        bulk_copy_g2s(b_hi, c.tc_operand, kPartsB * kOpBytesB, &sh.bar_b);
-        if (!mbar_wait(&sh.bar_b, sh.b_phase & 1u)) {
-            atomicExch(&sh.abort, 1);  // the copy may still land
-            return false;
-        }
-        ++sh.b_phase;
-        sh.loaded_n = c.n;
-    }
-    sh.cslot[b] = ps;
-    tc_fence_after();
-    const uint32_t zh0 = smem_u32(z_base + b * 2 * kOpBytesZ), zl0 = zh0 + kOpBytesZ;
-    const uint32_t bh = smem_u32(b_hi), b2 = bh + kOpBytesB, b3 = b2 + kOpBytesB;
-    const uint32_t d = tmem + static_cast<uint32_t>(b * 2 * kNpad);
-#pragma unroll
-    for (int ks = 0; ks < kNpad / (32 / ES); ++ks) {  // K per instruction: 16 bf16 or 8 tf32 = 32 bytes
-        const uint32_t kb = static_cast<uint32_t>(ks) * 32u;
-        const uint32_t koff = static_cast<uint32_t>(ks) * 256u;
-        const uint64_t zh = smem_desc_sw128(z_slice(zh0, kb));
-        const uint64_t zl = smem_desc_sw128(z_slice(zl0, kb));
-        const uint32_t acc = ks > 0 ? 1u : 0u;
-        mma<KIND>(d, zh, smem_desc(bh + koff, kLbo, kSbo), kIdesc, acc);
-        mma<KIND>(d + kNpad, zl, smem_desc(bh + koff, kLbo, kSbo), kIdesc, acc);
-        mma<KIND>(d + kNpad, zh, smem_desc(b2 + koff, kLbo, kSbo), kIdesc, 1u);
-        if constexpr (KIND == 0) {
-            mma<KIND>(d + kNpad, zl, smem_desc(b2 + koff, kLbo, kSbo), kIdesc, 1u);
-            mma<KIND>(d + kNpad, zh, smem_desc(b3 + koff, kLbo, kSbo), kIdesc, 1u);
-        }
-    }
-    mma_commit(&sh.mma_done[b]);
-    mbar_arrive(&sh.mma_done[b]);  // the work item is in cslot[b]
-    sh.issued = i + 1;
-    return true;
-}
-
-template <int KIND>
-__global__ void __launch_bounds__(kThreadsW, 2) pca_tcw_kernel(const __grid_constant__ LaunchParams p) {
-    constexpr int ES = KIND == 0 ? 2 : 4;
-    constexpr uint32_t kOpBytesZ = kM * kNpad * ES;        // one split part of Z
-    constexpr uint32_t kOpBytesB = kNpad * kNpad * ES;     // one split part of Ahat
-    constexpr int kPartsB = KIND == 0 ? 3 : 2;
-
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *z_base = aligned_smem(smem_raw);        // Z(b): hi then lo, b = 0, 1
-    unsigned char *b_hi = z_base + 4 * kOpBytesZ;          // Ahat parts (one bulk copy)
-    float *vals = reinterpret_cast<float *>(b_hi + kPartsB * kOpBytesB);  // consumers' tile sum, 8 x kM floats
-    __shared__ TcwShared sh;
-
-    const int warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sh.full[b], kProducerWarps);
-            mbar_init(&sh.mma_done[b], 2);
-            mbar_init(&sh.tmem_free[b], kConsumerWarps);
-        }
-        mbar_init(&sh.bar_b, 1);
-        sh.loaded_n = -1;
-        sh.abort = 0;
-        sh.issued = 0;
-        sh.b_phase = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) tmem_alloc(&sh.tmem_addr, kColsW);
-    // padding columns (k >= n) of both Z buffers are never written by the Sobol' phase
-    for (uint32_t i = threadIdx.x; i < 4 * kOpBytesZ / 4; i += kThreadsW) reinterpret_cast<uint32_t *>(z_base)[i] = 0u;
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = sh.tmem_addr;
-    volatile int32_t *abort = &sh.abort;
-
-    if (warp < kProducerWarps) {
-        // ---- producers
-        for (int i = 0;; ++i) {
-            const int b = i & 1;
-            if (threadIdx.x == 0) {
-                // Z(b) is free once the products of tile i - 2 have completed
-                if (i >= 2 && !mbar_wait_or_abort(&sh.mma_done[b], static_cast<uint32_t>((i - 2) >> 1) & 1u, abort))
-                    atomicCAS(&sh.abort, 0, 3);
-                TileSlot s{};
-                const uint64_t item = p.item_begin + atomicAdd(p.work_counter, 1ull);
-                s.item = item;
-                s.end = item >= p.item_end || *abort != 0;
-                if (!s.end) {
-                    const int ci = find_contract(p.item_base, p.count, item);
-                    const uint64_t local = item - p.contracts[ci].item_base;
-                    const uint64_t tiles = static_cast<uint64_t>(p.contracts[ci].tiles);
-                    const uint64_t r = local / tiles;
-                    s.ci = ci;
-                    s.rep = static_cast<uint32_t>(r) + static_cast<uint32_t>(p.contracts[ci].rep_first) + p.rep_offset;
-                    s.tile = local - r * tiles;
-                }
-                sh.pslot[b] = s;
-            }
-            named_sync(1, kProducers);
-            const TileSlot s = sh.pslot[b];
-            if (!s.end) {
-                const ContractDev &c = p.contracts[s.ci];
-                sobol_to_z<KIND, kProducerWarps, false>(p, c, s.rep, s.tile, z_base + b * 2 * kOpBytesZ,
-                                                         z_base + b * 2 * kOpBytesZ + kOpBytesZ, 0, c.n);
-                fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
-            }
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) mbar_arrive(&sh.full[b]);
-            if (threadIdx.x == 0 && !tcw_issue<KIND>(p, sh, i, tmem, z_base, b_hi))
-                atomicCAS(&sh.abort, 0, 3);
-            __syncwarp();
-            if (s.end) break;
-        }
-    } else {
-        // ---- consumers: thread ct owns point ct of the tile (TMEM lane ct)
-        const int ct = threadIdx.x - kProducers;
-        const int quarter = ct >> 5;
-        __shared__ int32_t c_go;
-        for (int i = 0;; ++i) {
-            const int b = i & 1;
-            if (ct == 0) c_go = mbar_wait_or_abort(&sh.mma_done[b], static_cast<uint32_t>(i >> 1) & 1u, abort) ? 1 : 0;
-            named_sync(2, 32 * kConsumerWarps);
-            if (!c_go) {
-                atomicCAS(&sh.abort, 0, 3);
-                break;
-            }
-            const TileSlot s = sh.cslot[b];
-            if (s.end) break;
-            const ContractDev &c = p.contracts[s.ci];
-            tc_fence_after();
-            PathAcc<float> acc;
-            epilogue_dispatch<kNpad, 1>(c, tmem + static_cast<uint32_t>(b * 2 * kNpad), acc, 0, quarter);
-            tc_fence_before();
-            __syncwarp();
-            if ((ct & 31) == 0) mbar_arrive(&sh.tmem_free[b]);
-            ff v[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-            const uint64_t local_point = s.tile * kM + ct;
-            if (local_point < c.N) {
-                float xhat, dhat;
-                finish_functional(c, acc, xhat, dhat);
-                values_mixed(c, xhat, dhat, v);
-                if (p.point_out) {
-                    double *o = p.point_out + local_point * 4;
-                    for (int g = 0; g < 4; ++g) o[g] = ff_to_double(v[g]);
-                }
-            }
-            consumer_tile_sum(p.tile_sums + s.item * 4, v, vals, ct);
-        }
-    }
-
-    // release tensor memory (after an abort, first let the copy or the last
-    // products in flight land, with the same bounded wait)
-    tc_fence_before();
-    __syncthreads();
-    if (sh.abort && threadIdx.x == 0) {
-        if (sh.abort == 1) mbar_wait(&sh.bar_b, sh.b_phase & 1u);
-        const int last = sh.issued - 1;
-        if (last >= 0) mbar_wait(&sh.mma_done[last & 1], static_cast<uint32_t>(last >> 1) & 1u);
-        if (p.error_flag) atomicExch(p.error_flag, QMCCPW_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kColsW);
-    }
-}
-
 // d up to 257 (N = K = 256), Ahat streamed.  Ahat (384 KB bf16 in three
 // parts, 512 KB tf32 in two) does not fit beside Z, so it comes from L2 in
 // K-chunks of 16 dimensions (all parts of a chunk in one bulk TMA copy, 24 or
@@ -904,9 +643,8 @@ size_t pca_tc_smem_bytes(int kind) {
     const size_t scratch = std::max<size_t>(16 * kM * 4, 8 * kThreads * sizeof(float));
     if (kind == 2) return 1024 + 2 * static_cast<size_t>(Streamed<0>::ZPart) + 2 * Streamed<0>::ChunkBytes + scratch;
     if (kind == 3) return 1024 + 2 * static_cast<size_t>(Streamed<1>::ZPart) + 2 * Streamed<1>::ChunkBytes + scratch;
-    if (kind == 0)  // the warp-specialised kernel: two Z buffers, Ahat in three parts, the consumers' tile sum
-        return 1024 + 4 * static_cast<size_t>(kM) * kNpad * 2 + 3 * kNpad * kNpad * 2 + 8 * kM * sizeof(float);
-    return 1024 + 2 * kM * kNpad * 4 + 2 * kNpad * kNpad * 4 + scratch;
+    const size_t es = kind == 0 ? 2 : 4, parts = kind == 0 ? 3 : 2;
+    return 1024 + 2 * kM * kNpad * es + parts * kNpad * kNpad * es + scratch;
 }
 
 int pca_tc_max_n(int kind) { return kind >= 2 ? kNbig : kNpad; }
@@ -914,7 +652,7 @@ int pca_tc_max_n(int kind) { return kind >= 2 ? kNbig : kNpad; }
 int pca_tc_prepare(int kind, size_t smem_bytes) {
     const int b = static_cast<int>(smem_bytes);
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = kind == 0   ? cudaFuncSetAttribute(pca_tcw_kernel<0>, a, b)
+    cudaError_t e = kind == 0   ? cudaFuncSetAttribute(pca_tc_kernel<0>, a, b)
                     : kind == 1 ? cudaFuncSetAttribute(pca_tc_kernel<1>, a, b)
                     : kind == 2 ? cudaFuncSetAttribute(pca_tcs_kernel<0>, a, b)
                                 : cudaFuncSetAttribute(pca_tcs_kernel<1>, a, b);
@@ -930,7 +668,7 @@ int pca_tc_prepare(int kind, size_t smem_bytes) {
 // here; a grid larger than fits would only queue, the work list is dynamic.
 int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks) {
     cudaFuncAttributes fa{};
-    cudaError_t e = kind == 0   ? cudaFuncGetAttributes(&fa, pca_tcw_kernel<0>)
+    cudaError_t e = kind == 0   ? cudaFuncGetAttributes(&fa, pca_tc_kernel<0>)
                     : kind == 1 ? cudaFuncGetAttributes(&fa, pca_tc_kernel<1>)
                     : kind == 2 ? cudaFuncGetAttributes(&fa, pca_tcs_kernel<0>)
                                 : cudaFuncGetAttributes(&fa, pca_tcs_kernel<1>);
@@ -944,18 +682,18 @@ int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks) {
         return static_cast<int>(e);
     const size_t per_block = smem_bytes + fa.sharedSizeBytes + static_cast<size_t>(reserved);
     const int by_smem = static_cast<int>(static_cast<size_t>(smem_sm) / per_block);
-    const int threads = kind >= 2 ? kThreadsS : kind == 0 ? kThreadsW : kThreads;
+    const int threads = kind >= 2 ? kThreadsS : kThreads;
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
     const int by_regs = regs_warp > 0 ? (regs_sm / regs_warp) / (threads / 32) : 0;
     const int by_threads = threads_sm / threads;
-    const int by_tmem = 512 / (kind >= 2 ? 2 * kNbig : kind == 0 ? kColsW : 2 * kNpad);
+    const int by_tmem = 512 / (kind >= 2 ? 2 * kNbig : 2 * kNpad);
     *blocks = std::max(0, std::min(std::min(by_smem, by_regs), std::min(by_threads, by_tmem)));
     return 0;
 }
 
 int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (kind == 0) pca_tcw_kernel<0><<<grid, kThreadsW, smem_bytes, s>>>(p);
+    if (kind == 0) pca_tc_kernel<0><<<grid, kThreads, smem_bytes, s>>>(p);
     else if (kind == 1) pca_tc_kernel<1><<<grid, kThreads, smem_bytes, s>>>(p);
     else if (kind == 2) pca_tcs_kernel<0><<<grid, kThreadsS, smem_bytes, s>>>(p);
     else pca_tcs_kernel<1><<<grid, kThreadsS, smem_bytes, s>>>(p);

@@ -626,8 +626,82 @@ template <typename T>
 __device__ void lead_values(const ContractDev &c, const T *R, typename LeadOut<T>::type out[4]);
 
 // FP64: the formulas as they stand
+// The lookback: its maximum max_j c_j e^{b_j x} (c_j = S0 e^{omega t_j +
+// sigma R_j}) is the upper envelope of the lines ln c_j + b_j x, all
+// increasing, so x* is the smallest of the lines' own roots; right of it the
+// envelope is a run of pieces [u, v], one date each, the next date the first
+// steeper line to overtake the current one, and each piece contributes its
+// closed-form integral c_j e^{b^2/2} [Phi-bar(u - b) - Phi-bar(v - b)] (and
+// the matching vega term); gamma comes from moving x* along the line active
+// there.  In double for both precisions (R converted from float): the roots
+// and crossings are compared as fractions by cross-multiplication, so a
+// point takes one division for x* and one per piece boundary.
+template <typename T>
+__device__ void lead_lookback(const ContractDev &c, const T *R, double out[4]) {
+    const int d = c.d;
+    const double sig = c.sigma, omega = c.omega, dt = c.dt, lnK = c.ln_K;
+    auto lc_of = [&](int j) { return c.ln_S0 + omega * ((j + 1) * dt) + sig * static_cast<double>(R[j + 1]); };
+    // x* = min_j (ln K - lc_j) / b_j, ties to the steeper line
+    double num = 0.0, den = 1.0;
+    int cur = -1;
+    for (int j = 0; j < d; ++j) {
+        const double nj = lnK - lc_of(j), bj = sig * lead_loading<double>(c, j);
+        if (cur < 0 || nj * den < num * bj || (nj * den == num * bj && bj > den)) {
+            num = nj;
+            den = bj;
+            cur = j;
+        }
+    }
+    const double xs = num / den, b_star = den;
+    double price = 0.0, vega = 0.0, u = xs;
+    for (int piece = 0; piece < d; ++piece) {
+        const double lcc = lc_of(cur), bc = sig * lead_loading<double>(c, cur);
+        // the first steeper line to overtake: smallest (lcc - lc_j) / (b_j - bc) >= u
+        double vn = 0.0, vd = 0.0;  // the crossing as a fraction, vd > 0 once found
+        int next = -1;
+        for (int j = 0; j < d; ++j) {
+            const double bj = sig * lead_loading<double>(c, j);
+            if (!(bj > bc)) continue;
+            double nj = lcc - lc_of(j);
+            const double dj = bj - bc;
+            if (nj < u * dj) nj = u * dj;  // level with it at u already
+            if (next < 0 || nj * vd < vn * dj || (nj * vd == vn * dj && bj > sig * lead_loading<double>(c, next))) {
+                vn = nj;
+                vd = dj;
+                next = j;
+            }
+        }
+        const double ch = exp(lcc + 0.5 * bc * bc);
+        const double a = lead_loading<double>(c, cur);
+        const double t = (cur + 1) * dt;
+        const double su = 0.5 * erfc((u - bc) * 0.70710678118654752440);
+        const double pu = 0.39894228040143267794 * exp(-0.5 * (u - bc) * (u - bc));
+        double mass = su, dens = pu;
+        double v = 0.0;
+        if (next >= 0) {
+            v = vn / vd;
+            mass -= 0.5 * erfc((v - bc) * 0.70710678118654752440);
+            dens -= 0.39894228040143267794 * exp(-0.5 * (v - bc) * (v - bc));
+        }
+        price += ch * mass;
+        vega += ch * ((static_cast<double>(R[cur + 1]) - sig * t + a * bc) * mass + a * dens);
+        if (next < 0) break;
+        u = v;
+        cur = next;
+    }
+    const double disc = c.disc, S0 = c.S0, K = c.K;
+    out[0] = disc * (price - K * 0.5 * erfc(xs * 0.70710678118654752440));
+    out[1] = disc * price / S0;
+    out[2] = disc * vega;
+    out[3] = disc * K * 0.39894228040143267794 * exp(-0.5 * xs * xs) / (S0 * S0 * b_star);
+}
+
 template <>
 __device__ void lead_values<double>(const ContractDev &c, const double *R, double out[4]) {
+    if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
+        lead_lookback<double>(c, R, out);
+        return;
+    }
     using M = LeadMath<double>;
     const int d = c.d;
     const double dt = c.dt, sig = c.sigma, omega = c.omega, K = c.K, S0 = c.S0, disc = c.disc;
@@ -721,6 +795,12 @@ __device__ __forceinline__ ff lead_loading_ff(const ContractDev &c, int j) {
 
 template <>
 __device__ void lead_values<float>(const ContractDev &c, const float *R, ff out[4]) {
+    if (c.type == QMCCPW_LOOKBACK_FIXED_CALL) {
+        double o[4];
+        lead_lookback<float>(c, R, o);
+        for (int g = 0; g < 4; ++g) out[g] = split_to_ff(o[g]);
+        return;
+    }
     const int d = c.d;
     const double K = c.K, S0 = c.S0, disc = c.disc;
     const float sh = c.ff_sig[0], sl = c.ff_sig[1];

@@ -95,6 +95,7 @@ struct ContractDev {
     double inv_sigma;
     double inv_d;                        // 1/d
     double ln_lead_c0;                   // ln(S0/d): leading-coordinate constructions
+    double ln_S0;                        // ln S0 (the lookback under leading-coordinate conditioning)
     double ln_K;
     double lead_amean;                   // leading-coordinate constructions: mean over the dates of the loading times sqrt(dt)
     // constants of the float path as float hi + lo pairs (split_ff)

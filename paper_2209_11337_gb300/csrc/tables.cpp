@@ -182,6 +182,7 @@ void contract_constants(ContractDev &c) {
     c.psi0 = std::log(c.K / c.S0) - c.omega * c.dt;
     c.disc = std::exp(-c.r * c.T);
     c.ln_lead_c0 = std::log(c.S0 / c.d);
+    c.ln_S0 = std::log(c.S0);
     c.ln_K = std::log(c.K);
     c.disc1 = std::exp(c.r * (c.dt - c.T));
     c.sqrt_t1 = std::sqrt(c.dt);

@@ -52,36 +52,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
-// A plain arrival (release at CTA scope), `count` of the expected arrivals.
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar, uint32_t count = 1) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-// The same poll as mbar_wait that also gives up once *abort is set (by
-// another role of the CTA whose own wait expired).
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int32_t *abort,
-                                                   uint64_t limit_ns = kWaitLimitNs) {
-    const uint32_t addr = smem_u32(bar);
-    const uint64_t start = global_ns();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (*abort != 0 || global_ns() - start > limit_ns) return false;
-    }
-}
-
-// Barrier over the `count` threads (whole warps) of one role of the CTA.
-__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
