@@ -90,6 +90,8 @@ struct DTables {
     int n_levels = 0;
     DevBuf steps, w64, w32, level_start, pca64, pca32;
     DevBuf pca32lo;  // A^T - float(A^T): the leading-coordinate PCA carries the factor as hi + lo
+    DevBuf slot_dim;  // the bridge dimension that drives each date (the inverse of the steps' node)
+    DevBuf sub_start[3];  // bridge subtrees per thread of a point, G = 2, 4, 8 (bridge_phase)
     DevBuf lead64, lead32;  // loadings of the leading coordinate, dates 1..n: bridge (j/sqrt(n)) then PCA (first column)
     double lead_sum[2] = {0.0, 0.0};  // the sum of each form's loadings
     DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32; resident or streamed form by n), built on first use
@@ -291,6 +293,38 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
     QMC_TRY(t->w64.alloc(sizeof(double) * std::max<size_t>(1, bp.w.size())));
     QMC_TRY(t->w32.alloc(sizeof(float) * std::max<size_t>(1, w32.size())));
     QMC_TRY(t->level_start.alloc(sizeof(int32_t) * bp.level_start.size()));
+    std::vector<int32_t> slot_dim(static_cast<size_t>(n) + 1, -1);
+    for (int j = 0; j < n; ++j) slot_dim[bp.steps[j].m] = j;
+    QMC_TRY(t->slot_dim.alloc(sizeof(int32_t) * slot_dim.size()));
+    QMC_CUDA(cudaMemcpy(t->slot_dim.ptr, slot_dim.data(), sizeof(int32_t) * slot_dim.size(), cudaMemcpyHostToDevice));
+    // G threads per point: after the top levels that leave G intervals, the
+    // nodes of each deeper level that fall in interval g (the number of top
+    // split dates below the node's date) are a contiguous run; its start per
+    // (level, g), G + 1 entries per level
+    for (int gi = 0; gi < 3; ++gi) {
+        const int G = 2 << gi, top = gi + 2;
+        const int levels = t->n_levels;
+        std::vector<int32_t> ss;
+        std::vector<int> splits;
+        for (int lvl = 1; lvl < std::min(top, levels); ++lvl)
+            for (int b = bp.level_start[lvl]; b < bp.level_start[lvl + 1]; ++b) splits.push_back(bp.steps[b].m);
+        for (int lvl = top; lvl < levels; ++lvl) {
+            const int b0 = bp.level_start[lvl], b1 = bp.level_start[lvl + 1];
+            for (int g = 0; g <= G; ++g) {
+                int b = b0;
+                while (b < b1) {
+                    int sub = 0;
+                    for (int m : splits) sub += m < bp.steps[b].m ? 1 : 0;
+                    if (sub >= g) break;
+                    ++b;
+                }
+                ss.push_back(g == G ? b1 : b);
+            }
+        }
+        if (ss.empty()) ss.push_back(0);
+        QMC_TRY(t->sub_start[gi].alloc(sizeof(int32_t) * ss.size()));
+        QMC_CUDA(cudaMemcpy(t->sub_start[gi].ptr, ss.data(), sizeof(int32_t) * ss.size(), cudaMemcpyHostToDevice));
+    }
     QMC_TRY(t->pca64.alloc(sizeof(double) * std::max<size_t>(1, A.size())));
     QMC_TRY(t->pca32.alloc(sizeof(float) * std::max<size_t>(1, A32.size())));
     QMC_TRY(t->pca32lo.alloc(sizeof(float) * std::max<size_t>(1, A32lo.size())));
@@ -415,6 +449,10 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.w64 = t->w64.as<double>();
     c.w32 = t->w32.as<float>();
     c.level_start = t->level_start.as<int32_t>();
+    c.slot_dim = (c.construction == QMCCPW_BB && !c.z_by_dim) ? t->slot_dim.as<int32_t>() : nullptr;
+    c.sub_start = nullptr;
+    if (c.construction == QMCCPW_BB && !c.z_by_dim && c.groups >= 2 && c.groups <= 8)
+        c.sub_start = t->sub_start[c.groups == 2 ? 0 : c.groups == 4 ? 1 : 2].as<int32_t>();
     c.pca64 = t->pca64.as<double>();
     c.pcaT32 = t->pca32.as<float>();
     c.pcaT32lo = t->pca32lo.as<float>();

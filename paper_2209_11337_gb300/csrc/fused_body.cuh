@@ -185,33 +185,46 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     const BridgeTables t(c);
     const int32_t *level_start = c.level_start;
     const int n_levels = c.n_levels;
-    for (int lvl = 0; lvl < n_levels; ++lvl) {
-        const int b_end = __ldg(level_start + lvl + 1);
-        // the nodes of a level are independent: a thread takes two at a time
-        // (float: their exponentials in packed form)
-        for (int b = __ldg(level_start + lvl) + grp; b < b_end; b += 2 * G) {
-            int4 s0, s1;
-            if constexpr (sizeof(T) == 4) {
-                const PathConst k(c);
-                const float w0 = bridge_node<float, false>(t, row, b, s0);
-                if (b + G < b_end) {
-                    const float w1 = bridge_node<float, false>(t, row, b + G, s1);
-                    acc.template add2<TYPE>(s0.x, s1.x, w0, w1, k);
-                    continue;
-                }
-                acc.template add<TYPE>(s0.x, w0, k);
+    // nodes b and b + stride of one level (both independent): float takes
+    // their exponentials in packed form
+    auto two_nodes = [&](int b, bool second, int stride) {
+        int4 s0, s1;
+        if constexpr (sizeof(T) == 4) {
+            const PathConst k(c);
+            const float w0 = bridge_node<float, false>(t, row, b, s0);
+            if (second) {
+                const float w1 = bridge_node<float, false>(t, row, b + stride, s1);
+                acc.template add2<TYPE>(s0.x, s1.x, w0, w1, k);
             } else {
-                double omega, sigma, dt;
-                market_of(c, omega, sigma, dt);
-                const T W0 = bridge_node<T>(t, row, b, s0);
-                acc.template add<TYPE>(s0.x, W0, omega, sigma, static_cast<T>(__int_as_float(s0.w)) * dt);
-                if (b + G < b_end) {
-                    const T W1 = bridge_node<T>(t, row, b + G, s1);
-                    acc.template add<TYPE>(s1.x, W1, omega, sigma, static_cast<T>(__int_as_float(s1.w)) * dt);
-                }
+                acc.template add<TYPE>(s0.x, w0, k);
+            }
+        } else {
+            double omega, sigma, dt;
+            market_of(c, omega, sigma, dt);
+            const T W0 = bridge_node<T>(t, row, b, s0);
+            acc.template add<TYPE>(s0.x, W0, omega, sigma, static_cast<T>(__int_as_float(s0.w)) * dt);
+            if (second) {
+                const T W1 = bridge_node<T>(t, row, b + stride, s1);
+                acc.template add<TYPE>(s1.x, W1, omega, sigma, static_cast<T>(__int_as_float(s1.w)) * dt);
             }
         }
+    };
+    // With G threads per point and the subtree table: the top levels (up to
+    // the one that leaves G intervals) level by level with a barrier after
+    // each, then each thread its own interval's subtree, level by level and
+    // without barriers (a subtree reads only its own nodes and its ends).
+    const int top = (G > 1 && c.sub_start) ? min(n_levels, __ffs(G)) : n_levels;
+    for (int lvl = 0; lvl < top; ++lvl) {
+        const int b_end = __ldg(level_start + lvl + 1);
+        for (int b = __ldg(level_start + lvl) + grp; b < b_end; b += 2 * G) two_nodes(b, b + G < b_end, G);
         if (G > 1) __syncthreads();
+    }
+    if (top < n_levels) {
+        const int32_t *ss = c.sub_start + grp;
+        for (int lvl = top; lvl < n_levels; ++lvl, ss += G + 1) {
+            const int b_end = __ldg(ss + 1);
+            for (int b = __ldg(ss); b < b_end; b += 2) two_nodes(b, b + 1 < b_end, 1);
+        }
     }
 }
 
@@ -531,16 +544,26 @@ __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *_
         const int work = by_warp ? nchunks * ((n + 31) >> 5) : nchunks * n;
         for (int it = first; it < work; it += step) {
             int j, ch;
+            int slot;
             if (by_warp) {
                 const int per = (n + 31) >> 5;            // 32-wide dimension blocks per chunk
                 ch = it / per;
-                j = (it - ch * per) * 32 + (threadIdx.x & 31);
-                if (j >= n) continue;
+                const int idx = (it - ch * per) * 32 + (threadIdx.x & 31);
+                if (idx >= n) continue;
+                if (c.slot_dim) {
+                    // the shared-memory bridge: lanes take 32 consecutive slots of the
+                    // row (distinct banks), each the dimension whose node sits there
+                    slot = idx + 1;
+                    j = __ldg(c.slot_dim + slot);
+                } else {
+                    j = idx;
+                    slot = c.z_by_dim ? j + 1 + c.slot_shift : __ldg(&c.steps[j + c.slot_shift].m);
+                }
             } else {
                 j = it % n;
                 ch = it / n;
+                slot = c.z_by_dim ? j + 1 + c.slot_shift : __ldg(&c.steps[j + c.slot_shift].m);
             }
-            const int slot = c.z_by_dim ? j + 1 + c.slot_shift : __ldg(&c.steps[j + c.slot_shift].m);
             T *dst = zw + static_cast<size_t>(ch * chunk) * stride + slot;
             // points at or past N (ragged last tile) are never generated: their
             // index could pass 2^32; they are zero-filled and left out of the sums

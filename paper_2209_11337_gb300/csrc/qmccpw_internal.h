@@ -71,6 +71,8 @@ struct ContractDev {
     const double *w64;                   // 3 per step: wl, wr, c (sd = c sqrt(dt))
     const float *w32;                    // (hi, lo) float pairs of wl, wr, sd + 2 pad: 8 per step
     const int32_t *level_start;
+    const int32_t *slot_dim;             // shared-memory bridge (BB, z at its node): the dimension driving date m, m = 1..n; else null
+    const int32_t *sub_start;            // shared-memory bridge with G = groups threads per point: per level below the top ones, G + 1 run starts of the threads' subtrees; else null
     const double *pca64;                 // n x n row-major
     const float *pcaT32;                 // A^T as float, [k][i], i padded to a multiple of 16 with zeros
     const float *pcaT32lo;               // A^T - float(A^T) in the same layout (leading-coordinate PCA)
