@@ -19,7 +19,8 @@ __all__ = [
     "ARITH", "BINARY", "LOOKBACK", "GEOMETRIC", "BB", "PCA", "STD", "forward",
     "build", "lib", "primitive_polys", "direction_numbers", "scramble",
     "sobol", "inv_normal", "bridge", "pca_matrix", "point", "point_values",
-    "greeks", "partial_sums", "using_library", "compile_source",
+    "greeks", "partial_sums", "using_library", "compile_source", "Basket", "cholesky",
+    "basket_point", "basket_point_values", "basket_greeks",
 ]
 
 ARITH, BINARY, LOOKBACK, GEOMETRIC = 0, 1, 2, 3
@@ -72,6 +73,10 @@ def _load(path: str) -> ctypes.CDLL:
     L.oracle_point_values.argtypes = [u64, i, i, d, d, d, d, d, i, u32, u64, u64, dp]
     L.oracle_greeks.argtypes = [u64, i, i, d, d, d, d, d, i, u64, i, i, dp, dp, dp]
     L.oracle_partial_sums.argtypes = [u64, i, i, d, d, d, d, d, i, u32, i, u64, u64, i, dp]
+    L.oracle_cholesky.argtypes = [i, dp, dp]
+    L.oracle_basket_point.argtypes = [i, i, i, d, d, d, d, d, dp, dp, dp, dp, dp, dp]
+    L.oracle_basket_point_values.argtypes = [u64, i, i, i, d, d, d, d, d, dp, dp, dp, dp, u32, u64, u64, dp]
+    L.oracle_basket_greeks.argtypes = [u64, i, i, i, d, d, d, d, d, dp, dp, dp, dp, u64, i, i, dp, dp, dp]
     return L
 
 
@@ -206,3 +211,63 @@ def partial_sums(seed: int, opt: int, d: int, K: float, T: float, S0: float, r: 
     _check(lib().oracle_partial_sums(seed, opt, d, K, T, S0, r, sigma, construction, r0, nrep, k0,
                                      count, threads, _f64(out)), "partial_sums")
     return out
+
+
+# ---------------------------------------------------------------------------
+# basket of m assets (Sec. 6's multi-asset extension; see qmccpw_oracle.h)
+# ---------------------------------------------------------------------------
+class Basket:
+    """A basket contract: type (ARITH or BINARY on the basket average), d
+    dates, strike K, maturity T, spot scale S0, rate r, volatility scale
+    sigma, and per asset the weight w, relative spot a, relative volatility
+    v, plus the correlation matrix corr (m x m)."""
+
+    def __init__(self, type_, d, K, T, S0, r, sigma, w, a, v, corr):
+        self.type, self.d, self.K, self.T, self.S0, self.r, self.sigma = type_, d, K, T, S0, r, sigma
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+        self.a = np.ascontiguousarray(a, dtype=np.float64)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        self.corr = np.ascontiguousarray(corr, dtype=np.float64)
+        self.m = len(self.w)
+
+    def replace(self, **kw):
+        args = dict(type_=self.type, d=self.d, K=self.K, T=self.T, S0=self.S0, r=self.r, sigma=self.sigma,
+                    w=self.w, a=self.a, v=self.v, corr=self.corr)
+        args.update(kw)
+        return Basket(**args)
+
+    def _args(self):
+        return (self.type, self.d, self.m, self.K, self.T, self.S0, self.r, self.sigma,
+                _f64(self.w), _f64(self.a), _f64(self.v), _f64(self.corr))
+
+
+def cholesky(C) -> np.ndarray:
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    m = C.shape[0]
+    L = np.zeros((m, m))
+    _check(lib().oracle_cholesky(m, _f64(C), _f64(L)), "cholesky")
+    return L
+
+
+def basket_point(b: Basket, z) -> np.ndarray:
+    """Values (price, delta, vega, gamma) of one point from its m d - 1 normals."""
+    z = np.ascontiguousarray(z if b.m * b.d > 1 else np.zeros(1), dtype=np.float64)
+    out = np.zeros(4)
+    _check(lib().oracle_basket_point(*b._args(), _f64(z), _f64(out)), "basket_point")
+    return out
+
+
+def basket_point_values(seed: int, b: Basket, rep: int, k0: int, count: int) -> np.ndarray:
+    out = np.zeros((count, 4))
+    _check(lib().oracle_basket_point_values(seed, *b._args(), rep, k0, count, _f64(out)), "basket_point_values")
+    return out
+
+
+def basket_greeks(seed: int, b: Basket, N: int, R: int, threads: int = 0):
+    """Full estimator of a basket: (mean[4], se[4], per_replicate[R,4])."""
+    per = np.zeros((R, 4))
+    mean = np.zeros(4)
+    se = np.zeros(4)
+    _check(lib().oracle_basket_greeks(seed, *b._args(), N, R, threads, _f64(per), _f64(mean), _f64(se)),
+           "basket_greeks")
+    return mean, se, per

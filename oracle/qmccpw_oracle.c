@@ -810,3 +810,268 @@ int oracle_greeks(uint64_t seed, int type, int d, double K, double T, double S0,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Basket of m assets (Sec. 6: the same simulation with several underlying   */
+/* assets, the path and the payoff formulas redefined).                       */
+/*   S_i(t) = a_i S0 exp(omega_i t + sigma_i W_i(t)), sigma_i = v_i sigma,    */
+/*   omega_i = r - sigma_i^2/2, W = L B with L the lower Cholesky factor of   */
+/*   the correlation matrix (L_11 = 1) and B m independent Brownian motions;  */
+/*   the basket average X = sum_i w_i (1/d) sum_j S_i(t_j).                   */
+/* The first increment of factor 1, B_1(t_1) = sqrt(t_1) x_1, is integrated  */
+/* out as in Sec. 3.3.1: each factor k is B_k(t_j) = sqrt(t_1) x_k +         */
+/* W~_k(t_j - t_1) with W~_k built by the bridge from its own n = d-1         */
+/* normals, so W_i(t_j) = L_i1 sqrt(t_1) x_1 + R_ij with                     */
+/*   R_ij = sum_k L_ik W~_k(t_j - t_1) + sum_{k>=2} L_ik sqrt(t_1) x_k,        */
+/* and X(x_1) = sum_i C_i e^{b_i x_1}, b_i = sigma_i L_i1 sqrt(t_1),          */
+/*   C_i = (w_i a_i S0 / d) sum_j exp(omega_i t_j + sigma_i R_ij).            */
+/* With every correlation to asset 1 positive, all b_i > 0: X is increasing */
+/* in x_1 from 0, and the switch point x* of X(x*) = K is found by Newton's  */
+/* method on ln X - ln K (convex, increasing).  Integrating x_1 out         */
+/* (E[e^{b x}; x > x*] = e^{b^2/2} Phi-bar(x* - b)):                          */
+/*   call:   e^{-rT} [ sum_i C_i e^{b_i^2/2} Phi-bar(x* - b_i) - K Phi-bar(x*) ] */
+/*   binary: e^{-rT} Phi-bar(x*)                                             */
+/* Greeks at fixed z: delta and gamma with respect to the spot scale S0 (all */
+/* spots move together), vega with respect to the volatility scale sigma     */
+/* (all volatilities move together); with D_i = (w_i a_i S0/d) sum_j         */
+/* exp(omega_i t_j + sigma_i R_ij) (R_ij - sigma_i t_j), X' = sum_i C_i b_i    */
+/* e^{b_i x*}, X'' = sum_i C_i b_i^2 e^{b_i x*}:                              */
+/*   call delta  e^{-rT} sum_i (C_i/S0) e^{b_i^2/2} Phi-bar(x* - b_i)          */
+/*   call gamma  e^{-rT} K^2 phi(x*) / (S0^2 X')                              */
+/*   call vega   e^{-rT} sum_i v_i e^{b_i^2/2} [D_i Phi-bar(x* - b_i)          */
+/*               + C_i L_i1 sqrt(t_1) (b_i Phi-bar(x* - b_i) + phi(x* - b_i))] */
+/*   binary delta e^{-rT} phi(x*) K / (S0 X')                                 */
+/*   binary gamma e^{-rT} K phi(x*) (x* K - 2 X' + K X''/X') / (S0 X')^2      */
+/*   binary vega  e^{-rT} phi(x*) sum_i v_i e^{b_i x*} [D_i + C_i L_i1 sqrt(t_1) x*] / X' */
+/* (the terms from moving x* cancel in the call price since X(x*) = K).      */
+/* Sobol' dimensions: b m + (k-1) drives bridge node b (0..n-1) of factor k  */
+/* (1..m); n m + (k-2) drives x_k, k = 2..m: m d - 1 in all.  With m = 1 this */
+/* is the single-asset bridge estimator point by point.                       */
+/* ------------------------------------------------------------------------ */
+#define ORACLE_ASSETS_MAX 8
+
+typedef struct {
+    int type, d, m;
+    double K, T, S0, r, sigma;
+    double w[ORACLE_ASSETS_MAX], a[ORACLE_ASSETS_MAX], v[ORACLE_ASSETS_MAX];
+    double L[ORACLE_ASSETS_MAX * ORACLE_ASSETS_MAX];
+} basket_t;
+
+/* Cholesky factor of a symmetric positive definite m x m matrix (row-major):
+ * L lower triangular with C = L L^T, by the Cholesky-Banachiewicz order.  */
+int oracle_cholesky(int m, const double *C, double *L)
+{
+    if (m < 1 || m > ORACLE_ASSETS_MAX || !C || !L) return -1;
+    for (int i = 0; i < m * m; ++i) L[i] = 0.0;
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = C[i * m + j];
+            for (int k = 0; k < j; ++k) s -= L[i * m + k] * L[j * m + k];
+            if (i == j) {
+                if (!(s > 0.0)) return -1;
+                L[i * m + i] = sqrt(s);
+            } else {
+                L[i * m + j] = s / L[j * m + j];
+            }
+        }
+    }
+    return 0;
+}
+
+static int basket_init(basket_t *b, int type, int d, int m, double K, double T, double S0, double r,
+                       double sigma, const double *w, const double *a, const double *v, const double *corr)
+{
+    memset(b, 0, sizeof(*b));
+    if (type != 0 && type != 1) return -1;
+    if (m < 1 || m > ORACLE_ASSETS_MAX || d < 1 || (int64_t)m * d > MAX_DIMS) return -1;
+    if (!w || !a || !v || !corr) return -1;
+    if (!(K > 0.0) || !(T > 0.0) || !(S0 > 0.0) || !(sigma > 0.0)) return -1;
+    if (!isfinite(K) || !isfinite(T) || !isfinite(S0) || !isfinite(sigma) || !isfinite(r)) return -1;
+    if (!(w[0] > 0.0)) return -1;
+    for (int i = 0; i < m; ++i) {
+        if (!(w[i] >= 0.0) || !(a[i] > 0.0) || !(v[i] > 0.0)) return -1;
+        if (!isfinite(w[i]) || !isfinite(a[i]) || !isfinite(v[i])) return -1;
+        if (!(corr[i] > 0.0) || corr[i * m + i] != 1.0) return -1;  /* positive correlation to asset 1, unit diagonal */
+        for (int k = 0; k < m; ++k)
+            if (corr[i * m + k] != corr[k * m + i] || !(fabs(corr[i * m + k]) <= 1.0)) return -1;
+    }
+    b->type = type; b->d = d; b->m = m;
+    b->K = K; b->T = T; b->S0 = S0; b->r = r; b->sigma = sigma;
+    for (int i = 0; i < m; ++i) { b->w[i] = w[i]; b->a[i] = a[i]; b->v[i] = v[i]; }
+    double L[ORACLE_ASSETS_MAX * ORACLE_ASSETS_MAX];
+    if (oracle_cholesky(m, corr, L) != 0) return -1;
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < m; ++k) b->L[i * ORACLE_ASSETS_MAX + k] = L[i * m + k];
+    return 0;
+}
+
+/* The four values of one point from its m d - 1 normals z. */
+static int basket_values(const basket_t *b, const double *z, double out[4])
+{
+    const int d = b->d, m = b->m, n = d - 1;
+    const double dt = b->T / d, t1 = dt, st1 = sqrt(t1);
+    double *Wt = (double *)malloc(sizeof(double) * (size_t)m * (size_t)(n + 1));
+    double *zk = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!Wt || !zk) { free(Wt); free(zk); return -1; }
+    for (int k = 0; k < m; ++k) {            /* factor k+1: W~ over s_0..s_n */
+        for (int bnode = 0; bnode < n; ++bnode) zk[bnode] = z[bnode * m + k];
+        if (oracle_bridge(n, dt, zk, Wt + (size_t)k * (n + 1)) != 0) { free(Wt); free(zk); return -1; }
+    }
+    double C[ORACLE_ASSETS_MAX], D[ORACLE_ASSETS_MAX], bb[ORACLE_ASSETS_MAX], sig[ORACLE_ASSETS_MAX];
+    for (int i = 0; i < m; ++i) {
+        const double *Li = b->L + i * ORACLE_ASSETS_MAX;
+        sig[i] = b->v[i] * b->sigma;
+        const double om = b->r - 0.5 * sig[i] * sig[i];
+        double first = 0.0;                  /* sum_{k>=2} L_ik sqrt(t_1) x_k */
+        for (int k = 1; k < m; ++k) first += Li[k] * st1 * z[n * m + (k - 1)];
+        double sc = 0.0, sd = 0.0;
+        for (int j = 1; j <= d; ++j) {
+            const double tj = j * dt;
+            double R = first;
+            for (int k = 0; k < m; ++k) R += Li[k] * Wt[(size_t)k * (n + 1) + (j - 1)];
+            const double e = exp(om * tj + sig[i] * R);
+            sc += e;
+            sd += e * (R - sig[i] * tj);
+        }
+        const double f = b->w[i] * b->a[i] * b->S0 / d;
+        C[i] = f * sc;
+        D[i] = f * sd;
+        bb[i] = sig[i] * Li[0] * st1;
+    }
+    free(Wt); free(zk);
+    /* Newton on ln X(x) - ln K from x = 0 (log-sum-exp with its largest term factored out) */
+    double x = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        double mx = -INFINITY;
+        for (int i = 0; i < m; ++i) if (C[i] > 0.0) mx = fmax(mx, log(C[i]) + bb[i] * x);
+        double s0 = 0.0, s1 = 0.0;
+        for (int i = 0; i < m; ++i) {
+            if (!(C[i] > 0.0)) continue;
+            const double e = exp(log(C[i]) + bb[i] * x - mx);
+            s0 += e;
+            s1 += bb[i] * e;
+        }
+        const double step = (mx + log(s0) - log(b->K)) / (s1 / s0);
+        x -= step;
+        if (fabs(step) <= 1e-15 * (1.0 + fabs(x))) break;
+    }
+    const double disc = exp(-b->r * b->T), pdf = norm_pdf(x), K = b->K, S0 = b->S0;
+    double F0 = 0.0, X1 = 0.0, X2 = 0.0, V = 0.0, B = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const double l1 = b->L[i * ORACLE_ASSETS_MAX] * st1;    /* L_i1 sqrt(t_1) */
+        const double e = C[i] * exp(bb[i] * x);                   /* C_i e^{b_i x*} */
+        const double eh = C[i] * exp(0.5 * bb[i] * bb[i]);        /* C_i e^{b_i^2/2} */
+        const double sfb = phi_bar(x - bb[i]);
+        F0 += eh * sfb;
+        X1 += bb[i] * e;
+        X2 += bb[i] * bb[i] * e;
+        V += b->v[i] * exp(0.5 * bb[i] * bb[i]) * (D[i] * sfb + C[i] * l1 * (bb[i] * sfb + norm_pdf(x - bb[i])));
+        B += b->v[i] * exp(bb[i] * x) * (D[i] + C[i] * l1 * x);
+    }
+    if (b->type == 0) {
+        out[0] = disc * (F0 - K * phi_bar(x));
+        out[1] = disc * F0 / S0;
+        out[2] = disc * V;
+        out[3] = disc * K * K * pdf / (S0 * S0 * X1);
+    } else {
+        out[0] = disc * phi_bar(x);
+        out[1] = disc * pdf * K / (S0 * X1);
+        out[2] = disc * pdf * B / X1;
+        out[3] = disc * K * pdf * (x * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1));
+    }
+    return 0;
+}
+
+int oracle_basket_point(int type, int d, int m, double K, double T, double S0, double r, double sigma,
+                        const double *w, const double *a, const double *v, const double *corr,
+                        const double *z, double out[4])
+{
+    basket_t b;
+    if (basket_init(&b, type, d, m, K, T, S0, r, sigma, w, a, v, corr) != 0 || !out) return -1;
+    if (m * d > 1 && !z) return -1;
+    return basket_values(&b, z, out);
+}
+
+/* Sums over points k0..k0+count-1 of replicate rep (per_point optional). */
+static int basket_replicate_sums(const basket_t *b, uint64_t seed, const uint32_t *v, uint32_t rep,
+                                 uint64_t k0, uint64_t count, double sums[4], double *per_point)
+{
+    const int nd = b->m * b->d - 1;
+    uint32_t *rows = NULL, *shift = NULL;
+    double *z = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+    int rc = z ? 0 : -1;
+    if (rc == 0 && nd > 0) {
+        rows = (uint32_t *)malloc(sizeof(uint32_t) * 32u * (size_t)nd);
+        shift = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)nd);
+        if (!rows || !shift) rc = -1;
+        else for (int j = 0; j < nd; ++j) oracle_scramble(seed, rep, (uint32_t)j, rows + 32 * j, shift + j);
+    }
+    neumaier_t acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (uint64_t t = 0; rc == 0 && t < count; ++t) {
+        const uint64_t k = k0 + t, index = k ^ (k >> 1);
+        for (int j = 0; j < nd; ++j) {
+            const uint32_t y = scramble_apply(rows + 32 * j, shift[j], sobol_unscrambled(v + 32 * j, index));
+            z[j] = oracle_inv_normal(((double)y + 0.5) * 0x1p-32);
+        }
+        double val[4];
+        rc = basket_values(b, z, val);
+        if (rc != 0) break;
+        for (int g = 0; g < 4; ++g) neumaier_add(&acc[g], val[g]);
+        if (per_point) for (int g = 0; g < 4; ++g) per_point[t * 4 + (uint64_t)g] = val[g];
+    }
+    for (int g = 0; g < 4; ++g) sums[g] = neumaier_value(&acc[g]);
+    free(z); free(rows); free(shift);
+    return rc;
+}
+
+int oracle_basket_point_values(uint64_t seed, int type, int d, int m, double K, double T, double S0,
+                               double r, double sigma, const double *w, const double *a, const double *v,
+                               const double *corr, uint32_t rep, uint64_t k0, uint64_t count, double *out)
+{
+    basket_t b;
+    if (basket_init(&b, type, d, m, K, T, S0, r, sigma, w, a, v, corr) != 0 || !out) return -1;
+    if (k0 + count > (1ull << 32) || k0 + count < k0) return -1;
+    const int nd = m * d - 1;
+    uint32_t *dirs = (uint32_t *)malloc(sizeof(uint32_t) * 32u * (size_t)(nd > 0 ? nd : 1));
+    if (!dirs || oracle_direction_numbers(nd, dirs) != 0) { free(dirs); return -1; }
+    double sums[4];
+    const int rc = basket_replicate_sums(&b, seed, dirs, rep, k0, count, sums, out);
+    free(dirs);
+    return rc;
+}
+
+int oracle_basket_greeks(uint64_t seed, int type, int d, int m, double K, double T, double S0, double r,
+                         double sigma, const double *w, const double *a, const double *v, const double *corr,
+                         uint64_t N, int R, int threads, double *per_rep, double *mean, double *se)
+{
+    basket_t b;
+    if (basket_init(&b, type, d, m, K, T, S0, r, sigma, w, a, v, corr) != 0) return -1;
+    if (N < 1 || N > (1ull << 32) || R < 2 || !per_rep || !mean || !se) return -1;
+    const int nd = m * d - 1;
+    uint32_t *dirs = (uint32_t *)malloc(sizeof(uint32_t) * 32u * (size_t)(nd > 0 ? nd : 1));
+    if (!dirs || oracle_direction_numbers(nd, dirs) != 0) { free(dirs); return -1; }
+    int bad = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (int i = 0; i < R; ++i)
+        if (basket_replicate_sums(&b, seed, dirs, (uint32_t)i, 0u, N, per_rep + 4 * i, NULL) != 0) bad |= 1;
+    (void)threads;
+    free(dirs);
+    if (bad) return -1;
+    for (int i = 0; i < R * 4; ++i) per_rep[i] /= (double)N;
+    for (int g = 0; g < 4; ++g) {
+        neumaier_t acc = {0, 0};
+        for (int i = 0; i < R; ++i) neumaier_add(&acc, per_rep[4 * i + g]);
+        const double mu = neumaier_value(&acc) / R;
+        neumaier_t dev = {0, 0};
+        for (int i = 0; i < R; ++i) {
+            const double e = per_rep[4 * i + g] - mu;
+            neumaier_add(&dev, e * e);
+        }
+        mean[g] = mu;
+        se[g] = sqrt(neumaier_value(&dev) / ((double)R * (double)(R - 1)));
+    }
+    return 0;
+}

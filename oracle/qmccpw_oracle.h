@@ -86,6 +86,27 @@ int oracle_partial_sums(uint64_t seed, int type, int d, double K, double T, doub
                         double r, double sigma, int construction, uint32_t r0, int nrep,
                         uint64_t k0, uint64_t count, int threads, double *sums);
 
+/* Basket of m <= 8 assets (Sec. 6's multi-asset extension): types 0
+ * (arithmetic-Asian call on the basket average) and 1 (binary on it), bridge
+ * per factor, the first increment of factor 1 integrated out, switch point
+ * by Newton's method.  w[m] weights (w[0] > 0, others >= 0), a[m] relative
+ * spots (S_i(0) = a_i S0), v[m] relative volatilities (sigma_i = v_i sigma),
+ * corr[m*m] the correlation matrix (row-major, symmetric positive definite,
+ * unit diagonal, corr[0][i] > 0).  Delta and gamma are with respect to the
+ * spot scale S0, vega to the volatility scale sigma.  z holds m*d-1 normals:
+ * z[b*m + k] drives bridge node b (0..d-2) of factor k+1 (k = 0..m-1), and
+ * z[(d-1)*m + k-1] the first increment of factor k+1 (k = 1..m-1). */
+int oracle_cholesky(int m, const double *C, double *L);
+int oracle_basket_point(int type, int d, int m, double K, double T, double S0, double r, double sigma,
+                        const double *w, const double *a, const double *v, const double *corr,
+                        const double *z, double out[4]);
+int oracle_basket_point_values(uint64_t seed, int type, int d, int m, double K, double T, double S0,
+                               double r, double sigma, const double *w, const double *a, const double *v,
+                               const double *corr, uint32_t rep, uint64_t k0, uint64_t count, double *out);
+int oracle_basket_greeks(uint64_t seed, int type, int d, int m, double K, double T, double S0, double r,
+                         double sigma, const double *w, const double *a, const double *v, const double *corr,
+                         uint64_t N, int R, int threads, double *per_rep, double *mean, double *se);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_basket as basket
 import test_oracle_cpw as cpw
 import test_oracle_lead as lead
 import test_oracle_paths as paths
@@ -82,6 +83,18 @@ MUTANTS = {
     "leading-coordinate loading read from the second PCA column": (
         "a[j] = A[(size_t)j * (size_t)d];", "a[j] = A[(size_t)j * (size_t)d + 1];",
         lambda o: lead.test_lead_value_equals_quadrature_over_the_leading_coordinate(o, 0, 7, 4)),
+    "basket loading of x_1 without the correlation": (
+        "bb[i] = sig[i] * Li[0] * st1;", "bb[i] = sig[i] * st1;",
+        lambda o: basket.test_basket_point_equals_quadrature_over_first_increment(o, 0, 5, 3)),
+    "basket vega without the relative volatility": (
+        "V += b->v[i] * exp(0.5 * bb[i] * bb[i])", "V += exp(0.5 * bb[i] * bb[i])",
+        lambda o: basket.test_basket_greeks_equal_finite_differences(o, 0, 4, 3)),
+    "basket binary vega without the switch-point term": (
+        "(D[i] + C[i] * l1 * x)", "(D[i])",
+        lambda o: basket.test_basket_greeks_equal_finite_differences(o, 1, 4, 3)),
+    "basket bridge nodes read factor-major": (
+        "zk[bnode] = z[bnode * m + k];", "zk[bnode] = z[k * n + bnode];",
+        lambda o: basket.test_sobol_layout_of_the_basket(o)),
     "inverse normal Halley step with the wrong sign": (
         "z -= step;", "z += step;",
         lambda o: paths.test_inverse_normal_published_quantiles(o)),
