@@ -787,15 +787,10 @@ int oracle_partial_sums(uint64_t seed, int type, int d, double K, double T, doub
     return bad ? -1 : 0;
 }
 
-int oracle_greeks(uint64_t seed, int type, int d, double K, double T, double S0, double r,
-                  double sigma, int construction, uint64_t N, int R, int threads,
-                  double *per_rep, double *mean, double *se)
+/* Mean over the R replicate estimates (rows of 4) and the standard error of
+ * that mean, sqrt(sum (C_r - C)^2 / (R (R-1))), both sums compensated. */
+static void replicate_mean_se(const double *per_rep, int R, double *mean, double *se)
 {
-    if (N < 1 || N > (1ull << 32) || R < 2 || !per_rep || !mean || !se) return -1;
-    int rc = oracle_partial_sums(seed, type, d, K, T, S0, r, sigma, construction, 0u, R, 0u, N,
-                                 threads, per_rep);
-    if (rc != 0) return rc;
-    for (int i = 0; i < R * 4; ++i) per_rep[i] /= (double)N;
     for (int g = 0; g < 4; ++g) {
         neumaier_t acc = {0, 0};
         for (int i = 0; i < R; ++i) neumaier_add(&acc, per_rep[4 * i + g]);
@@ -808,6 +803,18 @@ int oracle_greeks(uint64_t seed, int type, int d, double K, double T, double S0,
         mean[g] = m;
         se[g] = sqrt(neumaier_value(&dev) / ((double)R * (double)(R - 1)));
     }
+}
+
+int oracle_greeks(uint64_t seed, int type, int d, double K, double T, double S0, double r,
+                  double sigma, int construction, uint64_t N, int R, int threads,
+                  double *per_rep, double *mean, double *se)
+{
+    if (N < 1 || N > (1ull << 32) || R < 2 || !per_rep || !mean || !se) return -1;
+    int rc = oracle_partial_sums(seed, type, d, K, T, S0, r, sigma, construction, 0u, R, 0u, N,
+                                 threads, per_rep);
+    if (rc != 0) return rc;
+    for (int i = 0; i < R * 4; ++i) per_rep[i] /= (double)N;
+    replicate_mean_se(per_rep, R, mean, se);
     return 0;
 }
 
@@ -977,7 +984,8 @@ static int basket_values(const basket_t *b, const double *z, double out[4])
         out[0] = disc * phi_bar(x);
         out[1] = disc * pdf * K / (S0 * X1);
         out[2] = disc * pdf * B / X1;
-        out[3] = disc * K * pdf * (x * K - 2.0 * X1 + K * X2 / X1) / ((S0 * X1) * (S0 * X1));
+        const double sx = S0 * X1;
+        out[3] = disc * K * pdf * (K * x - 2.0 * X1 + K * X2 / X1) / (sx * sx);
     }
     return 0;
 }
@@ -1061,17 +1069,6 @@ int oracle_basket_greeks(uint64_t seed, int type, int d, int m, double K, double
     free(dirs);
     if (bad) return -1;
     for (int i = 0; i < R * 4; ++i) per_rep[i] /= (double)N;
-    for (int g = 0; g < 4; ++g) {
-        neumaier_t acc = {0, 0};
-        for (int i = 0; i < R; ++i) neumaier_add(&acc, per_rep[4 * i + g]);
-        const double mu = neumaier_value(&acc) / R;
-        neumaier_t dev = {0, 0};
-        for (int i = 0; i < R; ++i) {
-            const double e = per_rep[4 * i + g] - mu;
-            neumaier_add(&dev, e * e);
-        }
-        mean[g] = mu;
-        se[g] = sqrt(neumaier_value(&dev) / ((double)R * (double)(R - 1)));
-    }
+    replicate_mean_se(per_rep, R, mean, se);
     return 0;
 }
