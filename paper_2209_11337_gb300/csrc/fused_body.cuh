@@ -575,11 +575,10 @@ __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *_
                 const uint32_t y0 = from_tile ? sobol_from_gray(tab, jstride, j, tile_start[j], off ^ (off >> 1))
                                               : sobol_first(tab, jstride, j, __ldg(shf + j), k0);
                 if constexpr (sizeof(T) == 4) {
-                    sobol_point_pairs(
+                    sobol_point_deferred(
                         tab, jstride, j, y0, k0, len, c.chunk_log2,
                         [&](int s, uint32_t y) { dst[s * stride] = Arith<float>::inv_normal(y); },
-                        [&](int s, uint32_t y0, uint32_t y1) {
-                            const float2 z = Arith<float>::inv_normal2(y0, y1);
+                        [&](int s, float2 z) {
                             dst[s * stride] = z.x;
                             dst[(s + 1) * stride] = z.y;
                         });

@@ -172,38 +172,61 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
     tile_sum(p.tile_sums + item * 4, v, scratch);
 }
 
-// Two Gray-code chains (dimensions ja and jb) over the same run of points,
-// emit(s, y_ja(k0+s), y_jb(k0+s)); a full aligned run of 4..64 points is
-// unrolled with both dimensions' direction integers in registers.
-template <int LG, typename Emit>
-__device__ __forceinline__ void chain_pair_run(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
-                                               uint32_t ya, uint32_t yb, Emit &&emit) {
+// Two Gray-code chains (dimensions ja and jb) over the same run of points.
+// A full aligned run of 4..64 points is unrolled with both dimensions'
+// direction integers in registers and the inverse normal's tail test taken
+// out of the unrolled body: emitz(s, z) receives the central values of point
+// s and a bit per point records a tail draw; after the run each recorded
+// point (rare) is rebuilt from the run's first point by the bits of its Gray
+// index and its exact values emitted again.  Other runs go point by point,
+// emit(s, y_ja(k0+s), y_jb(k0+s)).
+template <int LG, typename EmitZ>
+__device__ __forceinline__ void chain_pair_run_deferred(const uint32_t *__restrict__ tab, int jstride, int ja,
+                                                        int jb, uint32_t ya, uint32_t yb, EmitZ &&emitz) {
     uint32_t va[LG], vb[LG];
 #pragma unroll
     for (int b = 0; b < LG; ++b) {
         va[b] = __ldg(tab + b * jstride + ja);
         vb[b] = __ldg(tab + b * jstride + jb);
     }
-    emit(0, ya, yb);
+    const uint32_t ya0 = ya, yb0 = yb;
+    uint64_t redo = 0;
 #pragma unroll
-    for (int s = 1; s < (1 << LG); ++s) {
-        ya ^= va[ctz_const(s)];
-        yb ^= vb[ctz_const(s)];
-        emit(s, ya, yb);
+    for (int s = 0; s < (1 << LG); ++s) {
+        if (s > 0) {
+            ya ^= va[ctz_const(s)];
+            yb ^= vb[ctz_const(s)];
+        }
+        float2 z;
+        if (Arith<float>::inv_normal2_central(ya, yb, z)) redo |= 1ull << s;
+        emitz(s, z);
+    }
+    while (redo) {
+        const int s = __ffsll(static_cast<long long>(redo)) - 1;
+        redo &= redo - 1ull;
+        const uint32_t g = static_cast<uint32_t>(s) ^ (static_cast<uint32_t>(s) >> 1);
+        uint32_t a = ya0, b2 = yb0;
+#pragma unroll
+        for (int b = 0; b < LG; ++b)
+            if ((g >> b) & 1u) {
+                a ^= va[b];
+                b2 ^= vb[b];
+            }
+        emitz(s, Arith<float>::inv_normal2(a, b2));
     }
 }
 
-template <typename Emit>
-__device__ __forceinline__ void sobol_chain_pair(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
-                                                 uint32_t ya, uint32_t yb, uint32_t k0, int len, int chunk_log2,
-                                                 Emit &&emit) {
+template <typename Emit, typename EmitZ>
+__device__ __forceinline__ void sobol_chain_deferred(const uint32_t *__restrict__ tab, int jstride, int ja, int jb,
+                                                     uint32_t ya, uint32_t yb, uint32_t k0, int len, int chunk_log2,
+                                                     Emit &&emit, EmitZ &&emitz) {
     if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
         switch (chunk_log2) {
-            case 2: chain_pair_run<2>(tab, jstride, ja, jb, ya, yb, emit); return;
-            case 3: chain_pair_run<3>(tab, jstride, ja, jb, ya, yb, emit); return;
-            case 4: chain_pair_run<4>(tab, jstride, ja, jb, ya, yb, emit); return;
-            case 5: chain_pair_run<5>(tab, jstride, ja, jb, ya, yb, emit); return;
-            case 6: chain_pair_run<6>(tab, jstride, ja, jb, ya, yb, emit); return;
+            case 2: chain_pair_run_deferred<2>(tab, jstride, ja, jb, ya, yb, emitz); return;
+            case 3: chain_pair_run_deferred<3>(tab, jstride, ja, jb, ya, yb, emitz); return;
+            case 4: chain_pair_run_deferred<4>(tab, jstride, ja, jb, ya, yb, emitz); return;
+            case 5: chain_pair_run_deferred<5>(tab, jstride, ja, jb, ya, yb, emitz); return;
+            case 6: chain_pair_run_deferred<6>(tab, jstride, ja, jb, ya, yb, emitz); return;
             default: break;
         }
     }
@@ -276,7 +299,8 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
             auto emit = [&](int s, uint32_t a, uint32_t b) {
                 split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), Arith<float>::inv_normal2(a, b));
             };
-            sobol_chain_pair(tab, p.jstride, ja, jb, ya, yb, k0, len, c.chunk_log2, emit);
+            auto emitz = [&](int s, float2 z) { split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), z); };
+            sobol_chain_deferred(tab, p.jstride, ja, jb, ya, yb, k0, len, c.chunk_log2, emit, emitz);
         }
         for (int s = len; s < chunk; ++s)
             split_store_pair<KIND>(z_hi, z_lo, z_offset<ES>(row0 + s, col), make_float2(0.0f, 0.0f));

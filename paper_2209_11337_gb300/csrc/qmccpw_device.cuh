@@ -259,6 +259,30 @@ template <> struct Arith<float> {
         const float2 z = mul2(xm, p);
         return make_float2(__uint_as_float(__float_as_uint(z.x) ^ s0), __uint_as_float(__float_as_uint(z.y) ^ s1));
     }
+    // The central branch of a pair alone (the results of inv_normal2 for a
+    // pair without a tail draw); returns whether the pair has a tail draw, in
+    // which case the caller redoes it with inv_normal2 (0.2% of pairs).  The
+    // Sobol' runs call it with the redo deferred to the end of the run: a
+    // test and branch per pair split the unrolled run into one basic block
+    // per pair, so the compiler could not interleave the polynomial chains
+    // of consecutive pairs (14% of the bridge kernel's time at d = 64).
+    __device__ static __forceinline__ bool inv_normal2_central(uint32_t y0, uint32_t y1, float2 &z) {
+        constexpr float c[] = QMC_INVN_CENTRAL;
+        constexpr int n = sizeof(c) / sizeof(c[0]);
+        uint32_t s0, s1;
+        const float2 nq = neg_q_of2(y0, y1, s0, s1);
+        const float2 xm = fma2(f2(-2.0f), nq, f2(-1.0f));
+        const float2 q4 = mul2(f2(-4.0f), nq);
+        const float2 w = fx::neg_ln2(fma2(q4, nq, q4));
+        const float2 t = add2(w, f2(-QMC_INVN_SHIFT_C));
+        float2 p = f2(c[n - 1]);
+#pragma unroll
+        for (int i = n - 2; i >= 0; --i) p = fma2(p, t, f2(c[i]));
+        p = add2(fma2(p, t, f2(QMC_INVN_C0_LO)), f2(QMC_INVN_C0_HI));
+        const float2 zz = mul2(xm, p);
+        z = make_float2(__uint_as_float(__float_as_uint(zz.x) ^ s0), __uint_as_float(__float_as_uint(zz.y) ^ s1));
+        return fmaxf(w.x, w.y) >= QMC_INVN_W0;
+    }
     // one draw: the pair form's second lane duplicated (the same operations)
     __device__ static float inv_normal(uint32_t y) { return inv_normal2(y, y).x; }
     __device__ static float ex(float x) { return fx::exp_f(x); }
@@ -1035,36 +1059,55 @@ __device__ __forceinline__ void sobol_points(const uint32_t *__restrict__ tab, i
     }
 }
 
-// The same points handed out in consecutive pairs, emit2(s, y(k0+s),
-// y(k0+s+1)) for s = 0, 2, 4, ..., and emit1 for an odd last point: for the
-// float paths, which evaluate the inverse normal two draws at a time.
+// The points of a run handed out in consecutive pairs for the float paths,
+// which evaluate the inverse normal two draws at a time.  A full aligned run
+// (first index a multiple of 2^LG) has the inverse normal's tail test taken
+// out of the unrolled body: emit2(s, z) receives the central
+// values of points s, s+1 and a bit per pair records a tail draw; after the
+// run each recorded pair (rare) is rebuilt from the run's first point by the
+// bits of its Gray index and its exact values emitted again.
 template <int LG, typename Emit2>
-__device__ __forceinline__ void sobol_run_pairs(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
-                                                Emit2 &&emit2) {
+__device__ __forceinline__ void sobol_run_deferred(const uint32_t *__restrict__ tab, int jstride, int j, uint32_t y,
+                                                   Emit2 &&emit2) {
+    static_assert(LG >= 1 && LG <= 6, "runs of 2..64 points");
     uint32_t v[LG];
 #pragma unroll
     for (int b = 0; b < LG; ++b) v[b] = __ldg(tab + b * jstride + j);
+    const uint32_t y_first = y;
+    uint32_t redo = 0;
 #pragma unroll
     for (int s = 0; s < (1 << LG); s += 2) {
         if (s > 0) y ^= v[ctz_const(s)];
-        const uint32_t y1 = y ^ v[0];  // ctz(s + 1) = 0 for even s
-        emit2(s, y, y1);
+        const uint32_t y1 = y ^ v[0];
+        float2 z;
+        if (Arith<float>::inv_normal2_central(y, y1, z)) redo |= 1u << (s >> 1);
+        emit2(s, z);
         y = y1;
+    }
+    while (redo) {
+        const int s = 2 * (__ffs(redo) - 1);
+        redo &= redo - 1u;
+        const uint32_t g = static_cast<uint32_t>(s) ^ (static_cast<uint32_t>(s) >> 1);
+        uint32_t ys = y_first;
+#pragma unroll
+        for (int b = 0; b < LG; ++b)
+            if ((g >> b) & 1u) ys ^= v[b];
+        emit2(s, Arith<float>::inv_normal2(ys, ys ^ v[0]));
     }
 }
 
 template <typename Emit1, typename Emit2>
-__device__ __forceinline__ void sobol_point_pairs(const uint32_t *__restrict__ tab, int jstride, int j,
-                                                  uint32_t y, uint32_t k0, int len, int chunk_log2,
-                                                  Emit1 &&emit1, Emit2 &&emit2) {
+__device__ __forceinline__ void sobol_point_deferred(const uint32_t *__restrict__ tab, int jstride, int j,
+                                                     uint32_t y, uint32_t k0, int len, int chunk_log2,
+                                                     Emit1 &&emit1, Emit2 &&emit2) {
     // y: the point k0 (sobol_first, or the tile's first point and sobol_from_gray)
     if (len == (1 << chunk_log2) && (k0 & (static_cast<uint32_t>(len) - 1u)) == 0u) {
         switch (chunk_log2) {
-            case 2: sobol_run_pairs<2>(tab, jstride, j, y, emit2); return;
-            case 3: sobol_run_pairs<3>(tab, jstride, j, y, emit2); return;
-            case 4: sobol_run_pairs<4>(tab, jstride, j, y, emit2); return;
-            case 5: sobol_run_pairs<5>(tab, jstride, j, y, emit2); return;
-            case 6: sobol_run_pairs<6>(tab, jstride, j, y, emit2); return;
+            case 2: sobol_run_deferred<2>(tab, jstride, j, y, emit2); return;
+            case 3: sobol_run_deferred<3>(tab, jstride, j, y, emit2); return;
+            case 4: sobol_run_deferred<4>(tab, jstride, j, y, emit2); return;
+            case 5: sobol_run_deferred<5>(tab, jstride, j, y, emit2); return;
+            case 6: sobol_run_deferred<6>(tab, jstride, j, y, emit2); return;
             default: break;
         }
     }
@@ -1072,7 +1115,7 @@ __device__ __forceinline__ void sobol_point_pairs(const uint32_t *__restrict__ t
     for (; s + 1 < len; s += 2) {
         if (s > 0) y ^= __ldg(tab + (__ffs(k0 + s) - 1) * jstride + j);
         const uint32_t y1 = y ^ __ldg(tab + (__ffs(k0 + s + 1) - 1) * jstride + j);
-        emit2(s, y, y1);
+        emit2(s, Arith<float>::inv_normal2(y, y1));
         y = y1;
     }
     if (s < len) {
