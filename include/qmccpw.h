@@ -364,6 +364,68 @@ int qmccpw_server_get_stats(qmccpw_plan_t plan, qmccpw_server_stats *out);
  * (no-op without a server). */
 int qmccpw_server_stop(qmccpw_plan_t plan);
 
+/* ---- baskets: several underlying assets (Sec. 6) ----------------------------
+ * Sec. 6 notes that the simulation extends to options on several underlying
+ * assets by redefining the path and the payoff formulas; this is that
+ * extension for a basket average of m <= QMCCPW_ASSETS_MAX correlated GBM
+ * assets:
+ *   S_i(t) = spot[i] * S0 * exp(omega_i t + sigma_i W_i(t)),
+ *   sigma_i = vol[i] * sigma, omega_i = r - sigma_i^2 / 2,
+ *   W = L B, L the lower Cholesky factor of corr (L_11 = 1), B independent
+ *   standard Brownian motions,
+ *   X = sum_i weight[i] * (1/d) sum_j S_i(t_j),  t_j = j T / d.
+ * Products: QMCCPW_ARITH_ASIAN_CALL pays (X - K)^+, QMCCPW_BINARY_ASIAN pays
+ * 1{X > K}.  Each factor B_k is its first increment sqrt(t_1) x_k plus the
+ * bridge of Sec. 4.4 over t_2..t_d (n = d - 1 nodes, the order of the
+ * single-asset bridge); x_1, the first increment of factor 1, is integrated
+ * out as in Sec. 3.3.1.  Then X(x_1) = sum_i C_i exp(b_i x_1) with
+ * b_i = sigma_i L_i1 sqrt(t_1) > 0, and the switch point x* of X(x*) = K is
+ * found per point by Newton's method on ln X - ln K; price and Greeks follow
+ * in closed form (E[e^{b x}; x > x*] = e^{b^2/2} Phi(b - x*)).  Greeks:
+ * delta and gamma with respect to the spot scale S0 (every spot moves with
+ * it), vega with respect to the volatility scale sigma (every volatility
+ * moves with it).  Sobol' dimension b*m + k (b = 0..d-2, k = 0..m-1) drives
+ * bridge node b of factor k+1, dimension (d-1)*m + k-1 the first increment of
+ * factor k+1 (k = 1..m-1): m*d - 1 dimensions, at most the plan's d_max - 1.
+ * With m = 1 the basket is the single-asset contract with the bridge, point
+ * for point. */
+#define QMCCPW_ASSETS_MAX 8
+typedef struct {
+    int32_t type;              /* QMCCPW_ARITH_ASIAN_CALL or QMCCPW_BINARY_ASIAN, on the basket average */
+    int32_t d;                 /* monitoring dates; m * d <= plan d_max */
+    int32_t m;                 /* assets, 1..QMCCPW_ASSETS_MAX */
+    int32_t reserved;          /* must be 0 */
+    double K, T;               /* strike > 0, maturity > 0 */
+    double S0, r, sigma;       /* spot scale > 0, rate (finite), volatility scale > 0 */
+    double weight[QMCCPW_ASSETS_MAX];   /* w_i >= 0, w_0 > 0 */
+    double spot[QMCCPW_ASSETS_MAX];     /* relative spots > 0: S_i(0) = spot[i] * S0 */
+    double vol[QMCCPW_ASSETS_MAX];      /* relative volatilities > 0: sigma_i = vol[i] * sigma */
+    double corr[QMCCPW_ASSETS_MAX * QMCCPW_ASSETS_MAX];  /* m x m correlation, row-major with row
+                                                             stride m (the first m*m entries), symmetric
+                                                             positive definite, unit diagonal,
+                                                             corr[i] > 0 (every asset positively
+                                                             correlated with asset 1) */
+} qmccpw_basket;
+
+/*
+ * Estimate price, delta, vega, gamma of a basket with N points per replicate
+ * and R replicates (replicates 0..R-1 of the plan's randomisation).
+ * Synchronous, like qmccpw_greeks; precision QMCCPW_FP64 (every step in
+ * double) or QMCCPW_MIXED (inverse normal, bridges and exponentials in float
+ * with the float path's own polynomials; per-asset sums, switch point and the
+ * per-point values in double; tile and replicate sums in double).
+ * Errors: INVALID_ARG (NULL, a field out of range, a correlation matrix that
+ * is not positive definite), UNSUPPORTED (another type or precision), OOM
+ * (workspace budget), CUDA.
+ */
+int qmccpw_basket_greeks(qmccpw_plan_t plan, const qmccpw_basket *basket, uint64_t N, int32_t R,
+                         int32_t precision, qmccpw_result *out);
+/* Per-point values (price, delta, vega, gamma) of points k0..k0+count-1 of
+ * replicate `replicate` into the host array out[count*4], from the same
+ * device code (diagnostics; count <= 2^20). */
+int qmccpw_basket_point_values(qmccpw_plan_t plan, const qmccpw_basket *basket, int32_t precision,
+                               uint32_t replicate, uint64_t k0, uint64_t count, double *out);
+
 /* Release a plan after waiting for its work; NULL is accepted (no-op). */
 int qmccpw_free(qmccpw_plan_t plan);
 

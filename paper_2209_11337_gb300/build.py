@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libqmccpw.so")
-SOURCES = ["api.cu", "kernels.cu", "serve_f32.cu", "serve_f64.cu", "pca_tc.cu", "peaks.cu", "tables.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "serve_f32.cu", "serve_f64.cu", "pca_tc.cu", "peaks.cu", "basket.cu", "tables.cpp"]
 HEADERS = [os.path.join(CSRC, h) for h in ("qmccpw_internal.h", "qmccpw_device.cuh", "fused_body.cuh", "serve_impl.cuh", "float_coeffs.h", "tc_ptx.cuh")] + \
     [os.path.join(ROOT, "include", "qmccpw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

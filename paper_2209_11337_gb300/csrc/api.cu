@@ -1070,6 +1070,7 @@ int qmccpw_plan(qmccpw_plan_t *out, const qmccpw_plan_desc *desc) {
     // allow every tile size up front (occupancy follows the bytes each launch asks for)
     for (int prec : {QMCCPW_FP64, QMCCPW_MIXED})
         QMC_CUDA(static_cast<cudaError_t>(fused_set_smem_limit(prec, static_cast<size_t>(smem_optin))));
+    QMC_CUDA(static_cast<cudaError_t>(basket_prepare(static_cast<size_t>(smem_optin))));
     p->seed = desc->seed;
     p->d_max = desc->d_max;
     p->r_max = desc->r_max;
@@ -1409,6 +1410,204 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
     return QMCCPW_OK;
 }
 
+
+}  // extern "C"
+
+namespace {
+
+// Validate a basket and fill its kernel descriptor (everything but the
+// device table of row slots, returned in slot_of_dim).
+int basket_build(qmccpw_plan_s *p, const qmccpw_basket &bk, int precision, uint64_t N, BasketDev &b,
+                 std::vector<int32_t> &slot_of_dim) {
+    if (bk.reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "qmccpw_basket.reserved must be 0");
+    if (bk.type != QMCCPW_ARITH_ASIAN_CALL && bk.type != QMCCPW_BINARY_ASIAN)
+        return fail(bk.type >= 0 && bk.type <= 3 ? QMCCPW_ERR_UNSUPPORTED : QMCCPW_ERR_INVALID_ARG,
+                    "basket type: the arithmetic-Asian call or the binary on the basket average");
+    if (precision != QMCCPW_FP64 && precision != QMCCPW_MIXED)
+        return fail(precision >= 0 && precision <= QMCCPW_MIXED_TC_TF32X3 ? QMCCPW_ERR_UNSUPPORTED
+                                                                          : QMCCPW_ERR_INVALID_ARG,
+                    "basket precision: QMCCPW_FP64 or QMCCPW_MIXED");
+    const int m = bk.m, d = bk.d;
+    if (m < 1 || m > QMCCPW_ASSETS_MAX) return fail(QMCCPW_ERR_INVALID_ARG, "basket m outside 1..8");
+    if (d < 1 || static_cast<int64_t>(m) * d > p->d_max)
+        return fail(QMCCPW_ERR_INVALID_ARG, "basket needs 1 <= d and m * d <= d_max=" + std::to_string(p->d_max));
+    if (!finite_pos(bk.K) || !finite_pos(bk.T) || !finite_pos(bk.S0) || !finite_pos(bk.sigma) || !std::isfinite(bk.r))
+        return fail(QMCCPW_ERR_INVALID_ARG, "basket K, T, S0, sigma must be positive and finite, r finite");
+    if (N < 1 || N > (1ull << 32)) return fail(QMCCPW_ERR_INVALID_ARG, "N must be in 1..2^32");
+    if (!(bk.weight[0] > 0.0)) return fail(QMCCPW_ERR_INVALID_ARG, "basket weight[0] must be positive");
+    for (int i = 0; i < m; ++i) {
+        if (!std::isfinite(bk.weight[i]) || bk.weight[i] < 0.0 || !finite_pos(bk.spot[i]) || !finite_pos(bk.vol[i]))
+            return fail(QMCCPW_ERR_INVALID_ARG, "basket weights >= 0, spots and vols > 0, all finite");
+        if (bk.corr[i * m + i] != 1.0) return fail(QMCCPW_ERR_INVALID_ARG, "basket correlation diagonal must be 1");
+        if (!(bk.corr[i] > 0.0))
+            return fail(QMCCPW_ERR_INVALID_ARG, "every asset must be positively correlated with asset 1 (corr[i] > 0)");
+        for (int k = 0; k < m; ++k)
+            if (!(std::fabs(bk.corr[i * m + k]) <= 1.0) || bk.corr[i * m + k] != bk.corr[k * m + i])
+                return fail(QMCCPW_ERR_INVALID_ARG, "basket correlation must be symmetric with entries in [-1, 1]");
+    }
+    double L[QMCCPW_ASSETS_MAX * QMCCPW_ASSETS_MAX];
+    if (!cholesky_lower(m, bk.corr, L)) return fail(QMCCPW_ERR_INVALID_ARG, "basket correlation is not positive definite");
+    const DTables *t = nullptr;
+    QMC_TRY(get_dtables(p, d, bk.T, &t));
+    const int n = d - 1;
+    b = BasketDev{};
+    b.type = bk.type;
+    b.d = d;
+    b.n = n;
+    b.m = m;
+    b.n_levels = t->n_levels;
+    b.steps = t->steps.as<BridgeStep>();
+    b.w64 = t->w64.as<double>();
+    b.w32 = t->w32.as<float>();
+    b.level_start = t->level_start.as<int32_t>();
+    const double dt = bk.T / d, sdt = std::sqrt(dt);
+    b.S0 = bk.S0;
+    b.K = bk.K;
+    b.disc = std::exp(-bk.r * bk.T);
+    b.sqrt_dt = sdt;
+    b.ln_K = std::log(bk.K);
+    for (int i = 0; i < m; ++i) {
+        const double sig = bk.vol[i] * bk.sigma, om = bk.r - 0.5 * sig * sig;
+        for (int k = 0; k < m; ++k) {
+            b.L[i * QMCCPW_ASSETS_MAX + k] = L[i * m + k];
+            split_ff(L[i * m + k], b.Lf[i * QMCCPW_ASSETS_MAX + k]);
+        }
+        b.sig_sdt[i] = sig * sdt;
+        b.om_dt[i] = om * dt;
+        b.sig_dt[i] = sig * dt;
+        b.f[i] = bk.weight[i] * bk.spot[i] * bk.S0 / d;
+        b.l1[i] = L[i * m] * sdt;
+        b.bcoef[i] = sig * b.l1[i];
+        b.v[i] = bk.vol[i];
+        b.ehalf[i] = std::exp(0.5 * b.bcoef[i] * b.bcoef[i]);
+        split_ff(b.sig_sdt[i], b.ff_sig_sdt[i]);
+        split_ff(b.om_dt[i], b.ff_om_dt[i]);
+    }
+    // the row: slot 0 = 0, factor k at date index s (1..n) in slot 1 + (s-1) m + k,
+    // the first increment of factor k >= 1 in slot 1 + n m + k - 1
+    const int nd = m * d - 1;
+    slot_of_dim.assign(std::max(1, nd), 0);
+    if (n > 0) {
+        const BridgePlan bp = bridge_plan(n, 1.0);
+        for (int j = 0; j < n * m; ++j) slot_of_dim[j] = 1 + (bp.steps[j / m].m - 1) * m + j % m;
+    }
+    for (int j = n * m; j < nd; ++j) slot_of_dim[j] = 1 + j;
+    // tile: P points with P * row <= 65 KiB (two CTAs per SM and room for the rest), P in 16..256
+    const size_t elem = precision == QMCCPW_FP64 ? 8 : 4;
+    b.row_stride = (m * d) | 1;
+    int lg = kMaxTileLog2;
+    while (lg > 4 && (static_cast<size_t>(1u << lg) * b.row_stride * elem) > kTileBudget) --lg;
+    b.tile_log2 = lg;
+    b.groups = kThreads >> lg;
+    b.chunk_log2 = chunk_log2_for(std::max(1, nd), lg, false);
+    b.N = N;
+    b.tiles = (N + (1u << lg) - 1) >> lg;
+    return QMCCPW_OK;
+}
+
+size_t basket_smem_bytes(const BasketDev &b, int precision) {
+    const size_t elem = precision == QMCCPW_FP64 ? 8 : 4;
+    const size_t tile = (static_cast<size_t>(1) << b.tile_log2) * b.row_stride * elem;
+    const size_t part = static_cast<size_t>(kThreads) * 3 * b.m * elem;  // the per-thread partial sums
+    return std::max({tile, part, static_cast<size_t>(4 * kThreads * sizeof(double))});
+}
+
+// Run the basket over replicates rep_offset .. rep_offset + R - 1: per-replicate
+// estimates and statistics into per_rep / stats (device), or with point_out
+// (R = 1) every point's values.
+int basket_run(qmccpw_plan_s *p, const qmccpw_basket &bk, int precision, uint64_t N, int R, uint32_t rep_offset,
+               uint64_t point_k0, double *point_out, DevBuf &per_rep, DevBuf &stats) {
+    BasketParams bp{};
+    std::vector<int32_t> slots;
+    QMC_TRY(basket_build(p, bk, precision, N, bp.b, slots));
+    const uint64_t items = static_cast<uint64_t>(R) * bp.b.tiles;
+    if (items * 4 * sizeof(double) > p->workspace_bytes)
+        return fail(QMCCPW_ERR_OOM, "basket tile sums exceed the plan's workspace budget");
+    QMC_CUDA(cudaSetDevice(p->device));
+    DevBuf dslots, tile_sums, cdesc, owner;
+    QMC_TRY(dslots.alloc(sizeof(int32_t) * slots.size()));
+    QMC_CUDA(cudaMemcpyAsync(dslots.ptr, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice,
+                             p->stream));
+    QMC_TRY(tile_sums.alloc(items * 4 * sizeof(double)));
+    bp.b.slot_of_dim = dslots.as<int32_t>();
+    bp.sobol_table = p->table.as<uint32_t>();
+    bp.sobol_shift = p->shift.as<uint32_t>();
+    bp.jstride = p->jstride;
+    bp.rep_offset = rep_offset;
+    bp.items = items;
+    bp.tile_sums = tile_sums.as<double>();
+    bp.point_out = point_out;
+    bp.point_k0 = point_k0;
+    const size_t smem = basket_smem_bytes(bp.b, precision);
+    int per_sm = 0;
+    QMC_CUDA(static_cast<cudaError_t>(basket_occupancy(precision, smem, &per_sm)));
+    const uint64_t cap = static_cast<uint64_t>(std::max(1, per_sm)) * p->sm_count;
+    const int grid = static_cast<int>(std::min<uint64_t>(items, cap));
+    QMC_CUDA(static_cast<cudaError_t>(launch_basket(bp, precision, smem, grid, p->stream)));
+    if (!point_out) {
+        // reduction in tile order and the statistics, by the batch's kernels
+        ContractDev c{};
+        c.R = R;
+        c.tiles = static_cast<int32_t>(bp.b.tiles);
+        c.N = N;
+        c.item_base = 0;
+        c.rep_base = 0;
+        std::vector<uint64_t> rep_owner(static_cast<size_t>(R), 0);
+        QMC_TRY(cdesc.alloc(sizeof(ContractDev)));
+        QMC_TRY(owner.alloc(sizeof(uint64_t) * rep_owner.size()));
+        QMC_TRY(per_rep.alloc(sizeof(double) * 4 * R));
+        QMC_TRY(stats.alloc(sizeof(double) * 8));
+        QMC_CUDA(cudaMemcpyAsync(cdesc.ptr, &c, sizeof(ContractDev), cudaMemcpyHostToDevice, p->stream));
+        QMC_CUDA(cudaMemcpyAsync(owner.ptr, rep_owner.data(), sizeof(uint64_t) * rep_owner.size(),
+                                 cudaMemcpyHostToDevice, p->stream));
+        QMC_CUDA(static_cast<cudaError_t>(launch_reduce(cdesc.as<ContractDev>(), 1, tile_sums.as<double>(),
+                                                        per_rep.as<double>(), stats.as<double>(),
+                                                        static_cast<uint64_t>(R), owner.as<uint64_t>(), p->stream)));
+    }
+    // the host buffers above and the DevBufs live until the work is done
+    QMC_CUDA(cudaStreamSynchronize(p->stream));
+    return QMCCPW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmccpw_basket_greeks(qmccpw_plan_t plan, const qmccpw_basket *basket, uint64_t N, int32_t R,
+                         int32_t precision, qmccpw_result *out) {
+    g_last_error.clear();
+    if (!plan || !basket || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    if (R < 2 || R > plan->r_max)
+        return fail(QMCCPW_ERR_INVALID_ARG, "R " + std::to_string(R) + " outside 2..r_max=" + std::to_string(plan->r_max));
+    std::lock_guard<std::mutex> lock(plan->mu);
+    DevBuf per_rep, stats;
+    QMC_TRY(basket_run(plan, *basket, precision, N, R, 0u, 0u, nullptr, per_rep, stats));
+    double st[8];
+    QMC_CUDA(cudaMemcpy(st, stats.ptr, sizeof(st), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < 4; ++g) {
+        out->mean[g] = st[g];
+        out->se[g] = st[4 + g];
+    }
+    if (out->per_replicate)
+        QMC_CUDA(cudaMemcpy(out->per_replicate, per_rep.ptr, sizeof(double) * 4 * R, cudaMemcpyDeviceToHost));
+    return QMCCPW_OK;
+}
+
+int qmccpw_basket_point_values(qmccpw_plan_t plan, const qmccpw_basket *basket, int32_t precision,
+                               uint32_t replicate, uint64_t k0, uint64_t count, double *out) {
+    g_last_error.clear();
+    if (!plan || !basket || !out) return fail(QMCCPW_ERR_INVALID_ARG, "NULL argument");
+    if (replicate >= static_cast<uint32_t>(plan->r_max)) return fail(QMCCPW_ERR_INVALID_ARG, "replicate >= r_max");
+    if (count < 1 || count > (1ull << 20) || k0 + count > (1ull << 32))
+        return fail(QMCCPW_ERR_INVALID_ARG, "count must be 1..2^20 and k0+count <= 2^32");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    QMC_CUDA(cudaSetDevice(plan->device));
+    DevBuf dout, per_rep, stats;
+    QMC_TRY(dout.alloc(sizeof(double) * 4 * count));
+    QMC_TRY(basket_run(plan, *basket, precision, count, 1, replicate, k0, dout.as<double>(), per_rep, stats));
+    QMC_CUDA(cudaMemcpy(out, dout.ptr, sizeof(double) * 4 * count, cudaMemcpyDeviceToHost));
+    return QMCCPW_OK;
+}
 
 int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market, uint64_t N,
                           int32_t R, int32_t construction, int32_t precision, double *out, void *stream) {

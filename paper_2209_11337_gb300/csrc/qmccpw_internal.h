@@ -285,6 +285,54 @@ int pca_tc_occupancy(int kind, size_t smem_bytes, int *blocks);
 int launch_pca_tc(const LaunchParams &p, int kind, size_t smem_bytes, int grid, void *stream);
 void pca_tc_operand(int kind, int n, const std::vector<double> &A_unit, std::vector<unsigned char> &out);
 
+// ----------------------------------------------------------------------------
+// Basket of m correlated assets (basket.cu; host side in api.cu)
+// ----------------------------------------------------------------------------
+// Lower Cholesky factor L of an m x m symmetric matrix C (row-major, m <= 8):
+// false if C is not positive definite.
+bool cholesky_lower(int m, const double *C, double *L);
+
+// Everything the basket kernel reads about its contract: a kernel parameter
+// (the constants reach the arithmetic as constant-bank operands).
+struct BasketDev {
+    int32_t type, d, n, m;
+    int32_t tile_log2, chunk_log2, groups, row_stride;
+    int32_t n_levels, pad0;
+    uint64_t N, tiles;
+    const BridgeStep *steps;             // unit-spacing bridge of the n nodes (shared with the single-asset tables)
+    const double *w64;
+    const float *w32;
+    const int32_t *level_start;
+    const int32_t *slot_of_dim;          // m d - 1 entries: the row slot Sobol' dimension j fills
+    double S0, K, disc, sqrt_dt, ln_K;
+    double L[QMCCPW_ASSETS_MAX * QMCCPW_ASSETS_MAX];  // Cholesky factor, [i*8 + k]
+    double sig_sdt[QMCCPW_ASSETS_MAX];   // sigma_i sqrt(dt)
+    double om_dt[QMCCPW_ASSETS_MAX];     // omega_i dt
+    double sig_dt[QMCCPW_ASSETS_MAX];    // sigma_i dt
+    double f[QMCCPW_ASSETS_MAX];         // w_i a_i S0 / d
+    double bcoef[QMCCPW_ASSETS_MAX];     // b_i = sigma_i L_i1 sqrt(dt)
+    double l1[QMCCPW_ASSETS_MAX];        // L_i1 sqrt(dt)
+    double v[QMCCPW_ASSETS_MAX];         // relative volatility (d sigma_i / d sigma)
+    double ehalf[QMCCPW_ASSETS_MAX];     // e^{b_i^2 / 2}
+    float Lf[QMCCPW_ASSETS_MAX * QMCCPW_ASSETS_MAX][2];  // L as float pairs (hi, lo)
+    float ff_sig_sdt[QMCCPW_ASSETS_MAX][2], ff_om_dt[QMCCPW_ASSETS_MAX][2];
+};
+
+struct BasketParams {
+    BasketDev b;
+    const uint32_t *sobol_table;         // [rep][b][j] scrambled direction integers
+    const uint32_t *sobol_shift;         // [rep][j]
+    int32_t jstride;
+    uint32_t rep_offset;                 // randomisation index of replicate 0
+    uint64_t items;                      // R x tiles work items, replicate-major
+    double *tile_sums;                   // items x 4
+    double *point_out;                   // optional per-point values (diagnostics)
+    uint64_t point_k0;                   // index of point 0 (diagnostics; 0 otherwise)
+};
+int launch_basket(const BasketParams &p, int precision, size_t smem_bytes, int grid, void *stream);
+int basket_prepare(size_t optin_bytes);
+int basket_occupancy(int precision, size_t smem_bytes, int *blocks_per_sm);
+
 // Pipe micro-benchmarks (peaks.cu): 0, a cudaError_t, or -QMCCPW_ERR_TIMEOUT.
 int measure_pipe_peaks(int device, qmccpw_pipe_peaks *out);
 

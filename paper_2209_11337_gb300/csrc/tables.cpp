@@ -225,4 +225,23 @@ void contract_constants(ContractDev &c) {
     split_ff(c.ln_K, c.ff_lnK);
 }
 
+// Cholesky factor by columns (the Cholesky-Crout order): column k's
+// diagonal from the entries left of it, then the entries below it.
+bool cholesky_lower(int m, const double *C, double *L) {
+    for (int i = 0; i < m * m; ++i) L[i] = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double diag = C[k * m + k];
+        for (int q = 0; q < k; ++q) diag -= L[k * m + q] * L[k * m + q];
+        if (!(diag > 0.0)) return false;
+        const double lkk = std::sqrt(diag);
+        L[k * m + k] = lkk;
+        for (int i = k + 1; i < m; ++i) {
+            double s = C[i * m + k];
+            for (int q = 0; q < k; ++q) s -= L[i * m + q] * L[k * m + q];
+            L[i * m + k] = s / lkk;
+        }
+    }
+    return true;
+}
+
 }  // namespace qmccpw

@@ -61,6 +61,7 @@ EXPORTS = (
     "qmccpw_wait", "qmccpw_server_get_stats", "qmccpw_server_stop", "qmccpw_autotune", "qmccpw_tuning_get",
     "qmccpw_tuning_set", "qmccpw_free", "qmccpw_last_error",
     "qmccpw_version", "qmccpw_measure_pipe_peaks", "qmccpw_batch_scatter_replicates", "qmccpw_replicate_stats",
+    "qmccpw_basket_greeks", "qmccpw_basket_point_values",
 )
 
 
@@ -88,6 +89,31 @@ class qmccpw_market(ctypes.Structure):
 class qmccpw_result(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double * 4), ("se", ctypes.c_double * 4),
                 ("per_replicate", ctypes.POINTER(ctypes.c_double))]
+
+
+QMCCPW_ASSETS_MAX = 8
+
+
+class qmccpw_basket(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("d", ctypes.c_int32), ("m", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("K", ctypes.c_double), ("T", ctypes.c_double), ("S0", ctypes.c_double), ("r", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("weight", ctypes.c_double * QMCCPW_ASSETS_MAX),
+                ("spot", ctypes.c_double * QMCCPW_ASSETS_MAX), ("vol", ctypes.c_double * QMCCPW_ASSETS_MAX),
+                ("corr", ctypes.c_double * (QMCCPW_ASSETS_MAX * QMCCPW_ASSETS_MAX))]
+
+
+def basket_struct(b) -> qmccpw_basket:
+    """qmccpw_basket from an object with type, d, K, T, S0, r, sigma, w, a, v, corr (m x m)."""
+    m = len(b.w)
+    out = qmccpw_basket()
+    out.type, out.d, out.m, out.reserved = b.type, b.d, m, 0
+    out.K, out.T, out.S0, out.r, out.sigma = b.K, b.T, b.S0, b.r, b.sigma
+    corr = np.asarray(b.corr, dtype=np.float64).reshape(m, m)
+    for i in range(m):
+        out.weight[i], out.spot[i], out.vol[i] = float(b.w[i]), float(b.a[i]), float(b.v[i])
+        for k in range(m):
+            out.corr[i * m + k] = float(corr[i, k])  # row stride m
+    return out
 
 
 class qmccpw_contract(ctypes.Structure):
@@ -151,6 +177,8 @@ def library() -> ctypes.CDLL:
                                               P(ctypes.c_double)]
             L.qmccpw_greeks_noalloc.argtypes = [vp, P(qmccpw_option), P(qmccpw_market), u64, i32, i32, i32,
                                                  ctypes.c_void_p, vp]
+            L.qmccpw_basket_greeks.argtypes = [vp, P(qmccpw_basket), u64, i32, i32, P(qmccpw_result)]
+            L.qmccpw_basket_point_values.argtypes = [vp, P(qmccpw_basket), i32, u32, u64, u64, P(ctypes.c_double)]
             L.qmccpw_server_start.argtypes = [vp, P(qmccpw_server_desc)]
             L.qmccpw_submit.argtypes = [vp, P(qmccpw_contract), P(u64)]
             L.qmccpw_poll.argtypes = [vp, u64, P(qmccpw_result)]
@@ -205,6 +233,21 @@ def qmccpw_greeks(plan, type: int, d: int, K: float, T: float, S0: float, r: flo
                                    ctypes.byref(qmccpw_market(S0, r, sigma)), N, R, construction, precision,
                                    ctypes.byref(res)))
     return np.array(res.mean[:]), np.array(res.se[:]), per
+
+
+def qmccpw_basket_greeks(plan, basket, N: int, R: int, precision: int = QMCCPW_FP64):
+    """A basket (see basket_struct); returns (mean[4], se[4], per_replicate[R,4])."""
+    res, per = _result(R)
+    _check(library().qmccpw_basket_greeks(plan, ctypes.byref(basket_struct(basket)), N, R, precision,
+                                          ctypes.byref(res)))
+    return np.array(res.mean[:]), np.array(res.se[:]), per
+
+
+def qmccpw_basket_point_values(plan, basket, precision: int, replicate: int, k0: int, count: int) -> np.ndarray:
+    out = np.zeros((count, 4))
+    _check(library().qmccpw_basket_point_values(plan, ctypes.byref(basket_struct(basket)), precision, replicate,
+                                                k0, count, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 def contract_array(contracts: Sequence) -> ctypes.Array:
