@@ -454,6 +454,35 @@ def pca_stress(q, local, rank, stream, steps: int) -> dict:
     return out
 
 
+def basket_section(q, local, stream, steps: int, N: int = 2 ** 18, R: int = 16) -> dict:
+    """Basket of 4 correlated assets (d = 64, arithmetic call and binary on
+    the basket average): MIXED and FP64 throughput in asset-point-dates
+    (N R d m) per second, host wall time around the synchronous call (the
+    kernel dominates at this size), and MIXED's worst error against FP64 in
+    units of the FP64 standard error."""
+    import time as _t
+    plan = q.qmccpw_plan(device=local, d_max=257, r_max=R, seed=W.SCRAMBLE_SEED, stream=stream.cuda_stream)
+    out = {"workload": f"basket of 4 assets (rho 0.5), d=64, N=2^{N.bit_length() - 1}, R={R}, "
+                       "arithmetic call and binary on the basket average",
+           "unit": "asset-point-dates/s"}
+    for typ, tname in ((W.ARITH, "arith"), (W.BINARY, "binary")):
+        b = W.basket_d64(typ)
+        el = N * R * b.d * b.m
+        res = {}
+        for name, prec, k in (("mixed", q.QMCCPW_MIXED, steps), ("fp64", q.QMCCPW_FP64, 1)):
+            q.qmccpw_basket_greeks(plan, b, N, R, prec)  # warm-up
+            t0 = _t.perf_counter()
+            for _ in range(k):
+                mean, se, _ = q.qmccpw_basket_greeks(plan, b, N, R, prec)
+            dt = (_t.perf_counter() - t0) / k
+            res[name] = {"value": el / dt, "ms": dt * 1e3, "mean": mean.tolist(), "se": se.tolist()}
+        err = [abs(res["mixed"]["mean"][g] - res["fp64"]["mean"][g]) / res["fp64"]["se"][g] for g in range(4)]
+        res["mixed_vs_fp64_err_in_se"] = dict(zip(("price", "delta", "vega", "gamma"), err))
+        out[tname] = res
+    q.qmccpw_free(plan)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -722,6 +751,8 @@ def run_ours(args):
         line["latency_small"] = latency_small(q, plan, stream, args.latency_calls)
     if rank == 0 and args.stress_steps > 0:
         line["pca_stress"] = pca_stress(q, local, rank, stream, args.stress_steps)
+    if rank == 0 and args.basket_steps > 0:
+        line["basket"] = basket_section(q, local, stream, args.basket_steps)
     if rank == 0 and args.serving_s > 0:
         # at the configured rate (2000/s), at a rate well within what the GPU serves, and FP64 at a rate
         # its path sustains
@@ -757,6 +788,7 @@ def main(argv=None):
     ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of Poisson arrivals (0: skip)")
     ap.add_argument("--latency-calls", type=int, default=200, help="calls timed in the small-case latency section")
     ap.add_argument("--stress-steps", type=int, default=1, help="timed steps of the d=256 PCA case (0: skip)")
+    ap.add_argument("--basket-steps", type=int, default=3, help="timed MIXED calls of the 4-asset basket (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0)
     ap.add_argument("--serving-rate-sustained", type=float, default=800.0,
                     help="a second MIXED arrival rate, within what the GPU serves")

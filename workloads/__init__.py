@@ -128,3 +128,36 @@ def arrivals(rate_hz: float = 2000.0, duration_s: float = 10.0, seed: int = 5, R
 
 def with_size(c: Contract, N: int = None, R: int = None) -> Contract:
     return replace(c, N=c.N if N is None else N, R=c.R if R is None else R)
+
+
+@dataclass(frozen=True)
+class BasketSpec:
+    """A basket of m assets (Sec. 6's multi-asset extension): type on the
+    basket average, d dates, strike K, maturity T, spot scale S0, rate r,
+    volatility scale sigma; per asset the weight w, relative spot a and
+    relative volatility v; corr the m x m correlation (rows as tuples)."""
+    type: int
+    d: int
+    K: float
+    T: float
+    S0: float
+    r: float
+    sigma: float
+    w: tuple
+    a: tuple
+    v: tuple
+    corr: tuple
+
+    @property
+    def m(self) -> int:
+        return len(self.w)
+
+
+def basket_d64(type_: int = ARITH, m: int = 4, K: float = 100.0) -> BasketSpec:
+    """The measured basket: m = 4 equally weighted assets, d = 64, spots
+    100 x (1, 0.95, 1.05, 1.1), volatilities 0.25 x (1, 0.8, 1.2, 1.4),
+    pairwise correlation 0.5 (first m of each list)."""
+    a = (1.0, 0.95, 1.05, 1.1, 0.9, 1.0, 1.2, 0.85)[:m]
+    v = (1.0, 0.8, 1.2, 1.4, 0.9, 1.1, 0.7, 1.3)[:m]
+    corr = tuple(tuple(1.0 if i == k else 0.5 for k in range(m)) for i in range(m))
+    return BasketSpec(type_, 64, K, 1.0, 100.0, 0.05, 0.25, tuple([1.0 / m] * m), a, v, corr)
