@@ -379,7 +379,7 @@ int choose_tile_log2(int precision, int n, int construction = QMCCPW_BB) {
 // the 8 warps (or is at least 32), since each run starts with a walk over
 // the bits of its first index (64-point runs were slower at d = 64: the
 // unrolled run no longer fits the instruction cache as well).
-// Tensor cores: 8 runs per tile.  Small n: (run, dim) items, at least two
+// Tensor cores: 8 runs per tile (16 for n > 64).  Small n: (run, dim) items, at least two
 // per thread.
 int chunk_log2_for(int n, int tile_log2, bool tc) {
     const int P = 1 << tile_log2;
@@ -393,7 +393,10 @@ int chunk_log2_for(int n, int tile_log2, bool tc) {
             --lg;
         }
     } else if (n >= 32) {
-        while (lg > 2 && (P >> lg) < kThreads / 32) --lg;
+        // at least one run per warp per 64-dimension block: 8 warps (resident
+        // kernel, n <= 64) or the streamed kernel's 15 producer warps
+        const int warps = n > 64 ? 16 : kThreads / 32;
+        while (lg > 2 && (P >> lg) < warps) --lg;
     } else {
         while (lg > 0 && static_cast<long>(n) * (P >> lg) < 2L * kThreads) --lg;
     }

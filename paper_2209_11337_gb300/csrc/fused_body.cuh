@@ -187,16 +187,20 @@ __device__ void bridge_phase(const ContractDev &c, T *zw, int stride, PathAcc<T>
     const int n_levels = c.n_levels;
     // nodes b and b + stride of one level (both independent): float takes
     // their exponentials in packed form
+    // the float path's constants in registers once per phase (read from the
+    // contract inside the loop, the stores to the row would make the
+    // compiler load them again at every node)
+    const PathConst kc = sizeof(T) == 4 ? PathConst(c) : PathConst();
     auto two_nodes = [&](int b, bool second, int stride) {
         int4 s0, s1;
         if constexpr (sizeof(T) == 4) {
-            const PathConst k(c);
+            // the steps carry float(date) in their last field
             const float w0 = bridge_node<float, false>(t, row, b, s0);
             if (second) {
                 const float w1 = bridge_node<float, false>(t, row, b + stride, s1);
-                acc.template add2<TYPE>(s0.x, s1.x, w0, w1, k);
+                acc.template add2<TYPE>(s0.x, s1.x, w0, w1, kc, __int_as_float(s0.w), __int_as_float(s1.w));
             } else {
-                acc.template add<TYPE>(s0.x, w0, k);
+                acc.template add<TYPE>(s0.x, w0, kc);
             }
         } else {
             double omega, sigma, dt;

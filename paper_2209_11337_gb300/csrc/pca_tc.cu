@@ -153,7 +153,7 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
                                            PathAcc<float> &acc, unsigned char *scratch) {
     const int warp = threadIdx.x >> 5;
     const int point = 32 * (warp & 3) + (threadIdx.x & 31);
-    stage_partial(scratch, kM, warp >> 2, point, acc, kM * NWG);
+    if (warp < 4 * NWG) stage_partial(scratch, kM, warp >> 2, point, acc, kM * NWG);  // not the product warp
     __syncthreads();
     ff v[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     const uint64_t local_point = tile * kM + point;
@@ -241,22 +241,41 @@ __device__ __forceinline__ void sobol_chain_deferred(const uint32_t *__restrict_
 }
 
 // Phase 1 of both variants: Sobol' + inverse normal of the tile's points for
-// dimensions j0 <= j < j1, split and stored into Z at column j - j0.  A lane
-// takes two adjacent dimensions (j even relative to j0) over a chunk of
-// consecutive points, the two Gray-code chains side by side, so each step
+// dimensions j0 <= j < j1, split and stored into Z at column col0 + j - j0.
+// A lane takes two adjacent dimensions (j even relative to j0) over a chunk
+// of consecutive points, the two Gray-code chains side by side, so each step
 // evaluates the inverse normal of two draws at once and stores both
 // dimensions' parts in one word; a warp covers 64 dimensions of a row
 // (128-byte swizzled rows: conflict-free).  Points past N are 0.  Columns of Z
 // at or beyond n meet only zero Ahat columns: an odd last dimension is
-// paired with a copy of itself in the next (padding) column.
-// the first Sobol' point of the current tile, per dimension of the Z columns
-// being built (phase 1 of both variants)
+// paired with a copy of itself in the next (padding) column.  `warp` counts
+// the NW warps that share the work.
+// The first Sobol' point of the current tile, per dimension (the streamed
+// variant): with it every run starts from the tile's point by the bits of its
+// own offset (sobol_from_gray) instead of a walk over the bits of its index.
+// The resident variant (at most 64 dimensions) measured 0.7% slower with it
+// (one more barrier per tile), so its runs walk from their own index.
 constexpr int kTcTileDims = 256;
 __shared__ uint32_t tc_tile_start[kTcTileDims];
 
-template <int KIND, int NW, bool TILE_START>
+// Fill tc_tile_start for dimensions 0..n-1 (every thread of the CTA; the
+// caller synchronises); false when the tile does not start on a multiple of
+// kM, whose runs then walk from their own index.
+__device__ __forceinline__ bool tile_start_dims(const LaunchParams &p, const ContractDev &c, uint32_t rep,
+                                                uint64_t tile) {
+    const uint64_t k_tile = p.point_k0 + tile * static_cast<uint64_t>(kM);
+    if ((k_tile & static_cast<uint64_t>(kM - 1)) != 0 || c.n > kTcTileDims || (kM >> c.chunk_log2) < 2) return false;
+    const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
+    const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
+    for (int j = static_cast<int>(threadIdx.x); j < c.n; j += static_cast<int>(blockDim.x))
+        tc_tile_start[j] = sobol_first(tab, p.jstride, j, __ldg(shf + j), static_cast<uint32_t>(k_tile));
+    return true;
+}
+
+template <int KIND, int NW>
 __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const ContractDev &c, uint32_t rep, uint64_t tile,
-                                           unsigned char *z_hi, unsigned char *z_lo, int j0, int j1) {
+                                           unsigned char *z_hi, unsigned char *z_lo, int j0, int j1, int col0,
+                                           bool from_tile, int warp) {
     constexpr int ES = KIND == 0 ? 2 : 4;
     const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
     const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
@@ -264,24 +283,12 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
     const int nchunks = kM >> c.chunk_log2;
     const int per = (j1 - j0 + 63) >> 6;
     const int work = nchunks * per;
-    // TILE_START (the streamed variant): the tile's first point for dimensions
-    // j0..j1, one walk each, when the tile starts on a multiple of kM; every
-    // run then starts from it by the bits of its own offset (sobol_from_gray).
-    // The resident variant (at most 64 dimensions) measured 0.7% slower with
-    // it (one more barrier per tile), so its runs walk from their own index.
-    const uint64_t k_tile = p.point_k0 + tile * static_cast<uint64_t>(kM);
-    const bool from_tile = TILE_START && nchunks > 1 && (k_tile & static_cast<uint64_t>(kM - 1)) == 0 &&
-                           j1 - j0 <= kTcTileDims;
-    if (from_tile) {
-        for (int j = j0 + static_cast<int>(threadIdx.x); j < j1; j += static_cast<int>(blockDim.x))
-            tc_tile_start[j - j0] = sobol_first(tab, p.jstride, j, __ldg(shf + j), static_cast<uint32_t>(k_tile));
-        __syncthreads();
-    }
-    for (int it = threadIdx.x >> 5; it < work; it += NW) {
+    for (int it = warp; it < work; it += NW) {
         const int ch = it / per;
-        const int col = (it - ch * per) * 64 + 2 * (threadIdx.x & 31);
-        const int ja = j0 + col;
+        const int rel = (it - ch * per) * 64 + 2 * (threadIdx.x & 31);
+        const int ja = j0 + rel;
         if (ja >= j1) continue;
+        const int col = col0 + rel;
         const int jb = ja + 1 < j1 ? ja + 1 : ja;  // odd last dimension: its own copy (in bounds of the tables)
         const uint64_t first_local = tile * kM + static_cast<uint64_t>(ch) * chunk;
         const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
@@ -291,8 +298,8 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
             uint32_t ya, yb;
             if (from_tile) {
                 const uint32_t off = static_cast<uint32_t>(row0);
-                sobol_from_gray_pair(tab, p.jstride, ja, jb, tc_tile_start[ja - j0], tc_tile_start[jb - j0],
-                                     off ^ (off >> 1), ya, yb);
+                sobol_from_gray_pair(tab, p.jstride, ja, jb, tc_tile_start[ja], tc_tile_start[jb], off ^ (off >> 1),
+                                     ya, yb);
             } else {
                 sobol_first_pair(tab, p.jstride, ja, jb, __ldg(shf + ja), __ldg(shf + jb), k0, ya, yb);
             }
@@ -379,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
         if (sh.abort) break;
 
         // ---- phase 1: Sobol' + inverse normal -> split operand
-        sobol_to_z<KIND, kThreads / 32, false>(p, c, rep, tile, z_hi, z_lo, 0, n);
+        sobol_to_z<KIND, kThreads / 32>(p, c, rep, tile, z_hi, z_lo, 0, n, 0, false, warp);
         fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
         tc_fence_before();
         __syncthreads();
@@ -437,25 +444,42 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
 // d up to 257 (N = K = 256), Ahat streamed.  Ahat (384 KB bf16 in three
 // parts, 512 KB tf32 in two) does not fit beside Z, so it comes from L2 in
 // K-chunks of 16 dimensions (all parts of a chunk in one bulk TMA copy, 24 or
-// 32 KB) through two buffers.
-// A buffer is refilled once the products that read it have completed
-// (tcgen05.commit to its release barrier), one chunk behind the issue front,
-// and the first two chunks of the next tile are fetched while the epilogue
-// of this one runs; only the chunks that hold dimensions below n are used.
-// Z hi/lo stays resident: all 256 columns for bf16 (128 KB); for tf32 the
-// same 128 KB holds 128 columns, so Z is generated in two K-halves, the
-// second after the products of the first are done.  D1 and D2 take all 512
-// TMEM columns: one CTA per SM.
+// 32 KB) through a ring of chunk buffers (three for bf16, two for tf32; six
+// for bf16, with Z in two slots, measured 2.5% slower).
+// Z is produced in blocks of 64 dimensions (one 128-byte swizzle column of
+// bf16, two of tf32) and the products of a block run while the next block is
+// produced: 16 producer warps write Z and arrive on the block's "full"
+// barrier; a 17th warp, the product warp, waits for each block, issues its
+// products chunk by chunk as the Ahat chunks land, refills each chunk buffer
+// once the products that read it are done (tcgen05.commit to the buffer's
+// barrier), and commits the block's Z slot free.  Z hi/lo holds all 256
+// columns for bf16 (128 KB, four block slots); for tf32 the same 128 KB holds
+// 128 columns (two block slots), a slot reused once its block's products are
+// done.  Measured at d = 256 (N = 2^20, R = 16): bf16 25.1 -> 23.8 ms, tf32
+// 27.5 -> 23.6 ms per launch; the products read about 90 bytes of shared
+// memory per clock while they run, so the producers' stores compete with
+// them and the overlap gains less than the product phase's share.
+// A buffer's next chunk wraps to the first chunks of the next tile, which
+// are fetched while the epilogue of this one runs.  D1 and D2 take all 512
+// TMEM columns: one CTA per SM.  Without any overlap (the product phase
+// after the whole Sobol' phase) the product phase was 44% of the kernel.
 constexpr int kNbig = 256;
-// The streamed kernel runs alone on its SM (all 512 TMEM columns), so it
-// takes 16 warps: four warpgroups share each point's dates in the epilogue
-// and twice as many warps hide the latency of the Sobol' phase.
+// Four warpgroups share each point's dates in the epilogue: 16 warps.  15 of
+// them produce Z; the 16th is the product warp during production and joins
+// the epilogue (512 threads, up to 128 registers).  A 17th warp for the
+// products instead (544 threads: five warps on one SM sub-partition cap the
+// registers at 96) measured 1-6% slower.
 constexpr int kThreadsS = 512;
+constexpr int kProducerWarpsS = 15;
+constexpr int kEpilogueWarpsS = 16;
 
 template <int KIND> struct Streamed {
     static constexpr int ES = KIND == 0 ? 2 : 4;
     static constexpr int Kc = 16;                          // K per chunk
     static constexpr int Kz = KIND == 0 ? 256 : 128;       // Z columns resident at a time
+    static constexpr int Bd = 64;                          // dimensions per produced block
+    static constexpr int Slots = Kz / Bd;                  // block slots of Z
+    static constexpr int Nb = KIND == 0 ? 3 : 2;           // Ahat chunk buffers
     static constexpr int Parts = KIND == 0 ? 3 : 2;        // Ahat parts
     static constexpr uint32_t ZPart = kM * Kz * ES;        // one split part of Z
     static constexpr uint32_t ChunkPart = kNbig * Kc * ES; // one part of one chunk (8 or 16 KB)
@@ -463,10 +487,16 @@ template <int KIND> struct Streamed {
 };
 
 struct TcSharedS {
-    uint64_t bar_b[2], bar_f[2], bar_mma;
+    uint64_t bar_b[3], bar_f[3];       // Ahat chunk buffer landed / free again
+    uint64_t bar_full[4], bar_free[4]; // Z block slot written by the producers / read by the products
+    uint64_t bar_mma;                  // every product of the tile done
     uint32_t tmem_addr;
     int32_t abort;
 };
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_constant__ LaunchParams p) {
@@ -476,20 +506,27 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
     constexpr uint32_t kSboB = (S::Kc * S::ES / 16) * 128;  // 8-row groups of a chunk
     constexpr uint32_t kCols = 2 * kNbig;
     constexpr int kSteps = S::Kc * S::ES / 32;             // instructions (32 bytes of K) per chunk
+    constexpr int kChunksPerBlock = S::Bd / S::Kc;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *z_hi = aligned_smem(smem_raw);
     unsigned char *z_lo = z_hi + S::ZPart;
-    unsigned char *bbuf = z_lo + S::ZPart;                 // two chunk buffers
-    unsigned char *scratch = bbuf + 2 * S::ChunkBytes;
+    unsigned char *bbuf = z_lo + S::ZPart;                 // S::Nb chunk buffers
+    unsigned char *scratch = bbuf + S::Nb * S::ChunkBytes;
     __shared__ TcSharedS sh;
     __shared__ WorkItem work;
 
     const int warp = threadIdx.x >> 5;
+    const bool producer = warp < kProducerWarpsS;
+    const bool issuer = warp == kProducerWarpsS && (threadIdx.x & 31) == 0;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < S::Nb; ++i) {
             mbar_init(&sh.bar_b[i], 1);
             mbar_init(&sh.bar_f[i], 1);
+        }
+        for (int i = 0; i < S::Slots; ++i) {
+            mbar_init(&sh.bar_full[i], 32 * kProducerWarpsS);
+            mbar_init(&sh.bar_free[i], 1);
         }
         mbar_init(&sh.bar_mma, 1);
         sh.abort = 0;
@@ -502,12 +539,16 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
     const uint32_t tmem = sh.tmem_addr;
     for (uint32_t i = threadIdx.x; i < 2 * S::ZPart / 4; i += kThreadsS) reinterpret_cast<uint32_t *>(z_hi)[i] = 0u;
 
-    // barrier phases and the chunk pipeline are thread 0's alone; chunk q of
-    // the CTA's running sequence uses buffer q & 1
-    uint32_t b_ph[2] = {0, 0}, f_ph[2] = {0, 0}, mma_ph = 0;
-    uint64_t q = 0;                // running index of the next chunk to consume
-    const void *loaded = nullptr;  // operand whose next two chunks are in flight or resident
-    bool ok = true;                // thread 0: no wait has expired
+    // the product thread's state: barrier phases, the running chunk index q
+    // (chunk q sits in buffer q % Nb), the operand whose next Nb chunks are in
+    // flight or resident
+    uint32_t b_ph[3] = {0, 0, 0}, f_ph[3] = {0, 0, 0}, full_ph[4] = {0, 0, 0, 0};
+    uint64_t q = 0;
+    const void *loaded = nullptr;
+    bool ok = true;  // the product thread: no wait has expired
+    // the producers' uses of each Z slot (parity of its "free" barrier)
+    uint32_t slot_uses[4] = {0, 0, 0, 0};
+    uint32_t mma_ph = 0;
     auto fetch = [&](const void *op, int chunk, int buf) {
         mbar_expect_tx(&sh.bar_b[buf], S::ChunkBytes);
         bulk_copy_g2s(bbuf + buf * S::ChunkBytes, static_cast<const unsigned char *>(op) + chunk * S::ChunkBytes,
@@ -532,55 +573,55 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
         const uint32_t rep = work.rep;
         const uint64_t tile = work.tile;
         const int nch = (c.n + S::Kc - 1) / S::Kc;        // chunks holding dimensions below n (>= 5)
-        if (threadIdx.x == 0 && ok && loaded != c.tc_operand) {
-            // first tile, or a contract with another d: let the prefetch of
-            // the previous operand land, then fetch this one's chunks 0 and 1
-            if (loaded != nullptr) {
-                wait_b(q & 1);
-                wait_b((q + 1) & 1);
-            }
-            if (ok) {
-                fetch(c.tc_operand, 0, q & 1);
-                fetch(c.tc_operand, 1, (q + 1) & 1);
-                loaded = c.tc_operand;
-            } else {
-                sh.abort = 1;
-            }
-        }
+        const int nblk = (c.n + S::Bd - 1) / S::Bd;
+        const bool from_tile = tile_start_dims(p, c, rep, tile);
+        __syncthreads();
 
-        bool late = false;  // a wait for the products expired: leave the item unfinished
-        for (int j0 = 0; j0 < c.n; j0 += S::Kz) {
-            if (j0 > 0) {
-                // Z is rewritten: the products of the previous half must be done
-                if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 2);  // 2: products may still run
-                __syncthreads();
-                if (sh.abort == 2) {
-                    late = true;
-                    break;
+        if (producer) {
+            // ---- Sobol' + inverse normal -> Z, one 64-dimension block at a time
+            for (int b = 0; b < nblk; ++b) {
+                const int slot = b % S::Slots;
+                // the slot's block of this tile before: its products must be done
+                if (b >= S::Slots && !sh.abort &&
+                    !mbar_wait(&sh.bar_free[slot], (slot_uses[slot] - 1u) & 1u))
+                    atomicExch(&sh.abort, 2);
+                ++slot_uses[slot];
+                const int j0 = b * S::Bd, j1 = min(c.n, j0 + S::Bd);
+                sobol_to_z<KIND, kProducerWarpsS>(p, c, rep, tile, z_hi, z_lo, j0, j1, j0 % S::Kz, from_tile, warp);
+                fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+                mbar_arrive(&sh.bar_full[slot]);
+            }
+        } else if (warp == kProducerWarpsS) {
+          if (issuer) {
+            // ---- the products of each block as it fills
+            if (ok && loaded != c.tc_operand) {
+                // first tile, or a contract with another d: let the prefetch of
+                // the previous operand land, then fetch this one's first chunks
+                if (loaded != nullptr)
+                    for (int i = 0; i < S::Nb; ++i) wait_b(static_cast<int>((q + i) % S::Nb));
+                if (ok) {
+                    for (int i = 0; i < S::Nb; ++i) fetch(c.tc_operand, i, static_cast<int>((q + i) % S::Nb));
+                    loaded = c.tc_operand;
                 }
-                ++mma_ph;
-                tc_fence_after();
             }
-            // ---- phase 1: Sobol' + inverse normal -> split Z, columns j0..
-            sobol_to_z<KIND, kThreadsS / 32, true>(p, c, rep, tile, z_hi, z_lo, j0, min(c.n, j0 + S::Kz));
-            fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-
-            // ---- phase 2: the chunks of this half; 3 (tf32) or 4 (bf16) products per k-step
-            if (threadIdx.x == 0) {
-                const int c_end = min(nch, (j0 + S::Kz) / S::Kc);
-                for (int cc = j0 / S::Kc; cc < c_end && ok; ++cc, ++q) {
-                    const int buf = static_cast<int>(q & 1);
+            int cc = 0;
+            for (int b = 0; b < nblk && ok; ++b) {
+                const int slot = b % S::Slots;
+                ok = mbar_wait(&sh.bar_full[slot], full_ph[slot] & 1u);
+                ++full_ph[slot];
+                if (!ok) break;
+                tc_fence_after();
+                const int c_end = min(nch, (b + 1) * kChunksPerBlock);
+                for (; cc < c_end && ok; ++cc, ++q) {
+                    const int buf = static_cast<int>(q % S::Nb);
                     wait_b(buf);
                     if (!ok) break;
                     const uint32_t bh = smem_u32(bbuf + buf * S::ChunkBytes), b2 = bh + S::ChunkPart,
                                    b3 = b2 + S::ChunkPart;
 #pragma unroll
                     for (int ks = 0; ks < kSteps; ++ks) {
-                        const uint32_t kb = static_cast<uint32_t>((cc * S::Kc - j0) * S::ES + ks * 32);  // Z byte offset
-                        const uint32_t koff = static_cast<uint32_t>(ks) * 256u;                       // chunk: two core matrices
+                        const uint32_t kb = static_cast<uint32_t>(((cc * S::Kc) % S::Kz) * S::ES + ks * 32);  // Z byte offset
+                        const uint32_t koff = static_cast<uint32_t>(ks) * 256u;  // chunk: two core matrices
                         const uint64_t zh = smem_desc_sw128(z_slice(smem_u32(z_hi), kb));
                         const uint64_t zl = smem_desc_sw128(z_slice(smem_u32(z_lo), kb));
                         const uint32_t acc = (cc | ks) ? 1u : 0u;
@@ -594,41 +635,45 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
                     }
                     mma_commit(&sh.bar_f[buf]);
                     if (cc >= 1) {
-                        // chunk cc-1's products are done with their buffer: refill it
-                        // with chunk cc+1 (chunk 0 of the next tile after the last)
-                        wait_f(buf ^ 1);
-                        if (ok) fetch(c.tc_operand, (cc + 1) % nch, buf ^ 1);
+                        // chunk cc-1's products are done with their buffer: refill it with
+                        // chunk cc-1+Nb (past the last: the first chunks of the next tile)
+                        const int pb = static_cast<int>((q - 1) % S::Nb);
+                        wait_f(pb);
+                        const int next = cc - 1 + S::Nb;
+                        if (ok) fetch(c.tc_operand, next < nch ? next : next - nch, pb);
                     }
                 }
-                if (ok && c_end == nch) {
-                    wait_f(static_cast<int>((q - 1) & 1));  // the last chunk's products: then chunk 1 of the next tile
-                    if (ok) fetch(c.tc_operand, 1, static_cast<int>((q + 1) & 1));
-                }
-                mma_commit(&sh.bar_mma);  // arrives when every product issued above is done
-                if (!ok) sh.abort = 1;
+                mma_commit(&sh.bar_free[slot]);  // the slot is free once this block's products are done
             }
+            if (ok) {  // the last chunk's buffer: then chunk Nb-1 of the next tile
+                const int pb = static_cast<int>((q - 1) % S::Nb);
+                wait_f(pb);
+                if (ok) fetch(c.tc_operand, S::Nb - 1, pb);
+            }
+            mma_commit(&sh.bar_mma);  // arrives when every product issued above is done
+            if (!ok) atomicExch(&sh.abort, 1);
+          }
+          __syncwarp();  // the rest of the product warp waits here, not in a poll beside the issuing lane
         }
-        if (late) break;
-        if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 2);
-        __syncthreads();
-        if (sh.abort == 2) break;  // an unfinished accumulator is never read or summed
+        if (!mbar_wait(&sh.bar_mma, mma_ph & 1u)) atomicExch(&sh.abort, 2);  // 2: products may still run
         ++mma_ph;
+        __syncthreads();
+        if (sh.abort) break;  // an unfinished accumulator is never read or summed
         tc_fence_after();
 
-        // ---- phase 3: path sums from D1 + D2, then values and the tile sum
+        // ---- path sums from D1 + D2 (the first 16 warps), then values and the tile sum
         PathAcc<float> acc;
-        epilogue_dispatch<kNbig, kThreadsS / 128>(c, tmem, acc, (threadIdx.x >> 5) >> 2, (threadIdx.x >> 5) & 3);
+        if (warp < kEpilogueWarpsS) epilogue_dispatch<kNbig, kEpilogueWarpsS / 4>(c, tmem, acc, warp >> 2, warp & 3);
         tc_fence_before();
-        finish_tile<kThreadsS / 128>(p, c, item, tile, acc, scratch);
+        finish_tile<kEpilogueWarpsS / 4>(p, c, item, tile, acc, scratch);
     }
 
     // the prefetched chunks, and products an expired wait left running, must
     // land before the CTA exits (bounded waits again)
-    if (threadIdx.x == 0 && sh.abort == 2) mbar_wait(&sh.bar_mma, mma_ph & 1u);
-    if (threadIdx.x == 0 && ok && loaded != nullptr) {
-        wait_b(q & 1);
-        wait_b((q + 1) & 1);
-        if (!ok) sh.abort = 1;
+    if (threadIdx.x == 0 && sh.abort == 2) mbar_wait(&sh.bar_mma, (mma_ph - 1u) & 1u);
+    if (issuer && ok && loaded != nullptr) {
+        for (int i = 0; i < S::Nb; ++i) wait_b(static_cast<int>((q + i) % S::Nb));
+        if (!ok) atomicExch(&sh.abort, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -665,8 +710,10 @@ size_t pca_tc_smem_bytes(int kind) {
     // staging of the warpgroups' partial sums (4 arrays of kM x 4 entries at most) and the
     // float-float tile sum (8 x kThreads floats)
     const size_t scratch = std::max<size_t>(16 * kM * 4, 8 * kThreads * sizeof(float));
-    if (kind == 2) return 1024 + 2 * static_cast<size_t>(Streamed<0>::ZPart) + 2 * Streamed<0>::ChunkBytes + scratch;
-    if (kind == 3) return 1024 + 2 * static_cast<size_t>(Streamed<1>::ZPart) + 2 * Streamed<1>::ChunkBytes + scratch;
+    if (kind == 2)
+        return 1024 + 2 * static_cast<size_t>(Streamed<0>::ZPart) + Streamed<0>::Nb * Streamed<0>::ChunkBytes + scratch;
+    if (kind == 3)
+        return 1024 + 2 * static_cast<size_t>(Streamed<1>::ZPart) + Streamed<1>::Nb * Streamed<1>::ChunkBytes + scratch;
     const size_t es = kind == 0 ? 2 : 4, parts = kind == 0 ? 3 : 2;
     return 1024 + 2 * kM * kNpad * es + parts * kNpad * kNpad * es + scratch;
 }

@@ -364,6 +364,7 @@ struct PathConst {
     float b_hi, b_lo;  // omega dt
     __device__ explicit PathConst(const ContractDev &c)
         : a_hi(c.ff_sig_sdt[0]), a_lo(c.ff_sig_sdt[1]), b_hi(c.ff_om_dt[0]), b_lo(c.ff_om_dt[1]) {}
+    __device__ PathConst() : a_hi(0.0f), a_lo(0.0f), b_hi(0.0f), b_lo(0.0f) {}
     // the exponent at a date: the small terms first, each FMA one rounding
     __device__ __forceinline__ float lx(float node, float w) const {
         return fmaf(w, a_hi, fmaf(node, b_hi, fmaf(w, a_lo, node * b_lo)));
@@ -424,14 +425,17 @@ template <> struct PathAcc<float> {
 
     // two dates (node0 before node1): exponents and exponentials in packed
     // form, the sums in date order (equal to two calls of add)
+    // (nf0, nf1: the dates as floats, when the caller has them; else formed here)
     template <int TYPE>
-    __device__ __forceinline__ void add2(int32_t node0, int32_t node1, float w0, float w1, const PathConst &k) {
+    __device__ __forceinline__ void add2(int32_t node0, int32_t node1, float w0, float w1, const PathConst &k,
+                                         float nf0 = -1.0f, float nf1 = -1.0f) {
         if constexpr (TYPE == QMCCPW_GEOMETRIC_ASIAN_CALL) {
             x += w0;
             x += w1;
         } else {
-            const float2 nf = make_float2(small_uint_to_float(static_cast<uint32_t>(node0)),
-                                          small_uint_to_float(static_cast<uint32_t>(node1)));
+            const float2 nf = nf0 >= 0.0f ? make_float2(nf0, nf1)
+                                          : make_float2(small_uint_to_float(static_cast<uint32_t>(node0)),
+                                                        small_uint_to_float(static_cast<uint32_t>(node1)));
             const float2 e = fx::exp_f2(k.lx2(nf, make_float2(w0, w1)));
             take<TYPE>(node0, nf.x, e.x, w0);
             take<TYPE>(node1, nf.y, e.y, w1);
