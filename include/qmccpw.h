@@ -67,7 +67,7 @@ typedef enum {
     QMCCPW_BB_LEAD = 3,              /* the whole path of the d dates by the bridge, its leading coordinate
                                         (the terminal value) integrated out instead of the first increment;
                                         switch point by Newton's method (Sec. 6-7 name this reduction);
-                                        arithmetic, binary and geometric Asians (no lookback) */
+                                        the lookback by the upper envelope of the dates' exponentials */
     QMCCPW_PCA_LEAD = 4              /* the same with the PCA of the d dates, its first component integrated out */
 } qmccpw_construction;
 
