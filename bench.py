@@ -21,6 +21,7 @@ on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -294,20 +295,26 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
     """Poisson arrivals through the device-resident serving loop.
 
     Each request is a book-like contract with a target delta standard error in
-    {1e-3, 1e-4, 1e-5}: a pilot run (N = 2^12, R = 16) gives the delta SE at
-    2^12, N is the smallest power of two in [2^12, 2^22] whose SE, scaled as
-    1/N, meets the target, and the main run uses it.  Latency = completion of
-    the main run - arrival.  Requests arriving in the first `warmup_s` seconds
-    are run but not counted."""
+    {1e-3, 1e-4, 1e-5}: a pilot run (N1 = 2^12, R = 16) gives the delta SE at
+    2^12, and N is the smallest power of two in [2^12, 2^22] whose SE, scaled
+    as 1/N, meets the target.  The pilot's points are the first 2^12 of the N
+    (the Sobol' sequence extends), so the main run covers points N1 .. N-1
+    only (first_point = N1) and each replicate's estimate is the
+    point-weighted mean of its two runs; a request whose pilot meets the
+    target is answered by the pilot.  Latency = completion of the request's
+    last run - arrival.  Offered load = the point-dates of the requests that
+    arrive in the window (sum of N R d), per second of the window; requests
+    arriving in the first `warmup_s` seconds are run but not counted."""
     import queue
 
+    N1 = 2 ** 12
     reqs = W.arrivals(rate_hz=rate_hz, duration_s=warmup_s + duration_s, seed=seed, R=16)
     # the requests are bridge contracts: the MIXED kernel without the PCA product fits three CTAs per SM
     q.qmccpw_server_start(plan, precision=precision, max_inflight=1024, max_inflight_bytes=256 << 20,
                           constructions=[q.QMCCPW_BB])
     pilots = queue.Queue()
     mains = queue.Queue()
-    lat, main_elems, Ns = [], [0], []
+    lat, offered_elems, Ns, answers = [], [0], [], {}
     t0 = time.perf_counter()
 
     def submitter():
@@ -325,26 +332,33 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
                 mains.put(None)
                 return
             i, rq, t = item
-            _, se, _ = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
+            _, se, per1 = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
             ratio = max(se[1], 1e-300) / rq.target_se
-            N = 2 ** 12
-            while N < 2 ** 22 and ratio * (2 ** 12) / N > 1.0:
+            N = N1
+            while N < 2 ** 22 and ratio * N1 / N > 1.0:
                 N *= 2
-            c = W.with_size(rq.contract, N=N)
-            mains.put((i, rq, c, q.qmccpw_submit(plan, c)))
+            if N == N1:
+                mains.put((i, rq, N, per1, None, time.perf_counter() - t0))
+            else:
+                rest = dataclasses.replace(rq.contract, N=N - N1, first_point=N1)
+                mains.put((i, rq, N, per1, q.qmccpw_submit(plan, rest), None))
 
     def finisher():
         while True:
             item = mains.get()
             if item is None:
                 return
-            i, rq, c, t = item
-            q.qmccpw_wait(plan, t, c.R, 600000)
-            done = time.perf_counter() - t0
+            i, rq, N, per1, t, done = item
+            if t is not None:
+                _, _, per2 = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
+                done = time.perf_counter() - t0
+                per1 = (N1 * per1 + (N - N1) * per2) / N   # the request's per-replicate estimates
+            # the request's answer: mean and standard error over its replicates
+            answers[i] = (per1.mean(axis=0), per1.std(axis=0, ddof=1) / math.sqrt(per1.shape[0]))
             if rq.arrival_s >= warmup_s:
                 lat.append(done - rq.arrival_s)
-                main_elems[0] += c.N * c.R * c.d
-                Ns.append(c.N)
+                offered_elems[0] += N * rq.contract.R * rq.contract.d
+                Ns.append(N)
 
     threads = [threading.Thread(target=f) for f in (submitter, sizer, finisher)]
     for t in threads:
@@ -356,14 +370,13 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
     q.qmccpw_server_stop(plan)
     lat_ms = sorted(1e3 * x for x in lat)
     pct = lambda p: lat_ms[min(len(lat_ms) - 1, int(p * len(lat_ms)))] if lat_ms else None
-    # offered load: pilot and main runs of the requests counted, per second of arrivals
-    offered = (sum(2 ** 12 * rq.contract.R * rq.contract.d for rq in reqs) + main_elems[0]) / (warmup_s + duration_s)
     return {"rate_hz": rate_hz, "window_s": duration_s, "requests": len(lat_ms), "p50_ms": pct(0.50),
             "p99_ms": pct(0.99), "max_ms": lat_ms[-1] if lat_ms else None,
             "throughput_point_dates_per_s": stats["point_dates"] / wall, "wall_s": wall,
-            "offered_point_dates_per_s": offered, "kernel_launches": stats["launches"],
+            "offered_point_dates_per_s": offered_elems[0] / duration_s, "kernel_launches": stats["launches"],
             "idle_exits": stats["idle_exits"],
             "mean_N": statistics.mean(Ns) if Ns else None,
+            "answered_by_pilot": (sum(1 for n in Ns if n == N1) / len(Ns)) if Ns else None,
             "precision": {0: "fp64", 1: "mixed", 2: "tc-bf16", 3: "tc-tf32"}[precision]}
 
 

@@ -132,7 +132,14 @@ typedef struct {
                                   ranges (plans with the same seed) gives per-replicate estimates
                                   bit-identical to one call over the whole range; mean and SE are
                                   those of the call's own R replicates */
-    int32_t reserved;          /* must be 0 */
+    uint32_t first_point;      /* the contract uses Sobol' points first_point .. first_point+N-1 of
+                                  each replicate (first_point + N <= 2^32); 0 for the usual estimate.
+                                  The Sobol' sequence extends (Sec. 2.2.2: the first 2^m points of
+                                  2^(m+1) are the 2^m-point set), so a run of N1 points from 0 and a
+                                  run of N2 points from N1 give, per replicate, (N1 e1 + N2 e2) /
+                                  (N1 + N2) = the estimate of N1 + N2 points from 0 (up to the order
+                                  of the sums): an estimate can be refined without recomputing the
+                                  points it already has */
 } qmccpw_contract;
 
 /*

@@ -247,7 +247,8 @@ int validate_contract(const qmccpw_plan_s *p, const qmccpw_option &o, const qmcc
 // A public contract descriptor: its replicate range within the plan's
 // randomisation, then the option, market and sizes.
 int validate_qc(const qmccpw_plan_s *p, const qmccpw_contract &c, int32_t precision, bool diagnostic) {
-    if (c.reserved != 0) return fail(QMCCPW_ERR_INVALID_ARG, "qmccpw_contract.reserved must be 0");
+    if (static_cast<uint64_t>(c.first_point) + c.N > (1ull << 32))
+        return fail(QMCCPW_ERR_INVALID_ARG, "first_point + N must be <= 2^32");
     if (c.first_replicate < 0 || (!diagnostic && static_cast<int64_t>(c.first_replicate) + c.R > p->r_max))
         return fail(QMCCPW_ERR_INVALID_ARG, "replicates first_replicate .. first_replicate + R - 1 must lie in "
                                             "0..r_max-1 (r_max=" + std::to_string(p->r_max) + ")");
@@ -428,6 +429,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.chunk_log2 = chunk_log2_for(c.n, c.tile_log2, is_tc(precision));
     c.R = in.R;
     c.rep_first = in.first_replicate;
+    c.k_first = in.first_point;
     c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
     c.groups = kThreads / P;
     c.n_levels = t->n_levels;
@@ -1922,6 +1924,7 @@ int qmccpw_autotune(qmccpw_plan_t plan, const qmccpw_contract *sample, int32_t c
         qmccpw_contract c = src;
         c.R = 4;
         c.first_replicate = 0;
+        c.first_point = 0;
         const uint64_t target = precision == QMCCPW_FP64 ? (1ull << 21) : (1ull << 24);
         c.N = std::max<uint64_t>(1024, target / (4ull * static_cast<uint64_t>(c.option.d)));
         int best = base;

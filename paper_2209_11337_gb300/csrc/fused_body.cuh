@@ -511,8 +511,9 @@ __shared__ uint32_t tile_start[kTileStartDims];
 // One work item: tile `tile` (points tile*P .. tile*P+P-1 of the contract,
 // the last tile ragged) of replicate `rep` (index into the plan's
 // randomisation tables), its four tile sums written to tile_out[0..3].
-// point_k0 shifts the point indices and point_out, when set, receives every
-// point's values (diagnostics).  `smem` is the CTA's dynamic shared memory
+// Point t of the contract is Sobol' point point_k0 + c.k_first + t
+// (point_k0: diagnostics; k_first: the contract's first point); point_out,
+// when set, receives every point's values (diagnostics).  `smem` is the CTA's dynamic shared memory
 // (fused_smem_bytes); every thread of the CTA calls this.
 template <typename T, int CONS>
 __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *__restrict__ sobol_table,
@@ -523,6 +524,7 @@ __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *_
     const int n = c.n;
     const int stride = c.row_stride;
     T *zw = reinterpret_cast<T *>(smem);
+    point_k0 += c.k_first;
 
     // ---- phase 1: Sobol' + inverse normal -> zw[point][slot]
     if (n > 0) {

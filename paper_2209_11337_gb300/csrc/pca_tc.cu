@@ -263,7 +263,7 @@ __shared__ uint32_t tc_tile_start[kTcTileDims];
 // kM, whose runs then walk from their own index.
 __device__ __forceinline__ bool tile_start_dims(const LaunchParams &p, const ContractDev &c, uint32_t rep,
                                                 uint64_t tile) {
-    const uint64_t k_tile = p.point_k0 + tile * static_cast<uint64_t>(kM);
+    const uint64_t k_tile = p.point_k0 + c.k_first + tile * static_cast<uint64_t>(kM);
     if ((k_tile & static_cast<uint64_t>(kM - 1)) != 0 || c.n > kTcTileDims || (kM >> c.chunk_log2) < 2) return false;
     const uint32_t *tab = p.sobol_table + static_cast<size_t>(rep) * 32u * p.jstride;
     const uint32_t *shf = p.sobol_shift + static_cast<size_t>(rep) * p.jstride;
@@ -294,7 +294,7 @@ __device__ __forceinline__ void sobol_to_z(const LaunchParams &p, const Contract
         const int len = first_local >= c.N ? 0 : static_cast<int>(min(static_cast<uint64_t>(chunk), c.N - first_local));
         const int row0 = ch * chunk;
         if (len > 0) {
-            const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + first_local);
+            const uint32_t k0 = static_cast<uint32_t>(p.point_k0 + c.k_first + first_local);
             uint32_t ya, yb;
             if (from_tile) {
                 const uint32_t off = static_cast<uint32_t>(row0);

@@ -64,6 +64,7 @@ struct ContractDev {
     int32_t slot_shift;                  // 1 for the leading-coordinate constructions (dimension j drives node j+1), else 0
     int32_t rep_first;                   // randomisation index of the contract's replicate 0
     uint64_t N;
+    uint64_t k_first;                    // Sobol' index of the contract's point 0
     uint64_t item_base;                  // first work item of this contract
     uint64_t rep_base;                   // first replicate slot of this contract (in per-replicate arrays)
     // per-d tables for unit spacing (device pointers); kernels scale by sqrt(dt)

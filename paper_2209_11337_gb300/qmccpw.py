@@ -119,7 +119,7 @@ def basket_struct(b) -> qmccpw_basket:
 class qmccpw_contract(ctypes.Structure):
     _fields_ = [("option", qmccpw_option), ("market", qmccpw_market), ("N", ctypes.c_uint64),
                 ("R", ctypes.c_int32), ("construction", ctypes.c_int32), ("first_replicate", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("first_point", ctypes.c_uint32)]
 
 
 class qmccpw_server_desc(ctypes.Structure):
@@ -255,7 +255,8 @@ def contract_array(contracts: Sequence) -> ctypes.Array:
     arr = (qmccpw_contract * len(contracts))()
     for i, c in enumerate(contracts):
         arr[i] = qmccpw_contract(qmccpw_option(c.type, c.d, c.K, c.T), qmccpw_market(c.S0, c.r, c.sigma),
-                                 c.N, c.R, c.construction, getattr(c, "first_replicate", 0), 0)
+                                 c.N, c.R, c.construction, getattr(c, "first_replicate", 0),
+                                 getattr(c, "first_point", 0))
     return arr
 
 

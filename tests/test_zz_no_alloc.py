@@ -2,10 +2,10 @@
 ordinary one (qmccpw_greeks).
 
 qmccpw_greeks_noalloc serves callers that must not allocate device memory
-per call (stream capture in progress, latency-critical services where
-cudaMalloc/cudaFree would block or synchronise the device, memory owned by
-another allocator): its per-call arrays live in a fixed array compiled into
-the library.  Here the test itself owns the output buffer; the results of two
+per call (latency-critical services where cudaMalloc/cudaFree would block or
+synchronise the device, hosts whose device memory is owned by another
+allocator): its per-call arrays live in a fixed array compiled into the
+library.  Here the test itself owns the output buffer; the results of two
 consecutive calls must match qmccpw_greeks within the parity tolerance of the
 other GPU tests.  The file name makes pytest collect it last.
 """

@@ -37,10 +37,12 @@ class Contract:
     R: int
     construction: int = BB
     first_replicate: int = 0  # replicates first_replicate .. first_replicate + R - 1 of the randomisation
+    first_point: int = 0      # Sobol' points first_point .. first_point + N - 1 of each replicate
 
     def label(self) -> str:
         return (f"{TYPE_NAMES[self.type]}-{CONS_NAMES[self.construction]}-d{self.d}-K{self.K:g}"
-                f"-s{self.sigma:g}-N{self.N}-R{self.R}" + (f"@{self.first_replicate}" if self.first_replicate else ""))
+                f"-s{self.sigma:g}-N{self.N}-R{self.R}" + (f"@{self.first_replicate}" if self.first_replicate else "")
+                + (f"+{self.first_point}" if self.first_point else ""))
 
 
 def splitmix64(state: int):
