@@ -130,8 +130,9 @@ SEGMENT_KERNELS = {
                 "pca_tc_kernel<tf32>"),
 }
 # DRAM read + write bytes of one full-size launch of the grid's kernels from
-# one ncu capture (profiles/); None for a kernel changed since
-GRID_TRAFFIC = {}
+# one ncu capture (profiles/dram_bytes_grid_d64_tcbf16.md); None for a kernel
+# changed since
+GRID_TRAFFIC = {"pca_tc_kernel<bf16>": 1408768 + 0, "fused_kernel<float, bridge>": 690944 + 0}
 # launch segments of a batch: bridge, standard, streamed and resident PCA (the
 # leading-coordinate segments that follow are not in the grid)
 ROOFLINE_SEGMENTS = 4

@@ -283,10 +283,12 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
  * array; serialise them on one stream.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) and caches it: make
  * that first call before any stream capture begins.
- * Errors: as qmccpw_greeks; OOM when the work of this call (about
- * 32 * R * N / P bytes of tile sums, P = 256 for d <= 65 in MIXED, plus the
- * d-dependent tables) exceeds the 16 MiB array; UNSUPPORTED for the
- * tensor-core precisions and the leading-coordinate constructions.
+ * Errors: as qmccpw_greeks; OOM when the work of this call (32 bytes per
+ * work item and replicate: about 32 * R * N / (P * g) bytes, P = 256 points
+ * per tile for d <= 65 in MIXED, g = 1..16 tiles per item as N / P grows
+ * past 512, plus the d-dependent tables) exceeds the 16 MiB array;
+ * UNSUPPORTED for the tensor-core precisions and the leading-coordinate
+ * constructions.
  */
 int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_market *market,
                           uint64_t N, int32_t R, int32_t construction, int32_t precision, double *out,
@@ -315,12 +317,13 @@ int qmccpw_tuning_set(qmccpw_plan_t plan, int32_t precision, int32_t constructio
  * entries and published through two host-written counters; one CTA of the
  * kernel copies each new entry into device memory and republishes it there,
  * and the other CTAs take the published requests' work items (replicate,
- * tile) in publication order from one device counter, so a request that
+ * run of tiles) in publication order from one device counter, so a request that
  * arrives while others run fills the SMs as they free up; the CTA that
  * finishes a request's last item reduces it on the device and raises the
  * request's completion flag in host-mapped memory.  Admission is in arrival order,
- * while the admitted requests' device scratch (32 bytes per tile slot and
- * per replicate: about 32 * R * N / P bytes, P the points per tile) fits
+ * while the admitted requests' device scratch (32 bytes per work item and
+ * replicate: about 32 * R * N / (P * g) bytes, P the points per tile, g =
+ * 1..16 the tiles per item) fits
  * `max_inflight_bytes` and at most `max_inflight` requests are on the
  * device; the rest wait on the host.  Every wait of the kernel is bounded by
  * %globaltimer: after `idle_limit_us` without a published work item its CTAs

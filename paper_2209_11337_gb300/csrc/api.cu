@@ -431,6 +431,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
     c.rep_first = in.first_replicate;
     c.k_first = in.first_point;
     c.tiles = static_cast<int32_t>((in.N + P - 1) / P);
+    set_item_grouping(c);
     c.groups = kThreads / P;
     c.n_levels = t->n_levels;
     c.row_stride = lead ? (c.n + 2) | 1 : (c.n + 1) | 1;
@@ -517,7 +518,7 @@ int batch_build(qmccpw_plan_s *p, const qmccpw_contract *cs, int32_t count, int3
         QMC_TRY(build_contract(p, in, precision, items, reps, &b->host[k]));
         const ContractDev &c = b->host[k];
         item_base[k] = items;
-        items += static_cast<uint64_t>(c.R) * c.tiles;
+        items += static_cast<uint64_t>(c.R) * c.items;
         const int kp = contract_precision(precision, in.construction);
         const int seg = segment_of(kp, in.construction, c.n);
         for (int g = seg + 1; g <= kSegments; ++g) b->seg_begin[g] = items;
@@ -1554,6 +1555,8 @@ int basket_run(qmccpw_plan_s *p, const qmccpw_basket &bk, int precision, uint64_
         ContractDev c{};
         c.R = R;
         c.tiles = static_cast<int32_t>(bp.b.tiles);
+        c.tpi = 1;  // the basket kernel writes one slot per tile
+        c.items = c.tiles;
         c.N = N;
         c.item_base = 0;
         c.rep_base = 0;
@@ -1646,6 +1649,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.chunk_log2 = chunk_log2_for(n, c.tile_log2, false);
     c.R = R;
     c.tiles = static_cast<int32_t>((N + P - 1) / P);
+    set_item_grouping(c);
     c.groups = kThreads / P;
     c.n_levels = static_cast<int>(bp.level_start.size()) - 1;
     c.row_stride = (n + 1) | 1;
@@ -1654,7 +1658,7 @@ int qmccpw_greeks_noalloc(qmccpw_plan_t plan, const qmccpw_option *option, const
     c.N = N;
     c.item_base = 0;
     c.rep_base = 0;
-    const uint64_t items = static_cast<uint64_t>(R) * c.tiles;
+    const uint64_t items = static_cast<uint64_t>(R) * c.items;
 
     // layout of the scratch array (256-byte aligned pieces)
     size_t off = 0;
@@ -1779,7 +1783,7 @@ int qmccpw_submit(qmccpw_plan_t plan, const qmccpw_contract *contract, uint64_t 
     QMC_TRY(build_contract(plan, *contract, sv->desc.precision, 0, 0, &pr.c));
     if (fused_smem_bytes(sv->desc.precision, contract->construction, pr.c.n, pr.c.tile_log2) > sv->smem)
         return fail(QMCCPW_ERR_UNSUPPORTED, "the request's tile needs more shared memory than the serving kernel has");
-    pr.items = static_cast<uint64_t>(pr.c.R) * static_cast<uint64_t>(pr.c.tiles);
+    pr.items = static_cast<uint64_t>(pr.c.R) * static_cast<uint64_t>(pr.c.items);
     pr.bytes = serve_bytes(pr.items, pr.c.R);
     if (((pr.bytes + 255) & ~uint64_t(255)) > sv->desc.max_inflight_bytes)
         return fail(QMCCPW_ERR_OOM, "the request needs more device scratch than max_inflight_bytes");

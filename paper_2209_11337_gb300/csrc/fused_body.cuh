@@ -19,11 +19,12 @@
 //   3. Conditional step (Sec. 3.3.2, 4.5): per point the switch point
 //      psi = (ln(K/S0) - omega t_1 - ln X^)/a, then price, delta, vega,
 //      gamma; a warp-shuffle + shared-memory tree sums the tile into 4
-//      doubles written to the item's slot (no atomics, so the result does
-//      not depend on scheduling).
-// The replicate estimate is the compensated (Neumaier) sum of its tile slots
-// in tile order, divided by N (reduce_replicate); mean and standard error
-// over replicates follow (replicate_stats).
+//      doubles, added (compensated, in tile order) to the work item's total,
+//      which goes to the item's slot after its last tile (no atomics, so the
+//      result does not depend on scheduling).
+// The replicate estimate is the compensated (Neumaier) sum of its item
+// slots in a fixed order, divided by N (reduce_replicate); mean and standard
+// error over replicates follow (replicate_stats).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -508,9 +509,10 @@ __device__ void path_phase(const ContractDev &c, T *zw, int stride, PathAcc<T> &
 constexpr int kTileStartDims = 1024;
 __shared__ uint32_t tile_start[kTileStartDims];
 
-// One work item: tile `tile` (points tile*P .. tile*P+P-1 of the contract,
-// the last tile ragged) of replicate `rep` (index into the plan's
-// randomisation tables), its four tile sums written to tile_out[0..3].
+// One tile of a work item: tile `tile` (points tile*P .. tile*P+P-1 of the
+// contract, the last tile ragged) of replicate `rep` (index into the plan's
+// randomisation tables), its four tile sums added to the item's
+// accumulator item_acc (shared memory: tile_acc).
 // Point t of the contract is Sobol' point point_k0 + c.k_first + t
 // (point_k0: diagnostics; k_first: the contract's first point); point_out,
 // when set, receives every point's values (diagnostics).  `smem` is the CTA's dynamic shared memory
@@ -518,7 +520,7 @@ __shared__ uint32_t tile_start[kTileStartDims];
 template <typename T, int CONS>
 __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *__restrict__ sobol_table,
                                          const uint32_t *__restrict__ sobol_shift, int jstride, uint32_t rep,
-                                         uint64_t tile, uint64_t point_k0, double *point_out, double *tile_out,
+                                         uint64_t tile, uint64_t point_k0, double *point_out, double *item_acc,
                                          unsigned char *smem) {
     const int P = 1 << c.tile_log2;
     const int n = c.n;
@@ -651,7 +653,8 @@ __device__ __forceinline__ void run_item(const ContractDev &c, const uint32_t *_
                 }
             }
         }
-    }    tile_sum(tile_out, v, smem);
+    }
+    tile_acc(item_acc, v, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -672,8 +675,8 @@ struct Neumaier {
     __device__ double value() const { return s + c; }
 };
 
-// Replicate estimate from its `tiles` tile slots (4 doubles each, in tile
-// order): thread t of a 256-thread block sums tiles t, t + 256, ... with
+// Replicate estimate from its `tiles` item slots (4 doubles each, in item
+// order): thread t of a 256-thread block sums slots t, t + 256, ... with
 // compensated arithmetic, then a fixed tree merges the 256 partial sums;
 // thread g < 4 returns Greek g divided by N (other threads: 0).
 // `part` is 256 x 4 shared Neumaier pairs.  Every thread of the block calls it.

@@ -1,12 +1,12 @@
 // The fused QMC-CPW kernel for sm_103a (one launch per batch segment) and
 // the reduction, statistics and set-up kernels.
 //
-// A launch covers the work items (contract, replicate, tile) of one
-// construction; each CTA takes items from an atomic counter in order and
-// runs them through the three phases of run_item (fused_body.cuh).  A second
-// kernel sums each replicate's tile slots in tile order with compensated
-// (Neumaier) arithmetic; a third forms mean and standard error over
-// replicates.
+// A launch covers the work items (contract, replicate, run of tiles) of one
+// construction; each CTA takes items from an atomic counter in order, runs
+// each tile of an item through the three phases of run_item (fused_body.cuh)
+// and writes the item's compensated tile total to its slot.  A second kernel
+// sums each replicate's item slots with compensated (Neumaier) arithmetic in
+// a fixed order; a third forms mean and standard error over replicates.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,17 +29,21 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && CONS != QMCCPW_PC
     fused_kernel(const __grid_constant__ LaunchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ WorkItem work;
+    __shared__ double item_acc[8];
+    item_acc_clear(item_acc);
     while (true) {
         next_work(p, work);
-        const uint64_t item = work.item;
-        if (item >= p.item_end) break;
-        run_item<T, CONS>(p.contracts[work.ci], p.sobol_table, p.sobol_shift, p.jstride, work.rep, work.tile,
-                          p.point_k0, p.point_out, p.tile_sums + item * 4, smem);
+        if (work.item >= p.item_end) break;
+        // the item stays in shared memory (`work`); tiles per replicate fit 32 bits
+        for (uint32_t tile = static_cast<uint32_t>(work.tile); tile < work.tile_end; ++tile)
+            run_item<T, CONS>(p.contracts[work.ci], p.sobol_table, p.sobol_shift, p.jstride, work.rep, tile,
+                              p.point_k0, p.point_out, item_acc, smem);
+        item_flush<PointValue<T>>(p.tile_sums + work.item * 4, item_acc);
     }
 }
 
 // ---------------------------------------------------------------------------
-// per-replicate compensated reduction of the tile slots, then statistics
+// per-replicate compensated reduction of the item slots, then statistics
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) reduce_kernel(const ContractDev *__restrict__ contracts,
                                                      const uint64_t *__restrict__ rep_owner,
@@ -49,8 +53,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ContractDev *__restri
     const uint64_t slot = blockIdx.x;  // global replicate slot
     const ContractDev &c = contracts[rep_owner[slot]];
     const uint64_t r = slot - c.rep_base;
-    const uint64_t first = c.item_base + r * static_cast<uint64_t>(c.tiles);
-    const double v = reduce_replicate(tile_sums + first * 4, static_cast<uint64_t>(c.tiles), c.N, part);
+    const uint64_t first = c.item_base + r * static_cast<uint64_t>(c.items);
+    const double v = reduce_replicate(tile_sums + first * 4, static_cast<uint64_t>(c.items), c.N, part);
     if (threadIdx.x < 4) per_rep[slot * 4 + threadIdx.x] = v;
 }
 

@@ -2,8 +2,8 @@
 //
 // W~ = A z with A A^T = Sigma (eq. WboldTilde); for equal spacing
 // A = sqrt(dt) * Ahat where Ahat (the factor for dt = 1) depends on n only.
-// One CTA (256 threads; 512 in the streamed variant) per work item of 128
-// points:
+// One CTA (256 threads; 512 in the streamed variant) per tile of 128 points
+// (a work item is a run of consecutive tiles of one replicate):
 //   1. Sobol' + inverse normal as in the CUDA-core kernel; z is split into
 //      hi + lo parts (bf16 or tf32) written straight into the operand layout
 //      (K-major, 128-byte swizzle, so a warp's stores hit distinct banks).
@@ -147,10 +147,11 @@ __device__ __forceinline__ void epilogue_dispatch(const ContractDev &c, uint32_t
 }
 
 // Merge the NWG warpgroups' partial sums of each point (in date order), the
-// conditional step and the tile sum (shared by both variants).
+// conditional step and the tile sum, added to the work item's total in
+// item_acc (shared by both variants).
 template <int NWG>
-__device__ __forceinline__ void finish_tile(const LaunchParams &p, const ContractDev &c, uint64_t item, uint64_t tile,
-                                           PathAcc<float> &acc, unsigned char *scratch) {
+__device__ __forceinline__ void finish_tile(const LaunchParams &p, const ContractDev &c, double *item_acc,
+                                           uint64_t tile, PathAcc<float> &acc, unsigned char *scratch) {
     const int warp = threadIdx.x >> 5;
     const int point = 32 * (warp & 3) + (threadIdx.x & 31);
     if (warp < 4 * NWG) stage_partial(scratch, kM, warp >> 2, point, acc, kM * NWG);  // not the product warp
@@ -169,7 +170,7 @@ __device__ __forceinline__ void finish_tile(const LaunchParams &p, const Contrac
             }
         }
     }
-    tile_sum(p.tile_sums + item * 4, v, scratch);
+    tile_acc(item_acc, v, scratch);
 }
 
 // Two Gray-code chains (dimensions ja and jb) over the same run of points.
@@ -362,17 +363,19 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
 
     uint32_t b_phase = 0, mma_phase = 0;
     __shared__ WorkItem work;
+    __shared__ double item_acc[8];
+    item_acc_clear(item_acc);
     while (true) {
-        next_work(p, work);
-        const uint64_t item = work.item;
-        if (item >= p.item_end) break;
+      next_work(p, work);
+      if (work.item >= p.item_end) break;
+      // the item stays in shared memory (`work`); tiles per replicate fit 32 bits
+      for (uint32_t tile = static_cast<uint32_t>(work.tile); tile < work.tile_end; ++tile) {
         const ContractDev &c = p.contracts[work.ci];
-        const int n = c.n;
         const uint32_t rep = work.rep;
-        const uint64_t tile = work.tile;
+        const int n = c.n;
 
-        // ---- Ahat (hi, lo) for this n: one bulk copy when n changes (the
-        // barrier that ends next_work orders this after the previous tile)
+        // ---- Ahat (hi, lo) for this n: one bulk copy when n changes (only
+        // at an item's first tile, after the barrier that ends next_work)
         if (sh.loaded_n != n) {
             if (threadIdx.x == 0) {
                 mbar_expect_tx(&sh.bar_b, kPartsB * kOpBytesB);
@@ -422,7 +425,10 @@ __global__ void __launch_bounds__(kThreads, KIND == 0 ? 3 : 2) pca_tc_kernel(con
         PathAcc<float> acc;
         epilogue_dispatch<kNpad, 2>(c, tmem, acc, warp >> 2, warp & 3);
         tc_fence_before();
-        finish_tile<2>(p, c, item, tile, acc, scratch);
+        finish_tile<2>(p, c, item_acc, tile, acc, scratch);
+      }
+      if (sh.abort) break;  // read after a barrier: the same in every thread
+      item_flush<ff>(p.tile_sums + work.item * 4, item_acc);
     }
 
     // release tensor memory (also after an abort: first, with the same bounded
@@ -563,15 +569,17 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
         ++f_ph[buf];
     };
 
+    __shared__ double item_acc[8];
+    item_acc_clear(item_acc);
     while (true) {
-        // the stop decision travels with the item: thread 0 reads the abort
-        // flag here and ends the loop for all (an expired wait stops it)
-        next_work(p, work, threadIdx.x == 0 && sh.abort);
-        const uint64_t item = work.item;
-        if (item >= p.item_end) break;
+      // the stop decision travels with the item: thread 0 reads the abort
+      // flag here and ends the loop for all (an expired wait stops it)
+      next_work(p, work, threadIdx.x == 0 && sh.abort);
+      if (work.item >= p.item_end) break;
+      // the item stays in shared memory (`work`); tiles per replicate fit 32 bits
+      for (uint32_t tile = static_cast<uint32_t>(work.tile); tile < work.tile_end; ++tile) {
         const ContractDev &c = p.contracts[work.ci];
         const uint32_t rep = work.rep;
-        const uint64_t tile = work.tile;
         const int nch = (c.n + S::Kc - 1) / S::Kc;        // chunks holding dimensions below n (>= 5)
         const int nblk = (c.n + S::Bd - 1) / S::Bd;
         const bool from_tile = tile_start_dims(p, c, rep, tile);
@@ -665,7 +673,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) pca_tcs_kernel(const __grid_cons
         PathAcc<float> acc;
         if (warp < kEpilogueWarpsS) epilogue_dispatch<kNbig, kEpilogueWarpsS / 4>(c, tmem, acc, warp >> 2, warp & 3);
         tc_fence_before();
-        finish_tile<kEpilogueWarpsS / 4>(p, c, item, tile, acc, scratch);
+        finish_tile<kEpilogueWarpsS / 4>(p, c, item_acc, tile, acc, scratch);
+      }
+      if (sh.abort) break;  // read after a barrier: the same in every thread
+      item_flush<ff>(p.tile_sums + work.item * 4, item_acc);
     }
 
     // the prefetched chunks, and products an expired wait left running, must

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "float_coeffs.h"
 #include "qmccpw_internal.h"
@@ -1141,26 +1142,35 @@ __device__ __forceinline__ int find_contract(const uint64_t *__restrict__ base, 
 // The next work item of the dynamic schedule (CTAs take items as they finish
 // one; an item's result never depends on which CTA ran it), decoded once by
 // thread 0 and handed to the CTA through shared memory: contract, replicate
-// and tile.  `stop` ends the loop for every thread.  Ends with a barrier;
-// the caller's loop must pass another barrier before the next call.
+// and its tiles [tile, tile_end).  `stop` ends the loop for every thread.
+// Starts and ends with a barrier, so every thread may read `w` from one call
+// to the next (the item's fields need not be held in registers).
 struct WorkItem {
-    uint64_t item, tile;
+    uint64_t item, tile, tile_end;
     int32_t ci;
     uint32_t rep;
 };
 
+// Tiles [tile, tile_end) of item `it` (0-based within its replicate) of c.
+__device__ __forceinline__ void item_tiles(const ContractDev &c, uint64_t it, uint64_t &tile, uint64_t &tile_end) {
+    tile = it * static_cast<uint64_t>(c.tpi);
+    tile_end = min(tile + static_cast<uint64_t>(c.tpi), static_cast<uint64_t>(c.tiles));
+}
+
 __device__ __forceinline__ void next_work(const LaunchParams &p, WorkItem &w, bool stop = false) {
+    __syncthreads();
     if (threadIdx.x == 0) {
         const uint64_t item = stop ? p.item_end : p.item_begin + atomicAdd(p.work_counter, 1ull);
         w.item = item;
         if (item < p.item_end) {
             const int ci = find_contract(p.item_base, p.count, item);
-            const uint64_t local = item - p.contracts[ci].item_base;
-            const uint64_t tiles = static_cast<uint64_t>(p.contracts[ci].tiles);
-            const uint64_t r = local / tiles;
+            const ContractDev &c = p.contracts[ci];
+            const uint64_t local = item - c.item_base;
+            const uint64_t items = static_cast<uint64_t>(c.items);
+            const uint64_t r = local / items;
             w.ci = ci;
-            w.rep = static_cast<uint32_t>(r) + static_cast<uint32_t>(p.contracts[ci].rep_first) + p.rep_offset;
-            w.tile = local - r * tiles;
+            w.rep = static_cast<uint32_t>(r) + static_cast<uint32_t>(c.rep_first) + p.rep_offset;
+            item_tiles(c, local - r * items, w.tile, w.tile_end);
         }
     }
     __syncthreads();
@@ -1279,9 +1289,11 @@ __device__ __forceinline__ void finish_functional(const ContractDev &c, const Pa
 // Tile sum of the 4 values of every thread (zero for threads without a
 // point): the kThreads x 4 values go through shared memory; warp g < 4 sums
 // Greek g (each lane kThreads/32 consecutive threads, then a shuffle tree),
-// a fixed order, and writes it to out[g].  `smem` needs 4 * kThreads doubles; the caller's shared
-// memory must be free on entry.  Ends with a barrier.
-__device__ __forceinline__ void tile_sum(double *out, const double (&v)[4], unsigned char *smem) {
+// a fixed order, and lane 0 of warp g hands it to sink(g, sum).  `smem`
+// needs 4 * kThreads doubles; the caller's shared memory must be free on
+// entry.  Ends with a barrier.
+template <typename Sink>
+__device__ __forceinline__ void tile_reduce(const double (&v)[4], unsigned char *smem, Sink &&sink) {
     __syncthreads();
     double *vals = reinterpret_cast<double *>(smem);
 #pragma unroll
@@ -1295,14 +1307,16 @@ __device__ __forceinline__ void tile_sum(double *out, const double (&v)[4], unsi
         for (int i = 0; i < kThreads / 32; ++i) s += col[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) out[warp] = s;
+        if (lane == 0) sink(warp, s);
     }
     __syncthreads();
 }
 
 // The same tile sum for float-float values: TwoSum-based adds on the FP32
-// pipe, one conversion to double per Greek.  `smem` needs 8 * kThreads floats.
-__device__ __forceinline__ void tile_sum(double *out, const ff (&v)[4], unsigned char *smem) {
+// pipe; the sink receives the float-float sum.  `smem` needs 8 * kThreads
+// floats.
+template <typename Sink>
+__device__ __forceinline__ void tile_reduce(const ff (&v)[4], unsigned char *smem, Sink &&sink) {
     __syncthreads();
     float *vals = reinterpret_cast<float *>(smem);
     if (threadIdx.x < kThreads) {  // larger blocks: the values live in the first kThreads threads
@@ -1325,10 +1339,65 @@ __device__ __forceinline__ void tile_sum(double *out, const ff (&v)[4], unsigned
             const ff o = {__shfl_down_sync(0xffffffffu, s.hi, off), __shfl_down_sync(0xffffffffu, s.lo, off)};
             s = ff_add(s, o);
         }
-        if (lane == 0) out[warp] = ff_to_double(s);
+        if (lane == 0) sink(warp, s);
     }
     __syncthreads();
 }
+
+// One tile's sums written to out[0..3] (the tile is the whole work item).
+__device__ __forceinline__ void tile_sum(double *out, const double (&v)[4], unsigned char *smem) {
+    tile_reduce(v, smem, [&](int g, double s) { out[g] = s; });
+}
+__device__ __forceinline__ void tile_sum(double *out, const ff (&v)[4], unsigned char *smem) {
+    tile_reduce(v, smem, [&](int g, ff s) { out[g] = ff_to_double(s); });
+}
+
+// The sums of a work item's tiles, in tile order, in `acc` (shared memory,
+// 8 doubles), owned per Greek g by lane 0 of warp g (the thread that adds the
+// tile sums into it and flushes it): zero it before the first item
+// (item_acc_clear), add each tile (tile_acc), write the item's slot and
+// restart (item_flush) after its last tile.  Double values: a Neumaier sum
+// and its compensation per Greek.  Float-float values (the float kernels):
+// the float-float sum itself (about 48 bits over at most 16 tiles), kept on
+// the FP32 pipe and converted to double once per item -- a double operation
+// holds its sub-partition's FP64 unit for dozens of cycles, and a chain of
+// them per tile, in the one lane the tile's last barrier waits for, stalled
+// the whole CTA.
+__device__ __forceinline__ bool item_acc_owner() { return (threadIdx.x & 31) == 0 && threadIdx.x < 128; }
+__device__ __forceinline__ void item_acc_clear(double *acc) {
+    if (item_acc_owner()) acc[threadIdx.x >> 5] = acc[4 + (threadIdx.x >> 5)] = 0.0;
+}
+__device__ __forceinline__ void tile_acc(double *acc, const double (&v)[4], unsigned char *smem) {
+    tile_reduce(v, smem, [&](int g, double x) {
+        const double s = acc[g], t = s + x;
+        acc[4 + g] += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+        acc[g] = t;
+    });
+}
+__device__ __forceinline__ void tile_acc(double *acc, const ff (&v)[4], unsigned char *smem) {
+    float *a = reinterpret_cast<float *>(acc);  // (hi, lo) of Greek g at 2g, 2g + 1
+    tile_reduce(v, smem, [&](int g, ff x) {
+        const ff t = ff_add(ff{a[2 * g], a[2 * g + 1]}, x);
+        a[2 * g] = t.hi;
+        a[2 * g + 1] = t.lo;
+    });
+}
+template <typename V>
+__device__ __forceinline__ void item_flush(double *out, double *acc) {
+    if (item_acc_owner()) {
+        const int g = threadIdx.x >> 5;
+        if constexpr (std::is_same<V, double>::value) {
+            out[g] = acc[g] + acc[4 + g];
+            acc[g] = acc[4 + g] = 0.0;
+        } else {
+            float *a = reinterpret_cast<float *>(acc);
+            out[g] = ff_to_double(ff{a[2 * g], a[2 * g + 1]});
+            a[2 * g] = a[2 * g + 1] = 0.0f;
+        }
+    }
+}
+// The value type of a kernel's per-point results: double, or float-float for the float kernels.
+template <typename T> using PointValue = typename std::conditional<sizeof(T) == 8, double, ff>::type;
 
 }  // namespace
 }  // namespace qmccpw

@@ -57,6 +57,7 @@ struct ContractDev {
     int32_t tile_log2;                   // P = 1 << tile_log2 points per tile
     int32_t chunk_log2;                  // Gray-code chunk length in the Sobol' phase
     int32_t R, tiles;                    // replicates, tiles per replicate
+    int32_t tpi, items;                  // tiles per work item, work items per replicate (set_item_grouping)
     int32_t groups;                      // kThreads / P threads per point in the path phase
     int32_t n_levels;                    // bridge levels
     int32_t row_stride;                  // shared-memory row (point) stride in elements, odd
@@ -121,6 +122,23 @@ struct ContractDev {
     // the leading-coordinate float path
     float ff_sig[2], ff_lnS0d[2], ff_lnK[2];
 };
+
+// A work item is a run of consecutive tiles of one replicate; its CTA adds
+// the tiles' block sums (compensated, in tile order) and writes one 32-byte
+// slot.  Large contracts take up to kMaxTilesPerItem tiles per item (one slot
+// instead of 16: less scratch and fewer writes), while every replicate keeps
+// at least kMinItemsPerRep items for the dynamic schedule to balance.  The
+// grouping depends on the tiles per replicate only (not on R, the batch or
+// the device), so a replicate's estimate is the same whichever call, batch,
+// replicate range or server computes it.
+constexpr int kMaxTilesPerItem = 16;
+constexpr int kMinItemsPerRep = 256;
+inline void set_item_grouping(ContractDev &c) {
+    int tpi = 1;
+    while (tpi < kMaxTilesPerItem && static_cast<int64_t>(tpi) * 2 * kMinItemsPerRep <= c.tiles) tpi *= 2;
+    c.tpi = tpi;
+    c.items = (c.tiles + tpi - 1) / tpi;
+}
 
 // hi + lo float pair of a double (hi = nearest float, lo = nearest float of the rest)
 inline void split_ff(double x, float out[2]) {

@@ -195,10 +195,10 @@ __device__ void finish_request(const ServeParams &p, const ServeRequest &req, un
     __threadfence();
     Neumaier(*part)[4] = reinterpret_cast<Neumaier(*)[4]>(smem);
     const ContractDev &c = req.c;
-    const uint64_t tiles = static_cast<uint64_t>(c.tiles);
+    const uint64_t items = static_cast<uint64_t>(c.items);
     double *per_rep = req.tile_sums + req.items * 4;
     for (int r = 0; r < c.R; ++r) {
-        const double v = reduce_replicate(req.tile_sums + static_cast<uint64_t>(r) * tiles * 4, tiles, c.N, part);
+        const double v = reduce_replicate(req.tile_sums + static_cast<uint64_t>(r) * items * 4, items, c.N, part);
         if (threadIdx.x < 4) per_rep[r * 4 + threadIdx.x] = v;
     }
     __syncthreads();
@@ -321,13 +321,15 @@ __device__ void leave(const ServeParams &p, ServeShared &sh, unsigned char *smem
     }
 }
 
-// One item of a request, a separate (not inlined) function per construction:
-// each keeps the register allocation the batch kernel's inlined form gets,
-// and the serving kernel stays small enough for the compiler.
+// One item of a request (its tiles [tile, tile_end), their sums added to
+// item_acc), a separate (not inlined) function per construction: each keeps
+// the register allocation the batch kernel's inlined form gets, and the
+// serving kernel stays small enough for the compiler.
 template <typename T, int CONS>
-__device__ __noinline__ void serve_item(const ContractDev &c, const ServeParams &p, uint32_t rep, uint64_t tile,
-                                        double *tile_out, unsigned char *smem) {
-    run_item<T, CONS>(c, p.sobol_table, p.sobol_shift, p.jstride, rep, tile, 0, nullptr, tile_out, smem);
+__device__ __noinline__ void serve_item(const ContractDev &c, const ServeParams &p, uint32_t rep, uint32_t tile,
+                                        uint32_t tile_end, double *item_acc, unsigned char *smem) {
+    for (; tile < tile_end; ++tile)  // tiles per replicate fit 32 bits
+        run_item<T, CONS>(c, p.sobol_table, p.sobol_shift, p.jstride, rep, tile, 0, nullptr, item_acc, smem);
 }
 
 // Workers are CTAs 0 .. gridDim.x - 2; the last CTA dispatches.  WITH_PCA
@@ -344,6 +346,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !WITH_PCA) ? 3 : 
         leave(p, sh, smem, smem_bytes);
         return;
     }
+    __shared__ double item_acc[8];
+    item_acc_clear(item_acc);
     if (threadIdx.x == 0) req.seq = ~0ull;
     __syncthreads();
     while (true) {
@@ -364,21 +368,23 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && !WITH_PCA) ? 3 : 
             }
             break;
         }
-        const uint64_t tiles = static_cast<uint64_t>(c.tiles);
-        const uint64_t r = local / tiles;
-        const uint64_t tile = local - r * tiles;
+        const uint64_t items = static_cast<uint64_t>(c.items);
+        const uint64_t r = local / items;
+        uint64_t tile64, tile_end64;
+        item_tiles(c, local - r * items, tile64, tile_end64);
+        const uint32_t tile = static_cast<uint32_t>(tile64), tile_end = static_cast<uint32_t>(tile_end64);
         const uint32_t rep = static_cast<uint32_t>(r) + static_cast<uint32_t>(c.rep_first);
-        double *tile_out = req.tile_sums + local * 4;
         switch (c.construction) {
-            case QMCCPW_BB: serve_item<T, QMCCPW_BB>(c, p, rep, tile, tile_out, smem); break;
-            case QMCCPW_STD: serve_item<T, QMCCPW_STD>(c, p, rep, tile, tile_out, smem); break;
-            case QMCCPW_BB_LEAD: serve_item<T, QMCCPW_BB_LEAD>(c, p, rep, tile, tile_out, smem); break;
-            case QMCCPW_PCA_LEAD: serve_item<T, QMCCPW_PCA_LEAD>(c, p, rep, tile, tile_out, smem); break;
+            case QMCCPW_BB: serve_item<T, QMCCPW_BB>(c, p, rep, tile, tile_end, item_acc, smem); break;
+            case QMCCPW_STD: serve_item<T, QMCCPW_STD>(c, p, rep, tile, tile_end, item_acc, smem); break;
+            case QMCCPW_BB_LEAD: serve_item<T, QMCCPW_BB_LEAD>(c, p, rep, tile, tile_end, item_acc, smem); break;
+            case QMCCPW_PCA_LEAD: serve_item<T, QMCCPW_PCA_LEAD>(c, p, rep, tile, tile_end, item_acc, smem); break;
             default:
-                if constexpr (WITH_PCA) serve_item<T, QMCCPW_PCA>(c, p, rep, tile, tile_out, smem);
+                if constexpr (WITH_PCA) serve_item<T, QMCCPW_PCA>(c, p, rep, tile, tile_end, item_acc, smem);
                 break;
         }
-        // the tile sums are written (run_item ends with a barrier); count the item
+        item_flush<PointValue<T>>(req.tile_sums + local * 4, item_acc);
+        // the item's sums are written (run_item ends with a barrier); count the item
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0)

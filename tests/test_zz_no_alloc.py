@@ -62,8 +62,9 @@ def test_no_alloc_rejects_work_beyond_its_array(q):
     plan = q.qmccpw_plan(device=0, d_max=65, r_max=64, seed=W.SCRAMBLE_SEED)
     try:
         out = torch.empty((64 + 2) * 4, dtype=torch.float64, device="cuda")
-        with pytest.raises(q.QmcCpwError) as e:  # 64 replicates x 2^24 points: far beyond 16 MiB of tile sums
-            q.qmccpw_greeks_noalloc(plan, 0, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 24, 64, 0, 1, out.data_ptr())
+        # 64 replicates x 2^30 points: 2^18 work items of 16 tiles per replicate, 512 MiB of item sums
+        with pytest.raises(q.QmcCpwError) as e:
+            q.qmccpw_greeks_noalloc(plan, 0, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 30, 64, 0, 1, out.data_ptr())
         assert e.value.code == q.QMCCPW_ERR_OOM
         assert "16777216" in str(e.value)
     finally:
