@@ -251,7 +251,8 @@ def qmccpw_basket_point_values(plan, basket, precision: int, replicate: int, k0:
 
 
 def contract_array(contracts: Sequence) -> ctypes.Array:
-    """ctypes array of qmccpw_contract from objects with type, d, K, T, S0, r, sigma, N, R, construction."""
+    """ctypes array of qmccpw_contract from objects with type, d, K, T, S0, r, sigma, N, R, construction
+    (and optionally first_replicate and first_point, 0 when absent)."""
     arr = (qmccpw_contract * len(contracts))()
     for i, c in enumerate(contracts):
         arr[i] = qmccpw_contract(qmccpw_option(c.type, c.d, c.K, c.T), qmccpw_market(c.S0, c.r, c.sigma),
