@@ -804,7 +804,7 @@ def main(argv=None):
     ap.add_argument("--stress-steps", type=int, default=1, help="timed steps of the d=256 PCA case (0: skip)")
     ap.add_argument("--basket-steps", type=int, default=3, help="timed MIXED calls of the 4-asset basket (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0)
-    ap.add_argument("--serving-rate-sustained", type=float, default=800.0,
+    ap.add_argument("--serving-rate-sustained", type=float, default=1000.0,
                     help="a second MIXED arrival rate, within what the GPU serves")
     ap.add_argument("--serving-rate-fp64", type=float, default=20.0)
     ap.add_argument("--errors-out", default=None, help="write the per-contract MIXED vs FP64 table (JSON)")
