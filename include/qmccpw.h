@@ -171,9 +171,10 @@ int qmccpw_greeks(qmccpw_plan_t plan, const qmccpw_option *option, const qmccpw_
 /*
  * Batched form: `count` contracts of any mix of products, d, N and R, run in
  * one persistent launch sequence (one grid over every (contract, replicate,
- * tile) work item).  out[i] receives contract i's result; each out[i]
- * .per_replicate may be NULL.  Results equal those of qmccpw_greeks for the
- * same contract (same points, same per-tile order).
+ * run of tiles) work item; the runs depend on the contract alone).  out[i]
+ * receives contract i's result; each out[i].per_replicate may be NULL.
+ * Results equal those of qmccpw_greeks for the same contract (same points,
+ * same tiles, same order of the sums).
  */
 int qmccpw_greeks_batch(qmccpw_plan_t plan, const qmccpw_contract *contracts, int32_t count,
                         int32_t precision, qmccpw_result *out);
@@ -265,7 +266,7 @@ int qmccpw_point_values(qmccpw_plan_t plan, const qmccpw_option *option, const q
  * cudaMalloc competes with that pool for the same memory.  This entry point
  * performs no cudaMalloc,
  * cudaFree or other device-memory allocation: every per-call device array
- * (tile partial sums, the contract descriptor, the bridge or PCA tables) is
+ * (work-item partial sums, the contract descriptor, the bridge or PCA tables) is
  * placed in one fixed 16 MiB array compiled into the library, which every
  * GPU that loads the library holds until the process exits.  The plan (made
  * beforehand with qmccpw_plan, which does allocate) supplies the Sobol'
