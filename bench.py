@@ -292,6 +292,25 @@ def cpu_baseline(contracts, budget_s: float = 12.0) -> dict:
                             "sample": f"{done1} contracts at N=2^9, R=32, d=64 ({e1} point-dates, {dt1:.1f} s)"}}
 
 
+PILOT_N = 2 ** 12
+
+
+def request_size(pilot_se: float, target_se: float, n_pilot: int = PILOT_N, n_max: int = 2 ** 22) -> int:
+    """Points of a request: the smallest power of two in [n_pilot, n_max] whose
+    standard error, the pilot's scaled as 1/N, meets the target."""
+    ratio = max(pilot_se, 1e-300) / target_se
+    N = n_pilot
+    while N < n_max and ratio * n_pilot / N > 1.0:
+        N *= 2
+    return N
+
+
+def combine_runs(per1, n1: int, per2, n2: int):
+    """Per-replicate estimates of points 0 .. n1+n2-1 from a run over the
+    first n1 points and a run over the next n2 (the point-weighted mean)."""
+    return (n1 * per1 + n2 * per2) / (n1 + n2)
+
+
 def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
     """Poisson arrivals through the device-resident serving loop.
 
@@ -308,7 +327,7 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
     arriving in the first `warmup_s` seconds are run but not counted."""
     import queue
 
-    N1 = 2 ** 12
+    N1 = PILOT_N
     reqs = W.arrivals(rate_hz=rate_hz, duration_s=warmup_s + duration_s, seed=seed, R=16)
     # the requests are bridge contracts: the MIXED kernel without the PCA product fits three CTAs per SM
     q.qmccpw_server_start(plan, precision=precision, max_inflight=1024, max_inflight_bytes=256 << 20,
@@ -334,10 +353,7 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
                 return
             i, rq, t = item
             _, se, per1 = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
-            ratio = max(se[1], 1e-300) / rq.target_se
-            N = N1
-            while N < 2 ** 22 and ratio * N1 / N > 1.0:
-                N *= 2
+            N = request_size(se[1], rq.target_se)
             if N == N1:
                 mains.put((i, rq, N, per1, None, time.perf_counter() - t0))
             else:
@@ -353,7 +369,7 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
             if t is not None:
                 _, _, per2 = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
                 done = time.perf_counter() - t0
-                per1 = (N1 * per1 + (N - N1) * per2) / N   # the request's per-replicate estimates
+                per1 = combine_runs(per1, N1, per2, N - N1)   # the request's per-replicate estimates
             # the request's answer: mean and standard error over its replicates
             answers[i] = (per1.mean(axis=0), per1.std(axis=0, ddof=1) / math.sqrt(per1.shape[0]))
             if rq.arrival_s >= warmup_s:
