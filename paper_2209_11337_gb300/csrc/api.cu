@@ -94,6 +94,7 @@ struct DTables {
     DevBuf sub_start[3];  // bridge subtrees per thread of a point, G = 2, 4, 8 (bridge_phase)
     DevBuf lead64, lead32;  // loadings of the leading coordinate, dates 1..n: bridge (j/sqrt(n)) then PCA (first column)
     double lead_sum[2] = {0.0, 0.0};  // the sum of each form's loadings
+    int32_t lead_increasing[2] = {0, 0};  // each form's loadings strictly increase with the date
     DevBuf tc[2];  // tensor-core split operands of Ahat (bf16, tf32; resident or streamed form by n), built on first use
 };
 
@@ -341,6 +342,14 @@ int get_dtables(qmccpw_plan_s *p, int d, double /*T*/, const DTables **out) {
         t->lead_sum[0] += lead[i];
         t->lead_sum[1] += lead[nl + i];
     }
+    // strictly increasing by far more than a rounding (both forms are: i / sqrt(n), and
+    // sin(i pi / (2n + 1)) for i <= n): then the lines steeper than date j's are the later dates'
+    for (int f = 0; f < 2; ++f) {
+        bool inc = true;
+        for (int i = 1; i < n && inc; ++i)
+            inc = lead[f * nl + i] - lead[f * nl + i - 1] > 1e-12 * std::fabs(lead[f * nl + i]);
+        t->lead_increasing[f] = inc ? 1 : 0;
+    }
     std::vector<float> lead32(2 * lead.size());  // float pairs (hi, lo)
     for (size_t i = 0; i < lead.size(); ++i) split_ff(lead[i], &lead32[2 * i]);
     QMC_TRY(t->lead64.alloc(sizeof(double) * lead.size()));
@@ -447,6 +456,7 @@ int build_contract(qmccpw_plan_s *p, const qmccpw_contract &in, int batch_precis
         c.lead_a64 = t->lead64.as<double>() + off;
         c.lead_a32 = t->lead32.as<float>() + 2 * off;
         c.lead_amean = t->lead_sum[c.construction == QMCCPW_PCA_LEAD ? 1 : 0] / c.d;  // times sqrt(dt) below
+        c.lead_increasing = t->lead_increasing[c.construction == QMCCPW_PCA_LEAD ? 1 : 0];
     }
     c.N = in.N;
     c.item_base = item_base;

@@ -683,12 +683,14 @@ __device__ void lead_lookback(const ContractDev &c, const T *R, double out[4]) {
     }
     const double xs = num / den, b_star = den;
     double price = 0.0, vega = 0.0, u = xs;
+    // with loadings increasing in the date, the steeper lines are the later dates'
+    const bool later_only = c.lead_increasing != 0;
     for (int piece = 0; piece < d; ++piece) {
         const double lcc = lc_of(cur), bc = sig * lead_loading<double>(c, cur);
         // the first steeper line to overtake: smallest (lcc - lc_j) / (b_j - bc) >= u
         double vn = 0.0, vd = 0.0;  // the crossing as a fraction, vd > 0 once found
         int next = -1;
-        for (int j = 0; j < d; ++j) {
+        for (int j = later_only ? cur + 1 : 0; j < d; ++j) {
             const double bj = sig * lead_loading<double>(c, j);
             if (!(bj > bc)) continue;
             double nj = lcc - lc_of(j);

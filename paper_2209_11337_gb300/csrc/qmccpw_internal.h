@@ -63,6 +63,7 @@ struct ContractDev {
     int32_t row_stride;                  // shared-memory row (point) stride in elements, odd
     int32_t z_by_dim;                    // 1: z of dimension j at column j+1+slot_shift; 0: at the date node j+slot_shift drives
     int32_t slot_shift;                  // 1 for the leading-coordinate constructions (dimension j drives node j+1), else 0
+    int32_t lead_increasing;             // leading-coordinate constructions: the loadings strictly increase with the date
     int32_t rep_first;                   // randomisation index of the contract's replicate 0
     uint64_t N;
     uint64_t k_first;                    // Sobol' index of the contract's point 0
