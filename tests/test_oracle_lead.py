@@ -164,3 +164,20 @@ def test_lead_and_first_increment_conditioning_agree(oracle_lib, opt):
     for cons in (3, 4):
         m1, s1, _ = oracle_lib.greeks(SEED, opt, d, K, T, S0, r, sig, cons, 2 ** 12, 16)
         assert np.all(np.abs(m1 - m0) <= 4.0 * np.sqrt(s0 ** 2 + s1 ** 2)), (cons, (m1 - m0) / np.sqrt(s0 ** 2 + s1 ** 2))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 16, 64, 257, 366, 1024])
+def test_leading_coordinate_loadings_increase_with_the_date(oracle_lib, n):
+    """The leading coordinate's loading on the dates of a whole path of n
+    dates rises strictly with the date in both forms -- the bridge's terminal
+    value (i / sqrt(n) for unit spacing) and the first principal component --
+    with gaps far above a rounding.  The lines of the lookback's envelope are
+    then ordered by slope as by date, which is what lets the GPU kernels seek
+    each next piece among the later dates only."""
+    bridge = np.arange(1, n + 1) / math.sqrt(n)
+    pca = oracle_lib.pca_matrix(n, 1.0)[:, 0]
+    for a in (bridge, pca):
+        assert np.all(a > 0)
+        if n > 1:
+            gaps = np.diff(a)
+            assert np.all(gaps > 1e-9 * np.abs(a[1:])), gaps.min()
