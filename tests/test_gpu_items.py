@@ -36,9 +36,9 @@ def plan(q):
 CASES = [
     # FP64, 256-point tiles: 515 tiles, items of two, the last item one ragged tile
     (W.Contract(W.ARITH, 16, 100.0, 1.0, 100.0, 0.05, 0.2, 256 * 514 + 1, 2, W.BB), 0, 1e-12),
-    # MIXED, shared-memory bridge with 64-point tiles: 1031 tiles
+    # MIXED, shared-memory bridge with 64-point tiles: 1031 tiles, items of four, the last of three
     (W.Contract(W.LOOKBACK, 200, 95.0, 1.0, 100.0, 0.05, 0.25, 64 * 1030 + 3, 2, W.BB), 1, 1e-11),
-    # tensor-core PCA (bf16), 128-point tiles: 1031 tiles
+    # tensor-core PCA (bf16), 128-point tiles: 1031 tiles, items of four, the last of three
     (W.Contract(W.BINARY, 64, 105.0, 1.0, 100.0, 0.05, 0.3, 128 * 1030 + 7, 2, W.PCA), 2, 1e-11),
     # standard construction, MIXED: 4100 tiles of 128 points (items of 16, the last of four) or 2050 of 256
     (W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 128 * 4099 + 50, 2, W.STD), 1, 1e-11),

@@ -22,7 +22,7 @@ CASES = [
     (W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 16, 8, W.BB), 1),         # MIXED
     (W.Contract(W.LOOKBACK, 33, 95.0, 1.5, 100.0, 0.03, 0.3, 5000, 4, W.PCA), 0),          # FP64, ragged N
     (W.Contract(W.BINARY, 16, 105.0, 0.5, 100.0, 0.02, 0.25, 2 ** 12, 2, W.PCA), 1),
-    (W.Contract(W.ARITH, 16, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 18 + 77, 4, W.BB), 1),    # work items of 2 tiles
+    (W.Contract(W.ARITH, 16, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 18 + 77, 4, W.BB), 1),    # items of 4 tiles, the last of 1
 ]
 
 
