@@ -2,8 +2,9 @@
 
 A replicate's tiles are grouped into work items of up to 16 consecutive
 tiles; the CTA that takes an item adds its tiles' sums in tile order and
-writes one slot.  Here the tile counts leave a one-tile last item (and a
-ragged last tile), and each replicate's estimate must equal the exactly
+writes one slot.  Here the tile counts leave a short last item (a single
+tile in the first case) and a ragged last tile, and each replicate's
+estimate must equal the exactly
 rounded mean of the same kernel's own per-point values (qmccpw_point_values,
 summed on the host with math.fsum): a grouping that dropped, repeated or
 misplaced a tile, or summed an item into the wrong slot, would move it by
