@@ -322,7 +322,9 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
     only (first_point = N1) and each replicate's estimate is the
     point-weighted mean of its two runs; a request whose pilot meets the
     target is answered by the pilot.  Latency = completion of the request's
-    last run - arrival.  Offered load = the point-dates of the requests that
+    last run - arrival; `delta_se_target_met` is the share of requests whose
+    answer's delta standard error meets the target (the 1/N scaling of the
+    sizing rule is a prediction).  Offered load = the point-dates of the requests that
     arrive in the window (sum of N R d), per second of the window; requests
     arriving in the first `warmup_s` seconds are run but not counted."""
     import queue
@@ -334,7 +336,7 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
                           constructions=[q.QMCCPW_BB])
     pilots = queue.Queue()
     mains = queue.Queue()
-    lat, offered_elems, Ns, answers = [], [0], [], {}
+    lat, offered_elems, Ns, met = [], [0], [], []
     t0 = time.perf_counter()
 
     def submitter():
@@ -370,12 +372,12 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
                 _, _, per2 = q.qmccpw_wait(plan, t, rq.contract.R, 600000)
                 done = time.perf_counter() - t0
                 per1 = combine_runs(per1, N1, per2, N - N1)   # the request's per-replicate estimates
-            # the request's answer: mean and standard error over its replicates
-            answers[i] = (per1.mean(axis=0), per1.std(axis=0, ddof=1) / math.sqrt(per1.shape[0]))
             if rq.arrival_s >= warmup_s:
                 lat.append(done - rq.arrival_s)
                 offered_elems[0] += N * rq.contract.R * rq.contract.d
                 Ns.append(N)
+                # the request's answer: its delta's standard error over the replicates, against the target
+                met.append(per1[:, 1].std(ddof=1) / math.sqrt(per1.shape[0]) <= rq.target_se)
 
     threads = [threading.Thread(target=f) for f in (submitter, sizer, finisher)]
     for t in threads:
@@ -394,6 +396,7 @@ def serve(q, plan, precision, rate_hz, duration_s, warmup_s=1.0, seed=5):
             "idle_exits": stats["idle_exits"],
             "mean_N": statistics.mean(Ns) if Ns else None,
             "answered_by_pilot": (sum(1 for n in Ns if n == N1) / len(Ns)) if Ns else None,
+            "delta_se_target_met": (sum(met) / len(met)) if met else None,
             "precision": {0: "fp64", 1: "mixed", 2: "tc-bf16", 3: "tc-tf32"}[precision]}
 
 
