@@ -179,3 +179,31 @@ def test_construction_mask(q):
             assert np.array_equal(p, p1), c.label()
     finally:
         q.qmccpw_free(plan)
+
+
+def test_admission_refuses_a_request_beyond_the_scratch_and_wait_times_out(q):
+    """A request whose work-item slots alone pass max_inflight_bytes is refused
+    with OOM at submission (nothing is queued); qmccpw_wait on an unfinished
+    request returns TIMEOUT and leaves the ticket collectable; requests that
+    fit run as usual."""
+    plan = q.qmccpw_plan(device=0, d_max=366, r_max=16, seed=W.SCRAMBLE_SEED)
+    try:
+        q.qmccpw_server_start(plan, precision=q.QMCCPW_MIXED, max_inflight_bytes=8 << 20)
+        big = W.Contract(W.ARITH, 64, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 26, 16, W.BB)   # 2^18 items: 8 MiB + 512 B
+        with pytest.raises(q.QmcCpwError) as e:
+            q.qmccpw_submit(plan, big)
+        assert e.value.code == q.QMCCPW_ERR_OOM
+        long = W.Contract(W.ARITH, 365, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 22, 16, W.BB)  # 4 MiB, ~0.1 s of work
+        t = q.qmccpw_submit(plan, long)
+        with pytest.raises(q.QmcCpwError) as e:
+            q.qmccpw_wait(plan, t, long.R, 0)
+        assert e.value.code == q.QMCCPW_ERR_TIMEOUT
+        mean, se, per = q.qmccpw_wait(plan, t, long.R, 120000)
+        assert np.all(np.isfinite(per)) and per.shape == (long.R, 4)
+        small = W.Contract(W.BINARY, 16, 100.0, 1.0, 100.0, 0.05, 0.2, 2 ** 12, 4, W.BB)
+        m2, s2, p2 = q.qmccpw_wait(plan, q.qmccpw_submit(plan, small), small.R, 60000)
+        q.qmccpw_server_stop(plan)
+        ref = q.qmccpw_greeks_batch(plan, [long, small], q.QMCCPW_MIXED)
+        assert np.array_equal(per, ref[0][2]) and np.array_equal(p2, ref[1][2])
+    finally:
+        q.qmccpw_free(plan)
